@@ -1,0 +1,264 @@
+/*
+ * rgg.h -- C ABI of the GB300 Red-Green-Gray edge-classification library
+ * (librgg.so).
+ *
+ * The library keeps a roadmap's serialized edge approximations resident in
+ * GPU memory and, after obstacles move, labels every edge RED (an inner
+ * sphere certainly hits a box), GREEN (no outer sphere touches any box) or
+ * GRAY (needs a full check).  The calls follow the paper's statement of the
+ * problem:
+ *   - the approximations are built once, offline, and stored persistently on
+ *     the GPU (Sec. 4.3, "Offline storage")          -> rgg_upload_edges,
+ *                                                       rgg_build_edges
+ *   - after an obstacle moves only its new transform is uploaded and its
+ *     rows are updated in place (Sec. 4.3, "Online updates"; Algorithm 1's
+ *     input is an obstacle and its transformation)   -> rgg_update_obstacles
+ *   - intersection tests over the serialized data certify red and green and
+ *     leave the rest gray (Sec. 4.1; Sec. 4.3, "Intersection queries";
+ *     Algorithm 1, lazy mode)                        -> rgg_classify
+ *   - labels stay on the device until asked for      -> rgg_fetch_labels
+ *
+ * Geometry (the approximations this library classifies with):
+ *   inner  K spheres per link inscribed in the link's capsule at every
+ *          configuration of the edge (the vertices of the paper's splines
+ *          L_{e,i}, Sec. 4.2);
+ *   outer  one sphere per link per sample interval enclosing the link's sweep
+ *          over that interval (stands in for the paper's per-edge OBB);
+ *   boxes  each obstacle is an exact oriented box, used as both its inner
+ *          and its outer approximation.
+ * With margin delta, a box b is HIT by an edge if some inner sphere (c, r)
+ * has dist(c, b) <= r - delta and TOUCHED if some outer sphere has
+ * dist(c, b) <= r + delta.  An edge is RED if any present box hits it,
+ * GREEN if no present box touches it, GRAY otherwise.  The library keeps,
+ * per edge, the set of boxes that hit it and the set that touch it (the
+ * per-component intersection lists of Algorithm 1), so an update only
+ * re-tests the moved boxes and the label always equals the label against
+ * the current pose of every box.
+ *
+ * Conventions
+ *   - Every call returns an rgg_status (0 = RGG_OK, negative = error) unless
+ *     stated otherwise.  A failed call leaves the roadmap unchanged unless
+ *     stated otherwise.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  All device work is stream-ordered; calls on one roadmap must
+ *     be issued on one stream or ordered by the caller.
+ *   - The caller owns every buffer it passes; the library copies what it
+ *     needs and never keeps a caller pointer after the call returns (for
+ *     pinned host or device sources the copy is stream-ordered: keep the
+ *     source alive and unchanged until the stream reaches it).
+ *   - Each roadmap lives on one CUDA device (rgg_roadmap_desc.device); calls
+ *     switch to that device and restore the caller's current device.
+ *   - Errors that only the device can see (a bounded wait that ran out)
+ *     are latched in a device status word and returned by the next
+ *     rgg_fetch_labels or rgg_check_status as RGG_ERR_TIMEOUT.
+ */
+#ifndef RGG_H_
+#define RGG_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rgg_roadmap* rgg_roadmap_t;
+
+enum rgg_status {
+  RGG_OK = 0,
+  RGG_ERR_INVALID = -1,  /* bad argument, size, layout or id               */
+  RGG_ERR_OOM = -2,      /* device or pinned-host allocation failed        */
+  RGG_ERR_CUDA = -3,     /* a CUDA runtime call failed                     */
+  RGG_ERR_TIMEOUT = -4,  /* a bounded device-side wait ran out             */
+  RGG_ERR_STATE = -5     /* call not valid in the roadmap's current state  */
+};
+
+/* Edge labels (Sec. 4.1): valid, unknown, invalid. */
+enum rgg_label { RGG_GREEN = 0, RGG_GRAY = 1, RGG_RED = 2 };
+
+/* Largest supported values. */
+enum {
+  RGG_MAX_LINKS = 32,          /* num_links                                    */
+  RGG_MAX_INNER = 16,          /* inner_per_link                               */
+  RGG_MAX_OBSTACLES = 4096,    /* max_obstacles                                */
+  RGG_BOXES_PER_PASS = 32      /* moved boxes tested per streaming pass        */
+};
+
+typedef struct {
+  uint32_t num_links;       /* L: robot links (= joints), 1..RGG_MAX_LINKS        */
+  uint32_t inner_per_link;  /* K: inner spheres per link, 1..RGG_MAX_INNER        */
+  uint32_t max_obstacles;   /* M: box ids are 0..M-1, 1..RGG_MAX_OBSTACLES        */
+  float margin_m;           /* delta in metres, >= 0 (2e-5 is the documented      */
+                            /* default; it must exceed the FP32 rounding error)   */
+  int device;               /* CUDA device ordinal                                */
+} rgg_roadmap_desc;
+
+/* A serial arm in standard Denavit-Hartenberg form, for rgg_build_edges.
+ * Joint i applies Rz(q_i) Tz(d_i) Tx(a_i) Rx(alpha_i); link i is the segment
+ * between frame origins i and i+1 (the base frame is the world frame), a
+ * capsule of radius radius[i].  Host arrays of num_links doubles. */
+typedef struct {
+  uint32_t num_links;
+  const double* a;
+  const double* alpha;
+  const double* d;
+  const double* radius;
+} rgg_robot_desc;
+
+/* Sizes of the resident data (rgg_roadmap_info). */
+typedef struct {
+  uint64_t num_edges;       /* N                                                  */
+  uint64_t num_samples;     /* S = sum over edges of n_e (configurations)         */
+  uint64_t num_inner;       /* K * L * S inner spheres                            */
+  uint64_t num_outer;       /* L * (S - N) outer spheres                          */
+  uint64_t record_bytes;    /* 16 * (num_inner + num_outer)                       */
+  uint64_t device_bytes;    /* all device memory held by the roadmap              */
+  uint32_t num_links, inner_per_link, max_obstacles, mask_words;
+  uint32_t tile_samples;    /* configurations per streaming tile                  */
+  uint64_t num_tiles;
+  uint32_t pending_boxes;   /* moved boxes not yet classified                     */
+  uint32_t grid_ctas;       /* CTAs of the classify launch                        */
+} rgg_info;
+
+/* ------------------------------------------------------------------------ */
+/* Create an empty roadmap on desc->device: no edges, no boxes present (every
+ * label GREEN once edges exist).  *out receives the handle; free it with
+ * rgg_roadmap_destroy.  RGG_ERR_INVALID for a NULL or out-of-range desc,
+ * RGG_ERR_OOM / RGG_ERR_CUDA if the device state cannot be allocated. */
+int rgg_roadmap_create(const rgg_roadmap_desc* desc, rgg_roadmap_t* out);
+
+/* Free every device and host resource of the roadmap (synchronises the
+ * device first).  NULL is accepted and ignored. */
+int rgg_roadmap_destroy(rgg_roadmap_t r);
+
+/* ------------------------------------------------------------------------ */
+/* Upload serialized edge approximations built by the caller (Sec. 4.3,
+ * "Offline storage": built once, kept on the GPU).  Replaces any edges the
+ * roadmap had and resets every label to GREEN and every per-edge box set
+ * to empty; every box already placed keeps its pose and becomes pending, so
+ * the next rgg_classify labels the new edges against all present boxes.
+ *
+ *   num_edges    N (0 allowed: an empty roadmap)
+ *   sample_off   N+1 host uint64: edge e has n_e = sample_off[e+1] -
+ *                sample_off[e] >= 2 configurations; sample_off[0] = 0.
+ *                Always a host array.
+ *   inner_xyzr   4 planes of K*L*S floats each (x plane, then y, z, radius),
+ *                S = sample_off[N].  Sphere (e, link i, sample k, sphere j)
+ *                is element K*(L*sample_off[e] + i*n_e + k) + j of each plane.
+ *   outer_xyzr   4 planes of L*(S-N) floats each.  Sphere (e, link i,
+ *                interval k), 0 <= k < n_e - 1, is element
+ *                L*(sample_off[e] - e) + i*(n_e - 1) + k of each plane.
+ *   src_is_device  0: inner/outer are host pointers; 1: device pointers.
+ * Every radius must be >= 0 and every value finite (checked for host
+ * sources only).  RGG_ERR_INVALID on a bad layout; RGG_ERR_OOM if the
+ * records do not fit in device memory. */
+int rgg_upload_edges(rgg_roadmap_t r, uint64_t num_edges, const uint64_t* sample_off,
+                     const float* inner_xyzr, const float* outer_xyzr, int src_is_device,
+                     void* stream);
+
+/* Build the serialized approximations on the GPU from the edges themselves
+ * (the offline preprocessing of Sec. 4.2 / 4.3), in FP64, stored as FP32
+ * (inner radii rounded down, outer radii rounded up).  Same effect on the
+ * roadmap state as rgg_upload_edges.
+ *
+ *   robot        the arm; robot->num_links must equal the roadmap's L.
+ *   q_from, q_to N x L host doubles (row-major): edge e goes from q_from[e]
+ *                to q_to[e] in joint space.
+ *   step         resolution eps > 0 in radians.  Edge e gets
+ *                n_e = max(2, ceil(max_j |q_to[e][j] - q_from[e][j]| / step) + 1)
+ *                configurations q_k = q_from + (k / (n_e - 1)) (q_to - q_from)
+ *                (Sec. 3.2's cfg(e), endpoints included).
+ * Inner sphere j of link i at configuration q_k: centre at fraction
+ * (j + 1/2)/K of the link segment, radius radius[i].  Outer sphere of link i
+ * over [q_k, q_{k+1}]: centre = midpoint of link i at (q_k + q_{k+1})/2,
+ * radius = l_i/2 + R_i + 1/2 sum_{j<=i} |dq_j| sum_{m=j..i} l_m with
+ * l_m = sqrt(a_m^2 + d_m^2) and dq = q_{k+1} - q_k, which encloses every
+ * point of the link's capsule over the whole interval.
+ * RGG_ERR_INVALID for bad robot/edges/step; RGG_ERR_OOM if the records do
+ * not fit in device memory. */
+int rgg_build_edges(rgg_roadmap_t r, const rgg_robot_desc* robot, uint64_t num_edges,
+                    const double* q_from, const double* q_to, double step, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Move (or place for the first time) obstacles: box ids[m] takes the
+ * absolute pose pose[15*m .. 15*m+14] = centre(3), R(9, row-major; its
+ * columns are the box axes in world coordinates), half-extents(3), metres.
+ * The box table row is overwritten in place on the stream (Sec. 4.3,
+ * "Online updates"); the ids join the roadmap's pending set, tested by the
+ * next rgg_classify.  Moving a box twice before classifying keeps the last
+ * pose.  A box never moved is absent and affects no label.
+ *   n_changed    number of ids (0 allowed)
+ *   ids          host array, each < max_obstacles, no repeats within a call
+ *   pose         n_changed * 15 floats, host (src_is_device = 0) or device
+ *                (src_is_device = 1).  Host poses are checked: finite,
+ *                half-extents >= 0, R orthonormal with det +1 to 1e-3.
+ * RGG_ERR_INVALID on a bad id or pose (nothing is changed). */
+int rgg_update_obstacles(rgg_roadmap_t r, uint32_t n_changed, const uint32_t* ids,
+                         const float* pose, int src_is_device, void* stream);
+
+/* Classify every edge against the pending moved boxes and merge with the
+ * per-edge box sets, so that each label equals the label against the
+ * current pose of every present box (Algorithm 1, lazy mode).  Streams all
+ * resident records once per RGG_BOXES_PER_PASS pending boxes.  Asynchronous:
+ * labels stay on the device.  Clears the pending set.  With no pending box
+ * it launches nothing.  RGG_ERR_STATE before any edges were set. */
+int rgg_classify(rgg_roadmap_t r, void* stream);
+
+/* Classify several roadmaps (each with its own edges, robot and pending
+ * boxes) in one persistent launch per pass over a shared work queue.  The
+ * labels are the same as rgg_classify on each roadmap alone.  All roadmaps
+ * must live on the same device; repeats are not allowed. */
+int rgg_classify_many(rgg_roadmap_t* roadmaps, uint32_t n, void* stream);
+
+/* Copy labels [first, first+count) (uint8, enum rgg_label) to `out`, a host
+ * (dst_is_device = 0) or device (1) buffer.  For a host destination the call
+ * waits for the stream and then reports any latched device error.
+ * RGG_ERR_INVALID if the range exceeds the edge count. */
+int rgg_fetch_labels(rgg_roadmap_t r, uint8_t* out, uint64_t first, uint64_t count,
+                     int dst_is_device, void* stream);
+
+/* Copy the per-edge box sets of edges [first, first+count): hit[e][w] and
+ * touch[e][w], w < mask_words = ceil(max_obstacles/32), bit b of word b/32
+ * for box id b (Algorithm 1's intersection lists).  Either pointer may be
+ * NULL.  Host or device destination as in rgg_fetch_labels. */
+int rgg_fetch_box_sets(rgg_roadmap_t r, uint32_t* hit, uint32_t* touch, uint64_t first,
+                       uint64_t count, int dst_is_device, void* stream);
+
+/* Copy the resident records of edges [first, first+count) to host buffers in
+ * the rgg_upload_edges layout restricted to that range (inner: 4 planes of
+ * K*L*(sample_off[first+count]-sample_off[first]) floats; outer: 4 planes of
+ * L*(samples - count) floats), and the N+1 sample offsets (host, may be NULL).
+ * Synchronous.  For inspection and tests. */
+int rgg_fetch_records(rgg_roadmap_t r, uint64_t first, uint64_t count, float* inner_xyzr,
+                      float* outer_xyzr, uint64_t* sample_off);
+
+/* Device pointer to the label array (N bytes, valid until the edges are
+ * replaced or the roadmap destroyed), for zero-copy use on the device. */
+int rgg_labels_device_ptr(rgg_roadmap_t r, const uint8_t** out);
+
+/* Sizes of the resident data. */
+int rgg_roadmap_info(rgg_roadmap_t r, rgg_info* out);
+
+/* Wait for the stream and report any latched device-side error
+ * (RGG_ERR_TIMEOUT), clearing it. */
+int rgg_check_status(rgg_roadmap_t r, void* stream);
+
+/* Kernel timing: when enabled, rgg_classify records CUDA events around each
+ * streaming classify launch on its stream; rgg_kernel_time returns the sum of
+ * their durations (ms) since the last call and the number of launches, and
+ * resets both (it synchronises on the events). */
+int rgg_set_kernel_timing(rgg_roadmap_t r, int enable);
+int rgg_kernel_time(rgg_roadmap_t r, double* ms, uint64_t* launches);
+
+/* Launch shape of the streaming classify kernel: CTAs per SM (0 = default)
+ * and consumer warps per CTA (0 = default).  Takes effect from the next
+ * rgg_classify.  RGG_ERR_INVALID if the shape cannot be launched. */
+int rgg_set_launch_shape(rgg_roadmap_t r, uint32_t ctas_per_sm, uint32_t consumer_warps);
+
+/* Static description of a status code (never NULL). */
+const char* rgg_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RGG_H_ */

@@ -1,0 +1,163 @@
+// Device-side structures and PTX helpers shared by the RGG kernels.
+//
+// Record layout on the device (one roadmap):
+//   inner spheres  4 FP32 planes (x, y, z, r), plane p at inner + p*in_stride;
+//                  sphere (edge e, link i, sample k, sphere j) at
+//                  K*(L*soff[e] + i*n_e + k) + j   (Sec. 4.3's E^- tensor,
+//                  unpadded: edge, body, configuration, sphere)
+//   outer spheres  4 FP32 planes; sphere (e, i, interval k) at
+//                  L*(soff[e] - e) + i*(n_e - 1) + k
+//   soff           N+1 uint64 per-edge configuration offsets
+// A "global sample" g indexes the concatenation over edges and links of the
+// configurations: edge e owns g in [L*soff[e], L*soff[e+1]), link i of it
+// the n_e consecutive values starting at L*soff[e] + i*n_e.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace rgg {
+
+constexpr int kMaxJobs = 128;          // roadmaps per batched launch
+constexpr int kBoxesPerPass = 32;      // moved boxes per streaming pass (one mask word)
+constexpr int kBoxRecFloats = 24;      // derived box record, 6 x float4 = 96 B
+constexpr int kStageHdrBytes = 256;
+
+// Derived record of one moved box, built by the box-prep kernel:
+//   r0 = (centre.xyz, bounding radius |h| rounded up)
+//   r1..r3 = (box axis k in world coordinates, axis_k . centre)
+//   r4 = (half-extents, box id as raw bits), r5 = padding
+// so that the box-frame coordinate k of a point x is dot(axis_k, x) - u_k.
+
+// One roadmap's part of a classify launch.
+struct ClassifyJob {
+  const float* inner;
+  const float* outer;
+  uint64_t in_stride, out_stride;   // floats between planes
+  const uint64_t* soff;             // [N+1]
+  const uint32_t* tile_edge;        // [T+1] edge holding the first sample of each tile
+  const float* boxes;               // [C][24] derived records of this pass's boxes
+  uint32_t* red;                    // [N][Wm] boxes that hit the edge
+  uint32_t* touch;                  // [N][Wm] boxes that touch the edge
+  uint8_t* labels;                  // [N]
+  uint32_t* edge_acc;               // [N][2] cross-tile (hit, touch) scratch, kept zero
+  uint32_t* edge_done;              // [N] cross-tile sample counter, kept zero
+  uint64_t num_edges;
+  uint64_t G;                       // L * soff[N] global samples
+  uint64_t tile_base;               // first queue index of this job's tiles
+  uint64_t num_tiles;
+  uint32_t L, K, S, C, Wm;          // links, inner/link, samples per tile, boxes, mask words
+  uint32_t off_edges, off_boxes;    // byte offsets inside a stage buffer
+  uint32_t off_in, off_out;         // byte offsets of the first inner / outer plane
+  uint32_t in_cap, out_cap;         // floats per plane slot in a stage
+  uint32_t max_edges;               // capacity of the per-tile edge table
+  float margin;
+};
+
+template <int MAXJ>
+struct ClassifyParams {
+  ClassifyJob job[MAXJ];
+  uint32_t njobs;
+  uint64_t total_tiles;
+  int* status;                      // device status word (0 = ok)
+};
+
+// Per-stage header written by the producer warp.
+struct StageHdr {
+  int32_t job;
+  int32_t n_samp;      // configurations in the tile
+  int32_t n_out;       // intervals in the tile (including the halo)
+  int32_t n_edges;     // local edges
+  int32_t in_shift;    // first inner float inside the aligned copy
+  int32_t out_shift;
+  int32_t valid;
+  int32_t pad0;
+  uint64_t e_first;    // global index of local edge 0
+  uint64_t g0;         // first global sample of the tile
+};
+static_assert(sizeof(StageHdr) <= kStageHdrBytes, "stage header too large");
+
+// Per local edge of a tile: {estart, n, ostart, cnt}
+//   estart  local sample index of the edge's first sample (may be < 0)
+//   n       configurations of the edge
+//   ostart  local interval index of the edge's first interval (may be < 0)
+//   cnt     samples of the edge inside this tile
+
+enum StatusCode : int {
+  kStatusOk = 0,
+  kStatusTimeoutFull = 1,
+  kStatusTimeoutEmpty = 2,
+  kStatusTimeoutBoxes = 3,
+  kStatusBadTile = 4,
+};
+
+// ---------------------------------------------------------------------------
+// PTX helpers (mbarrier + bulk async copy, sm_90+ / sm_100+ forms)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile(
+      "{\n\t.reg .b64 st;\n\t"
+      "mbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile(
+      "{\n\t.reg .b64 st;\n\t"
+      "mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(smem_u32(bar)),
+      "r"(bytes)
+      : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait: gives up after `limit` polls (each poll may suspend the thread
+// for a short hardware-defined time).  Returns false on timeout.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
+                                                  uint32_t limit) {
+  for (uint32_t i = 0; i < limit; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (i > 64) __nanosleep(64);
+  }
+  return false;
+}
+
+// Bulk copy global -> shared (this CTA), completion counted on `bar` in bytes.
+// Both addresses 16-byte aligned, size a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst_smem, const void* src_gmem, uint32_t bytes,
+                                         uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_u32(dst_smem)),
+      "l"(src_gmem), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void named_bar_sync(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+}  // namespace rgg

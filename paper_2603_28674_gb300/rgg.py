@@ -1,0 +1,306 @@
+"""Python binding of librgg.so (include/rgg.h): argument marshalling only.
+
+Every step of the classification runs in the library's CUDA kernels.  There
+is no CPU fallback: if librgg.so has not been built, or no GPU is present,
+the calls raise.
+
+Streams: every call takes ``stream`` as a CUDA stream handle (int), a
+``torch.cuda.Stream``, or None for torch's current stream on the roadmap's
+device.  Device buffers are torch CUDA tensors; host buffers numpy arrays.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+GREEN, GRAY, RED = 0, 1, 2
+RGG_OK, RGG_ERR_INVALID, RGG_ERR_OOM, RGG_ERR_CUDA, RGG_ERR_TIMEOUT, RGG_ERR_STATE = \
+    0, -1, -2, -3, -4, -5
+BOXES_PER_PASS = 32
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "librgg.so")
+
+# Entry points declared in include/rgg.h (checked by the test suite).
+EXPORTS = (
+    "rgg_roadmap_create", "rgg_roadmap_destroy", "rgg_upload_edges", "rgg_build_edges",
+    "rgg_update_obstacles", "rgg_classify", "rgg_classify_many", "rgg_fetch_labels",
+    "rgg_fetch_box_sets", "rgg_fetch_records", "rgg_labels_device_ptr", "rgg_roadmap_info",
+    "rgg_check_status", "rgg_set_kernel_timing", "rgg_kernel_time", "rgg_set_launch_shape",
+    "rgg_status_string",
+)
+
+
+class RGGError(RuntimeError):
+    def __init__(self, fn: str, status: int):
+        self.status = status
+        msg = _lib().rgg_status_string(status).decode() if _LIB is not None else str(status)
+        super().__init__(f"{fn} failed: {msg} ({status})")
+
+
+class _Desc(ctypes.Structure):
+    _fields_ = [("num_links", ctypes.c_uint32), ("inner_per_link", ctypes.c_uint32),
+                ("max_obstacles", ctypes.c_uint32), ("margin_m", ctypes.c_float),
+                ("device", ctypes.c_int)]
+
+
+class _Robot(ctypes.Structure):
+    _fields_ = [("num_links", ctypes.c_uint32), ("a", ctypes.POINTER(ctypes.c_double)),
+                ("alpha", ctypes.POINTER(ctypes.c_double)), ("d", ctypes.POINTER(ctypes.c_double)),
+                ("radius", ctypes.POINTER(ctypes.c_double))]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("num_edges", ctypes.c_uint64), ("num_samples", ctypes.c_uint64),
+                ("num_inner", ctypes.c_uint64), ("num_outer", ctypes.c_uint64),
+                ("record_bytes", ctypes.c_uint64), ("device_bytes", ctypes.c_uint64),
+                ("num_links", ctypes.c_uint32), ("inner_per_link", ctypes.c_uint32),
+                ("max_obstacles", ctypes.c_uint32), ("mask_words", ctypes.c_uint32),
+                ("tile_samples", ctypes.c_uint32), ("num_tiles", ctypes.c_uint64),
+                ("pending_boxes", ctypes.c_uint32), ("grid_ctas", ctypes.c_uint32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_LIB = None
+
+
+def _lib():
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                           "(there is no CPU fallback)")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, u32, u64, i32 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
+    dbl = ctypes.c_double
+    sig = {
+        "rgg_roadmap_create": [ctypes.POINTER(_Desc), ctypes.POINTER(vp)],
+        "rgg_roadmap_destroy": [vp],
+        "rgg_upload_edges": [vp, u64, vp, vp, vp, i32, vp],
+        "rgg_build_edges": [vp, ctypes.POINTER(_Robot), u64, vp, vp, dbl, vp],
+        "rgg_update_obstacles": [vp, u32, vp, vp, i32, vp],
+        "rgg_classify": [vp, vp],
+        "rgg_classify_many": [ctypes.POINTER(vp), u32, vp],
+        "rgg_fetch_labels": [vp, vp, u64, u64, i32, vp],
+        "rgg_fetch_box_sets": [vp, vp, vp, u64, u64, i32, vp],
+        "rgg_fetch_records": [vp, u64, u64, vp, vp, vp],
+        "rgg_labels_device_ptr": [vp, ctypes.POINTER(vp)],
+        "rgg_roadmap_info": [vp, ctypes.POINTER(Info)],
+        "rgg_check_status": [vp, vp],
+        "rgg_set_kernel_timing": [vp, i32],
+        "rgg_kernel_time": [vp, ctypes.POINTER(dbl), ctypes.POINTER(u64)],
+        "rgg_set_launch_shape": [vp, u32, u32],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = i32
+    lib.rgg_status_string.argtypes = [i32]
+    lib.rgg_status_string.restype = ctypes.c_char_p
+    _LIB = lib
+    return lib
+
+
+def library_path() -> str:
+    _lib()
+    return LIB_PATH
+
+
+def _check(fn: str, status: int) -> None:
+    if status != RGG_OK:
+        raise RGGError(fn, status)
+
+
+def _stream(stream, device: int) -> int:
+    if stream is None:
+        import torch
+        return int(torch.cuda.current_stream(device).cuda_stream)
+    if hasattr(stream, "cuda_stream"):
+        return int(stream.cuda_stream)
+    return int(stream)
+
+
+def _host(arr, dtype) -> np.ndarray:
+    return np.ascontiguousarray(arr, dtype=dtype)
+
+
+def _is_device(x) -> bool:
+    return hasattr(x, "is_cuda") and bool(x.is_cuda)
+
+
+def _ptr(x) -> int:
+    if _is_device(x):
+        if not x.is_contiguous():
+            raise ValueError("device buffers must be contiguous")
+        return int(x.data_ptr())
+    return int(x.ctypes.data)
+
+
+class Roadmap:
+    """One resident roadmap (wraps an rgg_roadmap_t)."""
+
+    def __init__(self, num_links: int, inner_per_link: int, max_obstacles: int,
+                 margin: float = 2e-5, device: int = 0):
+        lib = _lib()
+        desc = _Desc(num_links, inner_per_link, max_obstacles, margin, device)
+        h = ctypes.c_void_p()
+        _check("rgg_roadmap_create", lib.rgg_roadmap_create(ctypes.byref(desc), ctypes.byref(h)))
+        self._h = h
+        self.device = device
+        self.num_links = num_links
+        self.inner_per_link = inner_per_link
+        self.max_obstacles = max_obstacles
+        self.margin = margin
+
+    # -- lifetime -----------------------------------------------------------
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            _lib().rgg_roadmap_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        return self._h
+
+    # -- offline records ----------------------------------------------------
+    def build_edges(self, robot, q_from, q_to, step: float, stream=None) -> None:
+        """Build the sphere records on the GPU from edge endpoints (rgg_build_edges)."""
+        arrs = [_host(getattr(robot, k), np.float64) for k in ("a", "alpha", "d", "radius")]
+        p = [a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) for a in arrs]
+        rb = _Robot(len(arrs[0]), *p)
+        qa = _host(q_from, np.float64).reshape(-1, self.num_links)
+        qb = _host(q_to, np.float64).reshape(-1, self.num_links)
+        if qa.shape != qb.shape:
+            raise ValueError("q_from and q_to differ in shape")
+        _check("rgg_build_edges", _lib().rgg_build_edges(
+            self._h, ctypes.byref(rb), qa.shape[0], qa.ctypes.data, qb.ctypes.data, float(step),
+            _stream(stream, self.device)))
+
+    def upload_edges(self, sample_off, inner_xyzr, outer_xyzr, stream=None) -> None:
+        """Upload caller-built records (rgg_upload_edges); inner/outer are [4, n]
+        plane arrays, host numpy or device torch tensors."""
+        soff = _host(sample_off, np.uint64)
+        dev = _is_device(inner_xyzr)
+        if dev != _is_device(outer_xyzr):
+            raise ValueError("inner and outer records must both be host or both device")
+        if not dev:
+            inner_xyzr = _host(inner_xyzr, np.float32)
+            outer_xyzr = _host(outer_xyzr, np.float32)
+        _check("rgg_upload_edges", _lib().rgg_upload_edges(
+            self._h, soff.shape[0] - 1, soff.ctypes.data, _ptr(inner_xyzr), _ptr(outer_xyzr),
+            int(dev), _stream(stream, self.device)))
+
+    # -- online update and classification -------------------------------------
+    def update_obstacles(self, ids, poses, stream=None) -> None:
+        """Move boxes ``ids`` to absolute ``poses`` [m, 15] (float32; host numpy
+        or device tensor)."""
+        ids = _host(ids, np.uint32).reshape(-1)
+        dev = _is_device(poses)
+        if not dev:
+            poses = _host(poses, np.float32).reshape(-1, 15)
+            if poses.shape[0] != ids.shape[0]:
+                raise ValueError("one pose per id")
+        _check("rgg_update_obstacles", _lib().rgg_update_obstacles(
+            self._h, ids.shape[0], ids.ctypes.data, _ptr(poses), int(dev),
+            _stream(stream, self.device)))
+
+    def classify(self, stream=None) -> None:
+        _check("rgg_classify", _lib().rgg_classify(self._h, _stream(stream, self.device)))
+
+    # -- results --------------------------------------------------------------
+    def fetch_labels(self, first: int = 0, count: Optional[int] = None, out=None,
+                     stream=None):
+        """Labels [first, first+count) into ``out`` (numpy uint8 or a device
+        tensor), allocated as numpy when None."""
+        if count is None:
+            count = self.info()["num_edges"] - first
+        if out is None:
+            out = np.empty(count, dtype=np.uint8)
+        _check("rgg_fetch_labels", _lib().rgg_fetch_labels(
+            self._h, _ptr(out), first, count, int(_is_device(out)), _stream(stream, self.device)))
+        return out
+
+    def fetch_box_sets(self, first: int = 0, count: Optional[int] = None, stream=None):
+        """(hit, touch) box-id bitsets [count, mask_words] uint32, host."""
+        info = self.info()
+        if count is None:
+            count = info["num_edges"] - first
+        hit = np.empty((count, info["mask_words"]), dtype=np.uint32)
+        touch = np.empty_like(hit)
+        _check("rgg_fetch_box_sets", _lib().rgg_fetch_box_sets(
+            self._h, hit.ctypes.data, touch.ctypes.data, first, count, 0,
+            _stream(stream, self.device)))
+        return hit, touch
+
+    def fetch_records(self, first: int = 0, count: Optional[int] = None):
+        """(inner [4, n_in], outer [4, n_out], sample_off [N+1]) of edges
+        [first, first+count), host, in the rgg_upload_edges layout."""
+        info = self.info()
+        n = info["num_edges"]
+        soff = np.empty(n + 1, dtype=np.uint64)
+        _check("rgg_fetch_records", _lib().rgg_fetch_records(self._h, 0, 0, None, None,
+                                                             soff.ctypes.data))
+        if count is None:
+            count = n - first
+        s0, s1 = int(soff[first]), int(soff[first + count])
+        L, K = self.num_links, self.inner_per_link
+        inner = np.empty((4, K * L * (s1 - s0)), dtype=np.float32)
+        outer = np.empty((4, L * (s1 - s0 - count)), dtype=np.float32)
+        _check("rgg_fetch_records", _lib().rgg_fetch_records(
+            self._h, first, count, inner.ctypes.data, outer.ctypes.data, None))
+        return inner, outer, soff
+
+    def labels_device_ptr(self) -> int:
+        p = ctypes.c_void_p()
+        _check("rgg_labels_device_ptr", _lib().rgg_labels_device_ptr(self._h, ctypes.byref(p)))
+        return int(p.value or 0)
+
+    def info(self) -> dict:
+        inf = Info()
+        _check("rgg_roadmap_info", _lib().rgg_roadmap_info(self._h, ctypes.byref(inf)))
+        return inf.as_dict()
+
+    def check_status(self, stream=None) -> None:
+        _check("rgg_check_status", _lib().rgg_check_status(self._h, _stream(stream, self.device)))
+
+    # -- timing and launch shape ----------------------------------------------
+    def set_kernel_timing(self, enable: bool) -> None:
+        _check("rgg_set_kernel_timing", _lib().rgg_set_kernel_timing(self._h, int(enable)))
+
+    def kernel_time(self):
+        """(milliseconds, launches) of the timed classify launches since the last call."""
+        ms, n = ctypes.c_double(), ctypes.c_uint64()
+        _check("rgg_kernel_time", _lib().rgg_kernel_time(self._h, ctypes.byref(ms),
+                                                         ctypes.byref(n)))
+        return ms.value, n.value
+
+    def set_launch_shape(self, ctas_per_sm: int = 0, consumer_warps: int = 0) -> None:
+        _check("rgg_set_launch_shape", _lib().rgg_set_launch_shape(self._h, ctas_per_sm,
+                                                                   consumer_warps))
+
+
+def classify_many(roadmaps: Sequence[Roadmap], stream=None) -> None:
+    """One persistent launch per pass over all roadmaps (rgg_classify_many)."""
+    if not roadmaps:
+        return
+    arr = (ctypes.c_void_p * len(roadmaps))(*[r.handle for r in roadmaps])
+    _check("rgg_classify_many", _lib().rgg_classify_many(arr, len(roadmaps),
+                                                         _stream(stream, roadmaps[0].device)))
