@@ -1,0 +1,394 @@
+"""Benchmark of the RGG edge-classification pass on GB300.
+
+One step = one obstacle update (the update's moved boxes written into the
+device box table) followed by one classification of every roadmap edge
+against the moved boxes, merged into the per-edge box sets and labels.
+
+Default workload: the large single roadmap (7-DOF DH arm, ~500k edges,
+~80 configurations per edge, ~27 GB of FP32 sphere records resident in HBM,
+256 oriented boxes, 32 moved per update).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload large|7dof|planar]
+  python bench.py --impl reference ...   # the FP64 CPU oracle on the same metric
+
+Prints one JSON line (rank 0).  For N > 1 (launched by torch.distributed.run)
+every rank runs an independent replica on its own GPU: the edges are not
+sharded and no collective touches the data path (barrier and max-over-ranks
+timing only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2603_28674_gb300 import workloads as W  # noqa: E402
+
+METRIC = "RGG edges classified/s"
+UNIT = "edges/s"
+FALLBACK_HBM_GBS = 6800.0
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "classify_kernel_traffic.txt")
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_2603_28674_gb300", "csrc", f)
+                  for f in ("rgg_kernels.cu", "rgg_device.cuh", "rgg_kernels.h")]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="large", choices=["large", "7dof", "planar"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def make_scene(name: str, n_updates: int):
+    if name == "large":
+        return W.workload_large(n_updates=n_updates)
+    if name == "7dof":
+        return W.workload_7dof(n_updates=n_updates)
+    return W.workload_planar(n_updates=n_updates)
+
+
+def workload_config(name: str, sc) -> dict:
+    rm = sc.roadmap
+    moved = len(sc.updates[0].ids) if sc.updates else 0
+    cfg = {
+        "workload": {"large": "large single roadmap", "7dof": "7-DOF 10k-node roadmap",
+                     "planar": "planar 3-link 500-node roadmap"}[name],
+        "robot": f"{rm.robot.num_links}-link DH arm, {rm.robot.inner_per_link} inner spheres/link",
+        "edges": rm.num_edges,
+        "step_rad": rm.step,
+        "boxes": sc.boxes.count,
+        "moved_per_update": moved,
+        "record_dtype": "fp32",
+    }
+    return cfg
+
+
+def kernel_sha() -> str:
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        h.update(open(p, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(workload: str):
+    """DRAM bytes per classify launch from the committed ncu summary, or None
+    when it is missing, for another workload, or the kernel changed since."""
+    if not os.path.exists(PROFILE_TRAFFIC):
+        return None
+    kv = {}
+    for line in open(PROFILE_TRAFFIC):
+        if "=" in line and not line.startswith("#"):
+            k, v = line.strip().split("=", 1)
+            kv[k.strip()] = v.strip()
+    if kv.get("kernel_sha") != kernel_sha() or kv.get("workload") != workload:
+        return None
+    try:
+        return float(kv["bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def hbm_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            return float(json.load(open(p))["hbm_gbs"]), "measured"
+        except Exception:
+            pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.path = os.path.join("/tmp", f"rgg_clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.fh,
+                stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.remove(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def algorithmic_bytes(info: dict, moved: int) -> int:
+    """Bytes one classify launch must move: every sphere record once (16 B
+    per inner and outer sphere) and each edge's pass result (hit and touch
+    words, 8 B).  Tile descriptors, edge tables and the moved boxes' records
+    are implementation overhead and not counted."""
+    return info["record_bytes"] + 8 * info["num_edges"]
+
+
+# --------------------------------------------------------------------------
+# CPU oracle timing
+# --------------------------------------------------------------------------
+def oracle_rate(sc, seconds: float, seed: int = 0):
+    """Edges/s of the FP64 oracle classifying a random sample of the
+    workload's edges against the boxes moved in one update, on all host
+    cores.  The sample grows until it takes about `seconds`."""
+    import oracle
+    rm = sc.roadmap
+    up = sc.updates[0]
+    rng = np.random.default_rng(seed)
+    n = 64
+    total_e, total_t = 0, 0.0
+    while True:
+        idx = rng.choice(rm.num_edges, size=min(n, rm.num_edges), replace=False)
+        t0 = time.perf_counter()
+        oracle.classify(rm.robot, rm.q_from[idx], rm.q_to[idx], rm.step, up.poses)
+        dt = time.perf_counter() - t0
+        total_e += idx.size
+        total_t += dt
+        if total_t >= seconds or idx.size == rm.num_edges:
+            break
+        n = int(min(rm.num_edges, max(n * 2, idx.size * (seconds - total_t) / max(dt, 1e-3))))
+    return total_e / total_t, total_e, total_t, oracle.max_threads()
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    sc = make_scene(args.workload, n_updates=max(1, args.warmup + args.steps))
+    import oracle
+    rm = sc.roadmap
+    rng = np.random.default_rng(1)
+    # size each step so that the whole run takes about two and a half minutes
+    rate, _, _, _ = oracle_rate(sc, 3.0)
+    budget = 150.0 / max(1, args.steps + args.warmup)
+    per_step = int(max(16, min(rm.num_edges, rate * budget)))
+    times = []
+    for i in range(args.warmup + args.steps):
+        up = sc.updates[i % len(sc.updates)]
+        idx = rng.choice(rm.num_edges, size=per_step, replace=False)
+        t0 = time.perf_counter()
+        oracle.classify(rm.robot, rm.q_from[idx], rm.q_to[idx], rm.step, up.poses)
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    t = float(sum(times))
+    value = per_step * args.steps / t
+    sample = (f"{per_step} random edges per step, each classified from its endpoints against "
+              f"the {len(sc.updates[0].ids)} boxes one update moves (FP64, OpenMP over edges)")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000 * t / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(args.workload, sc),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.max_threads(),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# --------------------------------------------------------------------------
+# GPU arm
+# --------------------------------------------------------------------------
+def run_gpu(args):
+    import torch
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    from paper_2603_28674_gb300 import build
+    build.build()
+    from paper_2603_28674_gb300 import rgg
+
+    n_ups = 64
+    sc = make_scene(args.workload, n_updates=n_ups)
+    rm, robot = sc.roadmap, sc.roadmap.robot
+    moved = len(sc.updates[0].ids)
+    stream = torch.cuda.current_stream()
+    r = rgg.Roadmap(robot.num_links, robot.inner_per_link, sc.boxes.count, device=local)
+    r.build_edges(robot, rm.q_from, rm.q_to, rm.step, stream)
+    r.update_obstacles(np.arange(sc.boxes.count), sc.boxes.poses().astype(np.float32), stream)
+    r.classify(stream)
+    info = r.info()
+
+    # device-resident update inputs for the device-timed loop
+    dev_poses = [torch.from_numpy(u.poses.astype(np.float32)).to(f"cuda:{local}")
+                 for u in sc.updates]
+    ids = [u.ids for u in sc.updates]
+    # pinned host buffers for the end-to-end loop
+    host_poses = [torch.from_numpy(u.poses.astype(np.float32)).pin_memory().numpy()
+                  for u in sc.updates]
+    labels_host = torch.empty(info["num_edges"], dtype=torch.uint8).pin_memory().numpy()
+
+    def device_step(i):
+        k = i % n_ups
+        r.update_obstacles(ids[k], dev_poses[k], stream)
+        r.classify(stream)
+
+    for i in range(args.warmup):
+        device_step(i)
+    torch.cuda.synchronize()
+
+    # ---- device-timed region: inputs resident in HBM, records 27 GB >> L2
+    r.set_kernel_timing(True)
+    r.kernel_time()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clocks:
+        ev0.record(stream)
+        for i in range(args.steps):
+            device_step(args.warmup + i)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    k_ms, m_ms, k_launches = r.kernel_time()
+    r.set_kernel_timing(False)
+    if dist is not None:
+        t = torch.tensor([ms], device=f"cuda:{local}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    clk = clocks.summary()
+
+    # ---- end to end through the C ABI with host buffers
+    for i in range(min(args.warmup, 3)):
+        k = i % n_ups
+        r.update_obstacles(ids[k], host_poses[k], stream)
+        r.classify(stream)
+        r.fetch_labels(out=labels_host, stream=stream)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        k = (args.warmup + i) % n_ups
+        r.update_obstacles(ids[k], host_poses[k], stream)
+        r.classify(stream)
+        r.fetch_labels(out=labels_host, stream=stream)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([e2e_s], device=f"cuda:{local}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    r.check_status(stream)
+
+    n_edges = info["num_edges"]
+    value = world * n_edges * args.steps / (ms / 1000.0)
+    e2e_value = world * n_edges * args.steps / e2e_s
+    peak, peak_kind = hbm_peak()
+    b_alg = algorithmic_bytes(info, moved)
+    k_avg_ms = k_ms / max(1, k_launches)
+    achieved = b_alg / (k_avg_ms / 1000.0) / 1e9
+    traffic = profiled_traffic(args.workload)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, n_s, t_s, cores = oracle_rate(sc, args.cpu_seconds)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": (f"{n_s} random edges classified from their endpoints against the "
+                          f"{moved} boxes one update moves (FP64, OpenMP over edges), "
+                          f"{t_s:.1f} s")}
+
+    cfg = workload_config(args.workload, sc)
+    cfg.update({"samples": info["num_samples"], "record_gb": info["record_bytes"] / 1e9,
+                "l2": "records > L2 (129 MB); no flush needed", "parallelism":
+                f"replicas x{world}" if world > 1 else "single GPU",
+                "tile_samples": info["tile_samples"], "grid_ctas": info["grid_ctas"]})
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": cfg,
+        "sphere_box_tests_per_s": world * (info["num_inner"] + info["num_outer"]) * moved
+        * args.steps / (ms / 1000.0),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "peak_source": f"{peak_kind} HBM copy bandwidth",
+                     "kernel": "classify_kernel", "bytes_per_launch": b_alg,
+                     "kernel_ms": k_avg_ms,
+                     "merge_kernel_ms": m_ms / max(1, k_launches)},
+        "e2e": {"value": e2e_value, "unit": UNIT,
+                "h2d_bytes_per_step": moved * (4 + 60),
+                "d2h_bytes_per_step": n_edges + 4},
+        "gpu_launches": 4 * args.steps,
+        "clocks": clk,
+        "cpu_baseline": cpu,
+    }
+    r.close()
+    if rank == 0:
+        print(json.dumps(line))
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

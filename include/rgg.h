@@ -80,7 +80,8 @@ enum {
   RGG_MAX_LINKS = 32,          /* num_links                                    */
   RGG_MAX_INNER = 16,          /* inner_per_link                               */
   RGG_MAX_OBSTACLES = 4096,    /* max_obstacles                                */
-  RGG_BOXES_PER_PASS = 32      /* moved boxes tested per streaming pass        */
+  RGG_BOXES_PER_PASS = 32,     /* moved boxes tested per streaming pass        */
+  RGG_NUM_VARIANTS = 6         /* compiled pipeline shapes (rgg_set_launch_shape) */
 };
 
 typedef struct {
@@ -208,6 +209,7 @@ int rgg_classify(rgg_roadmap_t r, void* stream);
  * labels are the same as rgg_classify on each roadmap alone.  All roadmaps
  * must live on the same device; repeats are not allowed. */
 int rgg_classify_many(rgg_roadmap_t* roadmaps, uint32_t n, void* stream);
+/* (All roadmaps must also share the launch variant, see rgg_set_launch_shape.) */
 
 /* Copy labels [first, first+count) (uint8, enum rgg_label) to `out`, a host
  * (dst_is_device = 0) or device (1) buffer.  For a host destination the call
@@ -242,17 +244,23 @@ int rgg_roadmap_info(rgg_roadmap_t r, rgg_info* out);
  * (RGG_ERR_TIMEOUT), clearing it. */
 int rgg_check_status(rgg_roadmap_t r, void* stream);
 
-/* Kernel timing: when enabled, rgg_classify records CUDA events around each
- * streaming classify launch on its stream; rgg_kernel_time returns the sum of
- * their durations (ms) since the last call and the number of launches, and
- * resets both (it synchronises on the events). */
+/* Kernel timing: when enabled, rgg_classify records CUDA events on its stream
+ * around each pass's streaming classify launch and its merge launch;
+ * rgg_kernel_time returns the summed durations (ms) of each since the last
+ * call and the number of passes timed, and resets them (it synchronises on
+ * the events). */
 int rgg_set_kernel_timing(rgg_roadmap_t r, int enable);
-int rgg_kernel_time(rgg_roadmap_t r, double* ms, uint64_t* launches);
+int rgg_kernel_time(rgg_roadmap_t r, double* classify_ms, double* merge_ms, uint64_t* launches);
 
-/* Launch shape of the streaming classify kernel: CTAs per SM (0 = default)
- * and consumer warps per CTA (0 = default).  Takes effect from the next
- * rgg_classify.  RGG_ERR_INVALID if the shape cannot be launched. */
-int rgg_set_launch_shape(rgg_roadmap_t r, uint32_t ctas_per_sm, uint32_t consumer_warps);
+/* Launch shape of the streaming classify kernel: `variant` picks one of the
+ * compiled pipeline shapes (shared-memory ring depth x stage size x rounds of
+ * 31 configurations per tile; RGG_NUM_VARIANTS in all, 0 = smallest tiles,
+ * 4 the default) and `consumer_warps` the warps per CTA that test records
+ * (0 = default 24; 1..31).  With edges present the tiles are rebuilt for the new shape (the
+ * call synchronises the device).  Roadmaps classified together by
+ * rgg_classify_many must share the variant.  RGG_ERR_INVALID for an
+ * unsupported shape (nothing changes). */
+int rgg_set_launch_shape(rgg_roadmap_t r, uint32_t variant, uint32_t consumer_warps);
 
 /* Static description of a status code (never NULL). */
 const char* rgg_status_string(int status);

@@ -2,6 +2,7 @@
 // memory, tiling of the record stream, and kernel launches.  Every step of
 // the classification runs in the kernels of rgg_kernels.cu.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -49,38 +50,41 @@ cudaError_t dalloc(T** p, size_t count) {
 }
 
 // Streaming tile geometry of one roadmap (see the classify kernel): each
-// stage buffer holds a header, the tile's edge table, the pass's box
-// records, 4 inner planes and 4 outer planes.
+// stage buffer holds a header, the tile's edge table, 4 inner planes and 4
+// outer planes.
 struct Tiling {
   uint32_t S = 0, max_edges = 0;
-  uint32_t off_edges = 0, off_boxes = 0, off_in = 0, off_out = 0, in_cap = 0, out_cap = 0;
+  uint32_t off_in = 0, off_out = 0, in_cap = 0, out_cap = 0;
 };
 
 uint32_t align16(uint32_t x) { return (x + 15u) & ~15u; }
 uint32_t round4(uint32_t x) { return (x + 3u) & ~3u; }
 
-bool tiling_for(uint32_t L, uint32_t K, uint32_t S, Tiling* t) {
+// A window of S consecutive global samples meets at most S/(2L) + 2 edges
+// (every edge has at least 2L samples); one more entry of slack.
+bool tiling_for(uint32_t L, uint32_t K, uint32_t S, uint32_t stage_bytes, Tiling* t) {
   t->S = S;
   t->max_edges = S / (2 * L) + 3;
-  t->off_edges = kStageHdrBytes;
-  t->off_boxes = align16(t->off_edges + 16 * t->max_edges);
-  t->off_in = align16(t->off_boxes + kBoxesPerPass * kBoxRecFloats * 4);
+  t->off_in = align16(kStageEtabOff + 16 * t->max_edges);
   t->in_cap = round4(K * S + 8);
   t->off_out = t->off_in + 16 * t->in_cap;
   t->out_cap = round4(S + 1 + 8);
-  return (uint64_t)t->off_out + 16ull * t->out_cap <= (uint64_t)kStageBytes;
+  return t->max_edges <= (uint32_t)kMaxTileEdges &&
+         (uint64_t)t->off_out + 16ull * t->out_cap <= (uint64_t)stage_bytes;
 }
 
-// Largest tile that fits a stage, reduced for small roadmaps so that every
-// CTA of the launch gets a few tiles.
-Tiling choose_tiling(uint32_t L, uint32_t K, uint64_t G, uint32_t ctas) {
-  uint32_t smax = kStageBytes / (16 * (K + 1));
+// Tiles of 31*rounds samples (full rounds) when they fit a stage, else the
+// largest that does; smaller for tiny roadmaps so that the work spreads over
+// the launch's warps.
+Tiling choose_tiling(uint32_t L, uint32_t K, uint64_t G, uint32_t warps, int variant) {
+  const VariantShape v = variant_shape(variant);
+  uint32_t smax = 31 * v.rounds;
   Tiling t;
-  while (smax > 1 && !tiling_for(L, K, smax, &t)) --smax;
-  uint64_t want = (G + 4ull * ctas - 1) / (4ull * ctas);
-  uint32_t s = (uint32_t)std::min<uint64_t>(smax, std::max<uint64_t>(want, 128));
+  while (smax > 1 && !tiling_for(L, K, smax, v.stage_bytes, &t)) --smax;
+  const uint64_t want = (G + warps - 1) / std::max<uint32_t>(warps, 1);
+  uint32_t s = (uint32_t)std::min<uint64_t>(smax, std::max<uint64_t>(want, 31));
   s = std::max<uint32_t>(1, std::min(s, smax));
-  tiling_for(L, K, s, &t);
+  tiling_for(L, K, s, v.stage_bytes, &t);
   return t;
 }
 
@@ -91,26 +95,28 @@ struct EdgeState {
   uint64_t* d_soff = nullptr;
   float* d_inner = nullptr;
   float* d_outer = nullptr;
-  uint32_t* d_tile_edge = nullptr;
-  uint64_t T = 0;
+  TileDesc* d_tiles = nullptr;
+  int4* d_etab = nullptr;
+  uint64_t T = 0, n_etab = 0;
   Tiling tiling;
   uint32_t* d_red = nullptr;
   uint32_t* d_touch = nullptr;
+  uint32_t* d_counts = nullptr;
   uint8_t* d_labels = nullptr;
   uint32_t* d_edge_acc = nullptr;
-  uint32_t* d_edge_done = nullptr;
   uint64_t device_bytes = 0;
 
   void release() {
     cudaFree(d_soff);
     cudaFree(d_inner);
     cudaFree(d_outer);
-    cudaFree(d_tile_edge);
+    cudaFree(d_tiles);
+    cudaFree(d_etab);
     cudaFree(d_red);
     cudaFree(d_touch);
+    cudaFree(d_counts);
     cudaFree(d_labels);
     cudaFree(d_edge_acc);
-    cudaFree(d_edge_done);
     *this = EdgeState();
   }
 };
@@ -122,7 +128,8 @@ struct rgg_roadmap {
   uint32_t L = 0, K = 0, M = 0, Wm = 0;
   float margin = 2e-5f;
   int num_sms = 0;
-  uint32_t ctas_per_sm = 1, consumer_warps = 16;
+  uint32_t ctas_per_sm = 1, consumer_warps = kDefaultConsumerWarps;
+  int variant = kDefaultVariant;
   bool has_edges = false;
   EdgeState es;
   float* d_table = nullptr;    // [M][16] box poses
@@ -130,15 +137,95 @@ struct rgg_roadmap {
   int* d_status = nullptr;
   std::vector<uint8_t> present, is_pending;
   std::vector<uint32_t> pending;
-  // kernel timing
+  // kernel timing: events before classify, between classify and merge, after merge
   bool timing = false;
-  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;
+  std::vector<std::array<cudaEvent_t, 3>> events;
   size_t events_used = 0;
 };
 
 namespace {
 
 uint32_t launch_ctas(const rgg_roadmap* r) { return (uint32_t)r->num_sms * r->ctas_per_sm; }
+
+// Tile descriptors and per-tile edge tables of a roadmap (see
+// rgg_device.cuh): tile t covers global samples [t*S, min((t+1)*S, G)).
+bool build_tiles(uint32_t L, uint64_t N, const std::vector<uint64_t>& soff, uint64_t G,
+                 uint32_t S, std::vector<TileDesc>* tiles, std::vector<int4>* etab) {
+  const uint64_t T = (G + S - 1) / S;
+  tiles->resize(T);
+  etab->clear();
+  etab->reserve(N + T);
+  uint64_t ef = 0;  // edge holding the tile's first sample
+  for (uint64_t t = 0; t < T; ++t) {
+    const uint64_t g0 = t * S, g1 = std::min<uint64_t>(g0 + S, G);
+    while ((uint64_t)L * soff[ef + 1] <= g0) ++ef;
+    uint64_t el = ef;
+    while ((uint64_t)L * soff[el + 1] < g1) ++el;
+    const uint64_t so_f = soff[ef], n_f = soff[ef + 1] - so_f;
+    const uint64_t so_l = soff[el], n_l = soff[el + 1] - so_l;
+    // first interval: the halo before the first sample when the tile starts
+    // inside a link's run, else the run's first interval
+    const uint64_t rf = g0 - L * so_f, i_f = rf / n_f, k_f = rf - i_f * n_f;
+    const uint64_t o0 = L * (so_f - ef) + i_f * (n_f - 1) + (k_f > 0 ? k_f - 1 : 0);
+    // last interval: the one after the last sample, or before it at a run's end
+    const uint64_t rl = g1 - 1 - L * so_l, i_l = rl / n_l, k_l = rl - i_l * n_l;
+    const uint64_t o1 = L * (so_l - el) + i_l * (n_l - 1) + std::min(k_l, n_l - 2) + 1;
+    const uint64_t n_edges = el - ef + 1;
+    if (n_edges > kMaxTileEdges || o1 - o0 > 0xffff || o0 >= (1ull << 40) ||
+        etab->size() >= 0xffffffffull || el >= 0xffffffffull)
+      return false;
+    (*tiles)[t].packed = o0 | ((o1 - o0) << 40) | (n_edges << 56);
+    (*tiles)[t].etab = (uint32_t)etab->size();
+    (*tiles)[t].e_first = (uint32_t)ef;
+    for (uint64_t e = ef; e <= el; ++e) {
+      const int64_t estart = (int64_t)(L * soff[e]) - (int64_t)g0;
+      const int64_t ostart = (int64_t)(L * (soff[e] - e)) - (int64_t)o0;
+      const uint64_t n = soff[e + 1] - soff[e];
+      float inv = 1.0f / (float)n;
+      int inv_bits;
+      std::memcpy(&inv_bits, &inv, sizeof(inv_bits));
+      etab->push_back(make_int4((int)estart, (int)n, (int)ostart, inv_bits));
+    }
+  }
+  return true;
+}
+
+// (Re)build the tile descriptors and edge tables of `es` for the roadmap's
+// current launch shape and copy them to the device (synchronous).
+int set_tiles(rgg_roadmap* r, EdgeState* es, cudaStream_t s) {
+  Tiling tiling = choose_tiling(r->L, r->K, es->G, launch_ctas(r) * r->consumer_warps, r->variant);
+  std::vector<TileDesc> h_tiles;
+  std::vector<int4> h_etab;
+  if (es->N && !build_tiles(r->L, es->N, es->h_soff, es->G, tiling.S, &h_tiles, &h_etab))
+    return RGG_ERR_INVALID;
+  TileDesc* d_tiles = nullptr;
+  int4* d_etab = nullptr;
+  cudaError_t e = dalloc(&d_tiles, h_tiles.size());
+  if (e == cudaSuccess) e = dalloc(&d_etab, h_etab.size());
+  if (e == cudaSuccess && !h_tiles.empty())
+    e = cudaMemcpyAsync(d_tiles, h_tiles.data(), h_tiles.size() * sizeof(TileDesc),
+                        cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && !h_etab.empty())
+    e = cudaMemcpyAsync(d_etab, h_etab.data(), h_etab.size() * sizeof(int4),
+                        cudaMemcpyHostToDevice, s);
+  // the host vectors must outlive the copies
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    cudaFree(d_tiles);
+    cudaFree(d_etab);
+    return cuda_status(e);
+  }
+  es->device_bytes -= es->T * sizeof(TileDesc) + es->n_etab * sizeof(int4);
+  cudaFree(es->d_tiles);
+  cudaFree(es->d_etab);
+  es->d_tiles = d_tiles;
+  es->d_etab = d_etab;
+  es->T = h_tiles.size();
+  es->n_etab = h_etab.size();
+  es->tiling = tiling;
+  es->device_bytes += es->T * sizeof(TileDesc) + es->n_etab * sizeof(int4);
+  return RGG_OK;
+}
 
 // Allocate the per-edge state and record planes for N edges with per-edge
 // sample offsets h_soff (host), into `es` (not yet visible to the roadmap).
@@ -154,8 +241,6 @@ int alloc_edges(rgg_roadmap* r, EdgeState* es, uint64_t N, std::vector<uint64_t>
   // bulk copies, rounded to 64 floats (256 B) to keep planes aligned
   es->in_stride = ((es->n_inner + 4 + 63) / 64) * 64;
   es->out_stride = ((es->n_outer + 4 + 63) / 64) * 64;
-  es->tiling = choose_tiling(r->L, r->K, es->G, launch_ctas(r));
-  es->T = (es->G + es->tiling.S - 1) / es->tiling.S;
   cudaError_t e = cudaSuccess;
 #define RGG_AL(ptr, cnt)                 \
   if (e == cudaSuccess) {                \
@@ -165,12 +250,11 @@ int alloc_edges(rgg_roadmap* r, EdgeState* es, uint64_t N, std::vector<uint64_t>
   RGG_AL(es->d_soff, N + 1);
   RGG_AL(es->d_inner, 4 * es->in_stride);
   RGG_AL(es->d_outer, 4 * es->out_stride);
-  RGG_AL(es->d_tile_edge, es->T + 1);
   RGG_AL(es->d_red, N * r->Wm);
   RGG_AL(es->d_touch, N * r->Wm);
+  RGG_AL(es->d_counts, N);
   RGG_AL(es->d_labels, N);
   RGG_AL(es->d_edge_acc, 2 * N);
-  RGG_AL(es->d_edge_done, N);
 #undef RGG_AL
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(es->d_soff, es->h_soff.data(), (N + 1) * sizeof(uint64_t),
@@ -178,17 +262,22 @@ int alloc_edges(rgg_roadmap* r, EdgeState* es, uint64_t N, std::vector<uint64_t>
   if (e == cudaSuccess && N) {
     e = cudaMemsetAsync(es->d_red, 0, N * r->Wm * 4, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(es->d_touch, 0, N * r->Wm * 4, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(es->d_counts, 0, N * 4, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(es->d_labels, RGG_GREEN, N, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(es->d_edge_acc, 0, 2 * N * 4, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(es->d_edge_done, 0, N * 4, s);
+  }
+  if (e == cudaSuccess) {
+    const int rc = set_tiles(r, es, s);
+    if (rc != RGG_OK) {
+      es->release();
+      return rc;
+    }
   }
   if (e == cudaSuccess && N) {
     // zero the padded tails so that the rounded bulk copies read defined data
     e = cudaMemsetAsync(es->d_inner, 0, 4 * es->in_stride * sizeof(float), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(es->d_outer, 0, 4 * es->out_stride * sizeof(float), s);
   }
-  if (e == cudaSuccess && N)
-    e = launch_tile_edge(es->d_soff, N, r->L, es->tiling.S, es->T, es->d_tile_edge, s);
   if (e != cudaSuccess) {
     es->release();
     return cuda_status(e);
@@ -211,11 +300,12 @@ void install_edges(rgg_roadmap* r, EdgeState&& es) {
     }
 }
 
-bool valid_soff(const uint64_t* soff, uint64_t N) {
-  if (!soff || soff[0] != 0) return false;
+// n_e >= 2 per edge; L*n_e and the edge count fit the 32-bit tile tables.
+bool valid_soff(const uint64_t* soff, uint64_t N, uint32_t L) {
+  if (!soff || soff[0] != 0 || N >= 0xffffffffull) return false;
   for (uint64_t e = 0; e < N; ++e) {
     if (soff[e + 1] < soff[e] + 2) return false;
-    if (soff[e + 1] - soff[e] > 0x7fffffffull) return false;
+    if ((soff[e + 1] - soff[e]) * (uint64_t)L > 0x7fffffffull) return false;
   }
   return true;
 }
@@ -246,17 +336,17 @@ bool valid_pose(const float* p) {
   return std::fabs(det - 1.0) <= 1e-3;
 }
 
-cudaEvent_t* next_event_pair(rgg_roadmap* r) {
+cudaEvent_t* next_events(rgg_roadmap* r) {
   if (r->events_used == r->events.size()) {
-    cudaEvent_t a, b;
-    if (cudaEventCreate(&a) != cudaSuccess) return nullptr;
-    if (cudaEventCreate(&b) != cudaSuccess) {
-      cudaEventDestroy(a);
-      return nullptr;
-    }
-    r->events.emplace_back(a, b);
+    std::array<cudaEvent_t, 3> ev{};
+    for (int i = 0; i < 3; ++i)
+      if (cudaEventCreate(&ev[i]) != cudaSuccess) {
+        for (int j = 0; j < i; ++j) cudaEventDestroy(ev[j]);
+        return nullptr;
+      }
+    r->events.push_back(ev);
   }
-  return &r->events[r->events_used++].first;
+  return r->events[r->events_used++].data();
 }
 
 ClassifyJob make_job(rgg_roadmap* r, uint32_t C, uint64_t tile_base) {
@@ -266,15 +356,10 @@ ClassifyJob make_job(rgg_roadmap* r, uint32_t C, uint64_t tile_base) {
   j.outer = es.d_outer;
   j.in_stride = es.in_stride;
   j.out_stride = es.out_stride;
-  j.soff = es.d_soff;
-  j.tile_edge = es.d_tile_edge;
+  j.tiles = es.d_tiles;
+  j.etab = es.d_etab;
   j.boxes = r->d_changed;
-  j.red = es.d_red;
-  j.touch = es.d_touch;
-  j.labels = es.d_labels;
   j.edge_acc = es.d_edge_acc;
-  j.edge_done = es.d_edge_done;
-  j.num_edges = es.N;
   j.G = es.G;
   j.tile_base = tile_base;
   j.num_tiles = es.T;
@@ -282,16 +367,28 @@ ClassifyJob make_job(rgg_roadmap* r, uint32_t C, uint64_t tile_base) {
   j.K = r->K;
   j.S = es.tiling.S;
   j.C = C;
-  j.Wm = r->Wm;
-  j.off_edges = es.tiling.off_edges;
-  j.off_boxes = es.tiling.off_boxes;
   j.off_in = es.tiling.off_in;
   j.off_out = es.tiling.off_out;
   j.in_cap = es.tiling.in_cap;
   j.out_cap = es.tiling.out_cap;
-  j.max_edges = es.tiling.max_edges;
   j.margin = r->margin;
   return j;
+}
+
+MergeJob make_merge_job(rgg_roadmap* r, const uint32_t* ids, uint32_t C, uint64_t edge_base) {
+  MergeJob m{};
+  const EdgeState& es = r->es;
+  m.red = es.d_red;
+  m.touch = es.d_touch;
+  m.counts = es.d_counts;
+  m.labels = es.d_labels;
+  m.edge_acc = es.d_edge_acc;
+  m.num_edges = es.N;
+  m.edge_base = edge_base;
+  m.Wm = r->Wm;
+  m.C = C;
+  for (uint32_t b = 0; b < C; ++b) m.ids[b] = ids[b];
+  return m;
 }
 
 }  // namespace
@@ -362,10 +459,8 @@ int rgg_roadmap_destroy(rgg_roadmap_t r) {
   cudaFree(r->d_table);
   cudaFree(r->d_changed);
   cudaFree(r->d_status);
-  for (auto& p : r->events) {
-    cudaEventDestroy(p.first);
-    cudaEventDestroy(p.second);
-  }
+  for (auto& ev : r->events)
+    for (cudaEvent_t x : ev) cudaEventDestroy(x);
   delete r;
   return RGG_OK;
 }
@@ -374,7 +469,7 @@ int rgg_upload_edges(rgg_roadmap_t r, uint64_t num_edges, const uint64_t* sample
                      const float* inner_xyzr, const float* outer_xyzr, int src_is_device,
                      void* stream) {
   if (!r || !sample_off) return RGG_ERR_INVALID;
-  if (!valid_soff(sample_off, num_edges)) return RGG_ERR_INVALID;
+  if (!valid_soff(sample_off, num_edges, r->L)) return RGG_ERR_INVALID;
   if (num_edges && (!inner_xyzr || !outer_xyzr)) return RGG_ERR_INVALID;
   DeviceGuard g(r->device);
   if (!g.ok) return RGG_ERR_CUDA;
@@ -527,41 +622,56 @@ int rgg_update_obstacles(rgg_roadmap_t r, uint32_t n_changed, const uint32_t* id
 }
 
 // One streaming pass per group of <= 32 boxes; for several roadmaps, pass p
-// of every roadmap that has one goes into the same persistent launch.
+// of every roadmap that has one goes into the same persistent launch.  The
+// pending boxes are sorted so that each pass's ids ascend (the merge kernel
+// relies on it).
 static int classify_group(rgg_roadmap_t* rs, uint32_t n, cudaStream_t s) {
   uint32_t max_passes = 0;
-  for (uint32_t i = 0; i < n; ++i)
-    max_passes = std::max<uint32_t>(max_passes, (uint32_t)((rs[i]->pending.size() + kBoxesPerPass - 1) /
-                                                            kBoxesPerPass));
+  for (uint32_t i = 0; i < n; ++i) {
+    std::sort(rs[i]->pending.begin(), rs[i]->pending.end());
+    max_passes = std::max<uint32_t>(
+        max_passes, (uint32_t)((rs[i]->pending.size() + kBoxesPerPass - 1) / kBoxesPerPass));
+  }
   std::unique_ptr<BoxPrepParams> bpp(new (std::nothrow) BoxPrepParams);
   std::unique_ptr<ClassifyParams<kMaxJobs>> cpp;
-  if (n > 1) cpp.reset(new (std::nothrow) ClassifyParams<kMaxJobs>);
-  if (!bpp || (n > 1 && !cpp)) return RGG_ERR_OOM;
+  std::unique_ptr<MergeParams<kMaxJobs>> mpp;
+  if (n > 1) {
+    cpp.reset(new (std::nothrow) ClassifyParams<kMaxJobs>);
+    mpp.reset(new (std::nothrow) MergeParams<kMaxJobs>);
+  }
+  if (!bpp || (n > 1 && (!cpp || !mpp))) return RGG_ERR_OOM;
   for (uint32_t pass = 0; pass < max_passes; ++pass) {
     BoxPrepParams& bp = *bpp;
     bp.njobs = 0;
     ClassifyParams<1> cp1;
+    MergeParams<1> mp1;
     uint32_t nj = 0;
-    uint64_t tiles = 0;
-    uint32_t tw_cap = 0, acc_cap = 0;
+    uint64_t tiles = 0, edges = 0;
     rgg_roadmap* timed = nullptr;
     for (uint32_t i = 0; i < n; ++i) {
       rgg_roadmap* r = rs[i];
       const size_t lo = (size_t)pass * kBoxesPerPass;
       if (lo >= r->pending.size()) continue;
       const uint32_t C = (uint32_t)std::min<size_t>(kBoxesPerPass, r->pending.size() - lo);
+      const uint32_t* ids = r->pending.data() + lo;
       BoxPrepJob& pj = bp.job[bp.njobs++];
       pj.table = r->d_table;
       pj.out = r->d_changed;
       pj.C = C;
-      for (uint32_t b = 0; b < C; ++b) pj.ids[b] = r->pending[lo + b];
+      for (uint32_t b = 0; b < C; ++b) pj.ids[b] = ids[b];
       if (r->es.N == 0) continue;
-      ClassifyJob job = make_job(r, C, tiles);
-      if (n == 1) cp1.job[0] = job; else cpp->job[nj] = job;
+      const ClassifyJob job = make_job(r, C, tiles);
+      const MergeJob mj = make_merge_job(r, ids, C, edges);
+      if (n == 1) {
+        cp1.job[0] = job;
+        mp1.job[0] = mj;
+      } else {
+        cpp->job[nj] = job;
+        mpp->job[nj] = mj;
+      }
       ++nj;
       tiles += r->es.T;
-      tw_cap = std::max(tw_cap, r->es.tiling.S + 2);
-      acc_cap = std::max(acc_cap, r->es.tiling.max_edges);
+      edges += r->es.N;
       if (r->timing && !timed) timed = r;
     }
     RGG_CK(launch_box_prep(bp, s));
@@ -569,10 +679,10 @@ static int classify_group(rgg_roadmap_t* rs, uint32_t n, cudaStream_t s) {
     rgg_roadmap* r0 = rs[0];
     ClassifyLaunch lc;
     lc.consumer_warps = r0->consumer_warps;
-    lc.grid = (uint32_t)std::min<uint64_t>(tiles, launch_ctas(r0));
-    lc.tw_cap = tw_cap;
-    lc.acc_cap = acc_cap;
-    cudaEvent_t* ev = timed ? next_event_pair(timed) : nullptr;
+    lc.variant = r0->variant;
+    lc.grid = (uint32_t)std::min<uint64_t>((tiles + 1) / 2, launch_ctas(r0));
+    lc.grid = std::max<uint32_t>(lc.grid, 1);
+    cudaEvent_t* ev = timed ? next_events(timed) : nullptr;
     if (ev) RGG_CK(cudaEventRecord(ev[0], s));
     if (n == 1) {
       cp1.njobs = 1;
@@ -586,6 +696,16 @@ static int classify_group(rgg_roadmap_t* rs, uint32_t n, cudaStream_t s) {
       RGG_CK(launch_classify_batched(*cpp, lc, s));
     }
     if (ev) RGG_CK(cudaEventRecord(ev[1], s));
+    if (n == 1) {
+      mp1.njobs = 1;
+      mp1.total_edges = edges;
+      RGG_CK(launch_merge_single(mp1, s));
+    } else {
+      mpp->njobs = nj;
+      mpp->total_edges = edges;
+      RGG_CK(launch_merge_batched(*mpp, s));
+    }
+    if (ev) RGG_CK(cudaEventRecord(ev[2], s));
   }
   for (uint32_t i = 0; i < n; ++i) {
     for (uint32_t b : rs[i]->pending) rs[i]->is_pending[b] = 0;
@@ -608,7 +728,7 @@ int rgg_classify_many(rgg_roadmap_t* rs, uint32_t n, void* stream) {
   for (uint32_t i = 0; i < n; ++i) {
     if (!rs[i]) return RGG_ERR_INVALID;
     if (!rs[i]->has_edges) return RGG_ERR_STATE;
-    if (rs[i]->device != rs[0]->device) return RGG_ERR_INVALID;
+    if (rs[i]->device != rs[0]->device || rs[i]->variant != rs[0]->variant) return RGG_ERR_INVALID;
     for (uint32_t j = 0; j < i; ++j)
       if (rs[j] == rs[i]) return RGG_ERR_INVALID;
   }
@@ -732,31 +852,49 @@ int rgg_set_kernel_timing(rgg_roadmap_t r, int enable) {
   return RGG_OK;
 }
 
-int rgg_kernel_time(rgg_roadmap_t r, double* ms, uint64_t* launches) {
-  if (!r || !ms || !launches) return RGG_ERR_INVALID;
+int rgg_kernel_time(rgg_roadmap_t r, double* classify_ms, double* merge_ms,
+                    uint64_t* launches) {
+  if (!r || !classify_ms || !merge_ms || !launches) return RGG_ERR_INVALID;
   DeviceGuard g(r->device);
   if (!g.ok) return RGG_ERR_CUDA;
-  double total = 0.0;
+  double tc = 0.0, tm = 0.0;
   for (size_t i = 0; i < r->events_used; ++i) {
-    RGG_CK(cudaEventSynchronize(r->events[i].second));
-    float t = 0.f;
-    RGG_CK(cudaEventElapsedTime(&t, r->events[i].first, r->events[i].second));
-    total += t;
+    RGG_CK(cudaEventSynchronize(r->events[i][2]));
+    float a = 0.f, b = 0.f;
+    RGG_CK(cudaEventElapsedTime(&a, r->events[i][0], r->events[i][1]));
+    RGG_CK(cudaEventElapsedTime(&b, r->events[i][1], r->events[i][2]));
+    tc += a;
+    tm += b;
   }
-  *ms = total;
+  *classify_ms = tc;
+  *merge_ms = tm;
   *launches = r->events_used;
   r->events_used = 0;
   return RGG_OK;
 }
 
-int rgg_set_launch_shape(rgg_roadmap_t r, uint32_t ctas_per_sm, uint32_t consumer_warps) {
+int rgg_set_launch_shape(rgg_roadmap_t r, uint32_t variant, uint32_t consumer_warps) {
   if (!r) return RGG_ERR_INVALID;
-  const uint32_t cps = ctas_per_sm ? ctas_per_sm : 1;
-  const uint32_t cw = consumer_warps ? consumer_warps : 16;
-  if (cw < 1 || cw > 31 || cps < 1 || cps > 2) return RGG_ERR_INVALID;
-  if (cps * classify_smem_bytes(kStageBytes / 16 + 2, kStageBytes / 16) > 232448) return RGG_ERR_INVALID;
-  r->ctas_per_sm = cps;
+  const uint32_t cw = consumer_warps ? consumer_warps : kDefaultConsumerWarps;
+  if (variant >= (uint32_t)kNumVariants || cw < 1 || cw > 31) return RGG_ERR_INVALID;
+  if (classify_smem_bytes((int)variant, cw) > 232448) return RGG_ERR_INVALID;
+  if ((uint64_t)cw > (uint64_t)variant_shape((int)variant).stages * variant_shape((int)variant).rounds)
+    return RGG_ERR_INVALID;
+  const int old_v = r->variant;
+  const uint32_t old_cw = r->consumer_warps;
+  r->variant = (int)variant;
   r->consumer_warps = cw;
+  if (r->has_edges && r->es.N) {
+    DeviceGuard g(r->device);
+    if (!g.ok) return RGG_ERR_CUDA;
+    cudaDeviceSynchronize();  // no launch may still read the old tiles
+    const int rc = set_tiles(r, &r->es, nullptr);
+    if (rc != RGG_OK) {
+      r->variant = old_v;
+      r->consumer_warps = old_cw;
+      return rc;
+    }
+  }
   return RGG_OK;
 }
 

@@ -7,10 +7,15 @@
 //                  unpadded: edge, body, configuration, sphere)
 //   outer spheres  4 FP32 planes; sphere (e, i, interval k) at
 //                  L*(soff[e] - e) + i*(n_e - 1) + k
-//   soff           N+1 uint64 per-edge configuration offsets
 // A "global sample" g indexes the concatenation over edges and links of the
-// configurations: edge e owns g in [L*soff[e], L*soff[e+1]), link i of it
-// the n_e consecutive values starting at L*soff[e] + i*n_e.
+// configurations: edge e owns g in [L*soff[e], L*soff[e+1]), link i of it the
+// n_e consecutive values starting at L*soff[e] + i*n_e.  Sample g's inner
+// spheres are K consecutive records starting at K*g.
+//
+// Streaming tiles: tile t covers the global samples [t*S, min((t+1)*S, G)),
+// every interval adjacent to one of them (one halo interval before the first
+// sample when the tile starts inside a link's run), and a table with one
+// entry per edge that has samples in the tile.
 #pragma once
 
 #include <cstdint>
@@ -21,7 +26,12 @@ namespace rgg {
 constexpr int kMaxJobs = 128;          // roadmaps per batched launch
 constexpr int kBoxesPerPass = 32;      // moved boxes per streaming pass (one mask word)
 constexpr int kBoxRecFloats = 24;      // derived box record, 6 x float4 = 96 B
-constexpr int kStageHdrBytes = 256;
+constexpr int kStageHdrBytes = 32;
+constexpr int kAccMax = 64;            // per-stage accumulator entries (edges per tile)
+constexpr int kStageAccOff = kStageHdrBytes;                 // hit[kAccMax], touch[kAccMax]
+constexpr int kStageEtabOff = kStageAccOff + 8 * kAccMax;    // edge table
+constexpr int kMaxTileEdges = kAccMax;
+constexpr int kBoxSlots = 2;           // jobs whose box records a CTA stages in shared memory
 
 // Derived record of one moved box, built by the box-prep kernel:
 //   r0 = (centre.xyz, bounding radius |h| rounded up)
@@ -29,28 +39,32 @@ constexpr int kStageHdrBytes = 256;
 //   r4 = (half-extents, box id as raw bits), r5 = padding
 // so that the box-frame coordinate k of a point x is dot(axis_k, x) - u_k.
 
+// Per-tile descriptor (16 B), built on the host when edges are set.
+struct TileDesc {
+  uint64_t packed;   // bits 0..39 o0 (first outer sphere), 40..55 n_out, 56..63 n_edges
+  uint32_t etab;     // index of the tile's first edge-table entry
+  uint32_t e_first;  // global index of the tile's first edge
+};
+// Edge-table entry (int4): {estart, n, ostart, bits of (float)1/n}
+//   estart  local sample index of the edge's first sample (may be < 0)
+//   n       configurations of the edge
+//   ostart  local interval index of the edge's first interval (may be < 0)
+
 // One roadmap's part of a classify launch.
 struct ClassifyJob {
   const float* inner;
   const float* outer;
   uint64_t in_stride, out_stride;   // floats between planes
-  const uint64_t* soff;             // [N+1]
-  const uint32_t* tile_edge;        // [T+1] edge holding the first sample of each tile
+  const TileDesc* tiles;            // [T]
+  const int4* etab;                 // edge tables of all tiles
   const float* boxes;               // [C][24] derived records of this pass's boxes
-  uint32_t* red;                    // [N][Wm] boxes that hit the edge
-  uint32_t* touch;                  // [N][Wm] boxes that touch the edge
-  uint8_t* labels;                  // [N]
-  uint32_t* edge_acc;               // [N][2] cross-tile (hit, touch) scratch, kept zero
-  uint32_t* edge_done;              // [N] cross-tile sample counter, kept zero
-  uint64_t num_edges;
+  uint32_t* edge_acc;               // [N][2] (hit, touch) bits of this pass, kept zero between passes
   uint64_t G;                       // L * soff[N] global samples
   uint64_t tile_base;               // first queue index of this job's tiles
   uint64_t num_tiles;
-  uint32_t L, K, S, C, Wm;          // links, inner/link, samples per tile, boxes, mask words
-  uint32_t off_edges, off_boxes;    // byte offsets inside a stage buffer
-  uint32_t off_in, off_out;         // byte offsets of the first inner / outer plane
+  uint32_t L, K, S, C;              // links, inner/link, samples per tile, boxes
+  uint32_t off_in, off_out;         // byte offsets of the first inner / outer plane in a stage
   uint32_t in_cap, out_cap;         // floats per plane slot in a stage
-  uint32_t max_edges;               // capacity of the per-tile edge table
   float margin;
 };
 
@@ -70,25 +84,36 @@ struct StageHdr {
   int32_t n_edges;     // local edges
   int32_t in_shift;    // first inner float inside the aligned copy
   int32_t out_shift;
-  int32_t valid;
-  int32_t pad0;
-  uint64_t e_first;    // global index of local edge 0
-  uint64_t g0;         // first global sample of the tile
+  uint32_t e_first;
+  int32_t end;         // 1: no more tiles for the warp that takes this slot
 };
-static_assert(sizeof(StageHdr) <= kStageHdrBytes, "stage header too large");
+static_assert(sizeof(StageHdr) == kStageHdrBytes, "stage header size");
 
-// Per local edge of a tile: {estart, n, ostart, cnt}
-//   estart  local sample index of the edge's first sample (may be < 0)
-//   n       configurations of the edge
-//   ostart  local interval index of the edge's first interval (may be < 0)
-//   cnt     samples of the edge inside this tile
+// Merge of one roadmap's pass results into its per-edge box sets.
+struct MergeJob {
+  uint32_t* red;          // [N][Wm]
+  uint32_t* touch;        // [N][Wm]
+  uint32_t* counts;       // [N] red count | touch count << 16
+  uint8_t* labels;        // [N]
+  uint32_t* edge_acc;     // [N][2]
+  uint64_t num_edges;
+  uint64_t edge_base;     // first global thread index of this job
+  uint32_t Wm, C;
+  uint32_t ids[kBoxesPerPass];  // box id of pass position p, ascending
+};
+
+template <int MAXJ>
+struct MergeParams {
+  MergeJob job[MAXJ];
+  uint32_t njobs;
+  uint64_t total_edges;
+};
 
 enum StatusCode : int {
   kStatusOk = 0,
   kStatusTimeoutFull = 1,
   kStatusTimeoutEmpty = 2,
   kStatusTimeoutBoxes = 3,
-  kStatusBadTile = 4,
 };
 
 // ---------------------------------------------------------------------------
@@ -134,15 +159,37 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait: gives up after `limit` polls (each poll may suspend the thread
-// for a short hardware-defined time).  Returns false on timeout.
+// try_wait with a suspend-time hint: the thread sleeps in hardware until the
+// phase completes or about `hint_ns` pass, instead of spinning.
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* bar, uint32_t parity,
+                                                    uint32_t hint_ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded wait: suspended polls until the phase completes or `limit_ns` of
+// wall time have passed (then false).
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
-                                                  uint32_t limit) {
-  for (uint32_t i = 0; i < limit; ++i) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if (i > 64) __nanosleep(64);
+                                                  uint64_t limit_ns) {
+  if (mbar_try_wait_sleep(bar, parity, 10000u)) return true;
+  const uint64_t t0 = global_ns();
+  for (;;) {
+    if (mbar_try_wait_sleep(bar, parity, 10000u)) return true;
+    if (global_ns() - t0 > limit_ns) return false;
   }
-  return false;
 }
 
 // Bulk copy global -> shared (this CTA), completion counted on `bar` in bytes.
@@ -154,10 +201,6 @@ __device__ __forceinline__ void bulk_g2s(void* dst_smem, const void* src_gmem, u
           "r"(smem_u32(dst_smem)),
       "l"(src_gmem), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
-}
-
-__device__ __forceinline__ void named_bar_sync(int id, int nthreads) {
-  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
 }  // namespace rgg

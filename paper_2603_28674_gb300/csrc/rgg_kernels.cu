@@ -3,12 +3,12 @@
 //   count_samples_kernel   a0: configurations per edge (Sec. 3.2)
 //   build_records_kernel   a0: FP64 kinematics -> FP32 inner/outer spheres
 //                          (Sec. 4.2 inner spheres; swept outer spheres)
-//   tile_edge_kernel       streaming tiles -> first edge of each tile
 //   box_update_kernel      a1: write moved boxes' poses in place (Sec. 4.3,
 //                          "Online updates")
 //   box_prep_kernel        a1: derived per-pass box records
-//   classify_kernel        a2..a6: persistent streaming classification
-//                          (Sec. 4.1 labelling rule, Algorithm 1 merge)
+//   classify_kernel        a2..a5: persistent streaming classification
+//                          (Sec. 4.1 labelling rule)
+//   merge_kernel           a6: per-edge box sets and labels (Algorithm 1)
 #include <cstdio>
 
 #include "rgg_device.cuh"
@@ -152,28 +152,6 @@ __global__ void __launch_bounds__(256) build_records_kernel(const __grid_constan
 }
 
 // ===========================================================================
-// streaming tiles: edge holding the first sample of each tile
-// ===========================================================================
-__global__ void tile_edge_kernel(const uint64_t* __restrict__ soff, uint64_t n_edges, uint32_t L,
-                                 uint32_t S, uint64_t n_tiles, uint32_t* __restrict__ out) {
-  uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-  if (t > n_tiles) return;
-  const uint64_t G = (uint64_t)L * soff[n_edges];
-  const uint64_t g = t * (uint64_t)S;
-  if (g >= G) {
-    out[t] = (uint32_t)n_edges;
-    return;
-  }
-  // largest e < N with L*soff[e] <= g
-  uint64_t lo = 0, hi = n_edges - 1;
-  while (lo < hi) {
-    uint64_t mid = (lo + hi + 1) >> 1;
-    if ((uint64_t)L * soff[mid] <= g) lo = mid; else hi = mid - 1;
-  }
-  out[t] = (uint32_t)lo;
-}
-
-// ===========================================================================
 // a1: obstacle update and per-pass box records
 // ===========================================================================
 __global__ void box_update_kernel(const __grid_constant__ BoxUpdateParams p) {
@@ -220,8 +198,19 @@ __global__ void box_prep_kernel(const __grid_constant__ BoxPrepParams p) {
 }
 
 // ===========================================================================
-// a2..a6: persistent streaming classification
+// a2..a5: persistent streaming classification
 // ===========================================================================
+// One CTA per SM.  Warp 0 is the producer: it walks this CTA's contiguous
+// range of tiles and, for each, bulk-copies the tile's edge table and its 4
+// inner and 4 outer record planes into the next slot of an NSTAGE-deep ring
+// of shared-memory stages (TMA bulk copies completing on the slot's `full`
+// mbarrier).  Every other warp is a consumer that takes whole tiles on its
+// own (no CTA-wide barriers): it grabs the next slot, tests the tile's outer
+// spheres against the pass's moved boxes (a3), its inner spheres against the
+// boxes their enclosing outer spheres touched (a4), releases the slot, and
+// ORs the tile's per-edge hit / touch bits into the global per-edge
+// accumulators (a5).  The merge kernel then updates the per-edge box sets
+// and labels (a6).
 __device__ __forceinline__ float box_dist2(float x, float y, float z, const float4* __restrict__ B) {
   const float4 a0 = B[1], a1 = B[2], a2 = B[3], h = B[4];
   const float p0 = fmaf(a0.x, x, fmaf(a0.y, y, fmaf(a0.z, z, -a0.w)));
@@ -243,34 +232,6 @@ __device__ __forceinline__ int search_le(const int* tab, int field, int n, int v
   return lo;
 }
 
-// Algorithm 1 merge for one edge, by one warp: replace the bits of this
-// pass's boxes in the edge's hit / touch sets, then label from the sets.
-__device__ __forceinline__ void merge_edge(const ClassifyJob& J, uint64_t e, uint32_t hit,
-                                           uint32_t tch, const float4* __restrict__ bx, int lane) {
-  bool any_r = false, any_t = false;
-  for (uint32_t w = lane; w < J.Wm; w += 32) {
-    uint32_t* pr = J.red + e * J.Wm + w;
-    uint32_t* pt = J.touch + e * J.Wm + w;
-    const uint32_t rw = *pr, tw = *pt;
-    uint32_t rn = rw, tn = tw;
-    for (uint32_t b = 0; b < J.C; ++b) {
-      const uint32_t id = __float_as_uint(bx[6 * b + 4].w);
-      if ((id >> 5) == w) {
-        const uint32_t bit = 1u << (id & 31);
-        rn = ((hit >> b) & 1u) ? (rn | bit) : (rn & ~bit);
-        tn = ((tch >> b) & 1u) ? (tn | bit) : (tn & ~bit);
-      }
-    }
-    if (rn != rw) *pr = rn;
-    if (tn != tw) *pt = tn;
-    any_r |= rn != 0;
-    any_t |= tn != 0;
-  }
-  any_r = __any_sync(0xffffffffu, any_r);
-  any_t = __any_sync(0xffffffffu, any_t);
-  if (lane == 0) J.labels[e] = any_r ? 2 : (any_t ? 1 : 0);
-}
-
 template <int MAXJ>
 __device__ __forceinline__ int find_job(const ClassifyParams<MAXJ>& P, uint64_t t) {
   int lo = 0, hi = (int)P.njobs - 1;
@@ -281,287 +242,415 @@ __device__ __forceinline__ int find_job(const ClassifyParams<MAXJ>& P, uint64_t 
   return lo;
 }
 
-constexpr uint32_t kWaitLimit = 1u << 25;
+constexpr uint64_t kWaitLimit = 4000000000ull;  // 4 s of wall time per wait
 
-template <int MAXJ, int NSTAGE, int STAGE_BYTES>
-__global__ void __launch_bounds__(1024, 1) classify_kernel(const __grid_constant__ ClassifyParams<MAXJ> P,
-                                                           uint32_t tw_cap, uint32_t acc_cap) {
+constexpr int kPairQueue = 64;   // (sample, box) pairs a warp compacts per round
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Work items: tile t of this CTA has ROUNDS items (rounds of 31 samples);
+// warps take items in order from a shared counter.  Round r of a tile covers
+// the samples q = 31r .. 31r+30 on lanes 1..31; lane 0 takes sample 31r-1,
+// whose following interval the round needs (for r = 0 that is the tile's
+// halo interval).  The warp that finishes a tile's last round flushes the
+// tile's per-edge bits and releases the stage.
+template <int MAXJ, int NSTAGE, int STAGE_BYTES, int ROUNDS>
+__global__ void __launch_bounds__(1024, 1) classify_kernel(const __grid_constant__ ClassifyParams<MAXJ> P) {
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char* stages = smem;
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + NSTAGE * STAGE_BYTES);
   uint64_t* empty = full + NSTAGE;
-  volatile int* s_abort = reinterpret_cast<volatile int*>(empty + NSTAGE);
-  uint32_t* tw = reinterpret_cast<uint32_t*>(empty + NSTAGE + 2);
-  uint32_t* acc_hit = tw + tw_cap;
-  uint32_t* acc_touch = acc_hit + acc_cap;
+  uint64_t* boxbar = empty + NSTAGE;
+  uint32_t* s_item = reinterpret_cast<uint32_t*>(boxbar + 1);          // next work item
+  uint32_t* s_cnt = s_item + 2;                                        // rounds done per stage
+  TileDesc* s_desc = reinterpret_cast<TileDesc*>(s_cnt + ((NSTAGE + 3) & ~3));  // producer's batch
+  int* s_djob = reinterpret_cast<int*>(s_desc + 32);
+  float4* s_boxes = reinterpret_cast<float4*>(s_djob + 32);            // kBoxSlots x 32 x 6
+  uint32_t* queues = reinterpret_cast<uint32_t*>(s_boxes + kBoxSlots * kBoxesPerPass * 6);
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
   const int ncw = (blockDim.x >> 5) - 1;
-  const int nct = ncw * 32;
 
+  const uint64_t per_cta = (P.total_tiles + gridDim.x - 1) / gridDim.x;
+  const uint64_t t_begin = min(P.total_tiles, (uint64_t)blockIdx.x * per_cta);
+  const uint64_t t_end = min(P.total_tiles, t_begin + per_cta);
+  // the first kBoxSlots jobs of this CTA's range read their box records from
+  // shared memory, staged once by a bulk copy
+  const int job_lo = t_begin < t_end ? find_job(P, t_begin) : 0;
+  const int job_hi = t_begin < t_end ? find_job(P, t_end - 1) : -1;
+
+  // zero the stages (their accumulators must start at zero) and counters
+  for (uint32_t i = threadIdx.x; i < NSTAGE * STAGE_BYTES / 16; i += blockDim.x)
+    reinterpret_cast<uint4*>(stages)[i] = make_uint4(0, 0, 0, 0);
+  for (uint32_t i = threadIdx.x; i < NSTAGE; i += blockDim.x) s_cnt[i] = 0;
+  fence_proxy_async_smem();
   if (threadIdx.x == 0) {
     for (int s = 0; s < NSTAGE; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    *s_abort = 0;
+    mbar_init(boxbar, 1);
+    *s_item = 0;
     fence_mbar_init();
-  }
-  for (uint32_t i = threadIdx.x; i < acc_cap; i += blockDim.x) {
-    acc_hit[i] = 0;
-    acc_touch[i] = 0;
+    uint32_t bytes = 0;
+    for (int jb = job_lo; jb <= job_hi && jb - job_lo < kBoxSlots; ++jb)
+      bytes += P.job[jb].C * (uint32_t)(kBoxRecFloats * 4);
+    mbar_arrive_expect_tx(boxbar, bytes);
+    for (int jb = job_lo; jb <= job_hi && jb - job_lo < kBoxSlots; ++jb)
+      if (P.job[jb].C)
+        bulk_g2s(s_boxes + (jb - job_lo) * kBoxesPerPass * 6, P.job[jb].boxes,
+                 P.job[jb].C * (uint32_t)(kBoxRecFloats * 4), boxbar);
   }
   __syncthreads();
 
   if (warp == 0) {
     // ------------------------------------------------------------ producer
-    uint32_t it = 0;
-    for (uint64_t t = blockIdx.x; t < P.total_tiles; t += gridDim.x, ++it) {
-      const int stage = it % NSTAGE;
-      const uint32_t round = it / NSTAGE;
-      int ok = 1;
-      if (lane == 0) ok = mbar_wait_bounded(&empty[stage], (round & 1) ^ 1, kWaitLimit);
-      ok = __shfl_sync(0xffffffffu, ok, 0);
-      if (!ok) {
-        if (lane == 0) {
-          atomicCAS(P.status, 0, (int)kStatusTimeoutEmpty);
-          *s_abort = 1;
-        }
-        break;
-      }
-      if (*s_abort) break;
-      const int jb = find_job(P, t);
-      const ClassifyJob& J = P.job[jb];
-      const uint64_t lt = t - J.tile_base;
-      const uint64_t L = J.L, K = J.K;
-      const uint64_t g0 = lt * J.S;
-      const uint64_t g1 = min(g0 + J.S, J.G);
-      const uint64_t ef = J.tile_edge[lt];
-      uint64_t el = J.tile_edge[lt + 1];
-      if (el >= J.num_edges || L * J.soff[el] >= g1) el = el - 1;  // edge of sample g1-1
-      const uint64_t so_f = J.soff[ef], n_f = J.soff[ef + 1] - so_f;
-      const uint64_t so_l = J.soff[el], n_l = J.soff[el + 1] - so_l;
-      // first interval: the one before the first sample (halo) if the tile starts
-      // inside a link's run of configurations, else the run's first interval
-      const uint64_t rf = g0 - L * so_f, i_f = rf / n_f, k_f = rf - i_f * n_f;
-      const uint64_t o0 = L * (so_f - ef) + i_f * (n_f - 1) + (k_f > 0 ? k_f - 1 : 0);
-      // last interval: the one after the last sample, or the one before it if
-      // the last sample ends its run
-      const uint64_t rl = g1 - 1 - L * so_l, i_l = rl / n_l, k_l = rl - i_l * n_l;
-      const uint64_t o1 = L * (so_l - el) + i_l * (n_l - 1) + min(k_l, n_l - 2) + 1;
-      const int n_edges = (int)(el - ef + 1);
-      unsigned char* sb = stages + (size_t)stage * STAGE_BYTES;
-      int4* etab = reinterpret_cast<int4*>(sb + J.off_edges);
-      const bool fits = n_edges <= (int)J.max_edges && (o1 - o0) <= (uint64_t)tw_cap &&
-                        n_edges <= (int)acc_cap;
-      if (fits) {
-        for (int x = lane; x < n_edges; x += 32) {
-          const uint64_t e = ef + x;
-          const uint64_t so = J.soff[e], sn = J.soff[e + 1];
-          const int64_t estart = (int64_t)(L * so) - (int64_t)g0;
-          const int64_t ostart = (int64_t)(L * (so - e)) - (int64_t)o0;
-          const uint64_t lo = max(g0, L * so), hi = min(g1, L * sn);
-          etab[x] = make_int4((int)estart, (int)(sn - so), (int)ostart, (int)(hi - lo));
-        }
-      }
-      const uint64_t a0 = (K * g0) & ~3ull, a1 = (K * g1 + 3) & ~3ull;
-      const uint64_t b0 = o0 & ~3ull, b1 = (o1 + 3) & ~3ull;
-      if (lane == 0) {
-        StageHdr* h = reinterpret_cast<StageHdr*>(sb);
-        h->job = jb;
-        h->n_samp = (int)(g1 - g0);
-        h->n_out = (int)(o1 - o0);
-        h->n_edges = n_edges;
-        h->in_shift = (int)(K * g0 - a0);
-        h->out_shift = (int)(o0 - b0);
-        h->valid = fits ? 1 : 0;
-        h->e_first = ef;
-        h->g0 = g0;
+    uint32_t slot = 0;
+    bool ok = true;
+    for (uint64_t tb = t_begin; tb < t_end && ok; tb += 32) {
+      const uint64_t t = tb + lane;
+      __syncwarp();
+      if (t < t_end) {
+        const int jb = find_job(P, t);
+        const ClassifyJob& J = P.job[jb];
+        s_desc[lane] = J.tiles[t - J.tile_base];
+        s_djob[lane] = jb;
       }
       __syncwarp();
-      if (lane == 0) {
-        const uint32_t in_bytes = fits ? (uint32_t)((a1 - a0) * 4) : 0;
-        const uint32_t out_bytes = fits ? (uint32_t)((b1 - b0) * 4) : 0;
-        const uint32_t box_bytes = fits ? J.C * (uint32_t)(kBoxRecFloats * 4) : 0;
-        mbar_arrive_expect_tx(&full[stage], 4 * in_bytes + 4 * out_bytes + box_bytes);
-        if (fits) {
-          for (int pl = 0; pl < 4; ++pl) {
-            bulk_g2s(sb + J.off_in + (size_t)pl * J.in_cap * 4, J.inner + pl * J.in_stride + a0,
-                     in_bytes, &full[stage]);
-            bulk_g2s(sb + J.off_out + (size_t)pl * J.out_cap * 4, J.outer + pl * J.out_stride + b0,
-                     out_bytes, &full[stage]);
-          }
-          if (box_bytes) bulk_g2s(sb + J.off_boxes, J.boxes, box_bytes, &full[stage]);
+      const int nb = (int)(t_end - tb < 32 ? t_end - tb : 32);
+      for (int i = 0; i < nb; ++i, ++slot) {
+        const int stage = slot % NSTAGE;
+        const uint32_t round = slot / NSTAGE;
+        int good = 1;
+        if (lane == 0) good = mbar_wait_bounded(&empty[stage], (round & 1) ^ 1, kWaitLimit);
+        good = __shfl_sync(0xffffffffu, good, 0);
+        if (!good) {
+          if (lane == 0) atomicCAS(P.status, 0, (int)kStatusTimeoutEmpty);
+          ok = false;
+          break;
+        }
+        // every lane derives the tile's copies; lane 0 writes the header and
+        // arms the barrier, then lanes 0..8 issue the 9 bulk copies together
+        const int jb = s_djob[i];
+        const ClassifyJob& J = P.job[jb];
+        const TileDesc d = s_desc[i];
+        const uint64_t lt = tb + i - J.tile_base;
+        const uint64_t K = J.K;
+        const uint64_t g0 = lt * J.S;
+        const uint64_t g1 = min(g0 + J.S, J.G);
+        const uint64_t a0 = (K * g0) & ~3ull, a1 = (K * g1 + 3) & ~3ull;
+        const uint64_t o0 = d.packed & ((1ull << 40) - 1);
+        const uint32_t n_out = (uint32_t)((d.packed >> 40) & 0xffff);
+        const uint32_t n_edges = (uint32_t)(d.packed >> 56);
+        const uint64_t b0 = o0 & ~3ull, b1 = (o0 + n_out + 3) & ~3ull;
+        unsigned char* sb = stages + (size_t)stage * STAGE_BYTES;
+        const uint32_t in_bytes = (uint32_t)((a1 - a0) * 4);
+        const uint32_t out_bytes = (uint32_t)((b1 - b0) * 4);
+        const uint32_t et_bytes = n_edges * 16;
+        if (lane == 0) {
+          StageHdr* h = reinterpret_cast<StageHdr*>(sb);
+          h->job = jb;
+          h->n_samp = (int)(g1 - g0);
+          h->n_out = (int)n_out;
+          h->n_edges = (int)n_edges;
+          h->in_shift = (int)(K * g0 - a0);
+          h->out_shift = (int)(o0 - b0);
+          h->e_first = d.e_first;
+          h->end = 0;
+          mbar_arrive_expect_tx(&full[stage], et_bytes + 4 * in_bytes + 4 * out_bytes);
+        }
+        __syncwarp();
+        if (lane == 0) {
+          bulk_g2s(sb + kStageEtabOff, J.etab + d.etab, et_bytes, &full[stage]);
+        } else if (lane <= 4) {
+          const int pl = lane - 1;
+          bulk_g2s(sb + J.off_in + (size_t)pl * J.in_cap * 4, J.inner + pl * J.in_stride + a0,
+                   in_bytes, &full[stage]);
+        } else if (lane <= 8) {
+          const int pl = lane - 5;
+          bulk_g2s(sb + J.off_out + (size_t)pl * J.out_cap * 4, J.outer + pl * J.out_stride + b0,
+                   out_bytes, &full[stage]);
         }
       }
+      ok = __shfl_sync(0xffffffffu, ok, 0);
     }
-    // On abort, wait (bounded) for copies this CTA may still have in flight.
-    if (*s_abort && lane == 0) {
-      const uint32_t first = it > (uint32_t)NSTAGE ? it - NSTAGE : 0;
-      for (uint32_t k = first; k < it; ++k)
-        mbar_wait_bounded(&full[k % NSTAGE], (k / NSTAGE) & 1, 1u << 16);
+    // end markers: ROUNDS items each, enough for every consumer warp to take one
+    if (lane == 0 && ok) {
+      const int n_end = (ncw + ROUNDS - 1) / ROUNDS;
+      for (int i = 0; i < n_end; ++i, ++slot) {
+        const int stage = slot % NSTAGE;
+        const uint32_t round = slot / NSTAGE;
+        if (!mbar_wait_bounded(&empty[stage], (round & 1) ^ 1, kWaitLimit)) {
+          atomicCAS(P.status, 0, (int)kStatusTimeoutEmpty);
+          break;
+        }
+        StageHdr* h = reinterpret_cast<StageHdr*>(stages + (size_t)stage * STAGE_BYTES);
+        h->end = 1;
+        mbar_arrive(&full[stage]);
+      }
+    }
+    // Before leaving, make sure none of this CTA's bulk copies is still in
+    // flight (bounded; immediate when every issued slot has landed).
+    if (lane == 0) {
+      const uint32_t first = slot > (uint32_t)NSTAGE ? slot - NSTAGE : 0;
+      for (uint32_t k = first; k < slot; ++k)
+        mbar_wait_bounded(&full[k % NSTAGE], (k / NSTAGE) & 1, 500000000ull);
     }
     return;
   }
 
   // -------------------------------------------------------------- consumers
-  const int cw = warp - 1;
-  const int ctid = threadIdx.x - 32;
-  uint32_t it = 0;
-  for (uint64_t t = blockIdx.x; t < P.total_tiles; t += gridDim.x, ++it) {
-    const int stage = it % NSTAGE;
-    const uint32_t round = it / NSTAGE;
-    // One thread takes the bounded wait and the abort decision, so that all
-    // consumer threads leave the loop together (the named barriers below
-    // need every consumer thread).
-    if (ctid == 0) {
-      int stop = *s_abort;
-      if (!stop && !mbar_wait_bounded(&full[stage], round & 1, kWaitLimit)) {
-        atomicCAS(P.status, 0, (int)kStatusTimeoutFull);
-        *s_abort = 1;
-        stop = 1;
-      }
-      s_abort[1] = stop;
+  uint32_t* queue = queues + (size_t)(warp - 1) * kPairQueue;
+  {
+    int ok = 1;
+    if (lane == 0) ok = mbar_wait_bounded(boxbar, 0, kWaitLimit);
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    if (!ok) {
+      if (lane == 0) atomicCAS(P.status, 0, (int)kStatusTimeoutBoxes);
+      return;
     }
-    named_bar_sync(1, nct);
-    if (s_abort[1]) break;
-    // the phase is complete: this returns at once and orders the stage's
-    // bulk-copied data before this thread's reads
-    mbar_wait_bounded(&full[stage], round & 1, kWaitLimit);
+    mbar_wait_bounded(boxbar, 0, kWaitLimit);
+  }
+  for (;;) {
+    uint32_t item = 0;
+    if (lane == 0) item = atomicAdd(s_item, 1u);
+    item = __shfl_sync(0xffffffffu, item, 0);
+    const uint32_t slot = item / ROUNDS;
+    const int rnd = (int)(item - slot * ROUNDS);
+    const int stage = slot % NSTAGE;
+    const uint32_t parity = (slot / NSTAGE) & 1;
+    int ok = 1;
+    if (lane == 0) ok = mbar_wait_bounded(&full[stage], parity, kWaitLimit);
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    if (!ok) {
+      if (lane == 0) atomicCAS(P.status, 0, (int)kStatusTimeoutFull);
+      break;
+    }
+    // completed phase: returns at once and orders the stage's data for this lane
+    mbar_wait_bounded(&full[stage], parity, kWaitLimit);
     unsigned char* sb = stages + (size_t)stage * STAGE_BYTES;
-    const StageHdr* hdr = reinterpret_cast<const StageHdr*>(sb);
-    const ClassifyJob& J = P.job[hdr->job];
-    if (!hdr->valid) {
-      if (ctid == 0) atomicCAS(P.status, 0, (int)kStatusBadTile);
-      named_bar_sync(1, nct);
-      if (ctid == 0) mbar_arrive(&empty[stage]);
-      continue;
-    }
-    const int n_samp = hdr->n_samp, n_out = hdr->n_out, n_edges = hdr->n_edges;
-    const int K = (int)J.K;
-    const int L = (int)J.L;
-    const int C = (int)J.C;
-    const float margin = J.margin;
-    const float* ix = reinterpret_cast<const float*>(sb + J.off_in) + hdr->in_shift;
-    const float* iy = ix + J.in_cap;
-    const float* iz = iy + J.in_cap;
-    const float* ir = iz + J.in_cap;
-    const float* ox = reinterpret_cast<const float*>(sb + J.off_out) + hdr->out_shift;
-    const float* oy = ox + J.out_cap;
-    const float* oz = oy + J.out_cap;
-    const float* orad = oz + J.out_cap;
-    const float4* bx = reinterpret_cast<const float4*>(sb + J.off_boxes);
-    const int* etab = reinterpret_cast<const int*>(sb + J.off_edges);
+    const StageHdr hdr = *reinterpret_cast<const StageHdr*>(sb);
+    if (hdr.end) break;
+    const ClassifyJob& J = P.job[hdr.job];
+    const int n_samp = hdr.n_samp, n_edges = hdr.n_edges;
+    const int* etab = reinterpret_cast<const int*>(sb + kStageEtabOff);
+    // per-stage accumulators live at a fixed place whatever the job, so a
+    // stage reused by another roadmap's tile finds them zeroed
+    uint32_t* acc_hit = reinterpret_cast<uint32_t*>(sb + kStageAccOff);
+    uint32_t* acc_touch = acc_hit + kAccMax;
+    const int base = 31 * rnd;
 
-    // ---- a3: outer spheres vs moved boxes, warp-culled
-    for (int base = cw * 32; base < n_out; base += nct) {
-      const int o = base + lane;
-      const bool act = o < n_out;
+    if (base < n_samp) {
+      const int K = (int)J.K;
+      const int C = (int)J.C;
+      const float margin = J.margin;
+      const float inv_k = 1.0f / (float)K;
+      const float* ix = reinterpret_cast<const float*>(sb + J.off_in) + hdr.in_shift;
+      const float* iy = ix + J.in_cap;
+      const float* iz = iy + J.in_cap;
+      const float* ir = iz + J.in_cap;
+      const float* ox = reinterpret_cast<const float*>(sb + J.off_out) + hdr.out_shift;
+      const float* oy = ox + J.out_cap;
+      const float* oz = oy + J.out_cap;
+      const float* orad = oz + J.out_cap;
+      const float4* bx = MAXJ == 1 ? s_boxes
+                         : (hdr.job - job_lo < kBoxSlots
+                                ? s_boxes + (hdr.job - job_lo) * kBoxesPerPass * 6
+                                : reinterpret_cast<const float4*>(J.boxes));
+      const int q = base - 1 + lane;
+      const int q_end = min(base + 31, n_samp);
+      // locate q: its edge j, the position k in its link's run, and the
+      // local index o of the interval that follows it
+      int j = 0, n = 2, k = -1, o = 0;
+      bool valid = false;
+      if (q < q_end) {
+        j = q < 0 ? 0 : search_le(etab, 0, n_edges, q);
+        const int estart = etab[4 * j];
+        n = etab[4 * j + 1];
+        const int rr = q - estart;
+        valid = rr >= 0;
+        if (valid) {
+          // rr / n from the stored reciprocal, then an exact correction
+          int li = __float2int_rz(((float)rr + 0.5f) * __int_as_float(etab[4 * j + 3]));
+          k = rr - li * n;
+          if (k < 0) {
+            --li;
+            k += n;
+          } else if (k >= n) {
+            ++li;
+            k -= n;
+          }
+          o = etab[4 * j + 2] + li * (n - 1) + k;
+        }
+      }
+      // ---- a3: the outer sphere of the interval after q, against the moved
+      // boxes that survive a warp bounding-sphere cull
+      const bool has_next = valid && k < n - 1;
       float x = 0.f, y = 0.f, z = 0.f, r = 0.f;
-      if (act) {
+      if (has_next) {
         x = ox[o];
         y = oy[o];
         z = oz[o];
         r = orad[o];
       }
-      const int nact = min(32, n_out - base);
-      const int mid = nact >> 1;
-      const float mx = __shfl_sync(0xffffffffu, x, mid);
-      const float my = __shfl_sync(0xffffffffu, y, mid);
-      const float mz = __shfl_sync(0xffffffffu, z, mid);
-      const float dx = x - mx, dy = y - my, dz = z - mz;
-      const float reach = act ? sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) + r : 0.0f;
-      const float rw = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(reach)));
-      bool cb = false;
-      if (lane < C) {
-        const float4 b0 = bx[6 * lane];
-        const float ex = b0.x - mx, ey = b0.y - my, ez = b0.z - mz;
-        const float thr = (rw + b0.w + margin) * (1.0f + 1e-6f) + 1e-5f;
-        cb = fmaf(ex, ex, fmaf(ey, ey, ez * ez)) <= thr * thr;
-      }
-      uint32_t cand = __ballot_sync(0xffffffffu, cb);
-      const float rt = r + margin;
-      const float rt2 = rt * rt;
+      const uint32_t act = __ballot_sync(0xffffffffu, has_next);
       uint32_t bits = 0;
-      while (cand) {
-        const int b = __ffs(cand) - 1;
-        cand &= cand - 1;
-        if (box_dist2(x, y, z, bx + 6 * b) <= rt2) bits |= 1u << b;
-      }
       if (act) {
-        tw[o] = bits;
-        if (bits) {
-          const int j = search_le(etab, 2, n_edges, o);
-          atomicOr(&acc_touch[j], bits);
+        // any active lane's sphere can centre the bounding sphere
+        const int mid = (act & 0xffff0000u) ? __ffs(act & 0xffff0000u) - 1 : 31 - __clz(act);
+        const float mx = __shfl_sync(0xffffffffu, x, mid);
+        const float my = __shfl_sync(0xffffffffu, y, mid);
+        const float mz = __shfl_sync(0xffffffffu, z, mid);
+        const float dx = x - mx, dy = y - my, dz = z - mz;
+        const float reach = has_next ? sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) + r : 0.0f;
+        const float rw = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(reach)));
+        bool cb = false;
+        if (lane < C) {
+          const float4 b0 = bx[6 * lane];
+          const float ex = b0.x - mx, ey = b0.y - my, ez = b0.z - mz;
+          const float thr = (rw + b0.w + margin) * (1.0f + 1e-6f) + 1e-5f;
+          cb = fmaf(ex, ex, fmaf(ey, ey, ez * ez)) <= thr * thr;
         }
+        uint32_t cand = __ballot_sync(0xffffffffu, cb);
+        const float rt = r + margin;
+        const float rt2 = rt * rt;
+        while (cand) {
+          const int b = __ffs(cand) - 1;
+          cand &= cand - 1;
+          if (box_dist2(x, y, z, bx + 6 * b) <= rt2) bits |= 1u << b;
+        }
+        if (!has_next) bits = 0;
+        if (bits) atomicOr(&acc_touch[j], bits);
       }
-    }
-    named_bar_sync(1, nct);
-
-    // ---- a4: inner spheres, only against boxes their outer spheres touched
-    for (int q = ctid; q < n_samp; q += nct) {
-      const int j = search_le(etab, 0, n_edges, q);
-      const int estart = etab[4 * j], n = etab[4 * j + 1], ostart = etab[4 * j + 2];
-      const int rr = q - estart;
-      const int li = rr / n;
-      const int k = rr - li * n;
-      const int ib = ostart + li * (n - 1);
-      uint32_t need = (k < n - 1 ? tw[ib + k] : 0u) | (k > 0 ? tw[ib + k - 1] : 0u);
-      need &= ~*reinterpret_cast<volatile uint32_t*>(&acc_hit[j]);
-      uint32_t hits = 0;
-      while (need) {
-        const int b = __ffs(need) - 1;
-        need &= need - 1;
-        const float4* B = bx + 6 * b;
-        for (int s = K * q, se = K * q + K; s < se; ++s) {
+      // ---- a4: inner spheres of q against the boxes touched by the
+      // intervals before and after it
+      const uint32_t prev = __shfl_up_sync(0xffffffffu, bits, 1);
+      uint32_t need = 0;
+      if (valid && q >= base) {
+        need = (k < n - 1 ? bits : 0u) | (k > 0 ? prev : 0u);
+        if (need) need &= ~*reinterpret_cast<volatile uint32_t*>(&acc_hit[j]);
+      }
+      const int cnt = __popc(need);
+      int incl = cnt;
+      for (int d = 1; d < 32; d <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += v;
+      }
+      const int total = __shfl_sync(0xffffffffu, incl, 31);
+      if (total > 0 && total <= kPairQueue) {
+        // compact the (sample, box) pairs, then test (pair, sphere) items on all lanes
+        int pos = incl - cnt;
+        for (uint32_t m = need; m; m &= m - 1)
+          queue[pos++] = ((uint32_t)q << 13) | ((uint32_t)j << 5) | (uint32_t)(__ffs(m) - 1);
+        __syncwarp();
+        for (int it = lane; it < total * K; it += 32) {
+          const int pi = __float2int_rz(((float)it + 0.5f) * inv_k);
+          const int jj = it - pi * K;
+          const uint32_t e = queue[pi];
+          const int b = (int)(e & 31u), jl = (int)((e >> 5) & 255u), qq = (int)(e >> 13);
+          const int s = K * qq + jj;
           const float rin = ir[s] - margin;
-          if (rin > 0.0f && box_dist2(ix[s], iy[s], iz[s], B) <= rin * rin) {
-            hits |= 1u << b;
-            break;
+          if (rin > 0.0f && box_dist2(ix[s], iy[s], iz[s], bx + 6 * b) <= rin * rin)
+            atomicOr(&acc_hit[jl], 1u << b);
+        }
+      } else if (total > kPairQueue) {
+        // many pairs in one round: each lane tests its own
+        uint32_t hits = 0;
+        for (uint32_t m = need; m; m &= m - 1) {
+          const int b = __ffs(m) - 1;
+          for (int s = K * q, se = K * q + K; s < se; ++s) {
+            const float rin = ir[s] - margin;
+            if (rin > 0.0f && box_dist2(ix[s], iy[s], iz[s], bx + 6 * b) <= rin * rin) {
+              hits |= 1u << b;
+              break;
+            }
           }
         }
+        if (hits) atomicOr(&acc_hit[j], hits);
       }
-      if (hits) atomicOr(&acc_hit[j], hits);
     }
-    named_bar_sync(1, nct);
-
-    // ---- a5/a6: per-edge reduction and merge
-    for (int jl = cw; jl < n_edges; jl += ncw) {
-      const int estart = etab[4 * jl], n = etab[4 * jl + 1], cnt = etab[4 * jl + 3];
-      const uint64_t e = hdr->e_first + jl;
-      uint32_t h = acc_hit[jl], tc = acc_touch[jl];
-      const bool complete = estart >= 0 && estart + L * n <= n_samp;
-      bool do_merge = true;
-      if (!complete) {
-        int last = 0;
-        if (lane == 0) {
-          if (h) atomicOr(&J.edge_acc[2 * e], h);
-          if (tc) atomicOr(&J.edge_acc[2 * e + 1], tc);
-          __threadfence();
-          const uint32_t old = atomicAdd(&J.edge_done[e], (uint32_t)cnt);
-          last = (old + (uint32_t)cnt == (uint32_t)(L * n));
-          if (last) {
-            __threadfence();
-            h = atomicExch(&J.edge_acc[2 * e], 0u);
-            tc = atomicExch(&J.edge_acc[2 * e + 1], 0u);
-            J.edge_done[e] = 0;
-          }
-        }
-        last = __shfl_sync(0xffffffffu, last, 0);
-        h = __shfl_sync(0xffffffffu, h, 0);
-        tc = __shfl_sync(0xffffffffu, tc, 0);
-        do_merge = last != 0;
-      }
-      if (do_merge) merge_edge(J, e, h, tc, bx, lane);
-      if (lane == 0) {
+    // ---- round done; the tile's last round flushes and releases the stage
+    __syncwarp();
+    uint32_t done = 0;
+    if (lane == 0) {
+      __threadfence_block();
+      done = atomicAdd(&s_cnt[stage], 1u);
+    }
+    done = __shfl_sync(0xffffffffu, done, 0);
+    if (done == ROUNDS - 1) {
+      __threadfence_block();
+      // ---- a5: the tile's per-edge bits into the global accumulators
+      for (int jl = lane; jl < n_edges; jl += 32) {
+        const uint32_t h = *reinterpret_cast<volatile uint32_t*>(&acc_hit[jl]);
+        const uint32_t t = *reinterpret_cast<volatile uint32_t*>(&acc_touch[jl]);
+        const uint64_t e = (uint64_t)hdr.e_first + jl;
+        if (h) atomicOr(&J.edge_acc[2 * e], h);
+        if (t) atomicOr(&J.edge_acc[2 * e + 1], t);
         acc_hit[jl] = 0;
         acc_touch[jl] = 0;
       }
+      if (lane == 0) s_cnt[stage] = 0;
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[stage]);
     }
-    named_bar_sync(1, nct);
-    if (ctid == 0) mbar_arrive(&empty[stage]);
   }
+}
+
+// ===========================================================================
+// a6: merge the pass's bits into the per-edge box sets (Algorithm 1's
+// intersection lists) and relabel
+// ===========================================================================
+// One thread per edge.  The pass's box ids are ascending, so boxes sharing a
+// 32-bit mask word are consecutive and each touched word is read and written
+// once.  Per-edge counts of hitting and touching boxes give the label
+// without reading the untouched words.
+template <int MAXJ>
+__global__ void __launch_bounds__(256) merge_kernel(const __grid_constant__ MergeParams<MAXJ> P) {
+  const uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (g >= P.total_edges) return;
+  int lo = 0, hi = (int)P.njobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (P.job[mid].edge_base <= g) lo = mid; else hi = mid - 1;
+  }
+  const MergeJob& J = P.job[lo];
+  const uint64_t e = g - J.edge_base;
+  uint2* accp = reinterpret_cast<uint2*>(J.edge_acc) + e;
+  const uint2 acc = *accp;
+  if (acc.x | acc.y) *accp = make_uint2(0u, 0u);
+  uint32_t cnt = J.counts[e];
+  int rc = (int)(cnt & 0xffffu), tc = (int)(cnt >> 16);
+  uint32_t* red = J.red + e * J.Wm;
+  uint32_t* tch = J.touch + e * J.Wm;
+  uint32_t cur = 0xffffffffu, r_old = 0, t_old = 0, r_new = 0, t_new = 0;
+  for (uint32_t p = 0; p <= J.C; ++p) {
+    const uint32_t w = p < J.C ? (J.ids[p] >> 5) : 0xfffffffeu;
+    if (w != cur) {
+      if (cur != 0xffffffffu) {
+        if (r_new != r_old) {
+          red[cur] = r_new;
+          rc += __popc(r_new) - __popc(r_old);
+        }
+        if (t_new != t_old) {
+          tch[cur] = t_new;
+          tc += __popc(t_new) - __popc(t_old);
+        }
+      }
+      if (p == J.C) break;
+      cur = w;
+      r_old = r_new = red[w];
+      t_old = t_new = tch[w];
+    }
+    const uint32_t bit = 1u << (J.ids[p] & 31);
+    r_new = ((acc.x >> p) & 1u) ? (r_new | bit) : (r_new & ~bit);
+    t_new = ((acc.y >> p) & 1u) ? (t_new | bit) : (t_new & ~bit);
+  }
+  const uint32_t ncnt = (uint32_t)rc | ((uint32_t)tc << 16);
+  if (ncnt != cnt) J.counts[e] = ncnt;
+  J.labels[e] = rc > 0 ? 2 : (tc > 0 ? 1 : 0);
 }
 
 // ===========================================================================
@@ -585,14 +674,6 @@ cudaError_t launch_build_records(const BuildParams& p, int num_sms, cudaStream_t
   return cudaGetLastError();
 }
 
-cudaError_t launch_tile_edge(const uint64_t* soff, uint64_t n_edges, uint32_t L, uint32_t S,
-                             uint64_t n_tiles, uint32_t* out, cudaStream_t s) {
-  const uint32_t blk = 256;
-  const uint64_t grid = (n_tiles + 1 + blk - 1) / blk;
-  tile_edge_kernel<<<(unsigned)grid, blk, 0, s>>>(soff, n_edges, L, S, n_tiles, out);
-  return cudaGetLastError();
-}
-
 cudaError_t launch_box_update(const BoxUpdateParams& p, cudaStream_t s) {
   if (p.n == 0) return cudaSuccess;
   box_update_kernel<<<(p.n + 127) / 128, 128, 0, s>>>(p);
@@ -605,20 +686,45 @@ cudaError_t launch_box_prep(const BoxPrepParams& p, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template <int MAXJ>
-static cudaError_t launch_classify_t(const ClassifyParams<MAXJ>& p, const ClassifyLaunch& lc,
+template <int NSTAGE, int STAGE_BYTES>
+static size_t smem_bytes_t(uint32_t consumer_warps) {
+  return (size_t)NSTAGE * STAGE_BYTES + (2 * NSTAGE + 1) * sizeof(uint64_t) + 8 +
+         4 * (size_t)((NSTAGE + 3) & ~3) + 32 * sizeof(TileDesc) + 32 * sizeof(int) +
+         (size_t)kBoxSlots * kBoxesPerPass * kBoxRecFloats * sizeof(float) +
+         (size_t)consumer_warps * 4 * kPairQueue;
+}
+
+size_t classify_smem_bytes(int variant, uint32_t consumer_warps) {
+  switch (variant) {
+#define RGG_VARIANT(id, ns, sb, rd) \
+  case id: return smem_bytes_t<ns, sb>(consumer_warps);
+    RGG_VARIANTS(RGG_VARIANT)
+#undef RGG_VARIANT
+    default: return 0;
+  }
+}
+
+template <int MAXJ, int NSTAGE, int STAGE_BYTES, int ROUNDS>
+static cudaError_t launch_classify_v(const ClassifyParams<MAXJ>& p, const ClassifyLaunch& lc,
                                      cudaStream_t s) {
-  auto kern = classify_kernel<MAXJ, kNumStages, kStageBytes>;
-  const size_t smem = classify_smem_bytes(lc.tw_cap, lc.acc_cap);
+  auto kern = classify_kernel<MAXJ, NSTAGE, STAGE_BYTES, ROUNDS>;
+  const size_t smem = smem_bytes_t<NSTAGE, STAGE_BYTES>(lc.consumer_warps);
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
-  kern<<<lc.grid, 32 * (1 + lc.consumer_warps), smem, s>>>(p, lc.tw_cap, lc.acc_cap);
+  kern<<<lc.grid, 32 * (1 + lc.consumer_warps), smem, s>>>(p);
   return cudaGetLastError();
 }
 
-size_t classify_smem_bytes(uint32_t tw_cap, uint32_t acc_cap) {
-  return (size_t)kNumStages * kStageBytes + 2 * kNumStages * sizeof(uint64_t) + 16 +
-         4 * (size_t)tw_cap + 8 * (size_t)acc_cap;
+template <int MAXJ>
+static cudaError_t launch_classify_t(const ClassifyParams<MAXJ>& p, const ClassifyLaunch& lc,
+                                     cudaStream_t s) {
+  switch (lc.variant) {
+#define RGG_VARIANT(id, ns, sb, rd) \
+  case id: return launch_classify_v<MAXJ, ns, sb, rd>(p, lc, s);
+    RGG_VARIANTS(RGG_VARIANT)
+#undef RGG_VARIANT
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t launch_classify_single(const ClassifyParams<1>& p, const ClassifyLaunch& lc,
@@ -629,6 +735,22 @@ cudaError_t launch_classify_single(const ClassifyParams<1>& p, const ClassifyLau
 cudaError_t launch_classify_batched(const ClassifyParams<kMaxJobs>& p, const ClassifyLaunch& lc,
                                     cudaStream_t s) {
   return launch_classify_t<kMaxJobs>(p, lc, s);
+}
+
+template <int MAXJ>
+static cudaError_t launch_merge_t(const MergeParams<MAXJ>& p, cudaStream_t s) {
+  if (p.total_edges == 0) return cudaSuccess;
+  const uint32_t blk = 256;
+  merge_kernel<MAXJ><<<(unsigned)((p.total_edges + blk - 1) / blk), blk, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_merge_single(const MergeParams<1>& p, cudaStream_t s) {
+  return launch_merge_t<1>(p, s);
+}
+
+cudaError_t launch_merge_batched(const MergeParams<kMaxJobs>& p, cudaStream_t s) {
+  return launch_merge_t<kMaxJobs>(p, s);
 }
 
 }  // namespace rgg

@@ -9,8 +9,32 @@
 
 namespace rgg {
 
-constexpr int kNumStages = 3;          // smem ring depth of the streaming pipeline
-constexpr int kStageBytes = 48 * 1024; // bytes per stage (records + tile metadata)
+// Compiled shapes of the streaming pipeline: (id, stages in the shared-memory
+// ring, bytes per stage, rounds of 31 samples per tile).  Each stage holds one
+// tile: header, accumulators, edge table, inner and outer record planes.
+#define RGG_VARIANTS(X)          \
+  X(0, 20, 10 * 1024, 3)        \
+  X(1, 7, 28 * 1024, 9)         \
+  X(2, 6, 34 * 1024, 11)        \
+  X(3, 5, 40 * 1024, 13)        \
+  X(4, 4, 51 * 1024, 17)        \
+  X(5, 3, 69 * 1024, 23)
+constexpr int kNumVariants = 6;
+constexpr int kDefaultVariant = 4;
+constexpr uint32_t kDefaultConsumerWarps = 24;
+
+struct VariantShape {
+  int stages, stage_bytes, rounds;
+};
+inline VariantShape variant_shape(int v) {
+  switch (v) {
+#define RGG_VARIANT(id, ns, sb, rd) \
+  case id: return VariantShape{ns, sb, rd};
+    RGG_VARIANTS(RGG_VARIANT)
+#undef RGG_VARIANT
+    default: return VariantShape{0, 0, 0};
+  }
+}
 constexpr int kMaxBuildLinks = 32;
 constexpr uint32_t kMaxUpdateBoxes = 256;  // poses carried by value per update launch
 
@@ -49,22 +73,21 @@ struct BoxPrepParams {
 struct ClassifyLaunch {
   uint32_t grid;
   uint32_t consumer_warps;
-  uint32_t tw_cap;   // max intervals per tile over the launch's jobs
-  uint32_t acc_cap;  // max local edges per tile over the launch's jobs
+  int variant;
 };
 
-size_t classify_smem_bytes(uint32_t tw_cap, uint32_t acc_cap);
+size_t classify_smem_bytes(int variant, uint32_t consumer_warps);
 
 cudaError_t launch_count_samples(const double* qa, const double* qb, uint64_t n_edges, uint32_t L,
                                  double step, uint64_t* counts, int* bad, cudaStream_t s);
 cudaError_t launch_build_records(const BuildParams& p, int num_sms, cudaStream_t s);
-cudaError_t launch_tile_edge(const uint64_t* soff, uint64_t n_edges, uint32_t L, uint32_t S,
-                             uint64_t n_tiles, uint32_t* out, cudaStream_t s);
 cudaError_t launch_box_update(const BoxUpdateParams& p, cudaStream_t s);
 cudaError_t launch_box_prep(const BoxPrepParams& p, cudaStream_t s);
 cudaError_t launch_classify_single(const ClassifyParams<1>& p, const ClassifyLaunch& lc,
                                    cudaStream_t s);
 cudaError_t launch_classify_batched(const ClassifyParams<kMaxJobs>& p, const ClassifyLaunch& lc,
                                     cudaStream_t s);
+cudaError_t launch_merge_single(const MergeParams<1>& p, cudaStream_t s);
+cudaError_t launch_merge_batched(const MergeParams<kMaxJobs>& p, cudaStream_t s);
 
 }  // namespace rgg

@@ -20,6 +20,7 @@ GREEN, GRAY, RED = 0, 1, 2
 RGG_OK, RGG_ERR_INVALID, RGG_ERR_OOM, RGG_ERR_CUDA, RGG_ERR_TIMEOUT, RGG_ERR_STATE = \
     0, -1, -2, -3, -4, -5
 BOXES_PER_PASS = 32
+NUM_VARIANTS = 6
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "librgg.so")
@@ -94,7 +95,7 @@ def _lib():
         "rgg_roadmap_info": [vp, ctypes.POINTER(Info)],
         "rgg_check_status": [vp, vp],
         "rgg_set_kernel_timing": [vp, i32],
-        "rgg_kernel_time": [vp, ctypes.POINTER(dbl), ctypes.POINTER(u64)],
+        "rgg_kernel_time": [vp, ctypes.POINTER(dbl), ctypes.POINTER(dbl), ctypes.POINTER(u64)],
         "rgg_set_launch_shape": [vp, u32, u32],
     }
     for name, args in sig.items():
@@ -286,14 +287,15 @@ class Roadmap:
         _check("rgg_set_kernel_timing", _lib().rgg_set_kernel_timing(self._h, int(enable)))
 
     def kernel_time(self):
-        """(milliseconds, launches) of the timed classify launches since the last call."""
-        ms, n = ctypes.c_double(), ctypes.c_uint64()
-        _check("rgg_kernel_time", _lib().rgg_kernel_time(self._h, ctypes.byref(ms),
-                                                         ctypes.byref(n)))
-        return ms.value, n.value
+        """(classify ms, merge ms, passes) of the timed passes since the last call."""
+        cm, mm, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_uint64()
+        _check("rgg_kernel_time", _lib().rgg_kernel_time(self._h, ctypes.byref(cm),
+                                                         ctypes.byref(mm), ctypes.byref(n)))
+        return cm.value, mm.value, n.value
 
-    def set_launch_shape(self, ctas_per_sm: int = 0, consumer_warps: int = 0) -> None:
-        _check("rgg_set_launch_shape", _lib().rgg_set_launch_shape(self._h, ctas_per_sm,
+    def set_launch_shape(self, variant: int = 0, consumer_warps: int = 0) -> None:
+        """Pipeline shape of the classify kernel (see rgg_set_launch_shape)."""
+        _check("rgg_set_launch_shape", _lib().rgg_set_launch_shape(self._h, variant,
                                                                    consumer_warps))
 
 

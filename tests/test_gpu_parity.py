@@ -320,5 +320,5 @@ def test_kernel_timing_counts_launches(rgg):
         r.set_kernel_timing(True)
         r.update_obstacles(np.arange(16), f32(sc.boxes.poses()))
         r.classify()
-        ms, n = r.kernel_time()
-        assert n == 1 and ms > 0
+        ms, mm, n = r.kernel_time()
+        assert n == 1 and ms > 0 and mm > 0
