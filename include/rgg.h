@@ -69,7 +69,8 @@ enum rgg_status {
   RGG_ERR_OOM = -2,      /* device or pinned-host allocation failed        */
   RGG_ERR_CUDA = -3,     /* a CUDA runtime call failed                     */
   RGG_ERR_TIMEOUT = -4,  /* a bounded device-side wait ran out             */
-  RGG_ERR_STATE = -5     /* call not valid in the roadmap's current state  */
+  RGG_ERR_STATE = -5,    /* call not valid in the roadmap's current state  */
+  RGG_ERR_CAPACITY = -6  /* larger than rgg_classify_noalloc's fixed scratch */
 };
 
 /* Edge labels (Sec. 4.1): valid, unknown, invalid. */
@@ -81,7 +82,10 @@ enum {
   RGG_MAX_INNER = 16,          /* inner_per_link                               */
   RGG_MAX_OBSTACLES = 4096,    /* max_obstacles                                */
   RGG_BOXES_PER_PASS = 32,     /* moved boxes tested per streaming pass        */
-  RGG_NUM_VARIANTS = 6         /* compiled pipeline shapes (rgg_set_launch_shape) */
+  RGG_NUM_VARIANTS = 6,        /* compiled pipeline shapes (rgg_set_launch_shape) */
+  RGG_NOALLOC_MAX_EDGES = 131072,  /* rgg_classify_noalloc: edges per call          */
+  RGG_NOALLOC_MAX_TILES = 16384    /* rgg_classify_noalloc: tiles of up to 527      */
+                                   /* configurations x links per call               */
 };
 
 typedef struct {
@@ -261,6 +265,66 @@ int rgg_kernel_time(rgg_roadmap_t r, double* classify_ms, double* merge_ms, uint
  * rgg_classify_many must share the variant.  RGG_ERR_INVALID for an
  * unsupported shape (nothing changes). */
 int rgg_set_launch_shape(rgg_roadmap_t r, uint32_t variant, uint32_t consumer_warps);
+
+/* ------------------------------------------------------------------------ */
+/* One classification pass that allocates nothing.  (The paper has no
+ * counterpart: this entry point exists for callers of this library that may
+ * not allocate device memory -- a real-time loop that must not wait on the
+ * driver's allocator, a host whose memory manager owns every device byte, or
+ * a plugin that may only launch work on buffers it is handed.)
+ *
+ * The caller owns the serialized records and the per-edge state, in device
+ * memory, laid out as below; the call tests every edge against the given
+ * moved boxes and merges the results into the per-edge state exactly as
+ * rgg_classify does (same arithmetic, same labels).  It calls no cudaMalloc,
+ * cudaFree or other allocating routine: its scratch (tile tables, per-edge
+ * accumulators, box records; about 3.7 MB) is a fixed array inside the
+ * library, held by every device that loads the library until the process
+ * exits.  On each device the first call looks up that array's address; make
+ * that first call before any stream capture.  All calls share the array and
+ * clear what must start at zero, so calls that overlap on the GPU (on
+ * different streams, or from several threads) race: order them.  The call
+ * works on the current device and stream; it returns once the work is
+ * enqueued.
+ *
+ * Layout (all pointers device, except box_ids / box_poses which are host):
+ *   sample_off   N+1 uint64 configuration offsets, as for rgg_upload_edges
+ *                (n_e >= 2); num_samples must equal sample_off[N]
+ *   inner_xyzr   4 planes at inner_xyzr + p*inner_stride (floats), each with
+ *                K*L*num_samples spheres in the rgg_upload_edges order;
+ *                16-byte aligned, stride a multiple of 4 and >= count + 4
+ *   outer_xyzr   likewise, L*(num_samples - N) spheres per plane
+ *   box_ids      num_boxes (<= 32) distinct ids, each < 32*mask_words
+ *   box_poses    num_boxes x 15 floats: centre, R (row-major), half-extents
+ *   hit, touch   N x mask_words uint32 box sets (in/out), bit b of word b/32
+ *   counts       N uint32: hit-set size | touch-set size << 16 (in/out);
+ *                zero together with the sets before the first call
+ *   labels       N uint8 (out), enum rgg_label
+ * Limits: N <= RGG_NOALLOC_MAX_EDGES and at most RGG_NOALLOC_MAX_TILES tiles
+ * (tiles hold up to 527 configurations x links, fewer for robots with few
+ * links); larger inputs return RGG_ERR_CAPACITY and nothing is launched.
+ * RGG_ERR_INVALID for bad sizes, alignment, ids or poses.  A sample_off that
+ * breaks its rules gives undefined labels but no out-of-bounds access. */
+typedef struct {
+  uint32_t num_links, inner_per_link;
+  uint64_t num_edges, num_samples;
+  const uint64_t* sample_off;
+  const float* inner_xyzr;
+  uint64_t inner_stride;
+  const float* outer_xyzr;
+  uint64_t outer_stride;
+  uint32_t num_boxes;
+  const uint32_t* box_ids;
+  const float* box_poses;
+  uint32_t mask_words;
+  uint32_t* hit;
+  uint32_t* touch;
+  uint32_t* counts;
+  uint8_t* labels;
+  float margin_m;
+} rgg_noalloc_args;
+
+int rgg_classify_noalloc(const rgg_noalloc_args* args, void* stream);
 
 /* Static description of a status code (never NULL). */
 const char* rgg_status_string(int status);

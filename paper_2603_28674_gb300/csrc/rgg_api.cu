@@ -404,6 +404,7 @@ const char* rgg_status_string(int s) {
     case RGG_ERR_CUDA: return "CUDA runtime error";
     case RGG_ERR_TIMEOUT: return "device-side wait timed out";
     case RGG_ERR_STATE: return "call not valid in the current state";
+    case RGG_ERR_CAPACITY: return "larger than the no-alloc pass's fixed scratch";
     default: return "unknown status";
   }
 }

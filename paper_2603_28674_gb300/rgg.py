@@ -19,6 +19,9 @@ import numpy as np
 GREEN, GRAY, RED = 0, 1, 2
 RGG_OK, RGG_ERR_INVALID, RGG_ERR_OOM, RGG_ERR_CUDA, RGG_ERR_TIMEOUT, RGG_ERR_STATE = \
     0, -1, -2, -3, -4, -5
+RGG_ERR_CAPACITY = -6
+NOALLOC_MAX_EDGES = 131072
+NOALLOC_MAX_TILES = 16384
 BOXES_PER_PASS = 32
 NUM_VARIANTS = 6
 
@@ -31,7 +34,7 @@ EXPORTS = (
     "rgg_update_obstacles", "rgg_classify", "rgg_classify_many", "rgg_fetch_labels",
     "rgg_fetch_box_sets", "rgg_fetch_records", "rgg_labels_device_ptr", "rgg_roadmap_info",
     "rgg_check_status", "rgg_set_kernel_timing", "rgg_kernel_time", "rgg_set_launch_shape",
-    "rgg_status_string",
+    "rgg_status_string", "rgg_classify_noalloc",
 )
 
 
@@ -52,6 +55,18 @@ class _Robot(ctypes.Structure):
     _fields_ = [("num_links", ctypes.c_uint32), ("a", ctypes.POINTER(ctypes.c_double)),
                 ("alpha", ctypes.POINTER(ctypes.c_double)), ("d", ctypes.POINTER(ctypes.c_double)),
                 ("radius", ctypes.POINTER(ctypes.c_double))]
+
+
+class _NoallocArgs(ctypes.Structure):
+    _fields_ = [("num_links", ctypes.c_uint32), ("inner_per_link", ctypes.c_uint32),
+                ("num_edges", ctypes.c_uint64), ("num_samples", ctypes.c_uint64),
+                ("sample_off", ctypes.c_void_p), ("inner_xyzr", ctypes.c_void_p),
+                ("inner_stride", ctypes.c_uint64), ("outer_xyzr", ctypes.c_void_p),
+                ("outer_stride", ctypes.c_uint64), ("num_boxes", ctypes.c_uint32),
+                ("box_ids", ctypes.c_void_p), ("box_poses", ctypes.c_void_p),
+                ("mask_words", ctypes.c_uint32), ("hit", ctypes.c_void_p),
+                ("touch", ctypes.c_void_p), ("counts", ctypes.c_void_p),
+                ("labels", ctypes.c_void_p), ("margin_m", ctypes.c_float)]
 
 
 class Info(ctypes.Structure):
@@ -97,6 +112,7 @@ def _lib():
         "rgg_set_kernel_timing": [vp, i32],
         "rgg_kernel_time": [vp, ctypes.POINTER(dbl), ctypes.POINTER(dbl), ctypes.POINTER(u64)],
         "rgg_set_launch_shape": [vp, u32, u32],
+        "rgg_classify_noalloc": [ctypes.POINTER(_NoallocArgs), vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -306,3 +322,27 @@ def classify_many(roadmaps: Sequence[Roadmap], stream=None) -> None:
     arr = (ctypes.c_void_p * len(roadmaps))(*[r.handle for r in roadmaps])
     _check("rgg_classify_many", _lib().rgg_classify_many(arr, len(roadmaps),
                                                          _stream(stream, roadmaps[0].device)))
+
+
+def classify_noalloc(*, num_links: int, inner_per_link: int, sample_off, num_samples: int,
+                     inner, outer, box_ids, box_poses, mask_words: int, hit, touch, counts,
+                     labels, margin: float = 2e-5, stream=None) -> None:
+    """One pass of rgg_classify_noalloc on caller-owned device buffers.
+
+    ``sample_off`` (int64/uint64), ``inner`` / ``outer`` ([4, stride] float32
+    planes), ``hit`` / ``touch`` ([N, mask_words] int32/uint32), ``counts``
+    ([N] int32/uint32) and ``labels`` ([N] uint8) are CUDA tensors on the
+    current device; ``box_ids`` / ``box_poses`` are host arrays.  The call
+    itself allocates nothing on the device."""
+    ids = _host(box_ids, np.uint32).reshape(-1)
+    poses = _host(box_poses, np.float32).reshape(-1, 15)
+    if poses.shape[0] != ids.shape[0]:
+        raise ValueError("one pose per id")
+    args = _NoallocArgs(
+        num_links, inner_per_link, int(labels.shape[0]), int(num_samples), _ptr(sample_off),
+        _ptr(inner), int(inner.stride(0)), _ptr(outer), int(outer.stride(0)), ids.shape[0],
+        ids.ctypes.data, poses.ctypes.data, mask_words, _ptr(hit), _ptr(touch), _ptr(counts),
+        _ptr(labels), margin)
+    dev = inner.device.index if hasattr(inner, "device") else 0
+    _check("rgg_classify_noalloc", _lib().rgg_classify_noalloc(ctypes.byref(args),
+                                                               _stream(stream, dev)))
