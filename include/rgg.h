@@ -82,7 +82,7 @@ enum {
   RGG_MAX_INNER = 16,          /* inner_per_link                               */
   RGG_MAX_OBSTACLES = 4096,    /* max_obstacles                                */
   RGG_BOXES_PER_PASS = 32,     /* moved boxes tested per streaming pass        */
-  RGG_NUM_VARIANTS = 6,        /* compiled pipeline shapes (rgg_set_launch_shape) */
+  RGG_NUM_VARIANTS = 7,        /* compiled pipeline shapes (rgg_set_launch_shape) */
   RGG_NOALLOC_MAX_EDGES = 131072,  /* rgg_classify_noalloc: edges per call          */
   RGG_NOALLOC_MAX_TILES = 16384    /* rgg_classify_noalloc: tiles of up to 527      */
                                    /* configurations x links per call               */
@@ -260,7 +260,7 @@ int rgg_kernel_time(rgg_roadmap_t r, double* classify_ms, double* merge_ms, uint
  * compiled pipeline shapes (shared-memory ring depth x stage size x rounds of
  * 31 configurations per tile; RGG_NUM_VARIANTS in all, 0 = smallest tiles,
  * 4 the default) and `consumer_warps` the warps per CTA that test records
- * (0 = default 24; 1..31).  With edges present the tiles are rebuilt for the new shape (the
+ * (0 = default 24; 1..27).  With edges present the tiles are rebuilt for the new shape (the
  * call synchronises the device).  Roadmaps classified together by
  * rgg_classify_many must share the variant.  RGG_ERR_INVALID for an
  * unsupported shape (nothing changes). */

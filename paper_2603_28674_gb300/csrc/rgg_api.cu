@@ -877,9 +877,13 @@ int rgg_kernel_time(rgg_roadmap_t r, double* classify_ms, double* merge_ms,
 int rgg_set_launch_shape(rgg_roadmap_t r, uint32_t variant, uint32_t consumer_warps) {
   if (!r) return RGG_ERR_INVALID;
   const uint32_t cw = consumer_warps ? consumer_warps : kDefaultConsumerWarps;
-  if (variant >= (uint32_t)kNumVariants || cw < 1 || cw > 31) return RGG_ERR_INVALID;
+  if (variant >= (uint32_t)kNumVariants || cw < 1 || 32 * (cw + 1) > (uint32_t)kMaxClassifyThreads)
+    return RGG_ERR_INVALID;
   if (classify_smem_bytes((int)variant, cw) > 232448) return RGG_ERR_INVALID;
-  if ((uint64_t)cw > (uint64_t)variant_shape((int)variant).stages * variant_shape((int)variant).rounds)
+  // every consumer warp holds at most one work item; the ring's phase parity
+  // stays unambiguous while there are no more warps than items in the ring
+  const VariantShape vs = variant_shape((int)variant);
+  if ((uint64_t)cw > (uint64_t)vs.stages * ((vs.rounds + vs.rounds_per_item - 1) / vs.rounds_per_item))
     return RGG_ERR_INVALID;
   const int old_v = r->variant;
   const uint32_t old_cw = r->consumer_warps;

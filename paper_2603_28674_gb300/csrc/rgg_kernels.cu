@@ -250,14 +250,14 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
-// Work items: tile t of this CTA has ROUNDS items (rounds of 31 samples);
-// warps take items in order from a shared counter.  Round r of a tile covers
+// Work items: tile t of this CTA has ROUNDS rounds of 31 samples, grouped
+// RPI rounds per work item; warps take items in order from a shared counter.  Round r of a tile covers
 // the samples q = 31r .. 31r+30 on lanes 1..31; lane 0 takes sample 31r-1,
 // whose following interval the round needs (for r = 0 that is the tile's
 // halo interval).  The warp that finishes a tile's last round flushes the
 // tile's per-edge bits and releases the stage.
-template <int MAXJ, int NSTAGE, int STAGE_BYTES, int ROUNDS>
-__global__ void __launch_bounds__(1024, 1) classify_kernel(const __grid_constant__ ClassifyParams<MAXJ> P) {
+template <int MAXJ, int NSTAGE, int STAGE_BYTES, int ROUNDS, int RPI>
+__global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const __grid_constant__ ClassifyParams<MAXJ> P) {
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char* stages = smem;
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + NSTAGE * STAGE_BYTES);
@@ -377,9 +377,11 @@ __global__ void __launch_bounds__(1024, 1) classify_kernel(const __grid_constant
       }
       ok = __shfl_sync(0xffffffffu, ok, 0);
     }
-    // end markers: ROUNDS items each, enough for every consumer warp to take one
+    // end markers: one slot per items-per-tile consumer warps, so that every
+    // consumer warp takes one
     if (lane == 0 && ok) {
-      const int n_end = (ncw + ROUNDS - 1) / ROUNDS;
+      constexpr int IPT = (ROUNDS + RPI - 1) / RPI;
+      const int n_end = (ncw + IPT - 1) / IPT;
       for (int i = 0; i < n_end; ++i, ++slot) {
         const int stage = slot % NSTAGE;
         const uint32_t round = slot / NSTAGE;
@@ -414,12 +416,13 @@ __global__ void __launch_bounds__(1024, 1) classify_kernel(const __grid_constant
     }
     mbar_wait_bounded(boxbar, 0, kWaitLimit);
   }
+  constexpr int IPT = (ROUNDS + RPI - 1) / RPI;  // work items per tile
   for (;;) {
     uint32_t item = 0;
     if (lane == 0) item = atomicAdd(s_item, 1u);
     item = __shfl_sync(0xffffffffu, item, 0);
-    const uint32_t slot = item / ROUNDS;
-    const int rnd = (int)(item - slot * ROUNDS);
+    const uint32_t slot = item / IPT;
+    const int sub = (int)(item - slot * IPT);
     const int stage = slot % NSTAGE;
     const uint32_t parity = (slot / NSTAGE) & 1;
     int ok = 1;
@@ -441,61 +444,45 @@ __global__ void __launch_bounds__(1024, 1) classify_kernel(const __grid_constant
     // stage reused by another roadmap's tile finds them zeroed
     uint32_t* acc_hit = reinterpret_cast<uint32_t*>(sb + kStageAccOff);
     uint32_t* acc_touch = acc_hit + kAccMax;
-    const int base = 31 * rnd;
-
-    if (base < n_samp) {
-      const int K = (int)J.K;
-      const int C = (int)J.C;
-      const float margin = J.margin;
-      const float inv_k = 1.0f / (float)K;
-      const float* ix = reinterpret_cast<const float*>(sb + J.off_in) + hdr.in_shift;
-      const float* iy = ix + J.in_cap;
-      const float* iz = iy + J.in_cap;
-      const float* ir = iz + J.in_cap;
-      const float* ox = reinterpret_cast<const float*>(sb + J.off_out) + hdr.out_shift;
-      const float* oy = ox + J.out_cap;
-      const float* oz = oy + J.out_cap;
-      const float* orad = oz + J.out_cap;
-      const float4* bx = MAXJ == 1 ? s_boxes
-                         : (hdr.job - job_lo < kBoxSlots
-                                ? s_boxes + (hdr.job - job_lo) * kBoxesPerPass * 6
-                                : reinterpret_cast<const float4*>(J.boxes));
+    const int K = (int)J.K;
+    const int C = (int)J.C;
+    const float margin = J.margin;
+    const float inv_k = 1.0f / (float)K;
+    const float* ix = reinterpret_cast<const float*>(sb + J.off_in) + hdr.in_shift;
+    const float* iy = ix + J.in_cap;
+    const float* iz = iy + J.in_cap;
+    const float* ir = iz + J.in_cap;
+    const float* ox = reinterpret_cast<const float*>(sb + J.off_out) + hdr.out_shift;
+    const float* oy = ox + J.out_cap;
+    const float* oz = oy + J.out_cap;
+    const float* orad = oz + J.out_cap;
+    const float4* bx = MAXJ == 1 ? s_boxes
+                       : (hdr.job - job_lo < kBoxSlots
+                              ? s_boxes + (hdr.job - job_lo) * kBoxesPerPass * 6
+                              : reinterpret_cast<const float4*>(J.boxes));
+    const int r_end = min((sub + 1) * RPI, ROUNDS);
+    for (int rnd = sub * RPI; rnd < r_end; ++rnd) {
+      const int base = 31 * rnd;
+      if (base >= n_samp) break;
       const int q = base - 1 + lane;
       const int q_end = min(base + 31, n_samp);
-      // locate q: its edge j, the position k in its link's run, and the
-      // local index o of the interval that follows it
-      int j = 0, n = 2, k = -1, o = 0;
-      bool valid = false;
-      if (q < q_end) {
-        j = q < 0 ? 0 : search_le(etab, 0, n_edges, q);
-        const int estart = etab[4 * j];
-        n = etab[4 * j + 1];
-        const int rr = q - estart;
-        valid = rr >= 0;
-        if (valid) {
-          // rr / n from the stored reciprocal, then an exact correction
-          int li = __float2int_rz(((float)rr + 0.5f) * __int_as_float(etab[4 * j + 3]));
-          k = rr - li * n;
-          if (k < 0) {
-            --li;
-            k += n;
-          } else if (k >= n) {
-            ++li;
-            k -= n;
-          }
-          o = etab[4 * j + 2] + li * (n - 1) + k;
-        }
-      }
+      // locate q: its edge j, its position k in its link's run, and the local
+      // index o of the interval that follows it (branch-free)
+      const int j = search_le(etab, 0, n_edges, max(q, 0));
+      const int4 ej = *reinterpret_cast<const int4*>(etab + 4 * j);
+      const int n = ej.y;
+      const int rr = q - ej.x;
+      int li = __float2int_rz(((float)rr + 0.5f) * __int_as_float(ej.w));
+      int k = rr - li * n;
+      const int adj = k < 0 ? -1 : (k >= n ? 1 : 0);  // exact rr / n
+      li += adj;
+      k -= adj * n;
+      const bool valid = q < q_end && rr >= 0;
+      const bool has_next = valid && k < n - 1;
+      const int o = has_next ? ej.z + li * (n - 1) + k : 0;
       // ---- a3: the outer sphere of the interval after q, against the moved
       // boxes that survive a warp bounding-sphere cull
-      const bool has_next = valid && k < n - 1;
-      float x = 0.f, y = 0.f, z = 0.f, r = 0.f;
-      if (has_next) {
-        x = ox[o];
-        y = oy[o];
-        z = oz[o];
-        r = orad[o];
-      }
+      float x = ox[o], y = oy[o], z = oz[o], r = orad[o];
       const uint32_t act = __ballot_sync(0xffffffffu, has_next);
       uint32_t bits = 0;
       if (act) {
@@ -517,10 +504,15 @@ __global__ void __launch_bounds__(1024, 1) classify_kernel(const __grid_constant
         uint32_t cand = __ballot_sync(0xffffffffu, cb);
         const float rt = r + margin;
         const float rt2 = rt * rt;
+        // two candidate boxes per iteration for instruction-level parallelism
         while (cand) {
-          const int b = __ffs(cand) - 1;
+          const int b0 = __ffs(cand) - 1;
           cand &= cand - 1;
-          if (box_dist2(x, y, z, bx + 6 * b) <= rt2) bits |= 1u << b;
+          const int b1 = cand ? __ffs(cand) - 1 : b0;
+          cand &= cand - 1;
+          const float d0 = box_dist2(x, y, z, bx + 6 * b0);
+          const float d1 = box_dist2(x, y, z, bx + 6 * b1);
+          bits |= (d0 <= rt2 ? 1u << b0 : 0u) | (d1 <= rt2 ? 1u << b1 : 0u);
         }
         if (!has_next) bits = 0;
         if (bits) atomicOr(&acc_touch[j], bits);
@@ -535,27 +527,35 @@ __global__ void __launch_bounds__(1024, 1) classify_kernel(const __grid_constant
       }
       const int cnt = __popc(need);
       int incl = cnt;
+#pragma unroll
       for (int d = 1; d < 32; d <<= 1) {
         const int v = __shfl_up_sync(0xffffffffu, incl, d);
         if (lane >= d) incl += v;
       }
       const int total = __shfl_sync(0xffffffffu, incl, 31);
       if (total > 0 && total <= kPairQueue) {
-        // compact the (sample, box) pairs, then test (pair, sphere) items on all lanes
+        // compact the (sample, box) pairs, then test (pair, sphere) items on
+        // all lanes, two items per lane per iteration
         int pos = incl - cnt;
         for (uint32_t m = need; m; m &= m - 1)
           queue[pos++] = ((uint32_t)q << 13) | ((uint32_t)j << 5) | (uint32_t)(__ffs(m) - 1);
         __syncwarp();
-        for (int it = lane; it < total * K; it += 32) {
-          const int pi = __float2int_rz(((float)it + 0.5f) * inv_k);
-          const int jj = it - pi * K;
-          const uint32_t e = queue[pi];
-          const int b = (int)(e & 31u), jl = (int)((e >> 5) & 255u), qq = (int)(e >> 13);
-          const int s = K * qq + jj;
-          const float rin = ir[s] - margin;
-          if (rin > 0.0f && box_dist2(ix[s], iy[s], iz[s], bx + 6 * b) <= rin * rin)
-            atomicOr(&acc_hit[jl], 1u << b);
+        const int n_items = total * K;
+        for (int it = lane; it < n_items; it += 64) {
+          const int it2 = min(it + 32, n_items - 1);
+          const int p0 = __float2int_rz(((float)it + 0.5f) * inv_k);
+          const int p1 = __float2int_rz(((float)it2 + 0.5f) * inv_k);
+          const uint32_t e0 = queue[p0], e1 = queue[p1];
+          const int s0 = K * (int)(e0 >> 13) + (it - p0 * K);
+          const int s1 = K * (int)(e1 >> 13) + (it2 - p1 * K);
+          const float r0 = ir[s0] - margin, r1 = ir[s1] - margin;
+          const float d0 = box_dist2(ix[s0], iy[s0], iz[s0], bx + 6 * (int)(e0 & 31u));
+          const float d1 = box_dist2(ix[s1], iy[s1], iz[s1], bx + 6 * (int)(e1 & 31u));
+          if (r0 > 0.0f && d0 <= r0 * r0) atomicOr(&acc_hit[(e0 >> 5) & 255u], 1u << (e0 & 31u));
+          if (it + 32 < n_items && r1 > 0.0f && d1 <= r1 * r1)
+            atomicOr(&acc_hit[(e1 >> 5) & 255u], 1u << (e1 & 31u));
         }
+        __syncwarp();
       } else if (total > kPairQueue) {
         // many pairs in one round: each lane tests its own
         uint32_t hits = 0;
@@ -570,9 +570,10 @@ __global__ void __launch_bounds__(1024, 1) classify_kernel(const __grid_constant
           }
         }
         if (hits) atomicOr(&acc_hit[j], hits);
+        __syncwarp();
       }
     }
-    // ---- round done; the tile's last round flushes and releases the stage
+    // ---- item done; the tile's last item flushes and releases the stage
     __syncwarp();
     uint32_t done = 0;
     if (lane == 0) {
@@ -580,7 +581,7 @@ __global__ void __launch_bounds__(1024, 1) classify_kernel(const __grid_constant
       done = atomicAdd(&s_cnt[stage], 1u);
     }
     done = __shfl_sync(0xffffffffu, done, 0);
-    if (done == ROUNDS - 1) {
+    if (done == IPT - 1) {
       __threadfence_block();
       // ---- a5: the tile's per-edge bits into the global accumulators
       for (int jl = lane; jl < n_edges; jl += 32) {
@@ -696,7 +697,7 @@ static size_t smem_bytes_t(uint32_t consumer_warps) {
 
 size_t classify_smem_bytes(int variant, uint32_t consumer_warps) {
   switch (variant) {
-#define RGG_VARIANT(id, ns, sb, rd) \
+#define RGG_VARIANT(id, ns, sb, rd, rpi) \
   case id: return smem_bytes_t<ns, sb>(consumer_warps);
     RGG_VARIANTS(RGG_VARIANT)
 #undef RGG_VARIANT
@@ -704,10 +705,10 @@ size_t classify_smem_bytes(int variant, uint32_t consumer_warps) {
   }
 }
 
-template <int MAXJ, int NSTAGE, int STAGE_BYTES, int ROUNDS>
+template <int MAXJ, int NSTAGE, int STAGE_BYTES, int ROUNDS, int RPI>
 static cudaError_t launch_classify_v(const ClassifyParams<MAXJ>& p, const ClassifyLaunch& lc,
                                      cudaStream_t s) {
-  auto kern = classify_kernel<MAXJ, NSTAGE, STAGE_BYTES, ROUNDS>;
+  auto kern = classify_kernel<MAXJ, NSTAGE, STAGE_BYTES, ROUNDS, RPI>;
   const size_t smem = smem_bytes_t<NSTAGE, STAGE_BYTES>(lc.consumer_warps);
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
@@ -719,8 +720,8 @@ template <int MAXJ>
 static cudaError_t launch_classify_t(const ClassifyParams<MAXJ>& p, const ClassifyLaunch& lc,
                                      cudaStream_t s) {
   switch (lc.variant) {
-#define RGG_VARIANT(id, ns, sb, rd) \
-  case id: return launch_classify_v<MAXJ, ns, sb, rd>(p, lc, s);
+#define RGG_VARIANT(id, ns, sb, rd, rpi) \
+  case id: return launch_classify_v<MAXJ, ns, sb, rd, rpi>(p, lc, s);
     RGG_VARIANTS(RGG_VARIANT)
 #undef RGG_VARIANT
     default: return cudaErrorInvalidValue;

@@ -10,29 +10,31 @@
 namespace rgg {
 
 // Compiled shapes of the streaming pipeline: (id, stages in the shared-memory
-// ring, bytes per stage, rounds of 31 samples per tile).  Each stage holds one
-// tile: header, accumulators, edge table, inner and outer record planes.
-#define RGG_VARIANTS(X)          \
-  X(0, 20, 10 * 1024, 3)        \
-  X(1, 7, 28 * 1024, 9)         \
-  X(2, 6, 34 * 1024, 11)        \
-  X(3, 5, 40 * 1024, 13)        \
-  X(4, 4, 51 * 1024, 17)        \
-  X(5, 3, 69 * 1024, 23)
-constexpr int kNumVariants = 6;
+// ring, bytes per stage, rounds of 31 samples per tile, rounds per work item).
+// Each stage holds one tile: header, accumulators, edge table, inner and
+// outer record planes.
+#define RGG_VARIANTS(X)             \
+  X(0, 20, 10 * 1024, 3, 1)        \
+  X(1, 7, 28 * 1024, 9, 1)         \
+  X(2, 6, 34 * 1024, 11, 1)        \
+  X(3, 5, 40 * 1024, 13, 1)        \
+  X(4, 4, 51 * 1024, 17, 1)        \
+  X(5, 3, 69 * 1024, 23, 1)        \
+  X(6, 4, 51 * 1024, 16, 2)
+constexpr int kNumVariants = 7;
 constexpr int kDefaultVariant = 4;
 constexpr uint32_t kDefaultConsumerWarps = 24;
-
+constexpr int kMaxClassifyThreads = 896;  // producer warp + up to 27 consumer warps
 struct VariantShape {
-  int stages, stage_bytes, rounds;
+  int stages, stage_bytes, rounds, rounds_per_item;
 };
 inline VariantShape variant_shape(int v) {
   switch (v) {
-#define RGG_VARIANT(id, ns, sb, rd) \
-  case id: return VariantShape{ns, sb, rd};
+#define RGG_VARIANT(id, ns, sb, rd, rpi) \
+  case id: return VariantShape{ns, sb, rd, rpi};
     RGG_VARIANTS(RGG_VARIANT)
 #undef RGG_VARIANT
-    default: return VariantShape{0, 0, 0};
+    default: return VariantShape{0, 0, 0, 0};
   }
 }
 constexpr int kMaxBuildLinks = 32;

@@ -23,7 +23,7 @@ RGG_ERR_CAPACITY = -6
 NOALLOC_MAX_EDGES = 131072
 NOALLOC_MAX_TILES = 16384
 BOXES_PER_PASS = 32
-NUM_VARIANTS = 6
+NUM_VARIANTS = 7
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "librgg.so")
