@@ -74,9 +74,10 @@ bool tiling_for(uint32_t L, uint32_t K, uint32_t S, uint32_t stage_bytes, Tiling
 }
 
 // Tiles of 31*rounds samples (full rounds) when they fit a stage, else the
-// largest that does; smaller for tiny roadmaps so that the work spreads over
-// the launch's warps.
+// largest that does; smaller only for roadmaps too small to give every CTA of
+// a launch two tiles (big tiles keep the producer warp's per-tile cost low).
 Tiling choose_tiling(uint32_t L, uint32_t K, uint64_t G, uint32_t warps, int variant) {
+  // `warps`: how many tiles the roadmap should at least be cut into
   const VariantShape v = variant_shape(variant);
   uint32_t smax = 31 * v.rounds;
   Tiling t;
@@ -134,7 +135,7 @@ struct rgg_roadmap {
   EdgeState es;
   float* d_table = nullptr;    // [M][16] box poses
   float* d_changed = nullptr;  // [32][24] derived records of the current pass
-  int* d_status = nullptr;
+  int* d_status = nullptr;          // [0] status word, [1] classify work counter
   std::vector<uint8_t> present, is_pending;
   std::vector<uint32_t> pending;
   // kernel timing: events before classify, between classify and merge, after merge
@@ -193,7 +194,7 @@ bool build_tiles(uint32_t L, uint64_t N, const std::vector<uint64_t>& soff, uint
 // (Re)build the tile descriptors and edge tables of `es` for the roadmap's
 // current launch shape and copy them to the device (synchronous).
 int set_tiles(rgg_roadmap* r, EdgeState* es, cudaStream_t s) {
-  Tiling tiling = choose_tiling(r->L, r->K, es->G, launch_ctas(r) * r->consumer_warps, r->variant);
+  Tiling tiling = choose_tiling(r->L, r->K, es->G, 2 * launch_ctas(r), r->variant);
   std::vector<TileDesc> h_tiles;
   std::vector<int4> h_etab;
   if (es->N && !build_tiles(r->L, es->N, es->h_soff, es->G, tiling.S, &h_tiles, &h_etab))
@@ -438,9 +439,9 @@ int rgg_roadmap_create(const rgg_roadmap_desc* desc, rgg_roadmap_t* out) {
   cudaError_t e = cudaDeviceGetAttribute(&r->num_sms, cudaDevAttrMultiProcessorCount, r->device);
   if (e == cudaSuccess) e = dalloc(&r->d_table, (size_t)r->M * 16);
   if (e == cudaSuccess) e = dalloc(&r->d_changed, (size_t)kBoxesPerPass * kBoxRecFloats);
-  if (e == cudaSuccess) e = dalloc(&r->d_status, 1);
+  if (e == cudaSuccess) e = dalloc(&r->d_status, 4);
   if (e == cudaSuccess) e = cudaMemset(r->d_table, 0, (size_t)r->M * 16 * sizeof(float));
-  if (e == cudaSuccess) e = cudaMemset(r->d_status, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(r->d_status, 0, 4 * sizeof(int));
   if (e != cudaSuccess) {
     cudaFree(r->d_table);
     cudaFree(r->d_changed);
@@ -683,17 +684,21 @@ static int classify_group(rgg_roadmap_t* rs, uint32_t n, cudaStream_t s) {
     lc.variant = r0->variant;
     lc.grid = (uint32_t)std::min<uint64_t>((tiles + 1) / 2, launch_ctas(r0));
     lc.grid = std::max<uint32_t>(lc.grid, 1);
+    uint32_t* counter = reinterpret_cast<uint32_t*>(r0->d_status + 1);
+    RGG_CK(cudaMemsetAsync(counter, 0, sizeof(uint32_t), s));
     cudaEvent_t* ev = timed ? next_events(timed) : nullptr;
     if (ev) RGG_CK(cudaEventRecord(ev[0], s));
     if (n == 1) {
       cp1.njobs = 1;
       cp1.total_tiles = tiles;
       cp1.status = r0->d_status;
+      cp1.work_counter = counter;
       RGG_CK(launch_classify_single(cp1, lc, s));
     } else {
       cpp->njobs = nj;
       cpp->total_tiles = tiles;
       cpp->status = r0->d_status;
+      cpp->work_counter = counter;
       RGG_CK(launch_classify_batched(*cpp, lc, s));
     }
     if (ev) RGG_CK(cudaEventRecord(ev[1], s));

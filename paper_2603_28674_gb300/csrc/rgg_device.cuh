@@ -74,6 +74,7 @@ struct ClassifyParams {
   uint32_t njobs;
   uint64_t total_tiles;
   int* status;                      // device status word (0 = ok)
+  uint32_t* work_counter;           // tile-chunk counter, zero at launch
 };
 
 // Per-stage header written by the producer warp.

@@ -245,6 +245,7 @@ __device__ __forceinline__ int find_job(const ClassifyParams<MAXJ>& P, uint64_t 
 constexpr uint64_t kWaitLimit = 4000000000ull;  // 4 s of wall time per wait
 
 constexpr int kPairQueue = 64;   // (sample, box) pairs a warp compacts per round
+constexpr uint32_t kChunkTiles = 16;  // tiles a producer takes per grab (<= 32)
 
 __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -258,29 +259,35 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
 // tile's per-edge bits and releases the stage.
 template <int MAXJ, int NSTAGE, int STAGE_BYTES, int ROUNDS, int RPI>
 __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const __grid_constant__ ClassifyParams<MAXJ> P) {
+  // Shared-memory carve-up, by integer offsets from the __shared__ base so that
+  // every derived pointer stays a shared-memory pointer (plain LDS/STS).
+  // Box records: one area staged once for a single-roadmap launch; one per
+  // stage, refilled when the stage's roadmap changes, for batched launches.
+  constexpr int kBoxAreas = MAXJ == 1 ? 1 : NSTAGE;
+  constexpr size_t kOffFull = (size_t)NSTAGE * STAGE_BYTES;
+  constexpr size_t kOffEmpty = kOffFull + NSTAGE * sizeof(uint64_t);
+  constexpr size_t kOffBoxBar = kOffEmpty + NSTAGE * sizeof(uint64_t);
+  constexpr size_t kOffItem = kOffBoxBar + sizeof(uint64_t);
+  constexpr size_t kOffCnt = kOffItem + 8;
+  constexpr size_t kOffDesc = (kOffCnt + 4 * ((NSTAGE + 3) & ~3) + 15) & ~(size_t)15;
+  constexpr size_t kOffDjob = kOffDesc + 32 * sizeof(TileDesc);
+  constexpr size_t kOffBoxes = (kOffDjob + 32 * sizeof(int) + 127) & ~(size_t)127;
+  constexpr size_t kOffQueues = kOffBoxes + (size_t)kBoxAreas * kBoxesPerPass * kBoxRecFloats * 4;
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char* stages = smem;
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + NSTAGE * STAGE_BYTES);
-  uint64_t* empty = full + NSTAGE;
-  uint64_t* boxbar = empty + NSTAGE;
-  uint32_t* s_item = reinterpret_cast<uint32_t*>(boxbar + 1);          // next work item
-  uint32_t* s_cnt = s_item + 2;                                        // rounds done per stage
-  TileDesc* s_desc = reinterpret_cast<TileDesc*>(s_cnt + ((NSTAGE + 3) & ~3));  // producer's batch
-  int* s_djob = reinterpret_cast<int*>(s_desc + 32);
-  float4* s_boxes = reinterpret_cast<float4*>(s_djob + 32);            // kBoxSlots x 32 x 6
-  uint32_t* queues = reinterpret_cast<uint32_t*>(s_boxes + kBoxSlots * kBoxesPerPass * 6);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kOffFull);
+  uint64_t* empty = reinterpret_cast<uint64_t*>(smem + kOffEmpty);
+  uint64_t* boxbar = reinterpret_cast<uint64_t*>(smem + kOffBoxBar);
+  uint32_t* s_item = reinterpret_cast<uint32_t*>(smem + kOffItem);     // next work item
+  uint32_t* s_cnt = reinterpret_cast<uint32_t*>(smem + kOffCnt);       // items done per stage
+  TileDesc* s_desc = reinterpret_cast<TileDesc*>(smem + kOffDesc);     // producer's batch
+  int* s_djob = reinterpret_cast<int*>(smem + kOffDjob);
+  float4* s_boxes = reinterpret_cast<float4*>(smem + kOffBoxes);
+  uint32_t* queues = reinterpret_cast<uint32_t*>(smem + kOffQueues);
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
   const int ncw = (blockDim.x >> 5) - 1;
-
-  const uint64_t per_cta = (P.total_tiles + gridDim.x - 1) / gridDim.x;
-  const uint64_t t_begin = min(P.total_tiles, (uint64_t)blockIdx.x * per_cta);
-  const uint64_t t_end = min(P.total_tiles, t_begin + per_cta);
-  // the first kBoxSlots jobs of this CTA's range read their box records from
-  // shared memory, staged once by a bulk copy
-  const int job_lo = t_begin < t_end ? find_job(P, t_begin) : 0;
-  const int job_hi = t_begin < t_end ? find_job(P, t_end - 1) : -1;
 
   // zero the stages (their accumulators must start at zero) and counters
   for (uint32_t i = threadIdx.x; i < NSTAGE * STAGE_BYTES / 16; i += blockDim.x)
@@ -295,14 +302,13 @@ __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const 
     mbar_init(boxbar, 1);
     *s_item = 0;
     fence_mbar_init();
-    uint32_t bytes = 0;
-    for (int jb = job_lo; jb <= job_hi && jb - job_lo < kBoxSlots; ++jb)
-      bytes += P.job[jb].C * (uint32_t)(kBoxRecFloats * 4);
-    mbar_arrive_expect_tx(boxbar, bytes);
-    for (int jb = job_lo; jb <= job_hi && jb - job_lo < kBoxSlots; ++jb)
-      if (P.job[jb].C)
-        bulk_g2s(s_boxes + (jb - job_lo) * kBoxesPerPass * 6, P.job[jb].boxes,
-                 P.job[jb].C * (uint32_t)(kBoxRecFloats * 4), boxbar);
+    if (MAXJ == 1) {
+      const uint32_t bytes = P.job[0].C * (uint32_t)(kBoxRecFloats * 4);
+      mbar_arrive_expect_tx(boxbar, bytes);
+      if (bytes) bulk_g2s(s_boxes, P.job[0].boxes, bytes, boxbar);
+    } else {
+      mbar_arrive(boxbar);
+    }
   }
   __syncthreads();
 
@@ -310,7 +316,15 @@ __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const 
     // ------------------------------------------------------------ producer
     uint32_t slot = 0;
     bool ok = true;
-    for (uint64_t tb = t_begin; tb < t_end && ok; tb += 32) {
+    int stage_job = -1;  // lane s < NSTAGE: job whose boxes stage s holds
+    // Tiles are taken in chunks of kChunkTiles from a launch-wide counter, so
+    // that CTAs finish together however unevenly the tiles' work is spread.
+    for (;;) {
+      uint64_t tb = 0;
+      if (lane == 0) tb = (uint64_t)atomicAdd(P.work_counter, 1u) * kChunkTiles;
+      tb = __shfl_sync(0xffffffffu, tb, 0);
+      if (tb >= P.total_tiles || !ok) break;
+      const uint64_t t_end = min(P.total_tiles, tb + kChunkTiles);
       const uint64_t t = tb + lane;
       __syncwarp();
       if (t < t_end) {
@@ -320,7 +334,7 @@ __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const 
         s_djob[lane] = jb;
       }
       __syncwarp();
-      const int nb = (int)(t_end - tb < 32 ? t_end - tb : 32);
+      const int nb = (int)(t_end - tb);
       for (int i = 0; i < nb; ++i, ++slot) {
         const int stage = slot % NSTAGE;
         const uint32_t round = slot / NSTAGE;
@@ -350,6 +364,11 @@ __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const 
         const uint32_t in_bytes = (uint32_t)((a1 - a0) * 4);
         const uint32_t out_bytes = (uint32_t)((b1 - b0) * 4);
         const uint32_t et_bytes = n_edges * 16;
+        // the stage's box records are refreshed only when its job changes
+        const int held = __shfl_sync(0xffffffffu, stage_job, stage);
+        const uint32_t box_bytes =
+            (MAXJ != 1 && held != jb) ? J.C * (uint32_t)(kBoxRecFloats * 4) : 0u;
+        if (lane == stage) stage_job = jb;
         if (lane == 0) {
           StageHdr* h = reinterpret_cast<StageHdr*>(sb);
           h->job = jb;
@@ -360,11 +379,14 @@ __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const 
           h->out_shift = (int)(o0 - b0);
           h->e_first = d.e_first;
           h->end = 0;
-          mbar_arrive_expect_tx(&full[stage], et_bytes + 4 * in_bytes + 4 * out_bytes);
+          mbar_arrive_expect_tx(&full[stage], et_bytes + 4 * in_bytes + 4 * out_bytes + box_bytes);
         }
         __syncwarp();
         if (lane == 0) {
           bulk_g2s(sb + kStageEtabOff, J.etab + d.etab, et_bytes, &full[stage]);
+        } else if (lane == 9) {
+          if (box_bytes)
+            bulk_g2s(s_boxes + (size_t)stage * kBoxesPerPass * 6, J.boxes, box_bytes, &full[stage]);
         } else if (lane <= 4) {
           const int pl = lane - 1;
           bulk_g2s(sb + J.off_in + (size_t)pl * J.in_cap * 4, J.inner + pl * J.in_stride + a0,
@@ -456,10 +478,7 @@ __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const 
     const float* oy = ox + J.out_cap;
     const float* oz = oy + J.out_cap;
     const float* orad = oz + J.out_cap;
-    const float4* bx = MAXJ == 1 ? s_boxes
-                       : (hdr.job - job_lo < kBoxSlots
-                              ? s_boxes + (hdr.job - job_lo) * kBoxesPerPass * 6
-                              : reinterpret_cast<const float4*>(J.boxes));
+    const float4* bx = MAXJ == 1 ? s_boxes : s_boxes + (size_t)stage * kBoxesPerPass * 6;
     const int r_end = min((sub + 1) * RPI, ROUNDS);
     for (int rnd = sub * RPI; rnd < r_end; ++rnd) {
       const int base = 31 * rnd;
@@ -687,18 +706,24 @@ cudaError_t launch_box_prep(const BoxPrepParams& p, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template <int NSTAGE, int STAGE_BYTES>
+template <int MAXJ, int NSTAGE, int STAGE_BYTES>
 static size_t smem_bytes_t(uint32_t consumer_warps) {
-  return (size_t)NSTAGE * STAGE_BYTES + (2 * NSTAGE + 1) * sizeof(uint64_t) + 8 +
-         4 * (size_t)((NSTAGE + 3) & ~3) + 32 * sizeof(TileDesc) + 32 * sizeof(int) +
-         (size_t)kBoxSlots * kBoxesPerPass * kBoxRecFloats * sizeof(float) +
-         (size_t)consumer_warps * 4 * kPairQueue;
+  // mirrors the carve-up at the top of classify_kernel
+  constexpr int kBoxAreas = MAXJ == 1 ? 1 : NSTAGE;
+  constexpr size_t kOffFull = (size_t)NSTAGE * STAGE_BYTES;
+  constexpr size_t kOffCnt = kOffFull + (2 * NSTAGE + 1) * sizeof(uint64_t) + 8;
+  constexpr size_t kOffDesc = (kOffCnt + 4 * ((NSTAGE + 3) & ~3) + 15) & ~(size_t)15;
+  constexpr size_t kOffBoxes = (kOffDesc + 32 * sizeof(TileDesc) + 32 * sizeof(int) + 127) &
+                               ~(size_t)127;
+  constexpr size_t kOffQueues = kOffBoxes + (size_t)kBoxAreas * kBoxesPerPass * kBoxRecFloats * 4;
+  return kOffQueues + (size_t)consumer_warps * 4 * kPairQueue;
 }
 
 size_t classify_smem_bytes(int variant, uint32_t consumer_warps) {
+  // the batched kernel's (larger) footprint, which bounds both
   switch (variant) {
 #define RGG_VARIANT(id, ns, sb, rd, rpi) \
-  case id: return smem_bytes_t<ns, sb>(consumer_warps);
+  case id: return smem_bytes_t<kMaxJobs, ns, sb>(consumer_warps);
     RGG_VARIANTS(RGG_VARIANT)
 #undef RGG_VARIANT
     default: return 0;
@@ -709,7 +734,7 @@ template <int MAXJ, int NSTAGE, int STAGE_BYTES, int ROUNDS, int RPI>
 static cudaError_t launch_classify_v(const ClassifyParams<MAXJ>& p, const ClassifyLaunch& lc,
                                      cudaStream_t s) {
   auto kern = classify_kernel<MAXJ, NSTAGE, STAGE_BYTES, ROUNDS, RPI>;
-  const size_t smem = smem_bytes_t<NSTAGE, STAGE_BYTES>(lc.consumer_warps);
+  const size_t smem = smem_bytes_t<MAXJ, NSTAGE, STAGE_BYTES>(lc.consumer_warps);
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
   kern<<<lc.grid, 32 * (1 + lc.consumer_warps), smem, s>>>(p);

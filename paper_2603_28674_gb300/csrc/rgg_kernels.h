@@ -12,11 +12,11 @@ namespace rgg {
 // Compiled shapes of the streaming pipeline: (id, stages in the shared-memory
 // ring, bytes per stage, rounds of 31 samples per tile, rounds per work item).
 // Each stage holds one tile: header, accumulators, edge table, inner and
-// outer record planes.
+// outer record planes; beside it, 3 KB for the tile's job's box records.
 #define RGG_VARIANTS(X)             \
-  X(0, 20, 10 * 1024, 3, 1)        \
+  X(0, 14, 10 * 1024, 3, 1)        \
   X(1, 7, 28 * 1024, 9, 1)         \
-  X(2, 6, 34 * 1024, 11, 1)        \
+  X(2, 6, 33 * 1024, 10, 1)        \
   X(3, 5, 40 * 1024, 13, 1)        \
   X(4, 4, 51 * 1024, 17, 1)        \
   X(5, 3, 69 * 1024, 23, 1)        \
