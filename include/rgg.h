@@ -259,7 +259,7 @@ int rgg_kernel_time(rgg_roadmap_t r, double* classify_ms, double* merge_ms, uint
 /* Launch shape of the streaming classify kernel: `variant` picks one of the
  * compiled pipeline shapes (shared-memory ring depth x stage size x rounds of
  * 31 configurations per tile; RGG_NUM_VARIANTS in all, 0 = smallest tiles,
- * 4 the default) and `consumer_warps` the warps per CTA that test records
+ * 5 the default) and `consumer_warps` the warps per CTA that test records
  * (0 = default 24; 1..27).  With edges present the tiles are rebuilt for the new shape (the
  * call synchronises the device).  Roadmaps classified together by
  * rgg_classify_many must share the variant.  RGG_ERR_INVALID for an

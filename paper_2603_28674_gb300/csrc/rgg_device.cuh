@@ -27,7 +27,7 @@ constexpr int kMaxJobs = 128;          // roadmaps per batched launch
 constexpr int kBoxesPerPass = 32;      // moved boxes per streaming pass (one mask word)
 constexpr int kBoxRecFloats = 24;      // derived box record, 6 x float4 = 96 B
 constexpr int kStageHdrBytes = 32;
-constexpr int kAccMax = 64;            // per-stage accumulator entries (edges per tile)
+constexpr int kAccMax = 96;            // per-stage accumulator entries (edges per tile)
 constexpr int kStageAccOff = kStageHdrBytes;                 // hit[kAccMax], touch[kAccMax]
 constexpr int kStageEtabOff = kStageAccOff + 8 * kAccMax;    // edge table
 constexpr int kMaxTileEdges = kAccMax;

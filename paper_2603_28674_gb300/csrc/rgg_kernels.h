@@ -22,7 +22,7 @@ namespace rgg {
   X(5, 3, 69 * 1024, 23, 1)        \
   X(6, 4, 51 * 1024, 16, 2)
 constexpr int kNumVariants = 7;
-constexpr int kDefaultVariant = 4;
+constexpr int kDefaultVariant = 5;
 constexpr uint32_t kDefaultConsumerWarps = 24;
 constexpr int kMaxClassifyThreads = 896;  // producer warp + up to 27 consumer warps
 struct VariantShape {

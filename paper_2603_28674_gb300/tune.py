@@ -19,7 +19,7 @@ import json
 import numpy as np
 
 
-def sweep(workload: str = "7dof", steps: int = 20, warps=(12, 16, 20, 24, 28), variants=None,
+def sweep(workload: str = "7dof", steps: int = 20, warps=(16, 20, 24, 27), variants=None,
           log=print):
     import torch
 
