@@ -192,23 +192,23 @@ def algorithmic_bytes(info: dict, moved: int) -> int:
 def oracle_rate(sc, seconds: float, seed: int = 0):
     """Edges/s of the FP64 oracle classifying a random sample of the
     workload's edges against the boxes moved in one update, on all host
-    cores.  The sample grows until it takes about `seconds`."""
+    cores: a short calibration run, then runs sized to fill `seconds`."""
     import oracle
     rm = sc.roadmap
     up = sc.updates[0]
     rng = np.random.default_rng(seed)
-    n = 64
-    total_e, total_t = 0, 0.0
-    while True:
+    total_e, total_t, n = 0, 0.0, 256
+    for _ in range(3):
         idx = rng.choice(rm.num_edges, size=min(n, rm.num_edges), replace=False)
         t0 = time.perf_counter()
         oracle.classify(rm.robot, rm.q_from[idx], rm.q_to[idx], rm.step, up.poses)
         dt = time.perf_counter() - t0
         total_e += idx.size
         total_t += dt
-        if total_t >= seconds or idx.size == rm.num_edges:
+        left = seconds - total_t
+        if left <= 0.1 * seconds or idx.size == rm.num_edges:
             break
-        n = int(min(rm.num_edges, max(n * 2, idx.size * (seconds - total_t) / max(dt, 1e-3))))
+        n = int(min(rm.num_edges, max(64, idx.size * left / max(dt, 1e-4))))
     return total_e / total_t, total_e, total_t, oracle.max_threads()
 
 
