@@ -49,8 +49,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="large",
-                    choices=["large", "7dof", "planar", "batched"])
+                    choices=["large", "7dof", "planar", "batched", "serve"])
     ap.add_argument("--roadmaps", type=int, default=128, help="batched workload: roadmaps")
+    ap.add_argument("--serve-seconds", type=float, default=3.0,
+                    help="serve workload: seconds of Poisson arrivals at 2000 requests/s")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     return ap.parse_args()
@@ -61,6 +63,18 @@ def make_scene(name: str, n_updates: int):
         return W.workload_large(n_updates=n_updates)
     if name == "7dof":
         return W.workload_7dof(n_updates=n_updates)
+    if name == "batched":
+        # the oracle's sample: the largest roadmap of the batch, its own updates
+        scenes = W.workload_batched(n_updates=max(1, min(n_updates, 8)))
+        return max(scenes, key=lambda x: x.roadmap.num_edges)
+    if name == "serve":
+        # the oracle's sample: a ~200k-edge resident roadmap and the updates
+        # the request stream sends it
+        scenes, reqs = W.workload_serving(duration_s=2.0)
+        k = len(scenes) - 1
+        ups = [q.update for q in reqs if q.roadmap == k][:max(1, n_updates)]
+        sc = scenes[k]
+        return W.Scene(sc.name, sc.roadmap, sc.boxes, ups)
     return W.workload_planar(n_updates=n_updates)
 
 
@@ -69,7 +83,9 @@ def workload_config(name: str, sc) -> dict:
     moved = len(sc.updates[0].ids) if sc.updates else 0
     cfg = {
         "workload": {"large": "large single roadmap", "7dof": "7-DOF 10k-node roadmap",
-                     "planar": "planar 3-link 500-node roadmap"}[name],
+                     "planar": "planar 3-link 500-node roadmap",
+                     "batched": "largest roadmap of the 128-roadmap batch",
+                     "serve": "one ~200k-edge roadmap of the serving set"}[name],
         "robot": f"{rm.robot.num_links}-link DH arm, {rm.robot.inner_per_link} inner spheres/link",
         "edges": rm.num_edges,
         "step_rad": rm.step,
@@ -486,12 +502,76 @@ def run_batched(args):
     return 0
 
 
+def run_serve(args):
+    """Workload 5: a Poisson stream of obstacle-update requests against eight
+    resident roadmaps, served with continuous batching and, for comparison,
+    one request per classify launch.  Each mode starts from the same box
+    state; the final labels of every roadmap must agree between the modes."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2603_28674_gb300 import build
+    build.build()
+    from paper_2603_28674_gb300 import serve as SV
+    scenes, reqs = W.workload_serving(duration_s=args.serve_seconds)
+    srv = SV.Server(device=0)
+    for sc in scenes:
+        rm = sc.roadmap
+        srv.add_roadmap(rm.robot, rm.q_from, rm.q_to, rm.step, np.arange(sc.boxes.count),
+                        sc.boxes.poses())
+    requests = [SV.ServeRequest(q.arrival_s, q.roadmap, q.update.ids.astype(np.uint32),
+                                q.update.poses.astype(np.float32)) for q in reqs]
+    init = [sc.boxes.poses().astype(np.float32) for sc in scenes]
+
+    def reset():
+        for r, p in zip(srv.roadmaps, init):
+            r.update_obstacles(np.arange(len(p)), p, srv.stream)
+            r.classify(srv.stream)
+        srv.stream.synchronize()
+
+    n_warm = min(len(requests), 100 * max(args.warmup, 3))
+    warm = [SV.ServeRequest(q.arrival_s - requests[0].arrival_s, q.roadmap, q.ids, q.poses)
+            for q in requests[:n_warm]]
+    out, final = {}, {}
+    with ClockSampler(0) as clocks:
+        for mode in ("one_at_a_time", "batched"):
+            srv.serve(warm, mode)
+            reset()
+            out[mode] = srv.serve(requests, mode)
+            final[mode] = [srv.labels(k) for k in range(len(srv.roadmaps))]
+    same = all(np.array_equal(a, b) for a, b in zip(final["batched"], final["one_at_a_time"]))
+    b, p = out["batched"], out["one_at_a_time"]
+    infos = [r.info() for r in srv.roadmaps]
+    line = {
+        "metric": METRIC, "value": b["edges_per_s"], "unit": "request-edges/s", "n_gpus": 1,
+        "steps": len(requests), "warmup": n_warm,
+        "ms_per_step": 1e3 / b["throughput_req_s"] if b["throughput_req_s"] else None,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": f"serving {len(scenes)} resident roadmaps",
+                   "edges": [i["num_edges"] for i in infos],
+                   "record_gb": sum(i["record_bytes"] for i in infos) / 1e9,
+                   "offered_req_s": b["offered_req_s"], "boxes_per_roadmap": scenes[0].boxes.count,
+                   "moved_per_request": "1-8", "duration_s": args.serve_seconds,
+                   "l2": "records > L2; no flush needed"},
+        "serving": {"batched": b, "one_at_a_time": p,
+                    "p99_speedup": p["latency_ms_p99"] / b["latency_ms_p99"],
+                    "throughput_speedup": b["throughput_req_s"] / p["throughput_req_s"],
+                    "final_labels_identical": bool(same)},
+        "clocks": clocks.summary(),
+    }
+    srv.close()
+    print(json.dumps(line))
+    return 0 if same else 1
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batched":
         return run_batched(args)
+    if args.workload == "serve":
+        return run_serve(args)
     return run_gpu(args)
 
 

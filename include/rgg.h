@@ -70,7 +70,8 @@ enum rgg_status {
   RGG_ERR_CUDA = -3,     /* a CUDA runtime call failed                     */
   RGG_ERR_TIMEOUT = -4,  /* a bounded device-side wait ran out             */
   RGG_ERR_STATE = -5,    /* call not valid in the roadmap's current state  */
-  RGG_ERR_CAPACITY = -6  /* larger than rgg_classify_noalloc's fixed scratch */
+  RGG_ERR_CAPACITY = -6  /* over a fixed capacity: rgg_classify_noalloc's     */
+                         /* scratch, pending entries or open requests        */
 };
 
 /* Edge labels (Sec. 4.1): valid, unknown, invalid. */
@@ -83,6 +84,8 @@ enum {
   RGG_MAX_OBSTACLES = 4096,    /* max_obstacles                                */
   RGG_BOXES_PER_PASS = 32,     /* moved boxes tested per streaming pass        */
   RGG_NUM_VARIANTS = 7,        /* compiled pipeline shapes (rgg_set_launch_shape) */
+  RGG_MAX_REQUESTS = 64,       /* open requests per roadmap (rgg_update_request) */
+  RGG_PENDING_EXTRA = 4096,    /* pending entries beyond max_obstacles          */
   RGG_NOALLOC_MAX_EDGES = 131072,  /* rgg_classify_noalloc: edges per call          */
   RGG_NOALLOC_MAX_TILES = 16384    /* rgg_classify_noalloc: tiles of up to 527      */
                                    /* configurations x links per call               */
@@ -120,8 +123,10 @@ typedef struct {
   uint32_t num_links, inner_per_link, max_obstacles, mask_words;
   uint32_t tile_samples;    /* configurations per streaming tile                  */
   uint64_t num_tiles;
-  uint32_t pending_boxes;   /* moved boxes not yet classified                     */
+  uint32_t pending_boxes;   /* pending entries (moved boxes not yet classified)   */
   uint32_t grid_ctas;       /* CTAs of the classify launch                        */
+  uint32_t open_requests;   /* request handles in use (rgg_update_request)        */
+  uint32_t pending_capacity;/* max_obstacles + RGG_PENDING_EXTRA                  */
 } rgg_info;
 
 /* ------------------------------------------------------------------------ */
@@ -199,6 +204,46 @@ int rgg_build_edges(rgg_roadmap_t r, const rgg_robot_desc* robot, uint64_t num_e
  * RGG_ERR_INVALID on a bad id or pose (nothing is changed). */
 int rgg_update_obstacles(rgg_roadmap_t r, uint32_t n_changed, const uint32_t* ids,
                          const float* pose, int src_is_device, void* stream);
+/* Pending entries: the moved boxes wait, in the order they were moved, as
+ * entries (box id, staged pose).  A move of a box that already has an entry
+ * since the last request boundary (see rgg_update_request) replaces that
+ * entry's pose; otherwise it appends an entry.  At most max_obstacles +
+ * RGG_PENDING_EXTRA entries wait at once: a call that would exceed it
+ * returns RGG_ERR_CAPACITY and changes nothing (classify first). */
+
+/* A versioned move: the same as rgg_update_obstacles, and in addition the
+ * labels as they stand once this move (and every earlier one) is applied
+ * are kept as a snapshot under a request handle.  Several requests on one
+ * roadmap may wait together: the next rgg_classify (or rgg_classify_many)
+ * applies their moves in order in the same streaming passes, and request h's
+ * snapshot equals the labels that classifying after h's own moves alone
+ * would give.  (Sec. 4.3's online update, one obstacle change per request;
+ * the paper has no request handles: they let a server fuse the updates of
+ * many requests into one pass.)
+ *   n_changed    >= 1 ids (same rules as rgg_update_obstacles)
+ *   *handle      receives the request handle, 0 .. RGG_MAX_REQUESTS-1
+ * The first request after edges are set allocates RGG_MAX_REQUESTS x N bytes
+ * of snapshot memory.  RGG_ERR_STATE before edges exist; RGG_ERR_CAPACITY
+ * when all RGG_MAX_REQUESTS handles are open or the pending entries are
+ * full; RGG_ERR_INVALID as for rgg_update_obstacles.  Replacing the edges
+ * (rgg_upload_edges / rgg_build_edges) closes every open handle. */
+int rgg_update_request(rgg_roadmap_t r, uint32_t n_changed, const uint32_t* ids,
+                       const float* pose, int src_is_device, uint32_t* handle, void* stream);
+
+/* Copy request `handle`'s snapshot labels [first, first+count) to `out` (host,
+ * device or asynchronous page-locked host, as in rgg_fetch_labels).  Valid once a classify call has been
+ * enqueued after the request: the copy is ordered after it on `stream`.
+ * RGG_ERR_STATE if the handle is not open or its classify has not been
+ * enqueued yet. */
+int rgg_fetch_request_labels(rgg_roadmap_t r, uint32_t handle, uint8_t* out, uint64_t first,
+                             uint64_t count, int dst_is_device, void* stream);
+
+/* Close a request handle whose classify has been enqueued, so that a later
+ * request may reuse its snapshot memory.  Host-side only: a later classify
+ * that reuses the handle overwrites the snapshot in stream order, so enqueue
+ * (or finish) every copy of it before that classify on the same stream.
+ * RGG_ERR_STATE if the handle is not open or not yet classified. */
+int rgg_release_request(rgg_roadmap_t r, uint32_t handle);
 
 /* Classify every edge against the pending moved boxes and merge with the
  * per-edge box sets, so that each label equals the label against the
@@ -215,9 +260,12 @@ int rgg_classify(rgg_roadmap_t r, void* stream);
 int rgg_classify_many(rgg_roadmap_t* roadmaps, uint32_t n, void* stream);
 /* (All roadmaps must also share the launch variant, see rgg_set_launch_shape.) */
 
-/* Copy labels [first, first+count) (uint8, enum rgg_label) to `out`, a host
- * (dst_is_device = 0) or device (1) buffer.  For a host destination the call
- * waits for the stream and then reports any latched device error.
+/* Copy labels [first, first+count) (uint8, enum rgg_label) to `out`:
+ *   dst_is_device = 0  a host buffer: the call waits for the stream and then
+ *                      reports any latched device error;
+ *                   1  a device buffer (asynchronous);
+ *                   2  a page-locked host buffer, asynchronous: the caller
+ *                      waits on the stream and then calls rgg_check_status.
  * RGG_ERR_INVALID if the range exceeds the edge count. */
 int rgg_fetch_labels(rgg_roadmap_t r, uint8_t* out, uint64_t first, uint64_t count,
                      int dst_is_device, void* stream);

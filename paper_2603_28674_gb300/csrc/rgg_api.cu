@@ -105,6 +105,7 @@ struct EdgeState {
   uint32_t* d_counts = nullptr;
   uint8_t* d_labels = nullptr;
   uint32_t* d_edge_acc = nullptr;
+  uint8_t* d_hist = nullptr;   // [RGG_MAX_REQUESTS][N] request snapshots, allocated on first use
   uint64_t device_bytes = 0;
 
   void release() {
@@ -118,6 +119,7 @@ struct EdgeState {
     cudaFree(d_counts);
     cudaFree(d_labels);
     cudaFree(d_edge_acc);
+    cudaFree(d_hist);
     *this = EdgeState();
   }
 };
@@ -134,10 +136,24 @@ struct rgg_roadmap {
   bool has_edges = false;
   EdgeState es;
   float* d_table = nullptr;    // [M][16] box poses
+  float* d_stage = nullptr;    // [stage_rows][16] staged pose of each pending entry
+  uint32_t stage_rows = 0;
   float* d_changed = nullptr;  // [32][24] derived records of the current pass
   int* d_status = nullptr;          // [0] status word, [1] classify work counter
-  std::vector<uint8_t> present, is_pending;
-  std::vector<uint32_t> pending;
+  std::vector<uint8_t> present;
+  // Pending entries in application order.  Entry i stages its pose in row
+  // `row` of d_stage; `snap` >= 0 marks the last entry of a request whose
+  // snapshot is taken right after it.  The trailing run is the entries after
+  // the last snapshot; within it a box has at most one entry (run_idx[b]).
+  struct Entry {
+    uint32_t id, row;
+    int32_t snap;
+  };
+  std::vector<Entry> pending;
+  std::vector<int32_t> run_idx;
+  size_t run_start = 0;
+  // request handles: 0 free, 1 waiting for a classify, 2 classified
+  std::vector<uint8_t> req_state;
   // kernel timing: events before classify, between classify and merge, after merge
   bool timing = false;
   std::vector<std::array<cudaEvent_t, 3>> events;
@@ -286,19 +302,41 @@ int alloc_edges(rgg_roadmap* r, EdgeState* es, uint64_t N, std::vector<uint64_t>
   return RGG_OK;
 }
 
-// Swap in freshly built edges: labels GREEN, box sets empty, every present
-// box pending so that the next classify tests it against the new edges.
-void install_edges(rgg_roadmap* r, EdgeState&& es) {
+void clear_pending(rgg_roadmap* r) {
+  for (size_t i = r->run_start; i < r->pending.size(); ++i) r->run_idx[r->pending[i].id] = -1;
+  r->pending.clear();
+  r->run_start = 0;
+}
+
+// Swap in freshly built edges: labels GREEN, box sets empty, open requests
+// closed, and every present box pending (its staged pose copied from the
+// box table) so that the next classify tests it against the new edges.
+int install_edges(rgg_roadmap* r, EdgeState&& es, cudaStream_t s) {
   r->es.release();
   r->es = std::move(es);
   r->has_edges = true;
-  r->pending.clear();
-  std::fill(r->is_pending.begin(), r->is_pending.end(), 0);
-  for (uint32_t b = 0; b < r->M; ++b)
-    if (r->present[b]) {
-      r->pending.push_back(b);
-      r->is_pending[b] = 1;
+  clear_pending(r);
+  std::fill(r->req_state.begin(), r->req_state.end(), 0);
+  BoxUpdateParams p;
+  p.n = 0;
+  p.table = r->d_table;
+  p.stage = r->d_stage;
+  p.dev_pose = nullptr;
+  p.from_table = 1;
+  for (uint32_t b = 0; b < r->M; ++b) {
+    if (!r->present[b]) continue;
+    const uint32_t row = (uint32_t)r->pending.size();
+    r->run_idx[b] = (int32_t)row;
+    r->pending.push_back({b, row, -1});
+    p.ids[p.n] = b;
+    p.rows[p.n] = row;
+    if (++p.n == kMaxUpdateBoxes) {
+      RGG_CK(launch_box_update(p, s));
+      p.n = 0;
     }
+  }
+  RGG_CK(launch_box_update(p, s));
+  return RGG_OK;
 }
 
 // n_e >= 2 per edge; L*n_e and the edge count fit the 32-bit tile tables.
@@ -376,7 +414,10 @@ ClassifyJob make_job(rgg_roadmap* r, uint32_t C, uint64_t tile_base) {
   return j;
 }
 
-MergeJob make_merge_job(rgg_roadmap* r, const uint32_t* ids, uint32_t C, uint64_t edge_base) {
+// Merge job of entries [lo, lo+C) of the pending list.  `ordered` applies
+// them one by one and takes the requests' snapshots; otherwise their ids are
+// distinct and ascending.
+MergeJob make_merge_job(rgg_roadmap* r, size_t lo, uint32_t C, bool ordered, uint64_t edge_base) {
   MergeJob m{};
   const EdgeState& es = r->es;
   m.red = es.d_red;
@@ -388,7 +429,16 @@ MergeJob make_merge_job(rgg_roadmap* r, const uint32_t* ids, uint32_t C, uint64_
   m.edge_base = edge_base;
   m.Wm = r->Wm;
   m.C = C;
-  for (uint32_t b = 0; b < C; ++b) m.ids[b] = ids[b];
+  m.ordered = ordered ? 1u : 0u;
+  m.hist = es.d_hist;
+  for (uint32_t b = 0; b < C; ++b) {
+    const auto& en = r->pending[lo + b];
+    m.ids[b] = en.id;
+    if (en.snap >= 0) {
+      m.snap_mask |= 1u << b;
+      m.snap_slot[b] = (uint8_t)en.snap;
+    }
+  }
   return m;
 }
 
@@ -405,7 +455,7 @@ const char* rgg_status_string(int s) {
     case RGG_ERR_CUDA: return "CUDA runtime error";
     case RGG_ERR_TIMEOUT: return "device-side wait timed out";
     case RGG_ERR_STATE: return "call not valid in the current state";
-    case RGG_ERR_CAPACITY: return "larger than the no-alloc pass's fixed scratch";
+    case RGG_ERR_CAPACITY: return "over a fixed capacity (no-alloc scratch, pending entries, open requests)";
     default: return "unknown status";
   }
 }
@@ -435,15 +485,19 @@ int rgg_roadmap_create(const rgg_roadmap_desc* desc, rgg_roadmap_t* out) {
   r->Wm = (r->M + 31) / 32;
   r->margin = desc->margin_m;
   r->present.assign(r->M, 0);
-  r->is_pending.assign(r->M, 0);
+  r->run_idx.assign(r->M, -1);
+  r->req_state.assign(RGG_MAX_REQUESTS, 0);
+  r->stage_rows = r->M + RGG_PENDING_EXTRA;
   cudaError_t e = cudaDeviceGetAttribute(&r->num_sms, cudaDevAttrMultiProcessorCount, r->device);
   if (e == cudaSuccess) e = dalloc(&r->d_table, (size_t)r->M * 16);
+  if (e == cudaSuccess) e = dalloc(&r->d_stage, (size_t)r->stage_rows * 16);
   if (e == cudaSuccess) e = dalloc(&r->d_changed, (size_t)kBoxesPerPass * kBoxRecFloats);
   if (e == cudaSuccess) e = dalloc(&r->d_status, 4);
   if (e == cudaSuccess) e = cudaMemset(r->d_table, 0, (size_t)r->M * 16 * sizeof(float));
   if (e == cudaSuccess) e = cudaMemset(r->d_status, 0, 4 * sizeof(int));
   if (e != cudaSuccess) {
     cudaFree(r->d_table);
+    cudaFree(r->d_stage);
     cudaFree(r->d_changed);
     cudaFree(r->d_status);
     delete r;
@@ -459,6 +513,7 @@ int rgg_roadmap_destroy(rgg_roadmap_t r) {
   cudaDeviceSynchronize();
   r->es.release();
   cudaFree(r->d_table);
+  cudaFree(r->d_stage);
   cudaFree(r->d_changed);
   cudaFree(r->d_status);
   for (auto& ev : r->events)
@@ -500,8 +555,7 @@ int rgg_upload_edges(rgg_roadmap_t r, uint64_t num_edges, const uint64_t* sample
     es.release();
     return cuda_status(e);
   }
-  install_edges(r, std::move(es));
-  return RGG_OK;
+  return install_edges(r, std::move(es), s);
 }
 
 int rgg_build_edges(rgg_roadmap_t r, const rgg_robot_desc* robot, uint64_t num_edges,
@@ -583,7 +637,48 @@ int rgg_build_edges(rgg_roadmap_t r, const rgg_robot_desc* robot, uint64_t num_e
     es.release();
     return cuda_status(e);
   }
-  install_edges(r, std::move(es));
+  return install_edges(r, std::move(es), s);
+}
+
+// Checks a move's ids and host poses; counts the entries it would append.
+static int check_moves(rgg_roadmap_t r, uint32_t n, const uint32_t* ids, const float* pose,
+                       int src_is_device, uint32_t* new_entries) {
+  std::vector<uint8_t> seen(r->M, 0);
+  uint32_t fresh = 0;
+  for (uint32_t i = 0; i < n; ++i) {
+    if (ids[i] >= r->M || seen[ids[i]]) return RGG_ERR_INVALID;
+    seen[ids[i]] = 1;
+    if (!src_is_device && !valid_pose(pose + 15 * (size_t)i)) return RGG_ERR_INVALID;
+    if (r->run_idx[ids[i]] < 0) ++fresh;
+  }
+  *new_entries = fresh;
+  return RGG_OK;
+}
+
+// Writes the poses into the box table and into the staging rows of the
+// boxes' entries in the trailing run (appending entries where needed).
+static int stage_moves(rgg_roadmap_t r, uint32_t n, const uint32_t* ids, const float* pose,
+                       int src_is_device, cudaStream_t s) {
+  for (uint32_t base = 0; base < n; base += kMaxUpdateBoxes) {
+    BoxUpdateParams p;
+    p.n = std::min(kMaxUpdateBoxes, n - base);
+    p.table = r->d_table;
+    p.stage = r->d_stage;
+    p.from_table = 0;
+    p.dev_pose = src_is_device ? pose + 15 * (size_t)base : nullptr;
+    for (uint32_t i = 0; i < p.n; ++i) {
+      const uint32_t b = ids[base + i];
+      if (r->run_idx[b] < 0) {
+        r->run_idx[b] = (int32_t)r->pending.size();
+        r->pending.push_back({b, (uint32_t)r->pending.size(), -1});
+      }
+      p.ids[i] = b;
+      p.rows[i] = r->pending[r->run_idx[b]].row;
+      r->present[b] = 1;
+      if (!src_is_device) std::memcpy(p.pose[i], pose + 15 * (size_t)(base + i), 15 * sizeof(float));
+    }
+    RGG_CK(launch_box_update(p, s));
+  }
   return RGG_OK;
 }
 
@@ -592,45 +687,60 @@ int rgg_update_obstacles(rgg_roadmap_t r, uint32_t n_changed, const uint32_t* id
   if (!r) return RGG_ERR_INVALID;
   if (n_changed == 0) return RGG_OK;
   if (!ids || !pose) return RGG_ERR_INVALID;
-  std::vector<uint8_t> seen(r->M, 0);
-  for (uint32_t i = 0; i < n_changed; ++i) {
-    if (ids[i] >= r->M || seen[ids[i]]) return RGG_ERR_INVALID;
-    seen[ids[i]] = 1;
-    if (!src_is_device && !valid_pose(pose + 15 * (size_t)i)) return RGG_ERR_INVALID;
-  }
+  uint32_t fresh = 0;
+  int rc = check_moves(r, n_changed, ids, pose, src_is_device, &fresh);
+  if (rc != RGG_OK) return rc;
+  if (r->pending.size() + fresh > r->stage_rows) return RGG_ERR_CAPACITY;
   DeviceGuard g(r->device);
   if (!g.ok) return RGG_ERR_CUDA;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  for (uint32_t base = 0; base < n_changed; base += kMaxUpdateBoxes) {
-    BoxUpdateParams p;
-    p.n = std::min(kMaxUpdateBoxes, n_changed - base);
-    p.table = r->d_table;
-    p.dev_pose = src_is_device ? pose + 15 * (size_t)base : nullptr;
-    for (uint32_t i = 0; i < p.n; ++i) {
-      p.ids[i] = ids[base + i];
-      if (!src_is_device) std::memcpy(p.pose[i], pose + 15 * (size_t)(base + i), 15 * sizeof(float));
-    }
-    RGG_CK(launch_box_update(p, s));
+  return stage_moves(r, n_changed, ids, pose, src_is_device, static_cast<cudaStream_t>(stream));
+}
+
+int rgg_update_request(rgg_roadmap_t r, uint32_t n_changed, const uint32_t* ids,
+                       const float* pose, int src_is_device, uint32_t* handle, void* stream) {
+  if (!r || !handle || n_changed == 0 || !ids || !pose) return RGG_ERR_INVALID;
+  if (!r->has_edges) return RGG_ERR_STATE;
+  uint32_t fresh = 0;
+  int rc = check_moves(r, n_changed, ids, pose, src_is_device, &fresh);
+  if (rc != RGG_OK) return rc;
+  if (r->pending.size() + fresh > r->stage_rows) return RGG_ERR_CAPACITY;
+  uint32_t h = 0;
+  while (h < RGG_MAX_REQUESTS && r->req_state[h] != 0) ++h;
+  if (h == RGG_MAX_REQUESTS) return RGG_ERR_CAPACITY;
+  DeviceGuard g(r->device);
+  if (!g.ok) return RGG_ERR_CUDA;
+  EdgeState& es = r->es;
+  if (!es.d_hist && es.N) {
+    cudaError_t e = dalloc(&es.d_hist, (size_t)RGG_MAX_REQUESTS * es.N);
+    if (e != cudaSuccess) return cuda_status(e);
+    es.device_bytes += (uint64_t)RGG_MAX_REQUESTS * es.N;
   }
-  for (uint32_t i = 0; i < n_changed; ++i) {
-    const uint32_t b = ids[i];
-    r->present[b] = 1;
-    if (!r->is_pending[b]) {
-      r->is_pending[b] = 1;
-      r->pending.push_back(b);
-    }
-  }
+  rc = stage_moves(r, n_changed, ids, pose, src_is_device, static_cast<cudaStream_t>(stream));
+  if (rc != RGG_OK) return rc;
+  // the request ends the trailing run: its snapshot follows the run's last entry
+  r->pending.back().snap = (int32_t)h;
+  for (size_t i = r->run_start; i < r->pending.size(); ++i) r->run_idx[r->pending[i].id] = -1;
+  r->run_start = r->pending.size();
+  r->req_state[h] = 1;
+  *handle = h;
   return RGG_OK;
 }
 
-// One streaming pass per group of <= 32 boxes; for several roadmaps, pass p
-// of every roadmap that has one goes into the same persistent launch.  The
-// pending boxes are sorted so that each pass's ids ascend (the merge kernel
-// relies on it).
+// One streaming pass per group of <= 32 pending entries; for several
+// roadmaps, pass p of every roadmap that has one goes into the same
+// persistent launch.  Without requests the entries (distinct boxes) are
+// sorted so that each pass's ids ascend, for the merge kernel's word-grouped
+// update; with requests they keep their order and merge one by one.
 static int classify_group(rgg_roadmap_t* rs, uint32_t n, cudaStream_t s) {
   uint32_t max_passes = 0;
+  std::vector<uint8_t> ordered(n, 0);
   for (uint32_t i = 0; i < n; ++i) {
-    std::sort(rs[i]->pending.begin(), rs[i]->pending.end());
+    auto& pend = rs[i]->pending;
+    for (const auto& en : pend)
+      if (en.snap >= 0) ordered[i] = 1;
+    if (!ordered[i])
+      std::sort(pend.begin(), pend.end(), [](const rgg_roadmap::Entry& a,
+                                             const rgg_roadmap::Entry& b) { return a.id < b.id; });
     max_passes = std::max<uint32_t>(
         max_passes, (uint32_t)((rs[i]->pending.size() + kBoxesPerPass - 1) / kBoxesPerPass));
   }
@@ -655,15 +765,17 @@ static int classify_group(rgg_roadmap_t* rs, uint32_t n, cudaStream_t s) {
       const size_t lo = (size_t)pass * kBoxesPerPass;
       if (lo >= r->pending.size()) continue;
       const uint32_t C = (uint32_t)std::min<size_t>(kBoxesPerPass, r->pending.size() - lo);
-      const uint32_t* ids = r->pending.data() + lo;
       BoxPrepJob& pj = bp.job[bp.njobs++];
-      pj.table = r->d_table;
+      pj.stage = r->d_stage;
       pj.out = r->d_changed;
       pj.C = C;
-      for (uint32_t b = 0; b < C; ++b) pj.ids[b] = ids[b];
+      for (uint32_t b = 0; b < C; ++b) {
+        pj.ids[b] = r->pending[lo + b].id;
+        pj.rows[b] = (uint16_t)r->pending[lo + b].row;
+      }
       if (r->es.N == 0) continue;
       const ClassifyJob job = make_job(r, C, tiles);
-      const MergeJob mj = make_merge_job(r, ids, C, edges);
+      const MergeJob mj = make_merge_job(r, lo, C, ordered[i] != 0, edges);
       if (n == 1) {
         cp1.job[0] = job;
         mp1.job[0] = mj;
@@ -714,8 +826,9 @@ static int classify_group(rgg_roadmap_t* rs, uint32_t n, cudaStream_t s) {
     if (ev) RGG_CK(cudaEventRecord(ev[2], s));
   }
   for (uint32_t i = 0; i < n; ++i) {
-    for (uint32_t b : rs[i]->pending) rs[i]->is_pending[b] = 0;
-    rs[i]->pending.clear();
+    for (const auto& en : rs[i]->pending)
+      if (en.snap >= 0) rs[i]->req_state[en.snap] = 2;
+    clear_pending(rs[i]);
   }
   return RGG_OK;
 }
@@ -763,7 +876,7 @@ static int check_status_locked(rgg_roadmap_t r, cudaStream_t s) {
 
 int rgg_fetch_labels(rgg_roadmap_t r, uint8_t* out, uint64_t first, uint64_t count,
                      int dst_is_device, void* stream) {
-  if (!r || (!out && count)) return RGG_ERR_INVALID;
+  if (!r || (!out && count) || dst_is_device < 0 || dst_is_device > 2) return RGG_ERR_INVALID;
   if (!r->has_edges && count) return RGG_ERR_STATE;
   if (first > r->es.N || count > r->es.N - first) return RGG_ERR_INVALID;
   DeviceGuard g(r->device);
@@ -771,8 +884,32 @@ int rgg_fetch_labels(rgg_roadmap_t r, uint8_t* out, uint64_t first, uint64_t cou
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (count)
     RGG_CK(cudaMemcpyAsync(out, r->es.d_labels + first, count,
-                           dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
-  if (!dst_is_device) return check_status_locked(r, s);
+                           dst_is_device == 1 ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+  if (dst_is_device == 0) return check_status_locked(r, s);
+  return RGG_OK;
+}
+
+int rgg_fetch_request_labels(rgg_roadmap_t r, uint32_t handle, uint8_t* out, uint64_t first,
+                             uint64_t count, int dst_is_device, void* stream) {
+  if (!r || handle >= RGG_MAX_REQUESTS || (!out && count) || dst_is_device < 0 ||
+      dst_is_device > 2)
+    return RGG_ERR_INVALID;
+  if (!r->has_edges || r->req_state[handle] != 2) return RGG_ERR_STATE;
+  if (first > r->es.N || count > r->es.N - first) return RGG_ERR_INVALID;
+  DeviceGuard g(r->device);
+  if (!g.ok) return RGG_ERR_CUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (count)
+    RGG_CK(cudaMemcpyAsync(out, r->es.d_hist + (size_t)handle * r->es.N + first, count,
+                           dst_is_device == 1 ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+  if (dst_is_device == 0) return check_status_locked(r, s);
+  return RGG_OK;
+}
+
+int rgg_release_request(rgg_roadmap_t r, uint32_t handle) {
+  if (!r || handle >= RGG_MAX_REQUESTS) return RGG_ERR_INVALID;
+  if (r->req_state[handle] != 2) return RGG_ERR_STATE;
+  r->req_state[handle] = 0;
   return RGG_OK;
 }
 
@@ -832,7 +969,8 @@ int rgg_roadmap_info(rgg_roadmap_t r, rgg_info* out) {
   out->num_inner = es.n_inner;
   out->num_outer = es.n_outer;
   out->record_bytes = 16 * (es.n_inner + es.n_outer);
-  out->device_bytes = es.device_bytes + (uint64_t)r->M * 64 + kBoxesPerPass * kBoxRecFloats * 4 + 4;
+  out->device_bytes = es.device_bytes + (uint64_t)r->M * 64 + (uint64_t)r->stage_rows * 64 +
+                      kBoxesPerPass * kBoxRecFloats * 4 + 16;
   out->num_links = r->L;
   out->inner_per_link = r->K;
   out->max_obstacles = r->M;
@@ -840,6 +978,9 @@ int rgg_roadmap_info(rgg_roadmap_t r, rgg_info* out) {
   out->tile_samples = es.tiling.S;
   out->num_tiles = es.T;
   out->pending_boxes = (uint32_t)r->pending.size();
+  out->open_requests = (uint32_t)std::count_if(r->req_state.begin(), r->req_state.end(),
+                                                [](uint8_t x) { return x != 0; });
+  out->pending_capacity = r->stage_rows;
   out->grid_ctas = (uint32_t)std::min<uint64_t>(es.T, launch_ctas(r));
   return RGG_OK;
 }

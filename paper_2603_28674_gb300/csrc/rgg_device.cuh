@@ -100,7 +100,14 @@ struct MergeJob {
   uint64_t num_edges;
   uint64_t edge_base;     // first global thread index of this job
   uint32_t Wm, C;
-  uint32_t ids[kBoxesPerPass];  // box id of pass position p, ascending
+  uint32_t ids[kBoxesPerPass];  // box id of pass position p
+  // ordered == 0: ids ascend and are distinct (word-grouped update);
+  // ordered == 1: positions apply in order (a box may repeat), and after each
+  // position p in snap_mask the labels so far go to hist[snap_slot[p]][e]
+  uint32_t ordered;
+  uint32_t snap_mask;
+  uint8_t* hist;
+  uint8_t snap_slot[kBoxesPerPass];
 };
 
 template <int MAXJ>

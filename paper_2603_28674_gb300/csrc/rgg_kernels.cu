@@ -157,10 +157,20 @@ __global__ void __launch_bounds__(256) build_records_kernel(const __grid_constan
 __global__ void box_update_kernel(const __grid_constant__ BoxUpdateParams p) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= p.n) return;
+  float* srow = p.stage + 16 * (size_t)p.rows[i];
+  if (p.from_table) {
+    const float* src = p.table + 16 * (size_t)p.ids[i];
+    for (int c = 0; c < 16; ++c) srow[c] = src[c];
+    return;
+  }
   const float* src = p.dev_pose ? p.dev_pose + 15 * (size_t)i : p.pose[i];
   float* dst = p.table + 16 * (size_t)p.ids[i];
-  for (int c = 0; c < 15; ++c) dst[c] = src[c];
+  for (int c = 0; c < 15; ++c) {
+    dst[c] = src[c];
+    srow[c] = src[c];
+  }
   dst[15] = 0.0f;
+  srow[15] = 0.0f;
 }
 
 // Derived records (see rgg_device.cuh) from the box table, in FP64 then
@@ -171,7 +181,7 @@ __global__ void box_prep_kernel(const __grid_constant__ BoxPrepParams p) {
   const uint32_t b = threadIdx.x;
   if (b >= J.C) return;
   const uint32_t id = J.ids[b];
-  const float* row = J.table + 16 * (size_t)id;
+  const float* row = J.stage + 16 * (size_t)J.rows[b];
   const double c[3] = {row[0], row[1], row[2]};
   double R[9];
   for (int m = 0; m < 9; ++m) R[m] = row[3 + m];
@@ -623,10 +633,12 @@ __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const 
 // a6: merge the pass's bits into the per-edge box sets (Algorithm 1's
 // intersection lists) and relabel
 // ===========================================================================
-// One thread per edge.  The pass's box ids are ascending, so boxes sharing a
-// 32-bit mask word are consecutive and each touched word is read and written
-// once.  Per-edge counts of hitting and touching boxes give the label
-// without reading the untouched words.
+// One thread per edge.  Unordered passes have ascending, distinct box ids,
+// so boxes sharing a 32-bit mask word are consecutive and each touched word
+// is read and written once.  Ordered passes (pending requests) apply their
+// positions one at a time and store the label after each request's last
+// position into that request's snapshot row.  Per-edge counts of hitting and
+// touching boxes give the label without reading the untouched words.
 template <int MAXJ>
 __global__ void __launch_bounds__(256) merge_kernel(const __grid_constant__ MergeParams<MAXJ> P) {
   const uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
@@ -645,6 +657,30 @@ __global__ void __launch_bounds__(256) merge_kernel(const __grid_constant__ Merg
   int rc = (int)(cnt & 0xffffu), tc = (int)(cnt >> 16);
   uint32_t* red = J.red + e * J.Wm;
   uint32_t* tch = J.touch + e * J.Wm;
+  if (J.ordered) {
+    // positions in request order; a box may appear more than once, the later
+    // position replacing the earlier one's bits (its later pose)
+    for (uint32_t p = 0; p < J.C; ++p) {
+      const uint32_t w = J.ids[p] >> 5, bit = 1u << (J.ids[p] & 31);
+      const uint32_t r_old = red[w], t_old = tch[w];
+      const uint32_t r_new = ((acc.x >> p) & 1u) ? (r_old | bit) : (r_old & ~bit);
+      const uint32_t t_new = ((acc.y >> p) & 1u) ? (t_old | bit) : (t_old & ~bit);
+      if (r_new != r_old) {
+        red[w] = r_new;
+        rc += (r_new & bit) ? 1 : -1;
+      }
+      if (t_new != t_old) {
+        tch[w] = t_new;
+        tc += (t_new & bit) ? 1 : -1;
+      }
+      if ((J.snap_mask >> p) & 1u)
+        J.hist[(size_t)J.snap_slot[p] * J.num_edges + e] = rc > 0 ? 2 : (tc > 0 ? 1 : 0);
+    }
+    const uint32_t ncnt = (uint32_t)rc | ((uint32_t)tc << 16);
+    if (ncnt != cnt) J.counts[e] = ncnt;
+    J.labels[e] = rc > 0 ? 2 : (tc > 0 ? 1 : 0);
+    return;
+  }
   uint32_t cur = 0xffffffffu, r_old = 0, t_old = 0, r_new = 0, t_new = 0;
   for (uint32_t p = 0; p <= J.C; ++p) {
     const uint32_t w = p < J.C ? (J.ids[p] >> 5) : 0xfffffffeu;
@@ -770,6 +806,12 @@ static cudaError_t launch_merge_t(const MergeParams<MAXJ>& p, cudaStream_t s) {
   merge_kernel<MAXJ><<<(unsigned)((p.total_edges + blk - 1) / blk), blk, 0, s>>>(p);
   return cudaGetLastError();
 }
+
+// kernel parameters are limited to 32764 bytes
+static_assert(sizeof(MergeParams<kMaxJobs>) <= 32764, "merge parameters too large");
+static_assert(sizeof(BoxPrepParams) <= 32764, "box-prep parameters too large");
+static_assert(sizeof(BoxUpdateParams) <= 32764, "box-update parameters too large");
+static_assert(sizeof(ClassifyParams<kMaxJobs>) <= 32764, "classify parameters too large");
 
 cudaError_t launch_merge_single(const MergeParams<1>& p, cudaStream_t s) {
   return launch_merge_t<1>(p, s);

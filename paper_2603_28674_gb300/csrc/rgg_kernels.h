@@ -52,19 +52,25 @@ struct BuildParams {
   uint64_t n_edges;
 };
 
+// Writes boxes' poses into the box table and into the staging rows of their
+// pending entries; with from_table set, copies table rows into staging rows.
 struct BoxUpdateParams {
   uint32_t n;
   uint32_t ids[kMaxUpdateBoxes];
+  uint32_t rows[kMaxUpdateBoxes];   // staging row of each id's pending entry
   float pose[kMaxUpdateBoxes][15];
   const float* dev_pose;  // if non-null, poses are read from device memory
   float* table;           // [M][16]
+  float* stage;           // [rows][16]
+  uint32_t from_table;
 };
 
 struct BoxPrepJob {
-  const float* table;
+  const float* stage;     // staging rows of the pending entries
   float* out;             // [C][24]
   uint32_t C;
   uint32_t ids[kBoxesPerPass];
+  uint16_t rows[kBoxesPerPass];  // staging row of pass position p
 };
 
 struct BoxPrepParams {

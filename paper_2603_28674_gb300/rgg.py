@@ -24,6 +24,8 @@ NOALLOC_MAX_EDGES = 131072
 NOALLOC_MAX_TILES = 16384
 BOXES_PER_PASS = 32
 NUM_VARIANTS = 7
+MAX_REQUESTS = 64
+PENDING_EXTRA = 4096
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "librgg.so")
@@ -34,7 +36,8 @@ EXPORTS = (
     "rgg_update_obstacles", "rgg_classify", "rgg_classify_many", "rgg_fetch_labels",
     "rgg_fetch_box_sets", "rgg_fetch_records", "rgg_labels_device_ptr", "rgg_roadmap_info",
     "rgg_check_status", "rgg_set_kernel_timing", "rgg_kernel_time", "rgg_set_launch_shape",
-    "rgg_status_string", "rgg_classify_noalloc",
+    "rgg_status_string", "rgg_classify_noalloc", "rgg_update_request",
+    "rgg_fetch_request_labels", "rgg_release_request",
 )
 
 
@@ -76,7 +79,8 @@ class Info(ctypes.Structure):
                 ("num_links", ctypes.c_uint32), ("inner_per_link", ctypes.c_uint32),
                 ("max_obstacles", ctypes.c_uint32), ("mask_words", ctypes.c_uint32),
                 ("tile_samples", ctypes.c_uint32), ("num_tiles", ctypes.c_uint64),
-                ("pending_boxes", ctypes.c_uint32), ("grid_ctas", ctypes.c_uint32)]
+                ("pending_boxes", ctypes.c_uint32), ("grid_ctas", ctypes.c_uint32),
+                ("open_requests", ctypes.c_uint32), ("pending_capacity", ctypes.c_uint32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -113,6 +117,9 @@ def _lib():
         "rgg_kernel_time": [vp, ctypes.POINTER(dbl), ctypes.POINTER(dbl), ctypes.POINTER(u64)],
         "rgg_set_launch_shape": [vp, u32, u32],
         "rgg_classify_noalloc": [ctypes.POINTER(_NoallocArgs), vp],
+        "rgg_update_request": [vp, u32, vp, vp, i32, ctypes.POINTER(u32), vp],
+        "rgg_fetch_request_labels": [vp, u32, vp, u64, u64, i32, vp],
+        "rgg_release_request": [vp, u32],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -152,11 +159,20 @@ def _is_device(x) -> bool:
 
 
 def _ptr(x) -> int:
-    if _is_device(x):
+    if hasattr(x, "data_ptr"):
         if not x.is_contiguous():
-            raise ValueError("device buffers must be contiguous")
+            raise ValueError("torch buffers must be contiguous")
         return int(x.data_ptr())
     return int(x.ctypes.data)
+
+
+def _dst_kind(out) -> int:
+    """0 host (synchronous), 1 device, 2 page-locked torch CPU tensor (async)."""
+    if _is_device(out):
+        return 1
+    if hasattr(out, "is_pinned") and out.is_pinned():
+        return 2
+    return 0
 
 
 class Roadmap:
@@ -239,20 +255,52 @@ class Roadmap:
             self._h, ids.shape[0], ids.ctypes.data, _ptr(poses), int(dev),
             _stream(stream, self.device)))
 
+    def update_request(self, ids, poses, stream=None) -> int:
+        """Versioned move (rgg_update_request): like update_obstacles, and the
+        labels once this move is applied are kept under the returned handle."""
+        ids = _host(ids, np.uint32).reshape(-1)
+        dev = _is_device(poses)
+        if not dev:
+            poses = _host(poses, np.float32).reshape(-1, 15)
+            if poses.shape[0] != ids.shape[0]:
+                raise ValueError("one pose per id")
+        h = ctypes.c_uint32()
+        _check("rgg_update_request", _lib().rgg_update_request(
+            self._h, ids.shape[0], ids.ctypes.data, _ptr(poses), int(dev), ctypes.byref(h),
+            _stream(stream, self.device)))
+        return int(h.value)
+
+    def fetch_request_labels(self, handle: int, first: int = 0, count: Optional[int] = None,
+                             out=None, stream=None):
+        """Snapshot labels of request ``handle`` (numpy uint8, a device tensor,
+        or a pinned CPU tensor filled asynchronously)."""
+        if count is None:
+            count = self.info()["num_edges"] - first
+        if out is None:
+            out = np.empty(count, dtype=np.uint8)
+        _check("rgg_fetch_request_labels", _lib().rgg_fetch_request_labels(
+            self._h, handle, _ptr(out), first, count, _dst_kind(out),
+            _stream(stream, self.device)))
+        return out
+
+    def release_request(self, handle: int) -> None:
+        _check("rgg_release_request", _lib().rgg_release_request(self._h, handle))
+
     def classify(self, stream=None) -> None:
         _check("rgg_classify", _lib().rgg_classify(self._h, _stream(stream, self.device)))
 
     # -- results --------------------------------------------------------------
     def fetch_labels(self, first: int = 0, count: Optional[int] = None, out=None,
                      stream=None):
-        """Labels [first, first+count) into ``out`` (numpy uint8 or a device
-        tensor), allocated as numpy when None."""
+        """Labels [first, first+count) into ``out`` (numpy uint8, a device
+        tensor, or a pinned CPU tensor filled asynchronously), allocated as
+        numpy when None."""
         if count is None:
             count = self.info()["num_edges"] - first
         if out is None:
             out = np.empty(count, dtype=np.uint8)
         _check("rgg_fetch_labels", _lib().rgg_fetch_labels(
-            self._h, _ptr(out), first, count, int(_is_device(out)), _stream(stream, self.device)))
+            self._h, _ptr(out), first, count, _dst_kind(out), _stream(stream, self.device)))
         return out
 
     def fetch_box_sets(self, first: int = 0, count: Optional[int] = None, stream=None):

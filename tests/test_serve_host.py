@@ -1,0 +1,64 @@
+"""Host logic of the serving loop: admission and the memory estimate."""
+import collections
+
+import numpy as np
+
+import oracle
+from paper_2603_28674_gb300 import workloads as W
+from paper_2603_28674_gb300.serve import Planner, roadmap_bytes
+
+
+def test_admission_keeps_per_roadmap_order_and_capacities():
+    # items are (arrival index, roadmap)
+    q = collections.deque([(0, 0), (1, 1), (2, 0), (3, 2), (4, 0), (5, 1)])
+    pl = Planner(n_roadmaps=3, handles_per_roadmap=2, host_slots=5)
+    got = pl.admit(q, lambda it: it[1])
+    # roadmap 0 has two handles: request 4 waits; nothing else is blocked
+    assert [i for i, _ in got] == [0, 1, 2, 3, 5]
+    assert [i for i, _ in q] == [4]
+    assert pl.free_handles == [0, 0, 1] and pl.free_slots == 0
+    # no slot left: nothing is admitted even though roadmap 2 has a handle
+    q.append((6, 2))
+    assert pl.admit(q, lambda it: it[1]) == []
+    pl.release(0)
+    got = pl.admit(q, lambda it: it[1])
+    assert [i for i, _ in got] == [4]
+    assert [i for i, _ in q] == [6]
+
+
+def test_blocked_request_holds_back_only_its_own_roadmap():
+    q = collections.deque([(0, 0), (1, 0), (2, 1), (3, 0), (4, 1)])
+    pl = Planner(n_roadmaps=2, handles_per_roadmap=1, host_slots=10)
+    got = pl.admit(q, lambda it: it[1])
+    assert [i for i, _ in got] == [0, 2]
+    # request 3 (roadmap 0) must not overtake request 1 once a handle frees
+    pl.release(0)
+    got = pl.admit(q, lambda it: it[1])
+    assert [i for i, _ in got] == [1]
+    assert [i for i, _ in q] == [3, 4]
+
+
+def test_one_at_a_time_limit():
+    q = collections.deque([(i, i % 3) for i in range(6)])
+    pl = Planner(n_roadmaps=3, handles_per_roadmap=64, host_slots=64)
+    order = []
+    while q:
+        got = pl.admit(q, lambda it: it[1], limit=1)
+        assert len(got) == 1
+        order.append(got[0][0])
+        pl.release(got[0][1])
+    assert order == list(range(6))
+
+
+def test_memory_estimate_covers_the_records():
+    # the estimate's configuration count follows the sample-count rule
+    sc = W.workload_7dof(n_nodes=300, n_updates=0)
+    rm, robot = sc.roadmap, sc.roadmap.robot
+    n_e = np.array([oracle.num_samples(rm.q_from[e], rm.q_to[e], rm.step)
+                    for e in range(rm.num_edges)])
+    S, N = int(n_e.sum()), rm.num_edges
+    L, K = robot.num_links, robot.inner_per_link
+    records = 16 * (K * L * S + L * (S - N))
+    est = roadmap_bytes(L, K, sc.boxes.count, rm.q_from, rm.q_to, rm.step, 64)
+    assert est >= records + 64 * N
+    assert est <= records + 200 * N + (2 << 20)
