@@ -267,6 +267,27 @@ def run_reference(args):
 
 
 # --------------------------------------------------------------------------
+# replicas (N > 1): barrier + max-over-ranks timing, no data-path collective
+# --------------------------------------------------------------------------
+def max_over_ranks(dist, x: float, device=None) -> float:
+    """The largest x over all ranks (x itself without a process group).  NCCL
+    reduces a CUDA tensor on `device`; other backends a CPU tensor."""
+    if dist is None:
+        return float(x)
+    import torch
+    dev = device if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(world: int, units_per_rank: float, slowest_s: float) -> float:
+    """Whole-job rate of `world` replicas that each processed units_per_rank
+    units, timed by the slowest rank (weak scaling)."""
+    return world * units_per_rank / slowest_s
+
+
+# --------------------------------------------------------------------------
 # GPU arm
 # --------------------------------------------------------------------------
 def run_gpu(args):
@@ -329,10 +350,7 @@ def run_gpu(args):
     ms = ev0.elapsed_time(ev1)
     k_ms, m_ms, k_launches = r.kernel_time()
     r.set_kernel_timing(False)
-    if dist is not None:
-        t = torch.tensor([ms], device=f"cuda:{local}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(dist, ms, f"cuda:{local}")
     clk = clocks.summary()
 
     # ---- end to end through the C ABI with host buffers
@@ -352,15 +370,12 @@ def run_gpu(args):
         r.fetch_labels(out=labels_host, stream=stream)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([e2e_s], device=f"cuda:{local}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(dist, e2e_s, f"cuda:{local}")
     r.check_status(stream)
 
     n_edges = info["num_edges"]
-    value = world * n_edges * args.steps / (ms / 1000.0)
-    e2e_value = world * n_edges * args.steps / e2e_s
+    value = replica_throughput(world, n_edges * args.steps, ms / 1000.0)
+    e2e_value = replica_throughput(world, n_edges * args.steps, e2e_s)
     peak, peak_kind = hbm_peak()
     b_alg = algorithmic_bytes(info, moved)
     k_avg_ms = k_ms / max(1, k_launches)
