@@ -315,6 +315,63 @@ int rgg_kernel_time(rgg_roadmap_t r, double* classify_ms, double* merge_ms, uint
 int rgg_set_launch_shape(rgg_roadmap_t r, uint32_t variant, uint32_t consumer_warps);
 
 /* ------------------------------------------------------------------------ */
+/* Autotuner of the classify launch shape (the paper has none: its batched
+ * pass has fixed sizes).  Times one streaming classify launch over the given
+ * roadmaps at every supported shape -- each compiled pipeline variant (ring
+ * depth x tile size, i.e. records per block) with 16, 20, 24 and 27 consumer
+ * warps -- on their own resident records and their first 32 present boxes
+ * (warm-up launch, then `reps` timed launches, CUDA events on `stream`), and
+ * sets the fastest shape on every roadmap.  Labels, box sets and pending
+ * moves are not changed: the timed launches accumulate into scratch memory
+ * the call allocates and frees.  Synchronous; it synchronises the device
+ * whenever the tiles are rebuilt.
+ *   roadmaps, n  1 <= n <= 128 distinct roadmaps with edges, one device
+ *   reps         timed launches per shape (clamped to 1..100)
+ *   results      up to max_results entries, fastest first (may be NULL when
+ *                max_results is 0); *n_results (may be NULL) = shapes timed.
+ * With no present box on any roadmap nothing is timed and the shapes stay.
+ * RGG_ERR_STATE before edges exist. */
+typedef struct {
+  uint32_t variant;         /* pipeline variant (rgg_set_launch_shape)          */
+  uint32_t consumer_warps;  /* consumer warps per CTA                          */
+  float classify_ms;        /* mean duration of one timed launch, ms           */
+  float reserved;
+} rgg_tune_result;
+
+int rgg_autotune(rgg_roadmap_t* roadmaps, uint32_t n, uint32_t reps, rgg_tune_result* results,
+                 uint32_t max_results, uint32_t* n_results, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Step graphs: one update-and-classify step of several roadmaps captured once
+ * into a CUDA graph and replayed by a single launch (the paper launches each
+ * step's work from the host).  The captured step moves, for each roadmap i,
+ * the n_ids[i] boxes ids[i] to the poses read at each launch from the DEVICE
+ * pointer poses[i] (n_ids[i] x 15 floats, same layout as
+ * rgg_update_obstacles; the caller refreshes them between launches), then
+ * classifies every roadmap as rgg_classify_many does.  Creating the graph
+ * records the step's effect on the roadmaps' host-side state (boxes become
+ * present), enqueues no work, and returns the handle in *out.
+ * Rules:
+ *   - at creation and at every launch the roadmaps must have no pending
+ *     moves (RGG_ERR_STATE otherwise): the step uses the pending entries'
+ *     staging rows;
+ *   - replacing a roadmap's edges or changing its launch variant invalidates
+ *     the graph (its launch returns RGG_ERR_STATE);
+ *   - destroy the graph before any of its roadmaps.
+ * Launches are asynchronous on `stream`; labels equal those of the same
+ * update + rgg_classify_many issued call by call.  n_ids[i] may be 0 (the
+ * roadmap is only classified when it has pending boxes, i.e. not at all). */
+typedef struct rgg_step_graph* rgg_step_graph_t;
+
+int rgg_step_graph_create(rgg_roadmap_t* roadmaps, uint32_t n, const uint32_t* n_ids,
+                          const uint32_t* const* ids, const float* const* poses,
+                          rgg_step_graph_t* out);
+int rgg_step_graph_launch(rgg_step_graph_t g, void* stream);
+/* Number of nodes in the captured graph (kernel launches and memsets). */
+int rgg_step_graph_nodes(rgg_step_graph_t g, uint64_t* nodes);
+int rgg_step_graph_destroy(rgg_step_graph_t g);
+
+/* ------------------------------------------------------------------------ */
 /* One classification pass that allocates nothing.  (The paper has no
  * counterpart: this entry point exists for callers of this library that may
  * not allocate device memory -- a real-time loop that must not wait on the

@@ -134,6 +134,7 @@ struct rgg_roadmap {
   uint32_t ctas_per_sm = 1, consumer_warps = kDefaultConsumerWarps;
   int variant = kDefaultVariant;
   bool has_edges = false;
+  uint64_t gen = 0;            // bumped whenever tiles or edges are replaced
   EdgeState es;
   float* d_table = nullptr;    // [M][16] box poses
   float* d_stage = nullptr;    // [stage_rows][16] staged pose of each pending entry
@@ -241,6 +242,7 @@ int set_tiles(rgg_roadmap* r, EdgeState* es, cudaStream_t s) {
   es->n_etab = h_etab.size();
   es->tiling = tiling;
   es->device_bytes += es->T * sizeof(TileDesc) + es->n_etab * sizeof(int4);
+  ++r->gen;
   return RGG_OK;
 }
 
@@ -315,6 +317,7 @@ int install_edges(rgg_roadmap* r, EdgeState&& es, cudaStream_t s) {
   r->es.release();
   r->es = std::move(es);
   r->has_edges = true;
+  ++r->gen;
   clear_pending(r);
   std::fill(r->req_state.begin(), r->req_state.end(), 0);
   BoxUpdateParams p;
@@ -440,6 +443,38 @@ MergeJob make_merge_job(rgg_roadmap* r, size_t lo, uint32_t C, bool ordered, uin
     }
   }
   return m;
+}
+
+// A launch shape every kernel instance supports: threads within the launch
+// bounds, the batched kernel's shared memory within the opt-in limit, and no
+// more consumer warps than work items in the ring (so that the ring's phase
+// parity stays unambiguous).
+bool shape_ok(uint32_t variant, uint32_t cw) {
+  if (variant >= (uint32_t)kNumVariants || cw < 1 || 32 * (cw + 1) > (uint32_t)kMaxClassifyThreads)
+    return false;
+  if (classify_smem_bytes((int)variant, cw) > 232448) return false;
+  const VariantShape vs = variant_shape((int)variant);
+  return (uint64_t)cw <=
+         (uint64_t)vs.stages * ((vs.rounds + vs.rounds_per_item - 1) / vs.rounds_per_item);
+}
+
+// Switch a roadmap to a checked shape; the tiles depend on the variant only
+// and are rebuilt when it changes (after the device has drained).
+int apply_shape(rgg_roadmap* r, int variant, uint32_t cw) {
+  const int old_v = r->variant;
+  const uint32_t old_cw = r->consumer_warps;
+  r->variant = variant;
+  r->consumer_warps = cw;
+  if (variant != old_v && r->has_edges && r->es.N) {
+    cudaDeviceSynchronize();  // no launch may still read the old tiles
+    const int rc = set_tiles(r, &r->es, nullptr);
+    if (rc != RGG_OK) {
+      r->variant = old_v;
+      r->consumer_warps = old_cw;
+      return rc;
+    }
+  }
+  return RGG_OK;
 }
 
 }  // namespace
@@ -1023,29 +1058,263 @@ int rgg_kernel_time(rgg_roadmap_t r, double* classify_ms, double* merge_ms,
 int rgg_set_launch_shape(rgg_roadmap_t r, uint32_t variant, uint32_t consumer_warps) {
   if (!r) return RGG_ERR_INVALID;
   const uint32_t cw = consumer_warps ? consumer_warps : kDefaultConsumerWarps;
-  if (variant >= (uint32_t)kNumVariants || cw < 1 || 32 * (cw + 1) > (uint32_t)kMaxClassifyThreads)
-    return RGG_ERR_INVALID;
-  if (classify_smem_bytes((int)variant, cw) > 232448) return RGG_ERR_INVALID;
-  // every consumer warp holds at most one work item; the ring's phase parity
-  // stays unambiguous while there are no more warps than items in the ring
-  const VariantShape vs = variant_shape((int)variant);
-  if ((uint64_t)cw > (uint64_t)vs.stages * ((vs.rounds + vs.rounds_per_item - 1) / vs.rounds_per_item))
-    return RGG_ERR_INVALID;
-  const int old_v = r->variant;
-  const uint32_t old_cw = r->consumer_warps;
-  r->variant = (int)variant;
-  r->consumer_warps = cw;
-  if (r->has_edges && r->es.N) {
-    DeviceGuard g(r->device);
-    if (!g.ok) return RGG_ERR_CUDA;
-    cudaDeviceSynchronize();  // no launch may still read the old tiles
-    const int rc = set_tiles(r, &r->es, nullptr);
-    if (rc != RGG_OK) {
-      r->variant = old_v;
-      r->consumer_warps = old_cw;
-      return rc;
+  if (!shape_ok(variant, cw)) return RGG_ERR_INVALID;
+  DeviceGuard g(r->device);
+  if (!g.ok) return RGG_ERR_CUDA;
+  return apply_shape(r, (int)variant, cw);
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner: time the classify launch of these roadmaps at every supported
+// launch shape, on their own records and boxes, and keep the fastest.
+// ---------------------------------------------------------------------------
+// One classify launch over the roadmaps' tiles with C[i] boxes each, OR-ing
+// into the scratch accumulators acc[i] (labels and box sets are untouched).
+static int tune_launch(rgg_roadmap_t* rs, uint32_t n, const std::vector<uint32_t*>& acc,
+                const std::vector<uint32_t>& C, ClassifyParams<kMaxJobs>* cpp,
+                cudaStream_t s) {
+  ClassifyParams<1> cp1;
+  uint32_t nj = 0;
+  uint64_t tiles = 0;
+  for (uint32_t i = 0; i < n; ++i) {
+    rgg_roadmap* r = rs[i];
+    if (r->es.N == 0 || C[i] == 0) continue;
+    ClassifyJob j = make_job(r, C[i], tiles);
+    j.edge_acc = acc[i];
+    if (n == 1) cp1.job[0] = j; else cpp->job[nj] = j;
+    ++nj;
+    tiles += r->es.T;
+  }
+  if (nj == 0) return RGG_OK;
+  rgg_roadmap* r0 = rs[0];
+  ClassifyLaunch lc;
+  lc.consumer_warps = r0->consumer_warps;
+  lc.variant = r0->variant;
+  lc.grid = std::max<uint32_t>(1, (uint32_t)std::min<uint64_t>((tiles + 1) / 2, launch_ctas(r0)));
+  uint32_t* counter = reinterpret_cast<uint32_t*>(r0->d_status + 1);
+  RGG_CK(cudaMemsetAsync(counter, 0, sizeof(uint32_t), s));
+  if (n == 1) {
+    cp1.njobs = 1;
+    cp1.total_tiles = tiles;
+    cp1.status = r0->d_status;
+    cp1.work_counter = counter;
+    RGG_CK(launch_classify_single(cp1, lc, s));
+  } else {
+    cpp->njobs = nj;
+    cpp->total_tiles = tiles;
+    cpp->status = r0->d_status;
+    cpp->work_counter = counter;
+    RGG_CK(launch_classify_batched(*cpp, lc, s));
+  }
+  return RGG_OK;
+}
+
+struct EventPair {
+  cudaEvent_t a = nullptr, b = nullptr;
+  ~EventPair() {
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+  }
+};
+
+int rgg_autotune(rgg_roadmap_t* rs, uint32_t n, uint32_t reps, rgg_tune_result* results,
+                 uint32_t max_results, uint32_t* n_results, void* stream) {
+  if (!rs || n == 0 || n > (uint32_t)kMaxJobs || (max_results && !results)) return RGG_ERR_INVALID;
+  for (uint32_t i = 0; i < n; ++i) {
+    if (!rs[i]) return RGG_ERR_INVALID;
+    if (!rs[i]->has_edges) return RGG_ERR_STATE;
+    if (rs[i]->device != rs[0]->device) return RGG_ERR_INVALID;
+    for (uint32_t j = 0; j < i; ++j)
+      if (rs[j] == rs[i]) return RGG_ERR_INVALID;
+  }
+  if (n_results) *n_results = 0;
+  reps = std::max<uint32_t>(1, std::min<uint32_t>(reps, 100));
+  DeviceGuard g(rs[0]->device);
+  if (!g.ok) return RGG_ERR_CUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // the first 32 present boxes of each roadmap, prepared from the box table
+  // (table row = box id); a pending pass re-prepares its own boxes later
+  std::vector<uint32_t> C(n, 0);
+  std::unique_ptr<BoxPrepParams> bpp(new (std::nothrow) BoxPrepParams);
+  std::unique_ptr<ClassifyParams<kMaxJobs>> cpp(new (std::nothrow) ClassifyParams<kMaxJobs>);
+  if (!bpp || !cpp) return RGG_ERR_OOM;
+  bpp->njobs = 0;
+  bool any = false;
+  for (uint32_t i = 0; i < n; ++i) {
+    rgg_roadmap* r = rs[i];
+    BoxPrepJob& pj = bpp->job[bpp->njobs++];
+    pj.stage = r->d_table;
+    pj.out = r->d_changed;
+    pj.C = 0;
+    for (uint32_t b = 0; b < r->M && pj.C < (uint32_t)kBoxesPerPass; ++b)
+      if (r->present[b]) {
+        pj.ids[pj.C] = b;
+        pj.rows[pj.C] = (uint16_t)b;
+        ++pj.C;
+      }
+    C[i] = pj.C;
+    any = any || (pj.C > 0 && r->es.N > 0);
+  }
+  if (!any) return RGG_OK;  // nothing to time: the shape stays
+  RGG_CK(launch_box_prep(*bpp, s));
+  std::vector<uint32_t*> acc(n, nullptr);
+  auto free_acc = [&]() {
+    for (uint32_t* p : acc) cudaFree(p);
+  };
+  for (uint32_t i = 0; i < n; ++i) {
+    cudaError_t e = dalloc(&acc[i], 2 * rs[i]->es.N);
+    if (e != cudaSuccess) {
+      free_acc();
+      return cuda_status(e);
     }
   }
+  EventPair ev;
+  if (cudaEventCreate(&ev.a) != cudaSuccess || cudaEventCreate(&ev.b) != cudaSuccess) {
+    free_acc();
+    return RGG_ERR_CUDA;
+  }
+  static const uint32_t kWarps[] = {16, 20, 24, 27};
+  std::vector<rgg_tune_result> res;
+  int rc = RGG_OK;
+  for (int v = 0; v < kNumVariants && rc == RGG_OK; ++v)
+    for (uint32_t cw : kWarps) {
+      if (!shape_ok((uint32_t)v, cw)) continue;
+      for (uint32_t i = 0; i < n && rc == RGG_OK; ++i) rc = apply_shape(rs[i], v, cw);
+      if (rc != RGG_OK) break;
+      rc = tune_launch(rs, n, acc, C, cpp.get(), s);  // warm-up
+      if (rc == RGG_OK && cudaEventRecord(ev.a, s) != cudaSuccess) rc = RGG_ERR_CUDA;
+      for (uint32_t k = 0; k < reps && rc == RGG_OK; ++k) rc = tune_launch(rs, n, acc, C, cpp.get(), s);
+      if (rc == RGG_OK && cudaEventRecord(ev.b, s) != cudaSuccess) rc = RGG_ERR_CUDA;
+      float ms = 0.f;
+      if (rc == RGG_OK && (cudaEventSynchronize(ev.b) != cudaSuccess ||
+                           cudaEventElapsedTime(&ms, ev.a, ev.b) != cudaSuccess))
+        rc = RGG_ERR_CUDA;
+      if (rc != RGG_OK) break;
+      rgg_tune_result t{};
+      t.variant = (uint32_t)v;
+      t.consumer_warps = cw;
+      t.classify_ms = ms / (float)reps;
+      res.push_back(t);
+    }
+  cudaStreamSynchronize(s);
+  free_acc();
+  if (rc == RGG_OK) rc = check_status_locked(rs[0], s);
+  std::stable_sort(res.begin(), res.end(), [](const rgg_tune_result& a, const rgg_tune_result& b) {
+    return a.classify_ms < b.classify_ms;
+  });
+  // keep the fastest shape (the previous one if the sweep failed part-way)
+  if (!res.empty()) {
+    for (uint32_t i = 0; i < n; ++i) {
+      const int rc2 = apply_shape(rs[i], (int)res[0].variant, res[0].consumer_warps);
+      if (rc == RGG_OK) rc = rc2;
+    }
+  }
+  if (n_results) *n_results = (uint32_t)res.size();
+  for (uint32_t i = 0; i < std::min<uint32_t>(max_results, (uint32_t)res.size()); ++i)
+    results[i] = res[i];
+  return rc;
+}
+
+// ---------------------------------------------------------------------------
+// Step graphs: one update + classify of several roadmaps captured once and
+// replayed with cudaGraphLaunch.
+// ---------------------------------------------------------------------------
+struct rgg_step_graph {
+  int device = 0;
+  std::vector<rgg_roadmap*> rs;
+  std::vector<uint64_t> gens;
+  cudaGraphExec_t exec = nullptr;
+  size_t nodes = 0;
+};
+
+int rgg_step_graph_create(rgg_roadmap_t* rs, uint32_t n, const uint32_t* n_ids,
+                          const uint32_t* const* ids, const float* const* poses,
+                          rgg_step_graph_t* out) {
+  if (!out) return RGG_ERR_INVALID;
+  *out = nullptr;
+  if (!rs || n == 0 || !n_ids || !ids || !poses) return RGG_ERR_INVALID;
+  for (uint32_t i = 0; i < n; ++i) {
+    if (!rs[i]) return RGG_ERR_INVALID;
+    if (!rs[i]->has_edges || !rs[i]->pending.empty()) return RGG_ERR_STATE;
+    if (rs[i]->device != rs[0]->device || rs[i]->variant != rs[0]->variant) return RGG_ERR_INVALID;
+    for (uint32_t j = 0; j < i; ++j)
+      if (rs[j] == rs[i]) return RGG_ERR_INVALID;
+    if (n_ids[i] && (!ids[i] || !poses[i])) return RGG_ERR_INVALID;
+    uint32_t fresh = 0;
+    if (n_ids[i]) {
+      const int rc = check_moves(rs[i], n_ids[i], ids[i], poses[i], 1, &fresh);
+      if (rc != RGG_OK) return rc;
+    }
+  }
+  DeviceGuard g(rs[0]->device);
+  if (!g.ok) return RGG_ERR_CUDA;
+  std::unique_ptr<rgg_step_graph> G(new (std::nothrow) rgg_step_graph);
+  if (!G) return RGG_ERR_OOM;
+  G->device = rs[0]->device;
+  std::vector<std::vector<uint8_t>> present(n);
+  std::vector<uint8_t> timing(n);
+  for (uint32_t i = 0; i < n; ++i) {
+    present[i] = rs[i]->present;
+    timing[i] = rs[i]->timing;
+    rs[i]->timing = false;  // no event records inside the graph
+  }
+  cudaStream_t cs = nullptr;
+  RGG_CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  int rc = RGG_OK;
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) rc = cuda_status(e);
+  for (uint32_t i = 0; i < n && rc == RGG_OK; ++i)
+    if (n_ids[i]) rc = stage_moves(rs[i], n_ids[i], ids[i], poses[i], 1, cs);
+  for (uint32_t base = 0; base < n && rc == RGG_OK; base += kMaxJobs)
+    rc = classify_group(rs + base, std::min<uint32_t>(kMaxJobs, n - base), cs);
+  cudaGraph_t graph = nullptr;
+  if (e == cudaSuccess) {
+    const cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+    if (rc == RGG_OK && e2 != cudaSuccess) rc = cuda_status(e2);
+  }
+  if (rc == RGG_OK) {
+    e = cudaGraphInstantiate(&G->exec, graph, 0);
+    if (e != cudaSuccess) rc = cuda_status(e);
+    else cudaGraphGetNodes(graph, nullptr, &G->nodes);
+  }
+  if (graph) cudaGraphDestroy(graph);
+  cudaStreamDestroy(cs);
+  for (uint32_t i = 0; i < n; ++i) {
+    rs[i]->timing = timing[i] != 0;
+    if (rc != RGG_OK) {
+      // nothing ran: drop the entries the capture staged
+      clear_pending(rs[i]);
+      rs[i]->present = present[i];
+    }
+  }
+  if (rc != RGG_OK) return rc;
+  G->rs.assign(rs, rs + n);
+  for (uint32_t i = 0; i < n; ++i) G->gens.push_back(rs[i]->gen);
+  *out = G.release();
+  return RGG_OK;
+}
+
+int rgg_step_graph_launch(rgg_step_graph_t g, void* stream) {
+  if (!g) return RGG_ERR_INVALID;
+  for (size_t i = 0; i < g->rs.size(); ++i)
+    if (g->rs[i]->gen != g->gens[i] || !g->rs[i]->pending.empty()) return RGG_ERR_STATE;
+  DeviceGuard dg(g->device);
+  if (!dg.ok) return RGG_ERR_CUDA;
+  RGG_CK(cudaGraphLaunch(g->exec, static_cast<cudaStream_t>(stream)));
+  return RGG_OK;
+}
+
+int rgg_step_graph_nodes(rgg_step_graph_t g, uint64_t* nodes) {
+  if (!g || !nodes) return RGG_ERR_INVALID;
+  *nodes = g->nodes;
+  return RGG_OK;
+}
+
+int rgg_step_graph_destroy(rgg_step_graph_t g) {
+  if (!g) return RGG_OK;
+  DeviceGuard dg(g->device);
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  delete g;
   return RGG_OK;
 }
 

@@ -37,7 +37,9 @@ EXPORTS = (
     "rgg_fetch_box_sets", "rgg_fetch_records", "rgg_labels_device_ptr", "rgg_roadmap_info",
     "rgg_check_status", "rgg_set_kernel_timing", "rgg_kernel_time", "rgg_set_launch_shape",
     "rgg_status_string", "rgg_classify_noalloc", "rgg_update_request",
-    "rgg_fetch_request_labels", "rgg_release_request",
+    "rgg_fetch_request_labels", "rgg_release_request", "rgg_autotune",
+    "rgg_step_graph_create", "rgg_step_graph_launch", "rgg_step_graph_nodes",
+    "rgg_step_graph_destroy",
 )
 
 
@@ -70,6 +72,11 @@ class _NoallocArgs(ctypes.Structure):
                 ("mask_words", ctypes.c_uint32), ("hit", ctypes.c_void_p),
                 ("touch", ctypes.c_void_p), ("counts", ctypes.c_void_p),
                 ("labels", ctypes.c_void_p), ("margin_m", ctypes.c_float)]
+
+
+class _TuneResult(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_uint32), ("consumer_warps", ctypes.c_uint32),
+                ("classify_ms", ctypes.c_float), ("reserved", ctypes.c_float)]
 
 
 class Info(ctypes.Structure):
@@ -120,6 +127,14 @@ def _lib():
         "rgg_update_request": [vp, u32, vp, vp, i32, ctypes.POINTER(u32), vp],
         "rgg_fetch_request_labels": [vp, u32, vp, u64, u64, i32, vp],
         "rgg_release_request": [vp, u32],
+        "rgg_autotune": [ctypes.POINTER(vp), u32, u32, ctypes.POINTER(_TuneResult), u32,
+                         ctypes.POINTER(u32), vp],
+        "rgg_step_graph_create": [ctypes.POINTER(vp), u32, ctypes.POINTER(u32),
+                                  ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
+                                  ctypes.POINTER(vp)],
+        "rgg_step_graph_launch": [vp, vp],
+        "rgg_step_graph_nodes": [vp, ctypes.POINTER(u64)],
+        "rgg_step_graph_destroy": [vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -394,3 +409,76 @@ def classify_noalloc(*, num_links: int, inner_per_link: int, sample_off, num_sam
     dev = inner.device.index if hasattr(inner, "device") else 0
     _check("rgg_classify_noalloc", _lib().rgg_classify_noalloc(ctypes.byref(args),
                                                                _stream(stream, dev)))
+
+
+def autotune(roadmaps: Sequence[Roadmap], reps: int = 2, stream=None) -> list:
+    """Time every supported launch shape on these roadmaps' own records and
+    keep the fastest on all of them (rgg_autotune).  Returns the timed shapes,
+    fastest first, as dicts."""
+    if not roadmaps:
+        return []
+    arr = (ctypes.c_void_p * len(roadmaps))(*[r.handle for r in roadmaps])
+    cap = 64
+    res = (_TuneResult * cap)()
+    cnt = ctypes.c_uint32()
+    _check("rgg_autotune", _lib().rgg_autotune(arr, len(roadmaps), reps, res, cap,
+                                               ctypes.byref(cnt),
+                                               _stream(stream, roadmaps[0].device)))
+    return [{"variant": res[i].variant, "consumer_warps": res[i].consumer_warps,
+             "classify_ms": res[i].classify_ms} for i in range(min(cnt.value, cap))]
+
+
+class StepGraph:
+    """One captured update + classify step of several roadmaps (rgg_step_graph_*).
+
+    ``moves`` is a list with one (ids, poses) pair per roadmap: ids a host
+    array, poses a contiguous [m, 15] float32 CUDA tensor that every launch
+    reads (write the next poses into it between launches).  Keep the tensors
+    and the roadmaps alive while the graph exists."""
+
+    def __init__(self, roadmaps: Sequence[Roadmap], moves):
+        if len(moves) != len(roadmaps):
+            raise ValueError("one (ids, poses) pair per roadmap")
+        n = len(roadmaps)
+        self._ids = [_host(ids, np.uint32).reshape(-1) for ids, _ in moves]
+        self._poses = [p for _, p in moves]
+        for ids, p in zip(self._ids, self._poses):
+            if not _is_device(p) or tuple(p.shape) != (ids.shape[0], 15):
+                raise ValueError("poses must be [m, 15] CUDA tensors, one row per id")
+        self.roadmaps = list(roadmaps)
+        arr = (ctypes.c_void_p * n)(*[r.handle for r in roadmaps])
+        nid = (ctypes.c_uint32 * n)(*[ids.shape[0] for ids in self._ids])
+        idp = (ctypes.c_void_p * n)(*[ids.ctypes.data for ids in self._ids])
+        pp = (ctypes.c_void_p * n)(*[_ptr(p) for p in self._poses])
+        h = ctypes.c_void_p()
+        _check("rgg_step_graph_create", _lib().rgg_step_graph_create(arr, n, nid, idp, pp,
+                                                                     ctypes.byref(h)))
+        self._h = h
+        self.device = roadmaps[0].device
+
+    def launch(self, stream=None) -> None:
+        _check("rgg_step_graph_launch", _lib().rgg_step_graph_launch(
+            self._h, _stream(stream, self.device)))
+
+    def nodes(self) -> int:
+        n = ctypes.c_uint64()
+        _check("rgg_step_graph_nodes", _lib().rgg_step_graph_nodes(self._h, ctypes.byref(n)))
+        return int(n.value)
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            _lib().rgg_step_graph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
