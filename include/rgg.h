@@ -159,8 +159,15 @@ int rgg_roadmap_destroy(rgg_roadmap_t r);
  *                L*(sample_off[e] - e) + i*(n_e - 1) + k of each plane.
  *   src_is_device  0: inner/outer are host pointers; 1: device pointers.
  * Every radius must be >= 0 and every value finite (checked for host
- * sources only).  RGG_ERR_INVALID on a bad layout; RGG_ERR_OOM if the
- * records do not fit in device memory. */
+ * sources only).  The method assumes inner inside outer: each inner sphere
+ * of configuration k must lie inside the union of the outer spheres of the
+ * intervals next to k (k-1..k and k..k+1), because inner spheres are tested
+ * only against boxes those outer spheres touch.
+ * Host-source records whose inner spheres of every configuration share one
+ * radius and sit at equal steps on a segment (within 1e-6 m, as
+ * rgg_build_edges writes them) are tested with interpolated centres when
+ * margin_m >= 1e-5; all others sphere by sphere.  RGG_ERR_INVALID on a bad
+ * layout; RGG_ERR_OOM if the records do not fit in device memory. */
 int rgg_upload_edges(rgg_roadmap_t r, uint64_t num_edges, const uint64_t* sample_off,
                      const float* inner_xyzr, const float* outer_xyzr, int src_is_device,
                      void* stream);

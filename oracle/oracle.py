@@ -48,6 +48,10 @@ def _load():
     lib.or_classify.argtypes = [i32, _D, _D, _D, _D, i32, i64, _D, _D, dbl, i64, i32, _D,
                                 _U8, _U8, _D, _D, _D, _U32, _U32]
     lib.or_classify.restype = i32
+    _I64 = ctypes.POINTER(ctypes.c_int64)
+    lib.or_classify_spheres.argtypes = [i64, _I64, _D, _I64, _D, i32, _D, _U8, _U8, _D,
+                                        _U32, _U32]
+    lib.or_classify_spheres.restype = i32
     lib.or_segment_box_distance.argtypes = [_D, _D, _D]
     lib.or_segment_box_distance.restype = dbl
     lib.or_edge_dense_clearance.argtypes = [i32, _D, _D, _D, _D, _D, _D, dbl, i32, i32, _D,
@@ -149,6 +153,40 @@ def classify(robot, qa, qb, step: float, boxes, present=None, bits: bool = False
         raise ValueError("oracle classify rejected its arguments")
     if bits:
         out["hit"], out["touch"] = hit[:, :w], touch[:, :w]
+    return out
+
+
+def classify_spheres(in_off, inner, out_off, outer, boxes, present=None, bits: bool = False):
+    """Labels of edges given their sphere sets (or_classify_spheres): edge e
+    owns inner[in_off[e]:in_off[e+1]] and outer[out_off[e]:out_off[e+1]],
+    rows (x, y, z, r).  Returns ``labels``, ``kappa`` and, with ``bits``,
+    ``hit`` / ``touch``."""
+    _I64 = ctypes.POINTER(ctypes.c_int64)
+    io = np.ascontiguousarray(in_off, dtype=np.int64)
+    oo = np.ascontiguousarray(out_off, dtype=np.int64)
+    n_edges = io.shape[0] - 1
+    if oo.shape[0] != n_edges + 1:
+        raise ValueError("one offset table entry per edge for both sphere sets")
+    inner, pi = _d(np.asarray(inner, dtype=np.float64).reshape(-1, 4))
+    outer, po = _d(np.asarray(outer, dtype=np.float64).reshape(-1, 4))
+    if io[-1] > inner.shape[0] or oo[-1] > outer.shape[0]:
+        raise ValueError("offsets beyond the sphere arrays")
+    boxes, pbx = _d(np.asarray(boxes, dtype=np.float64).reshape(-1, 15))
+    m = boxes.shape[0]
+    pres = None if present is None else np.ascontiguousarray(present, dtype=np.uint8)
+    w = max((m + 31) // 32, 1)
+    out = {"labels": np.zeros(n_edges, dtype=np.uint8), "kappa": np.zeros(n_edges)}
+    hit = np.zeros((n_edges, w), dtype=np.uint32)
+    touch = np.zeros((n_edges, w), dtype=np.uint32)
+    rc = _load().or_classify_spheres(
+        n_edges, io.ctypes.data_as(_I64), pi, oo.ctypes.data_as(_I64), po, m, pbx,
+        pres.ctypes.data_as(_U8) if pres is not None else None,
+        out["labels"].ctypes.data_as(_U8), out["kappa"].ctypes.data_as(_D),
+        hit.ctypes.data_as(_U32), touch.ctypes.data_as(_U32))
+    if rc != 0:
+        raise ValueError("oracle classify_spheres rejected its arguments")
+    if bits:
+        out["hit"], out["touch"] = hit, touch
     return out
 
 

@@ -296,6 +296,51 @@ int or_classify(int L, const double* a, const double* alpha, const double* d,
 }
 
 /*
+ * Labels of edges whose approximations are given as sphere sets rather than
+ * built from a robot (Sec. 4.1 applied to caller-supplied approximations):
+ * edge e owns the inner spheres [in_off[e], in_off[e+1]) of inner[.][4] and
+ * the outer spheres [out_off[e], out_off[e+1]) of outer[.][4], each sphere
+ * (x, y, z, r).  Same rules as or_classify: box b is hit when some inner
+ * sphere reaches it (d <= r), touched when some outer sphere does; red if
+ * any box is hit, else green if none is touched, else gray; the clearance
+ * kappa as in or_classify.  Outputs other than labels may be NULL.
+ */
+int or_classify_spheres(int64_t n_edges, const int64_t* in_off, const double* inner,
+                        const int64_t* out_off, const double* outer, int n_boxes,
+                        const double* boxes, const uint8_t* present, uint8_t* labels,
+                        double* kappa, uint32_t* hit_bits, uint32_t* touch_bits) {
+  if (n_edges < 0 || n_boxes < 0) return -1;
+  const int W = (n_boxes + 31) / 32;
+#pragma omp parallel for schedule(dynamic, 16) num_threads(or_max_threads())
+  for (int64_t e = 0; e < n_edges; ++e) {
+    double h_in = -INFINITY, h_out = -INFINITY;
+    int any_hit = 0, any_touch = 0;
+    for (int b = 0; b < n_boxes; ++b) {
+      if (present && !present[b]) continue;
+      const double* box = boxes + 15 * (size_t)b;
+      int hit = 0, touch = 0;
+      for (int64_t s = in_off[e]; s < in_off[e + 1]; ++s) {
+        const double v = inner[4 * s + 3] - or_box_distance(box, inner + 4 * s);
+        if (v > h_in) h_in = v;
+        if (v >= 0.0) hit = 1;
+      }
+      for (int64_t s = out_off[e]; s < out_off[e + 1]; ++s) {
+        const double v = outer[4 * s + 3] - or_box_distance(box, outer + 4 * s);
+        if (v > h_out) h_out = v;
+        if (v >= 0.0) touch = 1;
+      }
+      any_hit |= hit;
+      any_touch |= touch;
+      if (hit_bits && hit) hit_bits[(size_t)e * W + (b >> 5)] |= 1u << (b & 31);
+      if (touch_bits && touch) touch_bits[(size_t)e * W + (b >> 5)] |= 1u << (b & 31);
+    }
+    labels[e] = any_hit ? OR_RED : (any_touch ? OR_GRAY : OR_GREEN);
+    if (kappa) kappa[e] = h_in >= 0.0 ? h_in : fmin(-h_in, fabs(h_out));
+  }
+  return 0;
+}
+
+/*
  * Distance from the segment p0 -> p1 to a solid box: the minimum over
  * t in [0, 1] of d(p0 + t (p1 - p0), box).  That function is convex in t (a
  * convex distance composed with an affine map), so a golden-section search

@@ -49,6 +49,10 @@ cudaError_t dalloc(T** p, size_t count) {
   return cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
 }
 
+// Smallest margin for which interpolated inner centres are used (their error
+// is below 2e-6 m, the FP32 tests' below 1e-6 m).
+constexpr float kRegularMinMargin = 1e-5f;
+
 // Streaming tile geometry of one roadmap (see the classify kernel): each
 // stage buffer holds a header, the tile's edge table, 4 inner planes and 4
 // outer planes.
@@ -107,6 +111,7 @@ struct EdgeState {
   uint32_t* d_edge_acc = nullptr;
   uint8_t* d_hist = nullptr;   // [RGG_MAX_REQUESTS][N] request snapshots, allocated on first use
   uint64_t device_bytes = 0;
+  bool regular = false;        // inner spheres equally spaced with one radius per sample
 
   void release() {
     cudaFree(d_soff);
@@ -360,6 +365,29 @@ bool finite_planes(const float* p, uint64_t count, bool radius_plane) {
   return true;
 }
 
+// True when every sample's K inner spheres (consecutive in each plane) share
+// one radius and their centres lie, within 1e-6 m per coordinate, at equal
+// steps on the segment from the first centre to the last.
+bool regular_inner(const float* inner, uint64_t n_in, uint32_t K) {
+  const float* X = inner;
+  const float* Y = inner + n_in;
+  const float* Z = inner + 2 * n_in;
+  const float* R = inner + 3 * n_in;
+  for (uint64_t s = 0; s + K <= n_in; s += K) {
+    for (uint32_t j = 1; j < K; ++j)
+      if (R[s + j] != R[s]) return false;
+    for (uint32_t j = 1; j + 1 < K; ++j) {
+      const double t = (double)j / (double)(K - 1);
+      const float* P[3] = {X, Y, Z};
+      for (const float* c : P) {
+        const double want = (double)c[s] + t * ((double)c[s + K - 1] - (double)c[s]);
+        if (std::fabs((double)c[s + j] - want) > 1e-6) return false;
+      }
+    }
+  }
+  return true;
+}
+
 bool valid_pose(const float* p) {
   for (int c = 0; c < 15; ++c)
     if (!std::isfinite(p[c])) return false;
@@ -414,6 +442,9 @@ ClassifyJob make_job(rgg_roadmap* r, uint32_t C, uint64_t tile_base) {
   j.in_cap = es.tiling.in_cap;
   j.out_cap = es.tiling.out_cap;
   j.margin = r->margin;
+  // interpolated inner centres add up to ~2e-6 m of error on top of the FP32
+  // rounding; the margin must cover both
+  j.regular = (es.regular && r->margin >= kRegularMinMargin) ? 1u : 0u;
   return j;
 }
 
@@ -590,6 +621,9 @@ int rgg_upload_edges(rgg_roadmap_t r, uint64_t num_edges, const uint64_t* sample
     es.release();
     return cuda_status(e);
   }
+  // device-resident uploads are not inspected: they take the exact
+  // per-sphere path
+  es.regular = !src_is_device && num_edges && regular_inner(inner_xyzr, n_in, r->K);
   return install_edges(r, std::move(es), s);
 }
 
@@ -672,6 +706,7 @@ int rgg_build_edges(rgg_roadmap_t r, const rgg_robot_desc* robot, uint64_t num_e
     es.release();
     return cuda_status(e);
   }
+  es.regular = true;  // centres at (j + 1/2)/K of each link, one radius per link
   return install_edges(r, std::move(es), s);
 }
 

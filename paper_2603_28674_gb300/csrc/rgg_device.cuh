@@ -66,6 +66,10 @@ struct ClassifyJob {
   uint32_t off_in, off_out;         // byte offsets of the first inner / outer plane in a stage
   uint32_t in_cap, out_cap;         // floats per plane slot in a stage
   float margin;
+  // 1: every sample's K inner spheres share one radius and sit at equal steps
+  // along a segment (the records rgg_build_edges writes), so the kernel may
+  // interpolate their centres from the first and the last
+  uint32_t regular;
 };
 
 template <int MAXJ>

@@ -232,6 +232,43 @@ __device__ __forceinline__ float box_dist2(float x, float y, float z, const floa
   return fmaf(e0, e0, fmaf(e1, e1, e2 * e2));
 }
 
+// a4 for regular records: does one of the K inner spheres of a sample (first
+// centre at s0 of the tile-local planes, common radius r - margin = rr > 0)
+// lie within rr of box B?  The centres are c_0 + j (c_{K-1} - c_0) / (K-1),
+// so in the box frame only c_0 and c_{K-1} are transformed and the rest are
+// interpolated.  A sample whose centres' box-frame bounding box is farther
+// than rr from the box is rejected first.
+__device__ __forceinline__ bool inner_hit_regular(const float* __restrict__ ix,
+                                                  const float* __restrict__ iy,
+                                                  const float* __restrict__ iz, int s0, int K,
+                                                  float inv_km1, float rr,
+                                                  const float4* __restrict__ B) {
+  const float4 a0 = B[1], a1 = B[2], a2 = B[3], h = B[4];
+  const int s1 = s0 + K - 1;
+  const float x0 = ix[s0], y0 = iy[s0], z0 = iz[s0];
+  const float x1 = ix[s1], y1 = iy[s1], z1 = iz[s1];
+  const float p0 = fmaf(a0.x, x0, fmaf(a0.y, y0, fmaf(a0.z, z0, -a0.w)));
+  const float p1 = fmaf(a1.x, x0, fmaf(a1.y, y0, fmaf(a1.z, z0, -a1.w)));
+  const float p2 = fmaf(a2.x, x0, fmaf(a2.y, y0, fmaf(a2.z, z0, -a2.w)));
+  const float q0 = fmaf(a0.x, x1, fmaf(a0.y, y1, fmaf(a0.z, z1, -a0.w)));
+  const float q1 = fmaf(a1.x, x1, fmaf(a1.y, y1, fmaf(a1.z, z1, -a1.w)));
+  const float q2 = fmaf(a2.x, x1, fmaf(a2.y, y1, fmaf(a2.z, z1, -a2.w)));
+  const float rr2 = rr * rr;
+  const float g0 = fmaxf(fmaxf(fminf(p0, q0) - h.x, -h.x - fmaxf(p0, q0)), 0.0f);
+  const float g1 = fmaxf(fmaxf(fminf(p1, q1) - h.y, -h.y - fmaxf(p1, q1)), 0.0f);
+  const float g2 = fmaxf(fmaxf(fminf(p2, q2) - h.z, -h.z - fmaxf(p2, q2)), 0.0f);
+  if (fmaf(g0, g0, fmaf(g1, g1, g2 * g2)) > rr2) return false;
+  const float d0 = (q0 - p0) * inv_km1, d1 = (q1 - p1) * inv_km1, d2 = (q2 - p2) * inv_km1;
+  for (int j = 0; j < K; ++j) {
+    const float t = (float)j;
+    const float e0 = fmaxf(fabsf(fmaf(t, d0, p0)) - h.x, 0.0f);
+    const float e1 = fmaxf(fabsf(fmaf(t, d1, p1)) - h.y, 0.0f);
+    const float e2 = fmaxf(fabsf(fmaf(t, d2, p2)) - h.z, 0.0f);
+    if (fmaf(e0, e0, fmaf(e1, e1, e2 * e2)) <= rr2) return true;
+  }
+  return false;
+}
+
 // largest j in [0, n) with tab[4*j + field] <= v (tab[field] <= v holds)
 __device__ __forceinline__ int search_le(const int* tab, int field, int n, int v) {
   int lo = 0, hi = n - 1;
@@ -480,6 +517,7 @@ __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const 
     const int C = (int)J.C;
     const float margin = J.margin;
     const float inv_k = 1.0f / (float)K;
+    const float inv_km1 = K > 1 ? 1.0f / (float)(K - 1) : 0.0f;
     const float* ix = reinterpret_cast<const float*>(sb + J.off_in) + hdr.in_shift;
     const float* iy = ix + J.in_cap;
     const float* iz = iy + J.in_cap;
@@ -562,7 +600,33 @@ __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const 
         if (lane >= d) incl += v;
       }
       const int total = __shfl_sync(0xffffffffu, incl, 31);
-      if (total > 0 && total <= kPairQueue) {
+      if (J.regular && total > 0) {
+        // one (sample, box) pair per lane, compacted when they fit the queue
+        if (total <= kPairQueue) {
+          int pos = incl - cnt;
+          for (uint32_t m = need; m; m &= m - 1)
+            queue[pos++] = ((uint32_t)q << 13) | ((uint32_t)j << 5) | (uint32_t)(__ffs(m) - 1);
+          __syncwarp();
+          for (int it = lane; it < total; it += 32) {
+            const uint32_t e = queue[it];
+            const int s0 = K * (int)(e >> 13);
+            const float rr = ir[s0] - margin;
+            if (rr > 0.0f && inner_hit_regular(ix, iy, iz, s0, K, inv_km1, rr, bx + 6 * (int)(e & 31u)))
+              atomicOr(&acc_hit[(e >> 5) & 255u], 1u << (e & 31u));
+          }
+          __syncwarp();
+        } else {
+          uint32_t hits = 0;
+          const float rr = need ? ir[K * q] - margin : 0.0f;
+          if (rr > 0.0f)
+            for (uint32_t m = need; m; m &= m - 1) {
+              const int b = __ffs(m) - 1;
+              if (inner_hit_regular(ix, iy, iz, K * q, K, inv_km1, rr, bx + 6 * b)) hits |= 1u << b;
+            }
+          if (hits) atomicOr(&acc_hit[j], hits);
+          __syncwarp();
+        }
+      } else if (total > 0 && total <= kPairQueue) {
         // compact the (sample, box) pairs, then test (pair, sphere) items on
         // all lanes, two items per lane per iteration
         int pos = incl - cnt;

@@ -322,3 +322,68 @@ def test_kernel_timing_counts_launches(rgg):
         r.classify()
         ms, mm, n = r.kernel_time()
         assert n == 1 and ms > 0 and mm > 0
+
+
+def test_interpolated_and_per_sphere_inner_tests(rgg):
+    """Records built in place take the interpolated inner test; the same
+    records uploaded from device memory are not inspected and take the
+    per-sphere test.  Both meet the oracle rule, and they differ only on
+    unpinned edges."""
+    import torch
+    sc = W.workload_7dof(n_nodes=600, n_updates=3)
+    rm, robot = sc.roadmap, sc.roadmap.robot
+    boxes = sc.boxes.copy()
+    ids = np.arange(boxes.count)
+    with make_roadmap(rgg, rm, boxes.count) as a:
+        inner, outer, soff = a.fetch_records()
+        with rgg.Roadmap(robot.num_links, robot.inner_per_link, boxes.count) as b:
+            b.upload_edges(soff, torch.from_numpy(inner).cuda(), torch.from_numpy(outer).cuda())
+            for x in (a, b):
+                x.update_obstacles(ids, f32(boxes.poses()))
+                x.classify()
+            for up in sc.updates:
+                boxes.centre[up.ids] = up.poses[:, :3]
+                for x in (a, b):
+                    x.update_obstacles(up.ids, f32(up.poses))
+                    x.classify()
+                want = oracle.classify(robot, rm.q_from, rm.q_to, rm.step, boxes.poses())
+                la, lb = a.fetch_labels(), b.fetch_labels()
+                check_labels(la, want, "interpolated")
+                check_labels(lb, want, "per-sphere")
+                assert np.all(want["kappa"][la != lb] <= PIN)
+
+
+def test_irregular_uploads_take_the_exact_sphere_test(rgg):
+    """Host-uploaded records whose inner spheres are not equally spaced with
+    one radius are classified sphere by sphere: a third of the samples get a
+    second sphere of radius 0.1 m next to the link's midpoint (still inside
+    the interval's outer spheres), and the labels follow the oracle on those
+    exact sphere sets."""
+    sc = W.workload_planar(n_nodes=200, n_updates=0)
+    rm, robot = sc.roadmap, sc.roadmap.robot
+    L, K = robot.num_links, robot.inner_per_link
+    n_boxes = 4
+    poses = sc.boxes.poses()[:n_boxes]
+    with make_roadmap(rgg, rm, n_boxes) as a:
+        inner, outer, soff = a.fetch_records()
+    soff = soff.astype(np.int64)
+    n_edges = len(soff) - 1
+    in_off = K * L * soff
+    out_off = L * (soff - np.arange(n_edges + 1))
+    original = oracle.classify_spheres(in_off, inner.T, out_off, outer.T, poses)
+    rng = np.random.default_rng(3)
+    bent = inner.copy()
+    n_samp = bent.shape[1] // K
+    s0 = rng.choice(n_samp, size=n_samp // 3, replace=False) * K
+    mid = (bent[:3, s0] + bent[:3, s0 + K - 1]) / 2
+    bent[:3, s0 + 1] = mid + np.array([[0.03], [0.03], [0.0]], dtype=np.float32)
+    bent[3, s0 + 1] = 0.1
+    want = oracle.classify_spheres(in_off, bent.T, out_off, outer.T, poses)
+    changed = (want["labels"] != original["labels"]) & (want["kappa"] > PIN)
+    assert changed.sum() >= 10, "the perturbation must matter for the test to mean anything"
+    with rgg.Roadmap(L, K, n_boxes) as b:
+        b.upload_edges(soff.astype(np.uint64), bent, outer)
+        b.update_obstacles(np.arange(n_boxes), f32(poses))
+        b.classify()
+        got = b.fetch_labels()
+    check_labels(got, want, "irregular upload")

@@ -367,3 +367,54 @@ def test_red_collides_and_green_is_free(oracle, which):
     for e in green:
         v, _ = oracle.edge_dense_clearance(rm.robot, rm.q_from[e], rm.q_to[e], rm.step, 10, poses)
         assert v > 0.0
+
+
+# --------------------------------------------------------------------------
+# labels from caller-supplied sphere sets
+# --------------------------------------------------------------------------
+def test_classify_spheres_hand_cases(oracle):
+    """Hand-derived labels and clearances for single spheres against the box
+    of half-extent 0.1 at the origin (a second, far box is absent)."""
+    box = box_pose([0, 0, 0], np.eye(3), [0.1] * 3)
+    far = box_pose([0.3, 0, 0], np.eye(3), [0.05] * 3)   # would hit edge 1: absent
+    inner = [[0.15, 0, 0, 0.06],      # e0: d = 0.05 <= 0.06: hit by 0.01
+             [0.3, 0, 0, 0.05],       # e1: d = 0.2: miss by 0.15
+             [1, 1, 1, 0.1],          # e2: d = 0.9 sqrt(3)
+             [0.2, 0, 0, 0.1]]        # e3: d = 0.1 = r: contact counts
+    outer = [[0.15, 0, 0, 0.2],       # e0
+             [0.25, 0, 0, 0.2],       # e1: d = 0.15 <= 0.2: touch by 0.05
+             [1, 1, 1, 0.2],          # e2: miss
+             [0.2, 0, 0, 0.15]]       # e3
+    in_off = [0, 1, 2, 3, 4, 4]       # e4 has no spheres at all
+    out_off = [0, 1, 2, 3, 4, 4]
+    out = oracle.classify_spheres(in_off, inner, out_off, outer, [box, far], present=[1, 0],
+                                  bits=True)
+    R, G, Y = oracle.RED, oracle.GREEN, oracle.GRAY
+    assert list(out["labels"]) == [R, Y, G, R, G]
+    d2 = 0.9 * math.sqrt(3)
+    np.testing.assert_allclose(out["kappa"][:4], [0.01, 0.05, min(d2 - 0.1, d2 - 0.2), 0.0],
+                               atol=1e-12)
+    assert math.isinf(out["kappa"][4])
+    assert list(out["hit"][:, 0]) == [1, 0, 0, 1, 0]
+    assert list(out["touch"][:, 0]) == [1, 1, 0, 1, 0]
+    # with the far box present, edge 1's inner sphere (d = 0.05 to it) is a hit
+    out = oracle.classify_spheres(in_off, inner, out_off, outer, [box, far], bits=True)
+    assert out["labels"][1] == R and out["hit"][1, 0] == 2
+
+
+def test_classify_spheres_agrees_with_robot_classify(oracle, small_7dof):
+    """The robot's own spheres fed as explicit sets give the robot
+    classification's labels and clearances."""
+    rm, boxes = small_7dof
+    ins, outs, io, oo = [], [], [0], [0]
+    for e in range(40):
+        si, so = oracle.edge_spheres(rm.robot, rm.q_from[e], rm.q_to[e], rm.step)
+        ins.append(si.reshape(-1, 4))
+        outs.append(so.reshape(-1, 4))
+        io.append(io[-1] + ins[-1].shape[0])
+        oo.append(oo[-1] + outs[-1].shape[0])
+    got = oracle.classify_spheres(io, np.concatenate(ins), oo, np.concatenate(outs),
+                                  boxes.poses())
+    want = oracle.classify(rm.robot, rm.q_from[:40], rm.q_to[:40], rm.step, boxes.poses())
+    np.testing.assert_array_equal(got["labels"], want["labels"])
+    np.testing.assert_allclose(got["kappa"], want["kappa"], rtol=0, atol=1e-12)
