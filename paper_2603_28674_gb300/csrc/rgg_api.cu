@@ -445,6 +445,8 @@ ClassifyJob make_job(rgg_roadmap* r, uint32_t C, uint64_t tile_base) {
   // interpolated inner centres add up to ~2e-6 m of error on top of the FP32
   // rounding; the margin must cover both
   j.regular = (es.regular && r->margin >= kRegularMinMargin) ? 1u : 0u;
+  j.inv_k = 1.0f / (float)r->K;
+  j.inv_km1 = r->K > 1 ? 1.0f / (float)(r->K - 1) : 0.0f;
   return j;
 }
 

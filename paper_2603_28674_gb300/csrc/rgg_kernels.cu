@@ -506,7 +506,9 @@ __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const 
     unsigned char* sb = stages + (size_t)stage * STAGE_BYTES;
     const StageHdr hdr = *reinterpret_cast<const StageHdr*>(sb);
     if (hdr.end) break;
-    const ClassifyJob& J = P.job[hdr.job];
+    // a single-roadmap launch has one job: a constant index lets every job
+    // field stay a plain parameter read
+    const ClassifyJob& J = P.job[MAXJ == 1 ? 0 : hdr.job];
     const int n_samp = hdr.n_samp, n_edges = hdr.n_edges;
     const int* etab = reinterpret_cast<const int*>(sb + kStageEtabOff);
     // per-stage accumulators live at a fixed place whatever the job, so a
@@ -516,8 +518,8 @@ __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const 
     const int K = (int)J.K;
     const int C = (int)J.C;
     const float margin = J.margin;
-    const float inv_k = 1.0f / (float)K;
-    const float inv_km1 = K > 1 ? 1.0f / (float)(K - 1) : 0.0f;
+    const float inv_k = J.inv_k;
+    const float inv_km1 = J.inv_km1;
     const float* ix = reinterpret_cast<const float*>(sb + J.off_in) + hdr.in_shift;
     const float* iy = ix + J.in_cap;
     const float* iz = iy + J.in_cap;

@@ -287,6 +287,8 @@ extern "C" int rgg_classify_noalloc(const rgg_noalloc_args* a, void* stream) {
   j.in_cap = tl.in_cap;
   j.out_cap = tl.out_cap;
   j.margin = a->margin_m;
+  j.inv_k = 1.0f / (float)K;
+  j.inv_km1 = K > 1 ? 1.0f / (float)(K - 1) : 0.0f;
   cp.njobs = 1;
   cp.total_tiles = T;
   cp.status = reinterpret_cast<int*>(base + kNaStatusOff);
