@@ -554,6 +554,7 @@ __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const 
       float x = ox[o], y = oy[o], z = oz[o], r = orad[o];
       const uint32_t act = __ballot_sync(0xffffffffu, has_next);
       uint32_t bits = 0;
+      uint32_t any_cand = 0;
       if (act) {
         // any active lane's sphere can centre the bounding sphere
         const int mid = (act & 0xffff0000u) ? __ffs(act & 0xffff0000u) - 1 : 31 - __clz(act);
@@ -571,6 +572,7 @@ __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const 
           cb = fmaf(ex, ex, fmaf(ey, ey, ez * ez)) <= thr * thr;
         }
         uint32_t cand = __ballot_sync(0xffffffffu, cb);
+        any_cand = cand;
         const float rt = r + margin;
         const float rt2 = rt * rt;
         // two candidate boxes per iteration for instruction-level parallelism
@@ -586,6 +588,8 @@ __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const 
         if (!has_next) bits = 0;
         if (bits) atomicOr(&acc_touch[j], bits);
       }
+      // no moved box near the round: nothing touched, so no inner test either
+      if (!any_cand) continue;
       // ---- a4: inner spheres of q against the boxes touched by the
       // intervals before and after it
       const uint32_t prev = __shfl_up_sync(0xffffffffu, bits, 1);
