@@ -70,8 +70,9 @@ enum rgg_status {
   RGG_ERR_CUDA = -3,     /* a CUDA runtime call failed                     */
   RGG_ERR_TIMEOUT = -4,  /* a bounded device-side wait ran out             */
   RGG_ERR_STATE = -5,    /* call not valid in the roadmap's current state  */
-  RGG_ERR_CAPACITY = -6  /* over a fixed capacity: rgg_classify_noalloc's     */
+  RGG_ERR_CAPACITY = -6, /* over a fixed capacity: rgg_classify_noalloc's     */
                          /* scratch, pending entries or open requests        */
+  RGG_ERR_IO = -7        /* a file could not be opened, read or written      */
 };
 
 /* Edge labels (Sec. 4.1): valid, unknown, invalid. */
@@ -320,6 +321,37 @@ int rgg_kernel_time(rgg_roadmap_t r, double* classify_ms, double* merge_ms, uint
  * rgg_classify_many must share the variant.  RGG_ERR_INVALID for an
  * unsupported shape (nothing changes). */
 int rgg_set_launch_shape(rgg_roadmap_t r, uint32_t variant, uint32_t consumer_warps);
+
+/* ------------------------------------------------------------------------ */
+/* Persistence: the resident roadmap to and from a file (Sec. 1: serialized
+ * roadmap data is stored and reloaded between planning iterations; Sec. 4.3:
+ * the serialized matrices are built once and kept).
+ *
+ * rgg_save writes the records, the per-edge state (box sets, counts,
+ * labels), the box table and which boxes are present.  The roadmap must have
+ * edges and no pending moves (RGG_ERR_STATE otherwise), so that the saved
+ * labels are those of the saved boxes.  It waits for `stream` first, then
+ * copies through a 64 MB page-locked buffer.
+ *
+ * rgg_load replaces the roadmap's edges and state with a saved file's.  The
+ * roadmap must have the file's num_links, inner_per_link and max_obstacles
+ * (RGG_ERR_INVALID otherwise, nothing changed); the margin and launch shape
+ * stay the roadmap's own.  Pending moves are dropped and open request
+ * handles closed.  After the call the labels, box sets and boxes equal the
+ * saved ones, and later updates classify as they would have on the saved
+ * roadmap.  Synchronous.
+ *
+ * File layout (little-endian): a 96-byte header ("RGGSAVE1", version, L, K,
+ * M, mask words, margin, flags, N, S, inner and outer counts), then
+ * sample_off[N+1] (uint64), inner planes (4 x K*L*S float), outer planes
+ * (4 x L*(S-N) float), hit and touch sets (2 x N x mask words uint32),
+ * counts[N] (uint32), labels[N] (uint8), box table (M x 16 float),
+ * present[M] (uint8), and a 64-bit checksum of everything before it.
+ * RGG_ERR_IO if the file cannot be opened, read or written; RGG_ERR_INVALID
+ * for a header that does not match, a truncated file or a checksum
+ * mismatch. */
+int rgg_save(rgg_roadmap_t r, const char* path, void* stream);
+int rgg_load(rgg_roadmap_t r, const char* path, void* stream);
 
 /* ------------------------------------------------------------------------ */
 /* Autotuner of the classify launch shape (the paper has none: its batched

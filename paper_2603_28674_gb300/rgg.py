@@ -20,6 +20,7 @@ GREEN, GRAY, RED = 0, 1, 2
 RGG_OK, RGG_ERR_INVALID, RGG_ERR_OOM, RGG_ERR_CUDA, RGG_ERR_TIMEOUT, RGG_ERR_STATE = \
     0, -1, -2, -3, -4, -5
 RGG_ERR_CAPACITY = -6
+RGG_ERR_IO = -7
 NOALLOC_MAX_EDGES = 131072
 NOALLOC_MAX_TILES = 16384
 BOXES_PER_PASS = 32
@@ -39,7 +40,7 @@ EXPORTS = (
     "rgg_status_string", "rgg_classify_noalloc", "rgg_update_request",
     "rgg_fetch_request_labels", "rgg_release_request", "rgg_autotune",
     "rgg_step_graph_create", "rgg_step_graph_launch", "rgg_step_graph_nodes",
-    "rgg_step_graph_destroy",
+    "rgg_step_graph_destroy", "rgg_save", "rgg_load",
 )
 
 
@@ -135,6 +136,8 @@ def _lib():
         "rgg_step_graph_launch": [vp, vp],
         "rgg_step_graph_nodes": [vp, ctypes.POINTER(u64)],
         "rgg_step_graph_destroy": [vp],
+        "rgg_save": [vp, ctypes.c_char_p, vp],
+        "rgg_load": [vp, ctypes.c_char_p, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -360,6 +363,17 @@ class Roadmap:
 
     def check_status(self, stream=None) -> None:
         _check("rgg_check_status", _lib().rgg_check_status(self._h, _stream(stream, self.device)))
+
+    # -- persistence ----------------------------------------------------------
+    def save(self, path, stream=None) -> None:
+        """Write the records, per-edge state and boxes to `path` (rgg_save)."""
+        _check("rgg_save", _lib().rgg_save(self._h, os.fsencode(path),
+                                           _stream(stream, self.device)))
+
+    def load(self, path, stream=None) -> None:
+        """Replace edges and state with a file rgg_save wrote (rgg_load)."""
+        _check("rgg_load", _lib().rgg_load(self._h, os.fsencode(path),
+                                           _stream(stream, self.device)))
 
     # -- timing and launch shape ----------------------------------------------
     def set_kernel_timing(self, enable: bool) -> None:
