@@ -19,6 +19,7 @@ timing only).
 from __future__ import annotations
 
 import argparse
+import ctypes
 import hashlib
 import json
 import os
@@ -51,6 +52,9 @@ def parse():
     ap.add_argument("--workload", default="large",
                     choices=["large", "7dof", "planar", "batched", "serve"])
     ap.add_argument("--roadmaps", type=int, default=128, help="batched workload: roadmaps")
+    ap.add_argument("--resolve", type=int, default=0, metavar="F",
+                    help="also time the non-lazy resolution of the gray edges at F-times "
+                         "finer resampling (0: off)")
     ap.add_argument("--serve-seconds", type=float, default=3.0,
                     help="serve workload: seconds of Poisson arrivals at 2000 requests/s")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -372,6 +376,8 @@ def run_gpu(args):
     e2e_s = time.perf_counter() - t0
     e2e_s = max_over_ranks(dist, e2e_s, f"cuda:{local}")
     r.check_status(stream)
+    resolve = measure_resolve(r, sc, args.resolve, stream, rank == 0 and world == 1) \
+        if args.resolve else None
 
     n_edges = info["num_edges"]
     value = replica_throughput(world, n_edges * args.steps, ms / 1000.0)
@@ -415,6 +421,8 @@ def run_gpu(args):
         "clocks": clk,
         "cpu_baseline": cpu,
     }
+    if resolve is not None:
+        line["resolve"] = resolve
     r.close()
     if rank == 0:
         print(json.dumps(line))
@@ -422,6 +430,56 @@ def run_gpu(args):
         dist.barrier()
         dist.destroy_process_group()
     return 0
+
+
+def measure_resolve(r, sc, factor: int, stream, with_oracle: bool) -> dict:
+    """Time rgg_resolve_gray on the roadmap's current state (one warm-up, then
+    three timed calls with CUDA events on the stream), and the oracle's dense
+    clearance on a sample of the same gray edges."""
+    import torch
+    from paper_2603_28674_gb300 import rgg
+    n = r.info()["num_edges"]
+    out = torch.empty(n, dtype=torch.uint8, device=stream.device)
+    clear = torch.empty(n, dtype=torch.float32, device=stream.device)
+    st = rgg._ResolveStats()
+    lib = rgg._lib()
+
+    def call(stats):
+        rgg._check("rgg_resolve_gray", lib.rgg_resolve_gray(
+            r.handle, factor, out.data_ptr(), clear.data_ptr(), 1,
+            ctypes.byref(st) if stats else None, int(stream.cuda_stream)))
+
+    call(True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(3):
+        call(False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / 3
+    res = {"factor": factor, "gray_edges": st.gray_edges, "resolved_red": st.resolved_red,
+           "resolved_green": st.resolved_green, "evaluations": st.evaluations, "ms": ms,
+           "gray_edges_per_s": st.gray_edges / (ms / 1e3),
+           "evaluations_per_s": st.evaluations / (ms / 1e3)}
+    if with_oracle and st.gray_edges:
+        import oracle
+        lazy = r.fetch_labels(stream=stream)
+        gray = np.flatnonzero(lazy == rgg.GRAY)
+        rng = np.random.default_rng(5)
+        sample = rng.choice(gray, size=min(16, gray.size), replace=False)
+        poses, present = r.fetch_boxes()
+        t0 = time.perf_counter()
+        for e in sample:
+            oracle.edge_dense_clearance(sc.roadmap.robot, sc.roadmap.q_from[e],
+                                        sc.roadmap.q_to[e], sc.roadmap.step, factor,
+                                        poses.astype(np.float64), present=present)
+        t = time.perf_counter() - t0
+        res["cpu_baseline"] = {"value": len(sample) / t, "unit": "gray edges/s", "cores": 1,
+                               "kind": "oracle",
+                               "sample": f"{len(sample)} gray edges, dense clearance over all "
+                                         "present boxes, one thread"}
+    return res
 
 
 def run_batched(args):

@@ -87,6 +87,7 @@ enum {
   RGG_NUM_VARIANTS = 7,        /* compiled pipeline shapes (rgg_set_launch_shape) */
   RGG_MAX_REQUESTS = 64,       /* open requests per roadmap (rgg_update_request) */
   RGG_PENDING_EXTRA = 4096,    /* pending entries beyond max_obstacles          */
+  RGG_MAX_RESOLVE_FACTOR = 100, /* rgg_resolve_gray: resampling factor           */
   RGG_NOALLOC_MAX_EDGES = 131072,  /* rgg_classify_noalloc: edges per call          */
   RGG_NOALLOC_MAX_TILES = 16384    /* rgg_classify_noalloc: tiles of up to 527      */
                                    /* configurations x links per call               */
@@ -293,6 +294,12 @@ int rgg_fetch_box_sets(rgg_roadmap_t r, uint32_t* hit, uint32_t* touch, uint64_t
 int rgg_fetch_records(rgg_roadmap_t r, uint64_t first, uint64_t count, float* inner_xyzr,
                       float* outer_xyzr, uint64_t* sample_off);
 
+/* Copy the box table: pose[15*b .. 15*b+14] (centre, R row-major,
+ * half-extents; the last pose given to the box, pending or not) and
+ * present[b] (1 once the box has been placed) for every box id b <
+ * max_obstacles, to host arrays (either may be NULL).  Waits for `stream`. */
+int rgg_fetch_boxes(rgg_roadmap_t r, float* pose, uint8_t* present, void* stream);
+
 /* Device pointer to the label array (N bytes, valid until the edges are
  * replaced or the roadmap destroyed), for zero-copy use on the device. */
 int rgg_labels_device_ptr(rgg_roadmap_t r, const uint8_t** out);
@@ -321,6 +328,44 @@ int rgg_kernel_time(rgg_roadmap_t r, double* classify_ms, double* merge_ms, uint
  * rgg_classify_many must share the variant.  RGG_ERR_INVALID for an
  * unsupported shape (nothing changes). */
 int rgg_set_launch_shape(rgg_roadmap_t r, uint32_t variant, uint32_t consumer_warps);
+
+/* ------------------------------------------------------------------------ */
+/* Non-lazy resolution of gray edges (Algorithm 1 with lazy = false: gray
+ * edges are validated by a full check).  For every edge whose current label
+ * is GRAY, the robot's link capsules (segment between consecutive frame
+ * origins, radius R_i) are checked at (n_e - 1) * factor + 1 configurations
+ * q(t) = q_from + t (q_to - q_from), t = c / ((n_e - 1) factor), which
+ * include the edge's own configurations, against the boxes of the edge's
+ * touch set (only boxes an outer sphere touched can meet a capsule).  The
+ * clearance is the minimum over those configurations, links and boxes of
+ * (distance from the capsule axis to the box - R_i), computed exactly per
+ * (configuration, link, box) in FP32.  With thr = max(margin_m, 1e-5 m)
+ * (the FP32 error stays below 5e-6 m):
+ *   clearance <= -thr: RED (the robot collides at some checked configuration)
+ *   clearance >= thr:  GREEN (it is free at every checked configuration)
+ *   otherwise:         GRAY (too close to decide in FP32).
+ * Edges that are not gray keep their label.  The roadmap's own labels and
+ * box sets are not changed (the next classify works on the lazy state).
+ *   factor         1 .. RGG_MAX_RESOLVE_FACTOR
+ *   labels_out     N resolved labels (may be NULL)
+ *   clearance_out  N floats: the gray edges' clearance (NaN for edges that
+ *                  were not gray; a RED edge reports the first clearance
+ *                  below -thr found, not the minimum) (may be NULL)
+ *   dst_is_device  0: host buffers (the call waits); 1: device buffers
+ *   stats          counts of gray edges, resolved red / green edges and
+ *                  capsule-box evaluations (may be NULL; the call then
+ *                  waits for the stream)
+ * Needs edges built by rgg_build_edges (the robot and the endpoints are
+ * kept) and no pending moves: RGG_ERR_STATE otherwise. */
+typedef struct {
+  uint64_t gray_edges;
+  uint64_t resolved_red;
+  uint64_t resolved_green;
+  uint64_t evaluations;
+} rgg_resolve_stats;
+
+int rgg_resolve_gray(rgg_roadmap_t r, uint32_t factor, uint8_t* labels_out, float* clearance_out,
+                     int dst_is_device, rgg_resolve_stats* stats, void* stream);
 
 /* ------------------------------------------------------------------------ */
 /* Persistence: the resident roadmap to and from a file (Sec. 1: serialized

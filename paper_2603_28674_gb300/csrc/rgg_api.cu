@@ -110,6 +110,10 @@ struct EdgeState {
   uint8_t* d_labels = nullptr;
   uint32_t* d_edge_acc = nullptr;
   uint8_t* d_hist = nullptr;   // [RGG_MAX_REQUESTS][N] request snapshots, allocated on first use
+  double* d_qa = nullptr;      // [N][L] edge endpoints (edges built by rgg_build_edges only)
+  double* d_qb = nullptr;
+  uint8_t* d_resolved = nullptr;  // [N] labels of the last gray resolution
+  float* d_clear = nullptr;       // [N] its clearances
   uint64_t device_bytes = 0;
   bool regular = false;        // inner spheres equally spaced with one radius per sample
 
@@ -125,6 +129,10 @@ struct EdgeState {
     cudaFree(d_labels);
     cudaFree(d_edge_acc);
     cudaFree(d_hist);
+    cudaFree(d_qa);
+    cudaFree(d_qb);
+    cudaFree(d_resolved);
+    cudaFree(d_clear);
     *this = EdgeState();
   }
 };
@@ -140,6 +148,10 @@ struct rgg_roadmap {
   int variant = kDefaultVariant;
   bool has_edges = false;
   uint64_t gen = 0;            // bumped whenever tiles or edges are replaced
+  // the robot of edges built by rgg_build_edges (for the gray resolution)
+  bool has_robot = false;
+  double dh_a[RGG_MAX_LINKS], dh_alpha[RGG_MAX_LINKS], dh_d[RGG_MAX_LINKS], dh_radius[RGG_MAX_LINKS];
+  unsigned long long* d_work = nullptr;  // [4] resolution counters
   EdgeState es;
   float* d_table = nullptr;    // [M][16] box poses
   float* d_stage = nullptr;    // [stage_rows][16] staged pose of each pending entry
@@ -562,6 +574,7 @@ int rgg_roadmap_create(const rgg_roadmap_desc* desc, rgg_roadmap_t* out) {
   if (e == cudaSuccess) e = dalloc(&r->d_stage, (size_t)r->stage_rows * 16);
   if (e == cudaSuccess) e = dalloc(&r->d_changed, (size_t)kBoxesPerPass * kBoxRecFloats);
   if (e == cudaSuccess) e = dalloc(&r->d_status, 4);
+  if (e == cudaSuccess) e = dalloc(&r->d_work, 4);
   if (e == cudaSuccess) e = cudaMemset(r->d_table, 0, (size_t)r->M * 16 * sizeof(float));
   if (e == cudaSuccess) e = cudaMemset(r->d_status, 0, 4 * sizeof(int));
   if (e != cudaSuccess) {
@@ -569,6 +582,7 @@ int rgg_roadmap_create(const rgg_roadmap_desc* desc, rgg_roadmap_t* out) {
     cudaFree(r->d_stage);
     cudaFree(r->d_changed);
     cudaFree(r->d_status);
+    cudaFree(r->d_work);
     delete r;
     return cuda_status(e);
   }
@@ -585,6 +599,7 @@ int rgg_roadmap_destroy(rgg_roadmap_t r) {
   cudaFree(r->d_stage);
   cudaFree(r->d_changed);
   cudaFree(r->d_status);
+  cudaFree(r->d_work);
   for (auto& ev : r->events)
     for (cudaEvent_t x : ev) cudaEventDestroy(x);
   delete r;
@@ -627,6 +642,7 @@ int rgg_upload_edges(rgg_roadmap_t r, uint64_t num_edges, const uint64_t* sample
   // device-resident uploads are not inspected: they take the exact
   // per-sphere path
   es.regular = !src_is_device && num_edges && regular_inner(inner_xyzr, n_in, r->K);
+  r->has_robot = false;
   return install_edges(r, std::move(es), s);
 }
 
@@ -704,13 +720,30 @@ int rgg_build_edges(rgg_roadmap_t r, const rgg_robot_desc* robot, uint64_t num_e
   bp.n_edges = num_edges;
   e = launch_build_records(bp, r->num_sms, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  cleanup();
+  cudaFree(d_counts);
+  cudaFree(d_bad);
   if (e != cudaSuccess) {
+    cudaFree(d_qa);
+    cudaFree(d_qb);
     es.release();
     return cuda_status(e);
   }
+  // the endpoints stay for the gray resolution
+  es.d_qa = d_qa;
+  es.d_qb = d_qb;
+  es.device_bytes += 2 * qn * sizeof(double);
   es.regular = true;  // centres at (j + 1/2)/K of each link, one radius per link
-  return install_edges(r, std::move(es), s);
+  rc = install_edges(r, std::move(es), s);
+  if (rc == RGG_OK) {
+    r->has_robot = true;
+    for (uint32_t i = 0; i < r->L; ++i) {
+      r->dh_a[i] = robot->a[i];
+      r->dh_alpha[i] = robot->alpha[i];
+      r->dh_d[i] = robot->d[i];
+      r->dh_radius[i] = robot->radius[i];
+    }
+  }
+  return rc;
 }
 
 // Checks a move's ids and host poses; counts the entries it would append.
@@ -1027,6 +1060,23 @@ int rgg_fetch_records(rgg_roadmap_t r, uint64_t first, uint64_t count, float* in
   return RGG_OK;
 }
 
+int rgg_fetch_boxes(rgg_roadmap_t r, float* pose, uint8_t* present, void* stream) {
+  if (!r) return RGG_ERR_INVALID;
+  DeviceGuard g(r->device);
+  if (!g.ok) return RGG_ERR_CUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (pose) {
+    std::vector<float> rows((size_t)r->M * 16);
+    RGG_CK(cudaMemcpyAsync(rows.data(), r->d_table, rows.size() * sizeof(float),
+                           cudaMemcpyDeviceToHost, s));
+    RGG_CK(cudaStreamSynchronize(s));
+    for (uint32_t b = 0; b < r->M; ++b)
+      std::memcpy(pose + 15 * (size_t)b, rows.data() + 16 * (size_t)b, 15 * sizeof(float));
+  }
+  if (present) std::memcpy(present, r->present.data(), r->M);
+  return RGG_OK;
+}
+
 int rgg_labels_device_ptr(rgg_roadmap_t r, const uint8_t** out) {
   if (!r || !out) return RGG_ERR_INVALID;
   if (!r->has_edges) return RGG_ERR_STATE;
@@ -1100,6 +1150,72 @@ int rgg_set_launch_shape(rgg_roadmap_t r, uint32_t variant, uint32_t consumer_wa
   DeviceGuard g(r->device);
   if (!g.ok) return RGG_ERR_CUDA;
   return apply_shape(r, (int)variant, cw);
+}
+
+// ---------------------------------------------------------------------------
+// Non-lazy resolution of gray edges
+// ---------------------------------------------------------------------------
+int rgg_resolve_gray(rgg_roadmap_t r, uint32_t factor, uint8_t* labels_out, float* clearance_out,
+                     int dst_is_device, rgg_resolve_stats* stats, void* stream) {
+  if (!r || factor < 1 || factor > RGG_MAX_RESOLVE_FACTOR || dst_is_device < 0 ||
+      dst_is_device > 1)
+    return RGG_ERR_INVALID;
+  if (!r->has_edges || !r->has_robot || !r->pending.empty()) return RGG_ERR_STATE;
+  DeviceGuard g(r->device);
+  if (!g.ok) return RGG_ERR_CUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  EdgeState& es = r->es;
+  const uint64_t N = es.N;
+  if (N && !es.d_resolved) {
+    cudaError_t e = dalloc(&es.d_resolved, N);
+    if (e == cudaSuccess) e = dalloc(&es.d_clear, N);
+    if (e != cudaSuccess) {
+      cudaFree(es.d_resolved);
+      es.d_resolved = nullptr;
+      return cuda_status(e);
+    }
+    es.device_bytes += 5 * N;
+  }
+  RGG_CK(cudaMemsetAsync(r->d_work, 0, 4 * sizeof(unsigned long long), s));
+  ResolveParams p{};
+  p.L = r->L;
+  p.Wm = r->Wm;
+  p.F = factor;
+  // FP32 kinematics and distances stay within ~5e-6 m; the margin covers that
+  p.thr = std::max(r->margin, kRegularMinMargin);
+  for (uint32_t i = 0; i < r->L; ++i) {
+    p.a[i] = (float)r->dh_a[i];
+    p.d[i] = (float)r->dh_d[i];
+    p.ca[i] = (float)std::cos(r->dh_alpha[i]);
+    p.sa[i] = (float)std::sin(r->dh_alpha[i]);
+    p.radius[i] = (float)r->dh_radius[i];
+  }
+  p.qa = es.d_qa;
+  p.qb = es.d_qb;
+  p.soff = es.d_soff;
+  p.labels = es.d_labels;
+  p.touch = es.d_touch;
+  p.table = r->d_table;
+  p.out = es.d_resolved;
+  p.clearance = es.d_clear;
+  p.work = r->d_work;
+  p.n_edges = N;
+  RGG_CK(launch_resolve_gray(p, r->num_sms, s));
+  const cudaMemcpyKind kind = dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (labels_out && N) RGG_CK(cudaMemcpyAsync(labels_out, es.d_resolved, N, kind, s));
+  if (clearance_out && N)
+    RGG_CK(cudaMemcpyAsync(clearance_out, es.d_clear, N * sizeof(float), kind, s));
+  if (stats) {
+    unsigned long long w[4] = {0, 0, 0, 0};
+    RGG_CK(cudaMemcpyAsync(w, r->d_work, sizeof(w), cudaMemcpyDeviceToHost, s));
+    RGG_CK(cudaStreamSynchronize(s));
+    stats->gray_edges = w[0];
+    stats->resolved_red = w[1];
+    stats->resolved_green = w[2];
+    stats->evaluations = w[3];
+  }
+  if (!dst_is_device && (labels_out || clearance_out)) return check_status_locked(r, s);
+  return RGG_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -1312,6 +1428,7 @@ int rgg_load(rgg_roadmap_t r, const char* path, void* stream) {
   r->es.release();
   r->es = std::move(es);
   r->has_edges = true;
+  r->has_robot = false;
   ++r->gen;
   clear_pending(r);
   std::fill(r->req_state.begin(), r->req_state.end(), 0);

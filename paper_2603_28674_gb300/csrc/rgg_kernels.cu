@@ -780,6 +780,202 @@ __global__ void __launch_bounds__(256) merge_kernel(const __grid_constant__ Merg
 }
 
 // ===========================================================================
+// Non-lazy resolution of gray edges (Algorithm 1, lazy = false)
+// ===========================================================================
+// Squared distance from the segment p -> p + dlt to the box [-h, h] (box
+// frame), exactly.  Along the segment each axis contributes
+// max(0, |x_k(t)| - h_k)^2, so the sum is a convex piecewise quadratic in t
+// whose pieces end where a coordinate crosses -h_k or +h_k.  The six
+// crossings, clamped to [0, 1], are sorted by a fixed 12-comparator network;
+// on each of the seven pieces the quadratic sum_k (o_k + t d_k)^2 over the
+// axes outside the box there is minimised in closed form.
+__device__ __forceinline__ float seg_box_dist2(const float p[3], const float dlt[3],
+                                               const float h[3]) {
+  float t[6];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    float lo = 0.0f, hi = 0.0f;
+    if (dlt[k] != 0.0f) {
+      lo = (-h[k] - p[k]) / dlt[k];
+      hi = (h[k] - p[k]) / dlt[k];
+    }
+    t[2 * k] = fminf(fmaxf(lo, 0.0f), 1.0f);
+    t[2 * k + 1] = fminf(fmaxf(hi, 0.0f), 1.0f);
+  }
+#define RGG_CX(i, j)                                    \
+  {                                                     \
+    const float lo_ = fminf(t[i], t[j]), hi_ = fmaxf(t[i], t[j]); \
+    t[i] = lo_;                                         \
+    t[j] = hi_;                                         \
+  }
+  RGG_CX(1, 2) RGG_CX(4, 5) RGG_CX(0, 2) RGG_CX(3, 5) RGG_CX(0, 1) RGG_CX(3, 4)
+  RGG_CX(2, 5) RGG_CX(0, 3) RGG_CX(1, 4) RGG_CX(2, 4) RGG_CX(1, 3) RGG_CX(2, 3)
+#undef RGG_CX
+  float best = INFINITY;
+#pragma unroll
+  for (int i = 0; i < 7; ++i) {
+    const float ta = i == 0 ? 0.0f : t[i - 1];
+    const float tb = i == 6 ? 1.0f : t[i];
+    const float tm = 0.5f * (ta + tb);
+    float A = 0.0f, B = 0.0f, o[3];
+    bool out[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const float x = fmaf(tm, dlt[k], p[k]);
+      out[k] = x > h[k] || x < -h[k];
+      o[k] = x > h[k] ? p[k] - h[k] : p[k] + h[k];
+      if (out[k]) {
+        A = fmaf(dlt[k], dlt[k], A);
+        B = fmaf(o[k], dlt[k], B);
+      }
+    }
+    const float ts = A > 0.0f ? fminf(fmaxf(-B / A, ta), tb) : ta;
+    float f = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      if (out[k]) {
+        const float v = fmaf(ts, dlt[k], o[k]);
+        f = fmaf(v, v, f);
+      }
+    best = fminf(best, f);
+  }
+  return best;
+}
+
+// One warp per edge.  Edges that are not gray keep their label.  For a gray
+// edge the warp gathers up to 32 boxes of its touch set at a time (only
+// boxes an outer sphere touched can meet the capsules) and lane k takes the
+// configurations k, k+32, ... of t_c = c / ((n_e - 1) F): FP32 kinematics,
+// then, per link and box, the capsule-axis-to-box distance minus the link
+// radius.  A (link, box) pair whose bounding spheres cannot beat the lane's
+// best is skipped, so the minimum is exact.  The warp stops at the first
+// clearance below -thr (RED); otherwise the edge is GREEN when the minimum
+// is at least thr, and stays GRAY in between.
+__global__ void __launch_bounds__(256) resolve_gray_kernel(const __grid_constant__ ResolveParams p) {
+  __shared__ float s_box[8][32][16];
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t wib = threadIdx.x >> 5;
+  const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  const uint32_t L = p.L, Wm = p.Wm;
+  for (uint64_t e = warp; e < p.n_edges; e += nwarps) {
+    const uint8_t lab = p.labels[e];
+    if (lab != 1) {
+      if (lane == 0) {
+        p.out[e] = lab;
+        p.clearance[e] = __int_as_float(0x7fc00000);
+      }
+      continue;
+    }
+    const uint64_t n = p.soff[e + 1] - p.soff[e];
+    const uint64_t m = (n - 1) * (uint64_t)p.F;
+    const double inv_m = 1.0 / (double)m;
+    const double* qa = p.qa + e * L;
+    const double* qb = p.qb + e * L;
+    const uint32_t* tw = p.touch + e * Wm;
+    float best = INFINITY;
+    unsigned long long evals = 0;
+    bool red = false;
+    uint32_t w = 0, word = Wm ? tw[0] : 0u;
+    for (;;) {
+      // the next up to 32 boxes of the touch set (every lane walks the words)
+      int cnt = 0;
+      while (cnt < 32 && w < Wm) {
+        if (word == 0u) {
+          if (++w < Wm) word = tw[w];
+          continue;
+        }
+        const uint32_t b = 32u * w + (uint32_t)(__ffs(word) - 1);
+        word &= word - 1u;
+        if ((uint32_t)cnt == lane) {
+          const float4* src = reinterpret_cast<const float4*>(p.table + 16 * (size_t)b);
+          float4* dst = reinterpret_cast<float4*>(s_box[wib][lane]);
+          for (int c = 0; c < 4; ++c) dst[c] = src[c];
+        }
+        ++cnt;
+      }
+      __syncwarp();
+      if (cnt == 0) break;
+      for (uint64_t c0 = 0; c0 <= m && !red; c0 += 32) {
+        const uint64_t c = c0 + lane;
+        if (c <= m) {
+          const double tt = (double)c * inv_m;
+          float R[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+          float o[3] = {0, 0, 0};
+          for (uint32_t i = 0; i < L; ++i) {
+            const float q = (float)(qa[i] + tt * (qb[i] - qa[i]));
+            float st, ct;
+            sincosf(q, &st, &ct);
+            const float v0 = p.a[i] * ct, v1 = p.a[i] * st, v2 = p.d[i];
+            float on[3];
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+              on[r] = fmaf(R[3 * r], v0, fmaf(R[3 * r + 1], v1, fmaf(R[3 * r + 2], v2, o[r])));
+            const float mx = 0.5f * (o[0] + on[0]), my = 0.5f * (o[1] + on[1]),
+                        mz = 0.5f * (o[2] + on[2]);
+            const float hl = 0.5f * sqrtf((on[0] - o[0]) * (on[0] - o[0]) +
+                                          (on[1] - o[1]) * (on[1] - o[1]) +
+                                          (on[2] - o[2]) * (on[2] - o[2]));
+            const float rad = p.radius[i];
+            for (int b = 0; b < cnt; ++b) {
+              const float* B = s_box[wib][b];
+              const float hx = B[12], hy = B[13], hz = B[14];
+              const float dx = mx - B[0], dy = my - B[1], dz = mz - B[2];
+              // lower bound of the pair's clearance from the two bounding spheres
+              const float lb = sqrtf(dx * dx + dy * dy + dz * dz) - hl -
+                               sqrtf(hx * hx + hy * hy + hz * hz) - rad;
+              if (lb > best + 1e-5f) continue;
+              // the segment in the box frame: coordinate k = column k of R_b . (x - c_b)
+              float pb[3], db[3];
+              const float h3[3] = {hx, hy, hz};
+#pragma unroll
+              for (int k = 0; k < 3; ++k) {
+                const float ax = B[3 + k], ay = B[6 + k], az = B[9 + k];
+                pb[k] = ax * (o[0] - B[0]) + ay * (o[1] - B[1]) + az * (o[2] - B[2]);
+                db[k] = ax * (on[0] - o[0]) + ay * (on[1] - o[1]) + az * (on[2] - o[2]);
+              }
+              const float cl = sqrtf(seg_box_dist2(pb, db, h3)) - rad;
+              best = fminf(best, cl);
+              ++evals;
+            }
+            // R <- R * Rz(q) Rx(alpha)
+            const float ca = p.ca[i], sa = p.sa[i];
+            const float A[9] = {ct, -st * ca, st * sa, st, ct * ca, -ct * sa, 0.0f, sa, ca};
+            float Rn[9];
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+#pragma unroll
+              for (int cc = 0; cc < 3; ++cc)
+                Rn[3 * r + cc] = fmaf(R[3 * r], A[cc], fmaf(R[3 * r + 1], A[3 + cc], R[3 * r + 2] * A[6 + cc]));
+#pragma unroll
+            for (int k = 0; k < 9; ++k) R[k] = Rn[k];
+#pragma unroll
+            for (int r = 0; r < 3; ++r) o[r] = on[r];
+          }
+        }
+        red = __any_sync(0xffffffffu, best <= -p.thr);
+      }
+      __syncwarp();
+      if (red) break;
+    }
+    // warp minimum of the lanes' clearances and of the evaluation counts
+    for (int off = 16; off; off >>= 1) {
+      best = fminf(best, __shfl_xor_sync(0xffffffffu, best, off));
+      evals += __shfl_xor_sync(0xffffffffu, evals, off);
+    }
+    if (lane == 0) {
+      const uint8_t res = best <= -p.thr ? 2 : (best >= p.thr ? 0 : 1);
+      p.out[e] = res;
+      p.clearance[e] = best;
+      atomicAdd(&p.work[0], 1ull);
+      if (res == 2) atomicAdd(&p.work[1], 1ull);
+      if (res == 0) atomicAdd(&p.work[2], 1ull);
+      atomicAdd(&p.work[3], evals);
+    }
+  }
+}
+
+// ===========================================================================
 // host-side launchers
 // ===========================================================================
 cudaError_t launch_count_samples(const double* qa, const double* qb, uint64_t n_edges, uint32_t L,
@@ -882,6 +1078,14 @@ static_assert(sizeof(MergeParams<kMaxJobs>) <= 32764, "merge parameters too larg
 static_assert(sizeof(BoxPrepParams) <= 32764, "box-prep parameters too large");
 static_assert(sizeof(BoxUpdateParams) <= 32764, "box-update parameters too large");
 static_assert(sizeof(ClassifyParams<kMaxJobs>) <= 32764, "classify parameters too large");
+
+cudaError_t launch_resolve_gray(const ResolveParams& p, int num_sms, cudaStream_t s) {
+  if (p.n_edges == 0) return cudaSuccess;
+  const uint64_t want = (p.n_edges + 7) / 8;  // 8 warps per block, a warp per edge
+  const uint64_t cap = (uint64_t)num_sms * 8;
+  resolve_gray_kernel<<<(unsigned)(want < cap ? want : cap), 256, 0, s>>>(p);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_merge_single(const MergeParams<1>& p, cudaStream_t s) {
   return launch_merge_t<1>(p, s);

@@ -84,6 +84,26 @@ struct ClassifyLaunch {
   int variant;
 };
 
+// Non-lazy resolution of gray edges (Algorithm 1 with lazy = false): each
+// gray edge's link capsules are checked at (n_e - 1) * F + 1 configurations
+// against the boxes of its touch set.
+struct ResolveParams {
+  uint32_t L, Wm, F;
+  float thr;                        // decision margin, metres
+  float a[kMaxBuildLinks], d[kMaxBuildLinks], ca[kMaxBuildLinks], sa[kMaxBuildLinks];
+  float radius[kMaxBuildLinks];
+  const double* qa;                 // [N][L] edge endpoints
+  const double* qb;
+  const uint64_t* soff;             // [N+1]
+  const uint8_t* labels;            // [N] lazy labels
+  const uint32_t* touch;            // [N][Wm] touch sets
+  const float* table;               // [M][16] box poses
+  uint8_t* out;                     // [N] resolved labels
+  float* clearance;                 // [N] minimum clearance found (NaN: not gray)
+  unsigned long long* work;         // [4]: gray edges, red, green, segment-box evaluations
+  uint64_t n_edges;
+};
+
 size_t classify_smem_bytes(int variant, uint32_t consumer_warps);
 
 cudaError_t launch_count_samples(const double* qa, const double* qb, uint64_t n_edges, uint32_t L,
@@ -97,5 +117,6 @@ cudaError_t launch_classify_batched(const ClassifyParams<kMaxJobs>& p, const Cla
                                     cudaStream_t s);
 cudaError_t launch_merge_single(const MergeParams<1>& p, cudaStream_t s);
 cudaError_t launch_merge_batched(const MergeParams<kMaxJobs>& p, cudaStream_t s);
+cudaError_t launch_resolve_gray(const ResolveParams& p, int num_sms, cudaStream_t s);
 
 }  // namespace rgg

@@ -40,7 +40,7 @@ EXPORTS = (
     "rgg_status_string", "rgg_classify_noalloc", "rgg_update_request",
     "rgg_fetch_request_labels", "rgg_release_request", "rgg_autotune",
     "rgg_step_graph_create", "rgg_step_graph_launch", "rgg_step_graph_nodes",
-    "rgg_step_graph_destroy", "rgg_save", "rgg_load",
+    "rgg_step_graph_destroy", "rgg_save", "rgg_load", "rgg_resolve_gray", "rgg_fetch_boxes",
 )
 
 
@@ -78,6 +78,11 @@ class _NoallocArgs(ctypes.Structure):
 class _TuneResult(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_uint32), ("consumer_warps", ctypes.c_uint32),
                 ("classify_ms", ctypes.c_float), ("reserved", ctypes.c_float)]
+
+
+class _ResolveStats(ctypes.Structure):
+    _fields_ = [("gray_edges", ctypes.c_uint64), ("resolved_red", ctypes.c_uint64),
+                ("resolved_green", ctypes.c_uint64), ("evaluations", ctypes.c_uint64)]
 
 
 class Info(ctypes.Structure):
@@ -137,6 +142,8 @@ def _lib():
         "rgg_step_graph_nodes": [vp, ctypes.POINTER(u64)],
         "rgg_step_graph_destroy": [vp],
         "rgg_save": [vp, ctypes.c_char_p, vp],
+        "rgg_resolve_gray": [vp, u32, vp, vp, i32, ctypes.POINTER(_ResolveStats), vp],
+        "rgg_fetch_boxes": [vp, vp, vp, vp],
         "rgg_load": [vp, ctypes.c_char_p, vp],
     }
     for name, args in sig.items():
@@ -351,6 +358,15 @@ class Roadmap:
             self._h, first, count, inner.ctypes.data, outer.ctypes.data, None))
         return inner, outer, soff
 
+    def fetch_boxes(self, stream=None):
+        """(poses [M, 15] float32, present [M] uint8) of the box table."""
+        poses = np.empty((self.max_obstacles, 15), dtype=np.float32)
+        present = np.empty(self.max_obstacles, dtype=np.uint8)
+        _check("rgg_fetch_boxes", _lib().rgg_fetch_boxes(self._h, poses.ctypes.data,
+                                                         present.ctypes.data,
+                                                         _stream(stream, self.device)))
+        return poses, present
+
     def labels_device_ptr(self) -> int:
         p = ctypes.c_void_p()
         _check("rgg_labels_device_ptr", _lib().rgg_labels_device_ptr(self._h, ctypes.byref(p)))
@@ -363,6 +379,18 @@ class Roadmap:
 
     def check_status(self, stream=None) -> None:
         _check("rgg_check_status", _lib().rgg_check_status(self._h, _stream(stream, self.device)))
+
+    def resolve_gray(self, factor: int = 10, stream=None):
+        """Non-lazy resolution of the gray edges (rgg_resolve_gray): returns
+        (labels [N] uint8, clearance [N] float32, stats dict), host arrays."""
+        n = self.info()["num_edges"]
+        labels = np.empty(n, dtype=np.uint8)
+        clear = np.empty(n, dtype=np.float32)
+        st = _ResolveStats()
+        _check("rgg_resolve_gray", _lib().rgg_resolve_gray(
+            self._h, int(factor), labels.ctypes.data, clear.ctypes.data, 0, ctypes.byref(st),
+            _stream(stream, self.device)))
+        return labels, clear, {k: getattr(st, k) for k, _ in st._fields_}
 
     # -- persistence ----------------------------------------------------------
     def save(self, path, stream=None) -> None:

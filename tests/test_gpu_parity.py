@@ -387,3 +387,18 @@ def test_irregular_uploads_take_the_exact_sphere_test(rgg):
         b.classify()
         got = b.fetch_labels()
     check_labels(got, want, "irregular upload")
+
+
+def test_fetch_boxes_returns_the_table(rgg):
+    sc = W.workload_planar(n_nodes=60, n_updates=2)
+    with make_roadmap(rgg, sc.roadmap, sc.boxes.count) as r:
+        poses, present = r.fetch_boxes()
+        assert not present.any()
+        r.update_obstacles(np.arange(sc.boxes.count), f32(sc.boxes.poses()))
+        up = sc.updates[0]
+        r.update_obstacles(up.ids, f32(up.poses))    # pending: the table has the new pose
+        poses, present = r.fetch_boxes()
+        want = f32(sc.boxes.poses())
+        want[up.ids] = f32(up.poses)
+        assert present.all()
+        np.testing.assert_array_equal(poses, want)

@@ -418,3 +418,24 @@ def test_classify_spheres_agrees_with_robot_classify(oracle, small_7dof):
     want = oracle.classify(rm.robot, rm.q_from[:40], rm.q_to[:40], rm.step, boxes.poses())
     np.testing.assert_array_equal(got["labels"], want["labels"])
     np.testing.assert_allclose(got["kappa"], want["kappa"], rtol=0, atol=1e-12)
+
+
+def test_dense_clearance_hand_cases(oracle):
+    """Closed-form clearances of a 1-link planar arm (length 0.3, R 0.03):
+    a resting arm 0.15 m from a box face; an arm sweeping 0 -> pi/2 through a
+    box centred on the 45 degree ray (the resampled configuration t = 0.5 is
+    exactly q = pi/4); and the same box moved out of reach along that ray."""
+    robot = W.planar_arm(1, 0.3, 0.03, 4)
+    box = box_pose([0.5, 0.0, 0.0], np.eye(3), [0.05] * 3)
+    v, t = oracle.edge_dense_clearance(robot, [0.0], [0.0], 0.05, 3, [box])
+    assert v == pytest.approx(0.15 - 0.03, abs=1e-9)
+    c45 = math.cos(math.pi / 4)
+    inside = box_pose([0.2 * c45, 0.2 * c45, 0.0], np.eye(3), [0.02] * 3)
+    v, t = oracle.edge_dense_clearance(robot, [0.0], [math.pi / 2], 0.05, 2, [inside])
+    # the axis meets the box over a range of angles around pi/4
+    assert v == pytest.approx(-0.03, abs=1e-9) and 0.3 < t <= 0.5
+    beyond = box_pose([0.5 * c45, 0.5 * c45, 0.0], np.eye(3), [0.02] * 3)
+    v, t = oracle.edge_dense_clearance(robot, [0.0], [math.pi / 2], 0.05, 2, [beyond])
+    # the nearest box corner lies on the ray at 0.5 - 0.02 sqrt(2)
+    assert v == pytest.approx(0.5 - 0.02 * math.sqrt(2) - 0.3 - 0.03, abs=1e-9)
+    assert t == pytest.approx(0.5)
