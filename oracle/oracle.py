@@ -52,6 +52,17 @@ def _load():
     lib.or_classify_spheres.argtypes = [i64, _I64, _D, _I64, _D, i32, _D, _U8, _U8, _D,
                                         _U32, _U32]
     lib.or_classify_spheres.restype = i32
+    lib.or_segment_point_distance.argtypes = [_D, _D, _D]
+    lib.or_segment_point_distance.restype = dbl
+    lib.or_obb_separation.argtypes = [_D, _D]
+    lib.or_obb_separation.restype = dbl
+    lib.or_edge_obbs.argtypes = [i32, _D, _D, _D, _D, _D, _D, dbl, _D]
+    lib.or_edge_obbs.restype = i64
+    lib.or_edge_splines.argtypes = [i32, _D, _D, _D, _D, i32, _D, _D, dbl, i64, _D, _I64]
+    lib.or_edge_splines.restype = i64
+    lib.or_classify_obb.argtypes = [i32, _D, _D, _D, _D, i32, i64, _D, _D, dbl, i64, i32, _D,
+                                    _U8, _U8, _D, _U32, _U32]
+    lib.or_classify_obb.restype = i32
     lib.or_segment_box_distance.argtypes = [_D, _D, _D]
     lib.or_segment_box_distance.restype = dbl
     lib.or_edge_dense_clearance.argtypes = [i32, _D, _D, _D, _D, _D, _D, dbl, i32, i32, _D,
@@ -187,6 +198,79 @@ def classify_spheres(in_off, inner, out_off, outer, boxes, present=None, bits: b
         raise ValueError("oracle classify_spheres rejected its arguments")
     if bits:
         out["hit"], out["touch"] = hit, touch
+    return out
+
+
+def segment_point_distance(p0, p1, x) -> float:
+    p0, a = _d(p0)
+    p1, b = _d(p1)
+    x, c = _d(x)
+    return float(_load().or_segment_point_distance(a, b, c))
+
+
+def obb_separation(A, B) -> float:
+    """Largest separation of two boxes (15 doubles each) over the 15 SAT axes:
+    > 0 disjoint, <= 0 they meet."""
+    A, pa = _d(np.asarray(A, dtype=np.float64).reshape(15))
+    B, pb = _d(np.asarray(B, dtype=np.float64).reshape(15))
+    return float(_load().or_obb_separation(pa, pb))
+
+
+def edge_obbs(robot, qa, qb, step: float):
+    """[L, 15] boxes of the edge's bodies (or_edge_obbs)."""
+    keep, ptrs, L, K = _robot(robot)
+    qa, pa = _d(qa)
+    qb, pb = _d(qb)
+    out = np.zeros((L, 15))
+    n = _load().or_edge_obbs(L, *ptrs, pa, pb, float(step), out.ctypes.data_as(_D))
+    if n < 0:
+        raise ValueError("oracle edge_obbs rejected its arguments")
+    return out
+
+
+def edge_splines(robot, qa, qb, step: float):
+    """Kept spline vertices per (body, sphere): a list of L lists of K arrays
+    [count, 3] (or_edge_splines)."""
+    _I64 = ctypes.POINTER(ctypes.c_int64)
+    keep, ptrs, L, K = _robot(robot)
+    qa, pa = _d(qa)
+    qb, pb = _d(qb)
+    n = num_samples(qa, qb, step)
+    verts = np.zeros((L, K, n, 3))
+    counts = np.zeros((L, K), dtype=np.int64)
+    got = _load().or_edge_splines(L, *ptrs, K, pa, pb, float(step), n, verts.ctypes.data_as(_D),
+                                  counts.ctypes.data_as(_I64))
+    if got < 0:
+        raise ValueError("oracle edge_splines rejected its arguments")
+    return [[verts[i, s, :counts[i, s]] for s in range(K)] for i in range(L)]
+
+
+def classify_obb(robot, qa, qb, step: float, boxes, present=None, bits: bool = False):
+    """Labels with the paper's OBB / spline primitives (or_classify_obb):
+    ``labels``, ``kappa`` and, with ``bits``, ``hit`` / ``touch``."""
+    keep, ptrs, L, K = _robot(robot)
+    qa, pa = _d(np.asarray(qa).reshape(-1, L))
+    qb, pb = _d(np.asarray(qb).reshape(-1, L))
+    n_edges = qa.shape[0]
+    boxes, pbx = _d(np.asarray(boxes, dtype=np.float64).reshape(-1, 15))
+    m = boxes.shape[0]
+    pres = None if present is None else np.ascontiguousarray(present, dtype=np.uint8)
+    max_s = 2
+    if n_edges:
+        max_s = int(np.ceil(np.abs(qb - qa).max(axis=1).max() / step)) + 3
+    w = max((m + 31) // 32, 1)
+    out = {"labels": np.zeros(n_edges, dtype=np.uint8), "kappa": np.zeros(n_edges)}
+    hit = np.zeros((n_edges, w), dtype=np.uint32)
+    touch = np.zeros((n_edges, w), dtype=np.uint32)
+    rc = _load().or_classify_obb(
+        L, *ptrs, K, n_edges, pa, pb, float(step), max_s, m, pbx,
+        pres.ctypes.data_as(_U8) if pres is not None else None,
+        out["labels"].ctypes.data_as(_U8), out["kappa"].ctypes.data_as(_D),
+        hit.ctypes.data_as(_U32), touch.ctypes.data_as(_U32))
+    if rc != 0:
+        raise ValueError("oracle classify_obb rejected its arguments")
+    if bits:
+        out["hit"], out["touch"] = hit[:, :(m + 31) // 32], touch[:, :(m + 31) // 32]
     return out
 
 

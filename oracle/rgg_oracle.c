@@ -426,3 +426,316 @@ double or_edge_dense_clearance(int L, const double* a, const double* alpha, cons
   if (argmin_t) *argmin_t = best_t;
   return best;
 }
+
+/* ========================================================================
+ * The paper's own primitives (Sec. 4.2, Sec. 4.3): per (edge, body) OBB
+ * outer approximations tested with the separating-axis test against the
+ * obstacles' boxes, and shortcut splines through the inscribed spheres'
+ * centres tested against the obstacles' inner spheres.
+ * ======================================================================== */
+
+static double dot3(const double* u, const double* v) { return u[0] * v[0] + u[1] * v[1] + u[2] * v[2]; }
+
+static void cross3(const double* u, const double* v, double* w) {
+  w[0] = u[1] * v[2] - u[2] * v[1];
+  w[1] = u[2] * v[0] - u[0] * v[2];
+  w[2] = u[0] * v[1] - u[1] * v[0];
+}
+
+/* Distance from point x to the segment p0 -> p1 (closest point by projection,
+ * clamped to the segment). */
+double or_segment_point_distance(const double* p0, const double* p1, const double* x) {
+  double dd[3], w[3], c[3];
+  for (int k = 0; k < 3; ++k) {
+    dd[k] = p1[k] - p0[k];
+    w[k] = x[k] - p0[k];
+  }
+  const double len2 = dot3(dd, dd);
+  double t = len2 > 0.0 ? dot3(w, dd) / len2 : 0.0;
+  if (t < 0.0) t = 0.0;
+  if (t > 1.0) t = 1.0;
+  for (int k = 0; k < 3; ++k) c[k] = p0[k] + t * dd[k] - x[k];
+  return sqrt(dot3(c, c));
+}
+
+/*
+ * Separation of two boxes along the 15 axes of the separating-axis test
+ * (Sec. 4.3).  Each box is 15 doubles: centre, R (row-major; column k is
+ * axis k), half-extents.  For a unit axis l the separation is
+ *   |(c_B - c_A).l| - sum_k hA_k |a_k.l| - sum_k hB_k |b_k.l|,
+ * over the 3 + 3 box axes and the 9 cross products a_j x b_k scaled to unit
+ * length (a product shorter than 1e-6 comes from a parallel pair and is
+ * skipped: the face axes cover it).  Returns the largest: > 0 means that axis
+ * separates the boxes, <= 0 that no axis does and the boxes meet.
+ */
+double or_obb_separation(const double* A, const double* B) {
+  double ax[3][3], bx[3][3], t[3];
+  for (int k = 0; k < 3; ++k)
+    for (int r = 0; r < 3; ++r) {
+      ax[k][r] = A[3 + 3 * r + k];
+      bx[k][r] = B[3 + 3 * r + k];
+    }
+  for (int r = 0; r < 3; ++r) t[r] = B[r] - A[r];
+  double best = -INFINITY;
+  double axes[15][3];
+  int na = 0;
+  for (int k = 0; k < 3; ++k) {
+    for (int r = 0; r < 3; ++r) axes[na][r] = ax[k][r];
+    ++na;
+  }
+  for (int k = 0; k < 3; ++k) {
+    for (int r = 0; r < 3; ++r) axes[na][r] = bx[k][r];
+    ++na;
+  }
+  for (int j = 0; j < 3; ++j)
+    for (int k = 0; k < 3; ++k) {
+      double w[3];
+      cross3(ax[j], bx[k], w);
+      const double len = sqrt(dot3(w, w));
+      if (len < 1e-6) continue;
+      for (int r = 0; r < 3; ++r) axes[na][r] = w[r] / len;
+      ++na;
+    }
+  for (int i = 0; i < na; ++i) {
+    const double* l = axes[i];
+    double s = fabs(dot3(t, l));
+    for (int k = 0; k < 3; ++k) {
+      s -= A[12 + k] * fabs(dot3(ax[k], l));
+      s -= B[12 + k] * fabs(dot3(bx[k], l));
+    }
+    if (s > best) best = s;
+  }
+  return best;
+}
+
+/* Joint positions of the edge's n configurations: joints[c][L+1][3]. */
+static double* edge_joints(int L, const double* a, const double* alpha, const double* d,
+                           const double* qa, const double* qb, int64_t n) {
+  double* J = (double*)malloc(sizeof(double) * 3 * (size_t)(L + 1) * (size_t)n);
+  if (!J) return NULL;
+  double q[OR_MAX_LINKS];
+  for (int64_t c = 0; c < n; ++c) {
+    lerp_config(L, qa, qb, (double)c / (double)(n - 1), q);
+    or_forward_kinematics(L, a, alpha, d, q, J + 3 * (size_t)(L + 1) * (size_t)c);
+  }
+  return J;
+}
+
+/*
+ * OBB of each body over an edge (Sec. 4.2's outer approximation: an OBB
+ * around the point cloud of the body's intermediates; the paper fits an
+ * approximately optimal-volume box, here the axes come from the motion):
+ *   u1 = link i's direction at the middle configuration q(1/2) (world x if
+ *        the link has zero length);
+ *   u2 = the part normal to u1 of the displacement of the link's midpoint
+ *        from q_a to q_b; when shorter than 1e-9 m, the world axis least
+ *        aligned with u1 (lowest index on ties) made normal to u1;
+ *   u3 = u1 x u2.
+ * The box spans the projections of both link endpoints at every
+ * configuration of cfg(e) on those axes; each half-extent then grows by
+ * R_i (the capsule) plus 1/2 sum_{j<=i} |dq_j| rho_{j,i}, half the largest
+ * motion of a link point between consecutive configurations (the bound the
+ * outer spheres use), so that the box holds the capsule over the whole edge.
+ * obbs receives L boxes of 15 doubles (centre, R row-major with columns
+ * u1 u2 u3, half-extents).  Returns n, or -1 on a bad argument.
+ */
+int64_t or_edge_obbs(int L, const double* a, const double* alpha, const double* d,
+                     const double* radius, const double* qa, const double* qb, double step,
+                     double* obbs) {
+  if (L <= 0 || L > OR_MAX_LINKS) return -1;
+  const int64_t n = or_num_samples(L, qa, qb, step);
+  if (n < 2) return -1;
+  double* J = edge_joints(L, a, alpha, d, qa, qb, n);
+  if (!J) return -1;
+  double q[OR_MAX_LINKS], jm[3 * (OR_MAX_LINKS + 1)];
+  lerp_config(L, qa, qb, 0.5, q);
+  or_forward_kinematics(L, a, alpha, d, q, jm);
+  const double* ja = J;
+  const double* jb = J + 3 * (size_t)(L + 1) * (size_t)(n - 1);
+  double prefix = 0.0, sweep = 0.0;
+  for (int i = 0; i < L; ++i) {
+    double u[3][3];
+    double len = 0.0;
+    for (int r = 0; r < 3; ++r) {
+      u[0][r] = jm[3 * (i + 1) + r] - jm[3 * i + r];
+      len += u[0][r] * u[0][r];
+    }
+    len = sqrt(len);
+    if (len < 1e-12) {
+      u[0][0] = 1.0;
+      u[0][1] = u[0][2] = 0.0;
+    } else {
+      for (int r = 0; r < 3; ++r) u[0][r] /= len;
+    }
+    double w[3];
+    for (int r = 0; r < 3; ++r)
+      w[r] = 0.5 * (jb[3 * i + r] + jb[3 * (i + 1) + r]) - 0.5 * (ja[3 * i + r] + ja[3 * (i + 1) + r]);
+    double wu = dot3(w, u[0]);
+    for (int r = 0; r < 3; ++r) u[1][r] = w[r] - wu * u[0][r];
+    double l2 = sqrt(dot3(u[1], u[1]));
+    if (l2 < 1e-9) {
+      int kmin = 0;
+      for (int k = 1; k < 3; ++k)
+        if (fabs(u[0][k]) < fabs(u[0][kmin])) kmin = k;
+      for (int r = 0; r < 3; ++r) u[1][r] = (r == kmin ? 1.0 : 0.0) - u[0][kmin] * u[0][r];
+      l2 = sqrt(dot3(u[1], u[1]));
+    }
+    for (int r = 0; r < 3; ++r) u[1][r] /= l2;
+    cross3(u[0], u[1], u[2]);
+    /* motion bound: the same prefix sums as the outer spheres */
+    prefix += fabs(qb[i] - qa[i]) / (double)(n - 1);
+    sweep += link_length(a, d, i) * prefix;
+    const double grow = radius[i] + 0.5 * sweep;
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t c = 0; c < n; ++c) {
+      const double* jc = J + 3 * (size_t)(L + 1) * (size_t)c;
+      for (int e = 0; e < 2; ++e) {
+        double p[3];
+        for (int r = 0; r < 3; ++r) p[r] = jc[3 * (i + e) + r] - jm[3 * i + r];
+        for (int k = 0; k < 3; ++k) {
+          const double s = dot3(p, u[k]);
+          if (s < lo[k]) lo[k] = s;
+          if (s > hi[k]) hi[k] = s;
+        }
+      }
+    }
+    double* out = obbs + 15 * (size_t)i;
+    for (int r = 0; r < 3; ++r) {
+      double c = jm[3 * i + r];
+      for (int k = 0; k < 3; ++k) c += 0.5 * (lo[k] + hi[k]) * u[k][r];
+      out[r] = c;
+      for (int k = 0; k < 3; ++k) out[3 + 3 * r + k] = u[k][r];
+    }
+    for (int k = 0; k < 3; ++k) out[12 + k] = 0.5 * (hi[k] - lo[k]) + grow;
+  }
+  free(J);
+  return n;
+}
+
+/*
+ * Shortcut splines (Sec. 4.2).  For body i and its inscribed sphere s (centre
+ * at fraction (s + 1/2)/K of the link axis, radius R_i), the centre's
+ * positions at the n configurations of cfg(e) form a polyline.  Vertices are
+ * dropped greedily: from the last kept vertex j, the next kept vertex is the
+ * largest p for which every vertex m strictly between j and p lies closer
+ * than R_i to the segment v_j v_p (the paper's shortcut criterion), and the
+ * last vertex is always kept.  verts receives, for (i, s) at slot
+ * (i*K + s)*max_vertices, the kept vertices (x, y, z); counts[i*K + s] their
+ * number.  Returns n, or -1 on a bad argument or too small a buffer.
+ */
+int64_t or_edge_splines(int L, const double* a, const double* alpha, const double* d,
+                        const double* radius, int K, const double* qa, const double* qb,
+                        double step, int64_t max_vertices, double* verts, int64_t* counts) {
+  if (L <= 0 || L > OR_MAX_LINKS || K <= 0) return -1;
+  const int64_t n = or_num_samples(L, qa, qb, step);
+  if (n < 2 || max_vertices < n) return -1;
+  double* J = edge_joints(L, a, alpha, d, qa, qb, n);
+  double* V = (double*)malloc(sizeof(double) * 3 * (size_t)n);
+  if (!J || !V) {
+    free(J);
+    free(V);
+    return -1;
+  }
+  for (int i = 0; i < L; ++i)
+    for (int s = 0; s < K; ++s) {
+      const double f = ((double)s + 0.5) / (double)K;
+      for (int64_t c = 0; c < n; ++c) {
+        const double* jc = J + 3 * (size_t)(L + 1) * (size_t)c;
+        for (int r = 0; r < 3; ++r)
+          V[3 * c + r] = jc[3 * i + r] + f * (jc[3 * (i + 1) + r] - jc[3 * i + r]);
+      }
+      double* out = verts + 3 * (size_t)((size_t)(i * K + s) * (size_t)max_vertices);
+      int64_t nk = 0;
+      for (int r = 0; r < 3; ++r) out[r] = V[r];
+      nk = 1;
+      int64_t j = 0;
+      while (j < n - 1) {
+        int64_t p = j + 1;
+        while (p + 1 <= n - 1) {
+          int ok = 1;
+          for (int64_t m = j + 1; m <= p && ok; ++m)
+            ok = or_segment_point_distance(V + 3 * j, V + 3 * (p + 1), V + 3 * m) < radius[i];
+          if (!ok) break;
+          ++p;
+        }
+        for (int r = 0; r < 3; ++r) out[3 * nk + r] = V[3 * p + r];
+        ++nk;
+        j = p;
+      }
+      counts[i * K + s] = nk;
+    }
+  free(J);
+  free(V);
+  return n;
+}
+
+/*
+ * Labels with the paper's primitives (Sec. 4.1 rule, Sec. 4.3 queries):
+ * box b is touched when some body's OBB meets it (separation <= 0), hit when
+ * some spline segment comes within its inner sphere (the largest inscribed
+ * sphere: the box centre, radius its smallest half-extent; distance <= that
+ * radius).  Red if any box is hit, else green if none is touched, else gray.
+ * Clearance: h_in = max over segments and boxes of (radius - distance); sep =
+ * the smallest |separation| over bodies and boxes; kappa = h_in when >= 0,
+ * else min(-h_in, sep).  Outputs other than labels may be NULL.
+ */
+int or_classify_obb(int L, const double* a, const double* alpha, const double* d,
+                    const double* radius, int K, int64_t n_edges, const double* qa,
+                    const double* qb, double step, int64_t max_samples, int n_boxes,
+                    const double* boxes, const uint8_t* present, uint8_t* labels,
+                    double* kappa, uint32_t* hit_bits, uint32_t* touch_bits) {
+  if (L <= 0 || L > OR_MAX_LINKS || K <= 0 || n_boxes < 0) return -1;
+  const int W = (n_boxes + 31) / 32;
+  int bad = 0;
+#pragma omp parallel num_threads(or_max_threads())
+  {
+    double* obbs = (double*)malloc(sizeof(double) * 15 * (size_t)L);
+    double* verts = (double*)malloc(sizeof(double) * 3 * (size_t)L * (size_t)K * (size_t)max_samples);
+    int64_t* cnt = (int64_t*)malloc(sizeof(int64_t) * (size_t)L * (size_t)K);
+#pragma omp for schedule(dynamic, 8)
+    for (int64_t e = 0; e < n_edges; ++e) {
+      const double* ea = qa + (size_t)e * L;
+      const double* eb = qb + (size_t)e * L;
+      if (!obbs || !verts || !cnt ||
+          or_edge_obbs(L, a, alpha, d, radius, ea, eb, step, obbs) < 0 ||
+          or_edge_splines(L, a, alpha, d, radius, K, ea, eb, step, max_samples, verts, cnt) < 0) {
+#pragma omp atomic write
+        bad = 1;
+        continue;
+      }
+      double h_in = -INFINITY, sep_min = INFINITY;
+      int any_hit = 0, any_touch = 0;
+      for (int b = 0; b < n_boxes; ++b) {
+        if (present && !present[b]) continue;
+        const double* box = boxes + 15 * (size_t)b;
+        double rb = box[12];
+        if (box[13] < rb) rb = box[13];
+        if (box[14] < rb) rb = box[14];
+        int hit = 0, touch = 0;
+        for (int i = 0; i < L; ++i) {
+          const double sp = or_obb_separation(obbs + 15 * (size_t)i, box);
+          if (fabs(sp) < sep_min) sep_min = fabs(sp);
+          if (sp <= 0.0) touch = 1;
+          for (int s = 0; s < K; ++s) {
+            const double* v = verts + 3 * (size_t)((size_t)(i * K + s) * (size_t)max_samples);
+            for (int64_t g = 0; g + 1 < cnt[i * K + s]; ++g) {
+              const double h = rb - or_segment_point_distance(v + 3 * g, v + 3 * (g + 1), box);
+              if (h > h_in) h_in = h;
+              if (h >= 0.0) hit = 1;
+            }
+          }
+        }
+        any_hit |= hit;
+        any_touch |= touch;
+        if (hit_bits && hit) hit_bits[(size_t)e * W + (b >> 5)] |= 1u << (b & 31);
+        if (touch_bits && touch) touch_bits[(size_t)e * W + (b >> 5)] |= 1u << (b & 31);
+      }
+      labels[e] = any_hit ? OR_RED : (any_touch ? OR_GRAY : OR_GREEN);
+      if (kappa) kappa[e] = h_in >= 0.0 ? h_in : fmin(-h_in, sep_min);
+    }
+    free(obbs);
+    free(verts);
+    free(cnt);
+  }
+  return bad ? -1 : 0;
+}

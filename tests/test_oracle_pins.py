@@ -439,3 +439,136 @@ def test_dense_clearance_hand_cases(oracle):
     # the nearest box corner lies on the ray at 0.5 - 0.02 sqrt(2)
     assert v == pytest.approx(0.5 - 0.02 * math.sqrt(2) - 0.3 - 0.03, abs=1e-9)
     assert t == pytest.approx(0.5)
+
+
+# --------------------------------------------------------------------------
+# the paper's primitives: OBBs, separating axes, shortcut splines
+# --------------------------------------------------------------------------
+def test_obb_separation_hand_values(oracle):
+    I = np.eye(3)
+    a = box_pose([0, 0, 0], I, [0.5] * 3)
+    assert oracle.obb_separation(a, box_pose([2, 0, 0], I, [0.5] * 3)) == pytest.approx(1.0)
+    assert oracle.obb_separation(a, box_pose([0.5, 0, 0], I, [0.5] * 3)) == pytest.approx(-0.5)
+    rz = Rotation.from_euler("z", 45, degrees=True).as_matrix()
+    # the rotated box reaches 0.5 sqrt(2) along x
+    assert oracle.obb_separation(a, box_pose([2, 0, 0], rz, [0.5] * 3)) == \
+        pytest.approx(2 - 0.5 - 0.5 * math.sqrt(2))
+
+
+def test_obb_separation_sign_matches_lp_feasibility(oracle):
+    """Boxes meet exactly when a point satisfies both boxes' slab
+    constraints (a linear feasibility problem); SAT must agree."""
+    from scipy.optimize import linprog
+    rng = np.random.default_rng(8)
+    agree = 0
+    for i in range(300):
+        A = box_pose(rng.uniform(-0.3, 0.3, 3), Rotation.random(random_state=2 * i).as_matrix(),
+                     rng.uniform(0.05, 0.4, 3))
+        B = box_pose(rng.uniform(-0.3, 0.3, 3) + rng.uniform(-1, 1, 3) * 0.6,
+                     Rotation.random(random_state=2 * i + 1).as_matrix(), rng.uniform(0.05, 0.4, 3))
+        rows, rhs = [], []
+        for box in (A, B):
+            c, R, h = box[:3], box[3:12].reshape(3, 3), box[12:]
+            for k in range(3):
+                u = R[:, k]
+                rows += [u, -u]
+                rhs += [h[k] + u @ c, h[k] - u @ c]
+        lp = linprog(np.zeros(3), A_ub=np.array(rows), b_ub=np.array(rhs), bounds=[(None, None)] * 3,
+                     method="highs")
+        sep = oracle.obb_separation(A, B)
+        if abs(sep) < 1e-9:
+            continue
+        assert (sep <= 0) == (lp.status == 0), (i, sep, lp.status)
+        agree += 1
+    assert agree > 250
+
+
+def test_edge_obbs_hold_the_swept_capsules(oracle):
+    """Points of every link capsule at a 10x finer resampling (axis points
+    pushed out by the radius in random directions) lie inside the body's
+    box; a resting planar link gets the hand-derived box."""
+    robot = W.planar_arm(1, 0.3, 0.03, 4)
+    ob = oracle.edge_obbs(robot, [0.0], [0.0], 0.05)[0]
+    np.testing.assert_allclose(ob[:3], [0.15, 0, 0], atol=1e-12)
+    np.testing.assert_allclose(np.abs(ob[3:12].reshape(3, 3)), np.eye(3), atol=1e-12)
+    np.testing.assert_allclose(ob[12:], [0.18, 0.03, 0.03], atol=1e-12)
+    rng = np.random.default_rng(4)
+    rm = W.prm_roadmap(rng, W.dh_arm(rng, 7), 60, 6, 0.05)
+    rob = rm.robot
+    for e in range(0, rm.num_edges, 7):
+        obbs = oracle.edge_obbs(rob, rm.q_from[e], rm.q_to[e], rm.step)
+        n = oracle.num_samples(rm.q_from[e], rm.q_to[e], rm.step)
+        for t in np.linspace(0, 1, 10 * (n - 1) + 1):
+            q = rm.q_from[e] + t * (rm.q_to[e] - rm.q_from[e])
+            J = oracle.forward_kinematics(rob, q)
+            for i in range(rob.num_links):
+                c, R, h = obbs[i, :3], obbs[i, 3:12].reshape(3, 3), obbs[i, 12:]
+                for f in (0.0, 0.5, 1.0):
+                    p = J[i] + f * (J[i + 1] - J[i])
+                    d = rng.normal(size=3)
+                    p = p + rob.radius[i] * d / np.linalg.norm(d)
+                    assert np.all(np.abs(R.T @ (p - c)) <= h + 1e-9), (e, t, i)
+
+
+def test_edge_splines_follow_the_shortcut_rule(oracle):
+    """Kept vertices are original centres, first and last included; every
+    dropped centre lies closer than R to its covering segment; and no kept
+    segment could be stretched to the next centre (greedy)."""
+    robot = W.planar_arm(1, 0.3, 0.03, 4)
+    sp = oracle.edge_splines(robot, [0.0], [0.0], 0.05)
+    assert all(v.shape == (2, 3) for v in sp[0])      # a resting link: one segment
+    rng = np.random.default_rng(6)
+    rm = W.prm_roadmap(rng, W.dh_arm(rng, 7), 40, 6, 0.02)
+    rob = rm.robot
+    L, K = rob.num_links, rob.inner_per_link
+    for e in range(0, rm.num_edges, 5):
+        n = oracle.num_samples(rm.q_from[e], rm.q_to[e], rm.step)
+        J = np.array([oracle.forward_kinematics(rob, rm.q_from[e] + c / (n - 1) *
+                                                (rm.q_to[e] - rm.q_from[e])) for c in range(n)])
+        sp = oracle.edge_splines(rob, rm.q_from[e], rm.q_to[e], rm.step)
+        for i in range(L):
+            R = rob.radius[i]
+            for s in range(K):
+                f = (s + 0.5) / K
+                V = J[:, i] + f * (J[:, i + 1] - J[:, i])
+                kept = [int(np.argmin(np.linalg.norm(V - v, axis=1))) for v in sp[i][s]]
+                np.testing.assert_allclose(sp[i][s], V[kept], atol=1e-12)
+                assert kept[0] == 0 and kept[-1] == n - 1
+                for j, p in zip(kept[:-1], kept[1:]):
+                    for m in range(j + 1, p):
+                        assert oracle.segment_point_distance(V[j], V[p], V[m]) < R
+                    if p < n - 1:
+                        assert max(oracle.segment_point_distance(V[j], V[p + 1], V[m])
+                                   for m in range(j + 1, p + 1)) >= R
+
+
+def test_classify_obb_hand_scenes(oracle):
+    """A resting planar link along +x (length 0.3, R 0.03, spheres at 0.0375,
+    0.1125, 0.1875, 0.2625): its box is [0, 0.3] x [-0.03, 0.03] grown to
+    half-extents (0.18, 0.03, 0.03) about (0.15, 0, 0)."""
+    robot = W.planar_arm(1, 0.3, 0.03, 4)
+    I = np.eye(3)
+    cases = [  # (box centre, half, label, kappa)
+        ([0.15, 0.0, 0.0], 0.05, oracle.RED, 0.05 - 0.0375),
+        ([0.15, 0.5, 0.0], 0.05, oracle.GREEN, 0.5 - 0.03 - 0.05),
+        ([0.15, 0.07, 0.0], 0.05, oracle.GRAY, 0.01),
+    ]
+    for c, h, lab, kap in cases:
+        out = oracle.classify_obb(robot, [[0.0]], [[0.0]], 0.05, [box_pose(c, I, [h] * 3)])
+        assert out["labels"][0] == lab, c
+        assert out["kappa"][0] == pytest.approx(kap, abs=1e-12), c
+
+
+def test_classify_obb_green_edges_are_free(oracle):
+    """Green by the boxes means no box meets the swept capsules: a 10x finer
+    exact capsule-box check finds every green edge free."""
+    rng = np.random.default_rng(9)
+    rm = W.prm_roadmap(rng, W.dh_arm(rng, 7), 100, 8, 0.05)
+    boxes = W.random_boxes(rng, 6, extent=1.0)
+    out = oracle.classify_obb(rm.robot, rm.q_from, rm.q_to, rm.step, boxes.poses())
+    green = np.flatnonzero(out["labels"] == oracle.GREEN)
+    assert green.size >= 10 and (out["labels"] != oracle.GREEN).any()
+    for e in green[:25]:
+        v, _ = oracle.edge_dense_clearance(rm.robot, rm.q_from[e], rm.q_to[e], rm.step, 10,
+                                           boxes.poses())
+        assert v > 0.0
