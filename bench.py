@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--workload", default="large",
                     choices=["large", "7dof", "planar", "batched", "serve"])
     ap.add_argument("--roadmaps", type=int, default=128, help="batched workload: roadmaps")
+    ap.add_argument("--geometry", default="spheres", choices=["spheres", "obb"],
+                    help="obb: time the paper's OBB / spline geometry beside the sphere one "
+                         "on the same roadmap and updates")
     ap.add_argument("--resolve", type=int, default=0, metavar="F",
                     help="also time the non-lazy resolution of the gray edges at F-times "
                          "finer resampling (0: off)")
@@ -482,6 +485,97 @@ def measure_resolve(r, sc, factor: int, stream, with_oracle: bool) -> dict:
     return res
 
 
+def run_geometry(args):
+    """The paper's OBB / shortcut-spline geometry (Sec. 4.2, 4.3) against the
+    sphere geometry on the same roadmap and update stream: classify time per
+    update (the grid-filtered queries, and without the filter), the tests
+    run, and the label mix each geometry reaches (gray fraction)."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2603_28674_gb300 import build
+    build.build()
+    from paper_2603_28674_gb300 import rgg
+    sc = make_scene(args.workload, n_updates=64)
+    rm, robot = sc.roadmap, sc.roadmap.robot
+    stream = torch.cuda.current_stream()
+    dev = [torch.from_numpy(u.poses.astype(np.float32)).cuda() for u in sc.updates]
+    out = {}
+    with ClockSampler(0) as clocks:
+        for name, geo, filt in (("spheres", rgg.GEOMETRY_SPHERES, True),
+                                ("obb", rgg.GEOMETRY_OBB, True),
+                                ("obb_unfiltered", rgg.GEOMETRY_OBB, False)):
+            r = rgg.Roadmap(robot.num_links, robot.inner_per_link, sc.boxes.count,
+                            geometry=geo)
+            t0 = time.perf_counter()
+            r.build_edges(robot, rm.q_from, rm.q_to, rm.step, stream)
+            torch.cuda.synchronize()
+            build_s = time.perf_counter() - t0
+            if not filt:
+                r.set_obb_filter(False)
+            r.update_obstacles(np.arange(sc.boxes.count), sc.boxes.poses().astype(np.float32), stream)
+            r.classify(stream)
+            for i in range(args.warmup):
+                k = i % len(sc.updates)
+                r.update_obstacles(sc.updates[k].ids, dev[k], stream)
+                r.classify(stream)
+            torch.cuda.synchronize()
+            if geo == rgg.GEOMETRY_OBB:
+                r.obb_work()
+            r.set_kernel_timing(True)
+            r.kernel_time()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for i in range(args.steps):
+                k = (args.warmup + i) % len(sc.updates)
+                r.update_obstacles(sc.updates[k].ids, dev[k], stream)
+                r.classify(stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / args.steps
+            k_ms, m_ms, n = r.kernel_time()
+            info = r.info()
+            lab = r.fetch_labels(stream=stream)
+            mix = np.bincount(lab, minlength=3) / max(1, lab.size)
+            res = {"ms_per_step": ms, "edges_per_s": info["num_edges"] / (ms / 1e3),
+                   "classify_ms": k_ms / max(1, n), "merge_ms": m_ms / max(1, n),
+                   "record_gb": info["record_bytes"] / 1e9, "build_s": build_s,
+                   "labels": {"green": float(mix[0]), "gray": float(mix[1]), "red": float(mix[2])}}
+            if geo == rgg.GEOMETRY_OBB:
+                sat, seg = r.obb_work()
+                res.update({"grid_cells": info["grid_cells"], "grid_items": info["grid_items"],
+                            "spline_vertices": info["spline_vertices"],
+                            "box_tests_per_step": sat / args.steps,
+                            "segment_tests_per_step": seg / args.steps})
+            r.check_status(stream)
+            r.close()
+            out[name] = res
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle
+        rng = np.random.default_rng(2)
+        idx = rng.choice(rm.num_edges, size=min(rm.num_edges, 2000), replace=False)
+        t0 = time.perf_counter()
+        oracle.classify_obb(robot, rm.q_from[idx], rm.q_to[idx], rm.step, sc.updates[0].poses)
+        t = time.perf_counter() - t0
+        cpu = {"value": len(idx) / t, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+               "sample": f"{len(idx)} random edges, OBB / spline labels against the "
+                         f"{len(sc.updates[0].ids)} boxes one update moves (FP64, OpenMP)"}
+    b = out["obb"]
+    line = {
+        "metric": METRIC, "value": b["edges_per_s"], "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": b["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": dict(workload_config(args.workload, sc), geometry="obb (Sec. 4.2 boxes and "
+                       "shortcut splines, grid-filtered queries)"),
+        "geometries": out, "cpu_baseline": cpu,
+        "gpu_launches": 5 * args.steps,
+        "clocks": clocks.summary(),
+    }
+    print(json.dumps(line))
+    return 0
+
+
 def run_batched(args):
     """Workload 4: many independent roadmaps, each with its own robot, boxes
     and update per step.  'plain' classifies them one launch sequence per
@@ -673,6 +767,8 @@ def main():
         return run_batched(args)
     if args.workload == "serve":
         return run_serve(args)
+    if args.geometry == "obb":
+        return run_geometry(args)
     return run_gpu(args)
 
 

@@ -75,6 +75,18 @@ enum rgg_status {
   RGG_ERR_IO = -7        /* a file could not be opened, read or written      */
 };
 
+/* Geometry of a roadmap's approximations (rgg_roadmap_desc.geometry):
+ *   SPHERES   inner spheres per configuration and outer spheres per interval
+ *             (the default; every record streamed each pass);
+ *   OBB       the paper's own primitives (Sec. 4.2, 4.3): one oriented box
+ *             per (edge, body) as the outer approximation, tested against the
+ *             moved boxes by the separating-axis test, and shortcut splines
+ *             through the inscribed spheres' centres as the inner
+ *             approximation, tested against each obstacle's inscribed sphere;
+ *             a uniform grid over the edge boxes limits each pass to the cells
+ *             the moved boxes meet (Sec. 4.3, spatial filtering). */
+enum rgg_geometry { RGG_GEOMETRY_SPHERES = 0, RGG_GEOMETRY_OBB = 1 };
+
 /* Edge labels (Sec. 4.1): valid, unknown, invalid. */
 enum rgg_label { RGG_GREEN = 0, RGG_GRAY = 1, RGG_RED = 2 };
 
@@ -100,6 +112,7 @@ typedef struct {
   float margin_m;           /* delta in metres, >= 0 (2e-5 is the documented      */
                             /* default; it must exceed the FP32 rounding error)   */
   int device;               /* CUDA device ordinal                                */
+  uint32_t geometry;        /* enum rgg_geometry (0 = spheres)                    */
 } rgg_roadmap_desc;
 
 /* A serial arm in standard Denavit-Hartenberg form, for rgg_build_edges.
@@ -129,6 +142,10 @@ typedef struct {
   uint32_t grid_ctas;       /* CTAs of the classify launch                        */
   uint32_t open_requests;   /* request handles in use (rgg_update_request)        */
   uint32_t pending_capacity;/* max_obstacles + RGG_PENDING_EXTRA                  */
+  uint32_t geometry;        /* enum rgg_geometry                                  */
+  uint32_t grid_cells;      /* OBB geometry: cells of the uniform grid            */
+  uint64_t grid_items;      /* OBB geometry: (box, cell) incidences               */
+  uint64_t spline_vertices; /* OBB geometry: kept spline vertices                 */
 } rgg_info;
 
 /* ------------------------------------------------------------------------ */
@@ -397,6 +414,23 @@ int rgg_resolve_gray(rgg_roadmap_t r, uint32_t factor, uint8_t* labels_out, floa
  * mismatch. */
 int rgg_save(rgg_roadmap_t r, const char* path, void* stream);
 int rgg_load(rgg_roadmap_t r, const char* path, void* stream);
+
+/* OBB geometry only.  rgg_set_obb_filter(r, 0) makes every pass test the
+ * moved boxes against the boxes of every non-empty grid cell instead of the
+ * cells they meet (same bits; for measuring the filter).  rgg_obb_work
+ * returns the separating-axis tests and spline-segment tests run since the
+ * last call, and resets them (it waits for the device).  RGG_ERR_STATE on a
+ * sphere-geometry roadmap. */
+int rgg_set_obb_filter(rgg_roadmap_t r, int enable);
+/* Copy the OBB geometry's records to host arrays (any may be NULL):
+ *   obb      N*L boxes of 16 floats: centre (3), 0, then for k = 1..3 the
+ *            axis u_k (3) and its half-extent -- box (e, body i) at e*L + i
+ *   spl_off  N*L*K + 1 offsets: spline (e, i, s) at (e*L + i)*K + s owns
+ *            vertices [spl_off[k], spl_off[k+1])
+ *   spl_v    spline_vertices (rgg_info) vertices of 4 floats (x, y, z, 0).
+ * Synchronous.  RGG_ERR_STATE without edges or for the sphere geometry. */
+int rgg_fetch_obb_records(rgg_roadmap_t r, float* obb, uint64_t* spl_off, float* spl_v);
+int rgg_obb_work(rgg_roadmap_t r, uint64_t* sat_tests, uint64_t* segment_tests);
 
 /* ------------------------------------------------------------------------ */
 /* Autotuner of the classify launch shape (the paper has none: its batched

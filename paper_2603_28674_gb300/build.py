@@ -1,6 +1,6 @@
 """Build librgg.so in-tree for sm_103a (GB300) with nvcc.
 
-Two translation units compiled in parallel, linked into
+The translation units are compiled in parallel, linked into
 paper_2603_28674_gb300/_build/librgg.so with the CUDA runtime linked
 statically, so the library has no run-time path dependencies beyond the
 driver.
@@ -19,7 +19,7 @@ SRC_DIR = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "librgg.so")
-SOURCES = ["rgg_kernels.cu", "rgg_api.cu", "rgg_noalloc.cu"]
+SOURCES = ["rgg_kernels.cu", "rgg_api.cu", "rgg_noalloc.cu", "rgg_obb.cu"]
 HEADERS = ["rgg_device.cuh", "rgg_kernels.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + SRC_DIR]

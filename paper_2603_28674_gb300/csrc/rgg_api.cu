@@ -114,6 +114,20 @@ struct EdgeState {
   double* d_qb = nullptr;
   uint8_t* d_resolved = nullptr;  // [N] labels of the last gray resolution
   float* d_clear = nullptr;       // [N] its clearances
+  // OBB / spline geometry (Sec. 4.2): boxes per (edge, body), spline CSR,
+  // the uniform grid over the boxes, and the per-pass work list
+  float4* d_obb = nullptr;        // [N * L][4]
+  uint64_t* d_spl_off = nullptr;  // [N * L * K + 1]
+  float4* d_spl_v = nullptr;      // spline vertices
+  uint64_t n_obb = 0, n_spl = 0, n_spl_v = 0;
+  GridSpec grid{};
+  uint32_t n_cells = 0;
+  uint64_t n_items = 0;
+  uint32_t* d_cell_off = nullptr;   // [cells + 1]
+  uint32_t* d_cell_items = nullptr;
+  uint2* d_pairs = nullptr;         // [pair_cap]
+  uint32_t pair_cap = 0;
+  uint32_t* d_qcnt = nullptr;       // [2] query counters
   uint64_t device_bytes = 0;
   bool regular = false;        // inner spheres equally spaced with one radius per sample
 
@@ -133,6 +147,13 @@ struct EdgeState {
     cudaFree(d_qb);
     cudaFree(d_resolved);
     cudaFree(d_clear);
+    cudaFree(d_obb);
+    cudaFree(d_spl_off);
+    cudaFree(d_spl_v);
+    cudaFree(d_cell_off);
+    cudaFree(d_cell_items);
+    cudaFree(d_pairs);
+    cudaFree(d_qcnt);
     *this = EdgeState();
   }
 };
@@ -148,6 +169,9 @@ struct rgg_roadmap {
   int variant = kDefaultVariant;
   bool has_edges = false;
   uint64_t gen = 0;            // bumped whenever tiles or edges are replaced
+  uint32_t geometry = RGG_GEOMETRY_SPHERES;
+  bool obb_filter = true;      // spatial grid filtering of the OBB queries
+  unsigned long long* d_obbwork = nullptr;  // [2] SAT tests, spline-segment tests
   // the robot of edges built by rgg_build_edges (for the gray resolution)
   bool has_robot = false;
   double dh_a[RGG_MAX_LINKS], dh_alpha[RGG_MAX_LINKS], dh_d[RGG_MAX_LINKS], dh_radius[RGG_MAX_LINKS];
@@ -266,12 +290,13 @@ int set_tiles(rgg_roadmap* r, EdgeState* es, cudaStream_t s) {
 // sample offsets h_soff (host), into `es` (not yet visible to the roadmap).
 int alloc_edges(rgg_roadmap* r, EdgeState* es, uint64_t N, std::vector<uint64_t>&& soff,
                 cudaStream_t s) {
+  const bool spheres = r->geometry == RGG_GEOMETRY_SPHERES;
   es->N = N;
   es->h_soff = std::move(soff);
   es->S_tot = es->h_soff[N];
   es->G = (uint64_t)r->L * es->S_tot;
-  es->n_inner = (uint64_t)r->K * es->G;
-  es->n_outer = (uint64_t)r->L * (es->S_tot - N);
+  es->n_inner = spheres ? (uint64_t)r->K * es->G : 0;
+  es->n_outer = spheres ? (uint64_t)r->L * (es->S_tot - N) : 0;
   // plane stride: count + 4 floats of tail slack for 16-byte rounding of the
   // bulk copies, rounded to 64 floats (256 B) to keep planes aligned
   es->in_stride = ((es->n_inner + 4 + 63) / 64) * 64;
@@ -283,8 +308,10 @@ int alloc_edges(rgg_roadmap* r, EdgeState* es, uint64_t N, std::vector<uint64_t>
     es->device_bytes += (cnt) * sizeof(*(ptr)); \
   }
   RGG_AL(es->d_soff, N + 1);
-  RGG_AL(es->d_inner, 4 * es->in_stride);
-  RGG_AL(es->d_outer, 4 * es->out_stride);
+  if (spheres) {
+    RGG_AL(es->d_inner, 4 * es->in_stride);
+    RGG_AL(es->d_outer, 4 * es->out_stride);
+  }
   RGG_AL(es->d_red, N * r->Wm);
   RGG_AL(es->d_touch, N * r->Wm);
   RGG_AL(es->d_counts, N);
@@ -301,14 +328,14 @@ int alloc_edges(rgg_roadmap* r, EdgeState* es, uint64_t N, std::vector<uint64_t>
     if (e == cudaSuccess) e = cudaMemsetAsync(es->d_labels, RGG_GREEN, N, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(es->d_edge_acc, 0, 2 * N * 4, s);
   }
-  if (e == cudaSuccess) {
+  if (e == cudaSuccess && spheres) {
     const int rc = set_tiles(r, es, s);
     if (rc != RGG_OK) {
       es->release();
       return rc;
     }
   }
-  if (e == cudaSuccess && N) {
+  if (e == cudaSuccess && N && spheres) {
     // zero the padded tails so that the rounded bulk copies read defined data
     e = cudaMemsetAsync(es->d_inner, 0, 4 * es->in_stride * sizeof(float), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(es->d_outer, 0, 4 * es->out_stride * sizeof(float), s);
@@ -509,7 +536,7 @@ int apply_shape(rgg_roadmap* r, int variant, uint32_t cw) {
   const uint32_t old_cw = r->consumer_warps;
   r->variant = variant;
   r->consumer_warps = cw;
-  if (variant != old_v && r->has_edges && r->es.N) {
+  if (variant != old_v && r->has_edges && r->es.N && r->geometry == RGG_GEOMETRY_SPHERES) {
     cudaDeviceSynchronize();  // no launch may still read the old tiles
     const int rc = set_tiles(r, &r->es, nullptr);
     if (rc != RGG_OK) {
@@ -547,7 +574,7 @@ int rgg_roadmap_create(const rgg_roadmap_desc* desc, rgg_roadmap_t* out) {
   if (desc->num_links < 1 || desc->num_links > RGG_MAX_LINKS || desc->inner_per_link < 1 ||
       desc->inner_per_link > RGG_MAX_INNER || desc->max_obstacles < 1 ||
       desc->max_obstacles > RGG_MAX_OBSTACLES || !(desc->margin_m >= 0.0f) ||
-      !std::isfinite(desc->margin_m))
+      !std::isfinite(desc->margin_m) || desc->geometry > RGG_GEOMETRY_OBB)
     return RGG_ERR_INVALID;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess) {
@@ -565,6 +592,7 @@ int rgg_roadmap_create(const rgg_roadmap_desc* desc, rgg_roadmap_t* out) {
   r->M = desc->max_obstacles;
   r->Wm = (r->M + 31) / 32;
   r->margin = desc->margin_m;
+  r->geometry = desc->geometry;
   r->present.assign(r->M, 0);
   r->run_idx.assign(r->M, -1);
   r->req_state.assign(RGG_MAX_REQUESTS, 0);
@@ -575,6 +603,8 @@ int rgg_roadmap_create(const rgg_roadmap_desc* desc, rgg_roadmap_t* out) {
   if (e == cudaSuccess) e = dalloc(&r->d_changed, (size_t)kBoxesPerPass * kBoxRecFloats);
   if (e == cudaSuccess) e = dalloc(&r->d_status, 4);
   if (e == cudaSuccess) e = dalloc(&r->d_work, 4);
+  if (e == cudaSuccess) e = dalloc(&r->d_obbwork, 2);
+  if (e == cudaSuccess) e = cudaMemset(r->d_obbwork, 0, 2 * sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMemset(r->d_table, 0, (size_t)r->M * 16 * sizeof(float));
   if (e == cudaSuccess) e = cudaMemset(r->d_status, 0, 4 * sizeof(int));
   if (e != cudaSuccess) {
@@ -583,6 +613,7 @@ int rgg_roadmap_create(const rgg_roadmap_desc* desc, rgg_roadmap_t* out) {
     cudaFree(r->d_changed);
     cudaFree(r->d_status);
     cudaFree(r->d_work);
+    cudaFree(r->d_obbwork);
     delete r;
     return cuda_status(e);
   }
@@ -600,6 +631,7 @@ int rgg_roadmap_destroy(rgg_roadmap_t r) {
   cudaFree(r->d_changed);
   cudaFree(r->d_status);
   cudaFree(r->d_work);
+  cudaFree(r->d_obbwork);
   for (auto& ev : r->events)
     for (cudaEvent_t x : ev) cudaEventDestroy(x);
   delete r;
@@ -610,6 +642,7 @@ int rgg_upload_edges(rgg_roadmap_t r, uint64_t num_edges, const uint64_t* sample
                      const float* inner_xyzr, const float* outer_xyzr, int src_is_device,
                      void* stream) {
   if (!r || !sample_off) return RGG_ERR_INVALID;
+  if (r->geometry != RGG_GEOMETRY_SPHERES) return RGG_ERR_STATE;  // boxes and splines are built here
   if (!valid_soff(sample_off, num_edges, r->L)) return RGG_ERR_INVALID;
   if (num_edges && (!inner_xyzr || !outer_xyzr)) return RGG_ERR_INVALID;
   DeviceGuard g(r->device);
@@ -644,6 +677,170 @@ int rgg_upload_edges(rgg_roadmap_t r, uint64_t num_edges, const uint64_t* sample
   es.regular = !src_is_device && num_edges && regular_inner(inner_xyzr, n_in, r->K);
   r->has_robot = false;
   return install_edges(r, std::move(es), s);
+}
+
+// OBB geometry (Sec. 4.2, 4.3): per (edge, body) boxes and shortcut splines
+// built on the GPU in FP64 (spline vertices counted, then written at their
+// offsets), then the uniform grid over the boxes: cells of about the boxes'
+// mean largest AABB side, at most 32 per axis, each listing the boxes whose
+// AABB meets it.
+static int build_obb(rgg_roadmap* r, EdgeState* es, const rgg_robot_desc* robot, const double* d_qa,
+                     const double* d_qb, cudaStream_t s) {
+  const uint64_t N = es->N;
+  const uint32_t L = r->L, K = r->K;
+  es->n_obb = N * L;
+  es->n_spl = N * L * K;
+  uint64_t max_n = 2;
+  for (uint64_t e = 0; e < N; ++e) max_n = std::max<uint64_t>(max_n, es->h_soff[e + 1] - es->h_soff[e]);
+  const uint64_t per_warp = max_n * 3 * (L + 1);
+  if (per_warp * sizeof(double) > (256ull << 20)) return RGG_ERR_CAPACITY;
+  uint64_t warps = std::min<uint64_t>(std::max<uint64_t>(N, 1), (uint64_t)r->num_sms * 32);
+  while (warps > 8 && warps * per_warp * sizeof(double) > (1ull << 30)) warps /= 2;
+  double* scratch = nullptr;
+  uint32_t* d_count = nullptr;
+  cudaError_t e = cudaSuccess;
+  auto done = [&](int rc) {
+    cudaFree(scratch);
+    cudaFree(d_count);
+    return rc;
+  };
+#define RGG_OB(ptr, cnt)                        \
+  if (e == cudaSuccess) {                       \
+    e = dalloc(&(ptr), (cnt));                  \
+    es->device_bytes += (cnt) * sizeof(*(ptr)); \
+  }
+  RGG_OB(es->d_obb, 4 * es->n_obb);
+  RGG_OB(es->d_spl_off, es->n_spl + 1);
+  if (e == cudaSuccess) e = dalloc(&scratch, warps * per_warp);
+  if (e == cudaSuccess) e = dalloc(&d_count, std::max<uint64_t>(es->n_spl, 1));
+  if (e != cudaSuccess) return done(cuda_status(e));
+  ObbBuildParams bp{};
+  bp.L = L;
+  bp.K = K;
+  for (uint32_t i = 0; i < L; ++i) {
+    bp.a[i] = robot->a[i];
+    bp.alpha[i] = robot->alpha[i];
+    bp.d[i] = robot->d[i];
+    bp.radius[i] = robot->radius[i];
+  }
+  bp.qa = d_qa;
+  bp.qb = d_qb;
+  bp.soff = es->d_soff;
+  bp.n_edges = N;
+  bp.scratch = scratch;
+  bp.scratch_per_warp = per_warp;
+  bp.obb = es->d_obb;
+  bp.spl_count = d_count;
+  bp.pass = 0;
+  e = launch_obb_build(bp, (uint32_t)warps, s);
+  std::vector<uint32_t> count(es->n_spl);
+  if (e == cudaSuccess && es->n_spl)
+    e = cudaMemcpyAsync(count.data(), d_count, es->n_spl * sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return done(cuda_status(e));
+  std::vector<uint64_t> off(es->n_spl + 1, 0);
+  for (uint64_t k = 0; k < es->n_spl; ++k) off[k + 1] = off[k] + count[k];
+  es->n_spl_v = off[es->n_spl];
+  RGG_OB(es->d_spl_v, std::max<uint64_t>(es->n_spl_v, 1));
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(es->d_spl_off, off.data(), off.size() * sizeof(uint64_t), cudaMemcpyHostToDevice, s);
+  bp.spl_off = es->d_spl_off;
+  bp.spl_v = es->d_spl_v;
+  bp.pass = 1;
+  if (e == cudaSuccess) e = launch_obb_build(bp, (uint32_t)warps, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return done(cuda_status(e));
+  cudaFree(scratch);
+  scratch = nullptr;
+  // ---- the grid
+  GridSpec g{};
+  g.gx = g.gy = g.gz = 1;
+  g.cell = 1.0f;
+  if (es->n_obb) {
+    const uint32_t blocks = (uint32_t)std::min<uint64_t>(1024, (es->n_obb + 255) / 256);
+    float* d_part = nullptr;
+    e = dalloc(&d_part, (size_t)blocks * 8);
+    std::vector<float> part((size_t)blocks * 8);
+    if (e == cudaSuccess) e = launch_obb_bounds(es->d_obb, es->n_obb, d_part, blocks, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(part.data(), d_part, part.size() * sizeof(float), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(d_part);
+    if (e != cudaSuccess) return done(cuda_status(e));
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    double side = 0.0;
+    for (uint32_t b = 0; b < blocks; ++b) {
+      for (int k = 0; k < 3; ++k) {
+        lo[k] = std::min(lo[k], part[8 * b + k]);
+        hi[k] = std::max(hi[k], part[8 * b + 3 + k]);
+      }
+      side += part[8 * b + 6];
+    }
+    if (!(std::isfinite(lo[0]) && std::isfinite(hi[0]) && std::isfinite(lo[1]) &&
+          std::isfinite(hi[1]) && std::isfinite(lo[2]) && std::isfinite(hi[2])))
+      return done(RGG_ERR_INVALID);
+    const float ext = std::max(hi[0] - lo[0], std::max(hi[1] - lo[1], hi[2] - lo[2]));
+    float cell = (float)(side / (double)es->n_obb);
+    cell = std::max(cell, std::max(ext / 32.0f, 1e-3f));
+    g.ox = lo[0];
+    g.oy = lo[1];
+    g.oz = lo[2];
+    g.cell = cell;
+    g.gx = std::min<uint32_t>(32, std::max<uint32_t>(1, (uint32_t)std::ceil((hi[0] - lo[0]) / cell)));
+    g.gy = std::min<uint32_t>(32, std::max<uint32_t>(1, (uint32_t)std::ceil((hi[1] - lo[1]) / cell)));
+    g.gz = std::min<uint32_t>(32, std::max<uint32_t>(1, (uint32_t)std::ceil((hi[2] - lo[2]) / cell)));
+  }
+  es->grid = g;
+  es->n_cells = g.gx * g.gy * g.gz;
+  uint32_t* d_cc = nullptr;
+  e = dalloc(&d_cc, es->n_cells);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_cc, 0, es->n_cells * sizeof(uint32_t), s);
+  ObbGridParams gp{};
+  gp.obb = es->d_obb;
+  gp.n_obb = es->n_obb;
+  gp.g = g;
+  gp.cell_count = d_cc;
+  gp.pass = 0;
+  if (e == cudaSuccess) e = launch_obb_grid(gp, s);
+  std::vector<uint32_t> cc(es->n_cells);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(cc.data(), d_cc, cc.size() * sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    cudaFree(d_cc);
+    return done(cuda_status(e));
+  }
+  std::vector<uint32_t> coff(es->n_cells + 1, 0);
+  uint64_t items = 0;
+  for (uint32_t c = 0; c < es->n_cells; ++c) {
+    items += cc[c];
+    if (items > 0xffffffffull) {
+      cudaFree(d_cc);
+      return done(RGG_ERR_CAPACITY);
+    }
+    coff[c + 1] = (uint32_t)items;
+  }
+  es->n_items = items;
+  RGG_OB(es->d_cell_off, (uint64_t)es->n_cells + 1);
+  RGG_OB(es->d_cell_items, std::max<uint64_t>(items, 1));
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(es->d_cell_off, coff.data(), coff.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_cc, 0, es->n_cells * sizeof(uint32_t), s);
+  gp.cell_off = es->d_cell_off;
+  gp.cell_cursor = d_cc;
+  gp.cell_items = es->d_cell_items;
+  gp.pass = 1;
+  if (e == cudaSuccess) e = launch_obb_grid(gp, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(d_cc);
+  // every moved box may list every chunk of every cell
+  es->pair_cap = (uint32_t)std::min<uint64_t>(
+      0xffffffffull, (uint64_t)kBoxesPerPass * (es->n_cells + items / kObbChunk + 1));
+  RGG_OB(es->d_pairs, es->pair_cap);
+  RGG_OB(es->d_qcnt, 2);
+#undef RGG_OB
+  if (e != cudaSuccess) return done(cuda_status(e));
+  return done(RGG_OK);
 }
 
 int rgg_build_edges(rgg_roadmap_t r, const rgg_robot_desc* robot, uint64_t num_edges,
@@ -701,24 +898,33 @@ int rgg_build_edges(rgg_roadmap_t r, const rgg_robot_desc* robot, uint64_t num_e
     cleanup();
     return rc;
   }
-  BuildParams bp{};
-  bp.L = r->L;
-  bp.K = r->K;
-  for (uint32_t i = 0; i < r->L; ++i) {
-    bp.a[i] = robot->a[i];
-    bp.alpha[i] = robot->alpha[i];
-    bp.d[i] = robot->d[i];
-    bp.radius[i] = robot->radius[i];
+  if (r->geometry == RGG_GEOMETRY_OBB) {
+    rc = build_obb(r, &es, robot, d_qa, d_qb, s);
+    if (rc != RGG_OK) {
+      cleanup();
+      es.release();
+      return rc;
+    }
+  } else {
+    BuildParams bp{};
+    bp.L = r->L;
+    bp.K = r->K;
+    for (uint32_t i = 0; i < r->L; ++i) {
+      bp.a[i] = robot->a[i];
+      bp.alpha[i] = robot->alpha[i];
+      bp.d[i] = robot->d[i];
+      bp.radius[i] = robot->radius[i];
+    }
+    bp.qa = d_qa;
+    bp.qb = d_qb;
+    bp.soff = es.d_soff;
+    bp.inner = es.d_inner;
+    bp.outer = es.d_outer;
+    bp.in_stride = es.in_stride;
+    bp.out_stride = es.out_stride;
+    bp.n_edges = num_edges;
+    e = launch_build_records(bp, r->num_sms, s);
   }
-  bp.qa = d_qa;
-  bp.qb = d_qb;
-  bp.soff = es.d_soff;
-  bp.inner = es.d_inner;
-  bp.outer = es.d_outer;
-  bp.in_stride = es.in_stride;
-  bp.out_stride = es.out_stride;
-  bp.n_edges = num_edges;
-  e = launch_build_records(bp, r->num_sms, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   cudaFree(d_counts);
   cudaFree(d_bad);
@@ -732,7 +938,7 @@ int rgg_build_edges(rgg_roadmap_t r, const rgg_robot_desc* robot, uint64_t num_e
   es.d_qa = d_qa;
   es.d_qb = d_qb;
   es.device_bytes += 2 * qn * sizeof(double);
-  es.regular = true;  // centres at (j + 1/2)/K of each link, one radius per link
+  es.regular = r->geometry == RGG_GEOMETRY_SPHERES;  // centres at (j + 1/2)/K, one radius per link
   rc = install_edges(r, std::move(es), s);
   if (rc == RGG_OK) {
     r->has_robot = true;
@@ -939,12 +1145,80 @@ static int classify_group(rgg_roadmap_t* rs, uint32_t n, cudaStream_t s) {
   return RGG_OK;
 }
 
+// OBB geometry: each roadmap's passes in turn.  Per pass: the moved boxes'
+// records, the (box, cell) work list and the box / spline tests (Sec. 4.3
+// queries with the spatial filter), then the same merge as the sphere path.
+static int classify_group_obb(rgg_roadmap_t* rs, uint32_t n, cudaStream_t s) {
+  std::unique_ptr<BoxPrepParams> bpp(new (std::nothrow) BoxPrepParams);
+  if (!bpp) return RGG_ERR_OOM;
+  for (uint32_t i = 0; i < n; ++i) {
+    rgg_roadmap* r = rs[i];
+    auto& pend = r->pending;
+    bool ordered = false;
+    for (const auto& en : pend)
+      if (en.snap >= 0) ordered = true;
+    if (!ordered)
+      std::sort(pend.begin(), pend.end(), [](const rgg_roadmap::Entry& a,
+                                             const rgg_roadmap::Entry& b) { return a.id < b.id; });
+    for (size_t lo = 0; lo < pend.size(); lo += kBoxesPerPass) {
+      const uint32_t C = (uint32_t)std::min<size_t>(kBoxesPerPass, pend.size() - lo);
+      BoxPrepParams& bp = *bpp;
+      bp.njobs = 1;
+      BoxPrepJob& pj = bp.job[0];
+      pj.stage = r->d_stage;
+      pj.out = r->d_changed;
+      pj.C = C;
+      for (uint32_t b = 0; b < C; ++b) {
+        pj.ids[b] = pend[lo + b].id;
+        pj.rows[b] = (uint16_t)pend[lo + b].row;
+      }
+      RGG_CK(launch_box_prep(bp, s));
+      const EdgeState& es = r->es;
+      if (es.N == 0) continue;
+      ObbQueryParams q{};
+      q.L = r->L;
+      q.K = r->K;
+      q.C = C;
+      q.margin = r->margin;
+      q.g = es.grid;
+      q.obb = es.d_obb;
+      q.spl_off = es.d_spl_off;
+      q.spl_v = es.d_spl_v;
+      q.cell_off = es.d_cell_off;
+      q.cell_items = es.d_cell_items;
+      q.boxes = r->d_changed;
+      q.edge_acc = es.d_edge_acc;
+      q.pairs = es.d_pairs;
+      q.counters = es.d_qcnt;
+      q.pair_cap = es.pair_cap;
+      q.filter = r->obb_filter ? 1u : 0u;
+      q.work = r->d_obbwork;
+      RGG_CK(cudaMemsetAsync(es.d_qcnt, 0, 2 * sizeof(uint32_t), s));
+      cudaEvent_t* ev = r->timing ? next_events(r) : nullptr;
+      if (ev) RGG_CK(cudaEventRecord(ev[0], s));
+      RGG_CK(launch_obb_query(q, r->num_sms, s));
+      if (ev) RGG_CK(cudaEventRecord(ev[1], s));
+      MergeParams<1> mp;
+      mp.job[0] = make_merge_job(r, lo, C, ordered, 0);
+      mp.njobs = 1;
+      mp.total_edges = es.N;
+      RGG_CK(launch_merge_single(mp, s));
+      if (ev) RGG_CK(cudaEventRecord(ev[2], s));
+    }
+    for (const auto& en : pend)
+      if (en.snap >= 0) r->req_state[en.snap] = 2;
+    clear_pending(r);
+  }
+  return RGG_OK;
+}
+
 int rgg_classify(rgg_roadmap_t r, void* stream) {
   if (!r) return RGG_ERR_INVALID;
   if (!r->has_edges) return RGG_ERR_STATE;
   if (r->pending.empty()) return RGG_OK;
   DeviceGuard g(r->device);
   if (!g.ok) return RGG_ERR_CUDA;
+  if (r->geometry == RGG_GEOMETRY_OBB) return classify_group_obb(&r, 1, static_cast<cudaStream_t>(stream));
   return classify_group(&r, 1, static_cast<cudaStream_t>(stream));
 }
 
@@ -953,7 +1227,9 @@ int rgg_classify_many(rgg_roadmap_t* rs, uint32_t n, void* stream) {
   for (uint32_t i = 0; i < n; ++i) {
     if (!rs[i]) return RGG_ERR_INVALID;
     if (!rs[i]->has_edges) return RGG_ERR_STATE;
-    if (rs[i]->device != rs[0]->device || rs[i]->variant != rs[0]->variant) return RGG_ERR_INVALID;
+    if (rs[i]->device != rs[0]->device || rs[i]->variant != rs[0]->variant ||
+        rs[i]->geometry != rs[0]->geometry)
+      return RGG_ERR_INVALID;
     for (uint32_t j = 0; j < i; ++j)
       if (rs[j] == rs[i]) return RGG_ERR_INVALID;
   }
@@ -961,6 +1237,7 @@ int rgg_classify_many(rgg_roadmap_t* rs, uint32_t n, void* stream) {
   DeviceGuard g(rs[0]->device);
   if (!g.ok) return RGG_ERR_CUDA;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (rs[0]->geometry == RGG_GEOMETRY_OBB) return classify_group_obb(rs, n, s);
   for (uint32_t base = 0; base < n; base += kMaxJobs) {
     int rc = classify_group(rs + base, std::min<uint32_t>(kMaxJobs, n - base), s);
     if (rc != RGG_OK) return rc;
@@ -1038,7 +1315,7 @@ int rgg_fetch_box_sets(rgg_roadmap_t r, uint32_t* hit, uint32_t* touch, uint64_t
 int rgg_fetch_records(rgg_roadmap_t r, uint64_t first, uint64_t count, float* inner_xyzr,
                       float* outer_xyzr, uint64_t* sample_off) {
   if (!r) return RGG_ERR_INVALID;
-  if (!r->has_edges) return RGG_ERR_STATE;
+  if (!r->has_edges || r->geometry != RGG_GEOMETRY_SPHERES) return RGG_ERR_STATE;
   const EdgeState& es = r->es;
   if (first > es.N || count > es.N - first) return RGG_ERR_INVALID;
   DeviceGuard g(r->device);
@@ -1104,6 +1381,16 @@ int rgg_roadmap_info(rgg_roadmap_t r, rgg_info* out) {
   out->open_requests = (uint32_t)std::count_if(r->req_state.begin(), r->req_state.end(),
                                                 [](uint8_t x) { return x != 0; });
   out->pending_capacity = r->stage_rows;
+  out->geometry = r->geometry;
+  out->grid_cells = es.n_cells;
+  out->grid_items = es.n_items;
+  out->spline_vertices = es.n_spl_v;
+  if (r->geometry == RGG_GEOMETRY_OBB) {
+    // boxes, spline vertices and spline offsets
+    out->num_inner = es.n_spl_v;
+    out->num_outer = es.n_obb;
+    out->record_bytes = 64 * es.n_obb + 16 * es.n_spl_v + 8 * (es.n_spl + 1);
+  }
   out->grid_ctas = (uint32_t)std::min<uint64_t>(es.T, launch_ctas(r));
   return RGG_OK;
 }
@@ -1140,6 +1427,42 @@ int rgg_kernel_time(rgg_roadmap_t r, double* classify_ms, double* merge_ms,
   *merge_ms = tm;
   *launches = r->events_used;
   r->events_used = 0;
+  return RGG_OK;
+}
+
+int rgg_set_obb_filter(rgg_roadmap_t r, int enable) {
+  if (!r) return RGG_ERR_INVALID;
+  if (r->geometry != RGG_GEOMETRY_OBB) return RGG_ERR_STATE;
+  r->obb_filter = enable != 0;
+  return RGG_OK;
+}
+
+int rgg_fetch_obb_records(rgg_roadmap_t r, float* obb, uint64_t* spl_off, float* spl_v) {
+  if (!r) return RGG_ERR_INVALID;
+  if (!r->has_edges || r->geometry != RGG_GEOMETRY_OBB) return RGG_ERR_STATE;
+  DeviceGuard g(r->device);
+  if (!g.ok) return RGG_ERR_CUDA;
+  const EdgeState& es = r->es;
+  RGG_CK(cudaDeviceSynchronize());
+  if (obb && es.n_obb)
+    RGG_CK(cudaMemcpy(obb, es.d_obb, es.n_obb * 4 * sizeof(float4), cudaMemcpyDeviceToHost));
+  if (spl_off) RGG_CK(cudaMemcpy(spl_off, es.d_spl_off, (es.n_spl + 1) * sizeof(uint64_t), cudaMemcpyDeviceToHost));
+  if (spl_v && es.n_spl_v)
+    RGG_CK(cudaMemcpy(spl_v, es.d_spl_v, es.n_spl_v * sizeof(float4), cudaMemcpyDeviceToHost));
+  return RGG_OK;
+}
+
+int rgg_obb_work(rgg_roadmap_t r, uint64_t* sat_tests, uint64_t* segment_tests) {
+  if (!r || !sat_tests || !segment_tests) return RGG_ERR_INVALID;
+  if (r->geometry != RGG_GEOMETRY_OBB) return RGG_ERR_STATE;
+  DeviceGuard g(r->device);
+  if (!g.ok) return RGG_ERR_CUDA;
+  unsigned long long w[2] = {0, 0};
+  RGG_CK(cudaDeviceSynchronize());
+  RGG_CK(cudaMemcpy(w, r->d_obbwork, sizeof(w), cudaMemcpyDeviceToHost));
+  RGG_CK(cudaMemset(r->d_obbwork, 0, sizeof(w)));
+  *sat_tests = w[0];
+  *segment_tests = w[1];
   return RGG_OK;
 }
 
@@ -1320,7 +1643,8 @@ static int load_device(FileIO& io, void* dst, size_t bytes, cudaStream_t s) {
 
 int rgg_save(rgg_roadmap_t r, const char* path, void* stream) {
   if (!r || !path) return RGG_ERR_INVALID;
-  if (!r->has_edges || !r->pending.empty()) return RGG_ERR_STATE;
+  if (!r->has_edges || !r->pending.empty() || r->geometry != RGG_GEOMETRY_SPHERES)
+    return RGG_ERR_STATE;
   DeviceGuard g(r->device);
   if (!g.ok) return RGG_ERR_CUDA;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -1367,6 +1691,7 @@ int rgg_save(rgg_roadmap_t r, const char* path, void* stream) {
 
 int rgg_load(rgg_roadmap_t r, const char* path, void* stream) {
   if (!r || !path) return RGG_ERR_INVALID;
+  if (r->geometry != RGG_GEOMETRY_SPHERES) return RGG_ERR_STATE;
   DeviceGuard g(r->device);
   if (!g.ok) return RGG_ERR_CUDA;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -1493,7 +1818,7 @@ int rgg_autotune(rgg_roadmap_t* rs, uint32_t n, uint32_t reps, rgg_tune_result* 
   if (!rs || n == 0 || n > (uint32_t)kMaxJobs || (max_results && !results)) return RGG_ERR_INVALID;
   for (uint32_t i = 0; i < n; ++i) {
     if (!rs[i]) return RGG_ERR_INVALID;
-    if (!rs[i]->has_edges) return RGG_ERR_STATE;
+    if (!rs[i]->has_edges || rs[i]->geometry != RGG_GEOMETRY_SPHERES) return RGG_ERR_STATE;
     if (rs[i]->device != rs[0]->device) return RGG_ERR_INVALID;
     for (uint32_t j = 0; j < i; ++j)
       if (rs[j] == rs[i]) return RGG_ERR_INVALID;
@@ -1606,7 +1931,8 @@ int rgg_step_graph_create(rgg_roadmap_t* rs, uint32_t n, const uint32_t* n_ids,
   if (!rs || n == 0 || !n_ids || !ids || !poses) return RGG_ERR_INVALID;
   for (uint32_t i = 0; i < n; ++i) {
     if (!rs[i]) return RGG_ERR_INVALID;
-    if (!rs[i]->has_edges || !rs[i]->pending.empty()) return RGG_ERR_STATE;
+    if (!rs[i]->has_edges || !rs[i]->pending.empty() || rs[i]->geometry != RGG_GEOMETRY_SPHERES)
+      return RGG_ERR_STATE;
     if (rs[i]->device != rs[0]->device || rs[i]->variant != rs[0]->variant) return RGG_ERR_INVALID;
     for (uint32_t j = 0; j < i; ++j)
       if (rs[j] == rs[i]) return RGG_ERR_INVALID;

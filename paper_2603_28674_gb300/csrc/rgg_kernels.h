@@ -104,6 +104,62 @@ struct ResolveParams {
   uint64_t n_edges;
 };
 
+// ---------------------------------------------------------------------------
+// The paper's primitives (Sec. 4.2, 4.3): per (edge, body) OBBs and shortcut
+// splines, a uniform grid over the OBBs, and the per-pass queries.
+// ---------------------------------------------------------------------------
+// OBB record: 4 float4 = (centre, 0), (u1, h1), (u2, h2), (u3, h3).
+constexpr uint32_t kObbChunk = 4096;  // grid-cell boxes per query work item
+struct ObbBuildParams {
+  uint32_t L, K;
+  double a[kMaxBuildLinks], alpha[kMaxBuildLinks], d[kMaxBuildLinks], radius[kMaxBuildLinks];
+  const double* qa;
+  const double* qb;
+  const uint64_t* soff;
+  uint64_t n_edges;
+  double* scratch;            // per warp: max_n * (L + 1) * 3 doubles of joint positions
+  uint64_t scratch_per_warp;  // doubles
+  float4* obb;                // [N * L][4] (pass 0 only)
+  uint32_t* spl_count;        // [N * L * K] kept vertices per spline (pass 0)
+  const uint64_t* spl_off;    // [N * L * K + 1] (pass 1)
+  float4* spl_v;              // vertices (pass 1)
+  int pass;                   // 0: boxes and counts; 1: vertices
+};
+
+struct GridSpec {
+  float ox, oy, oz, cell;     // origin and cell side
+  uint32_t gx, gy, gz;        // cells per axis
+};
+
+struct ObbGridParams {
+  const float4* obb;
+  uint64_t n_obb;
+  GridSpec g;
+  uint32_t* cell_count;       // pass 0: incidences per cell (atomic)
+  const uint32_t* cell_off;   // pass 1: offsets
+  uint32_t* cell_cursor;      // pass 1: fill cursors (atomic)
+  uint32_t* cell_items;       // pass 1: OBB indices
+  int pass;
+};
+
+struct ObbQueryParams {
+  uint32_t L, K, C;
+  float margin;
+  GridSpec g;
+  const float4* obb;
+  const uint64_t* spl_off;
+  const float4* spl_v;
+  const uint32_t* cell_off;
+  const uint32_t* cell_items;
+  const float* boxes;         // [C][24] derived records of the pass's boxes
+  uint32_t* edge_acc;         // [N][2]
+  uint2* pairs;               // (box position | chunk << 5, cell) work list
+  uint32_t* counters;         // [0] pairs listed, [1] pairs taken
+  uint32_t pair_cap;
+  uint32_t filter;            // 0: every non-empty cell for every box (no spatial filter)
+  unsigned long long* work;   // [2] SAT tests, spline-segment tests (may be null)
+};
+
 size_t classify_smem_bytes(int variant, uint32_t consumer_warps);
 
 cudaError_t launch_count_samples(const double* qa, const double* qb, uint64_t n_edges, uint32_t L,
@@ -118,5 +174,10 @@ cudaError_t launch_classify_batched(const ClassifyParams<kMaxJobs>& p, const Cla
 cudaError_t launch_merge_single(const MergeParams<1>& p, cudaStream_t s);
 cudaError_t launch_merge_batched(const MergeParams<kMaxJobs>& p, cudaStream_t s);
 cudaError_t launch_resolve_gray(const ResolveParams& p, int num_sms, cudaStream_t s);
+cudaError_t launch_obb_build(const ObbBuildParams& p, uint32_t warps, cudaStream_t s);
+cudaError_t launch_obb_bounds(const float4* obb, uint64_t n_obb, float* partial, uint32_t blocks,
+                              cudaStream_t s);
+cudaError_t launch_obb_grid(const ObbGridParams& p, cudaStream_t s);
+cudaError_t launch_obb_query(const ObbQueryParams& p, int num_sms, cudaStream_t s);
 
 }  // namespace rgg

@@ -17,6 +17,7 @@ from typing import Optional, Sequence
 import numpy as np
 
 GREEN, GRAY, RED = 0, 1, 2
+GEOMETRY_SPHERES, GEOMETRY_OBB = 0, 1
 RGG_OK, RGG_ERR_INVALID, RGG_ERR_OOM, RGG_ERR_CUDA, RGG_ERR_TIMEOUT, RGG_ERR_STATE = \
     0, -1, -2, -3, -4, -5
 RGG_ERR_CAPACITY = -6
@@ -41,6 +42,7 @@ EXPORTS = (
     "rgg_fetch_request_labels", "rgg_release_request", "rgg_autotune",
     "rgg_step_graph_create", "rgg_step_graph_launch", "rgg_step_graph_nodes",
     "rgg_step_graph_destroy", "rgg_save", "rgg_load", "rgg_resolve_gray", "rgg_fetch_boxes",
+    "rgg_set_obb_filter", "rgg_obb_work", "rgg_fetch_obb_records",
 )
 
 
@@ -54,7 +56,7 @@ class RGGError(RuntimeError):
 class _Desc(ctypes.Structure):
     _fields_ = [("num_links", ctypes.c_uint32), ("inner_per_link", ctypes.c_uint32),
                 ("max_obstacles", ctypes.c_uint32), ("margin_m", ctypes.c_float),
-                ("device", ctypes.c_int)]
+                ("device", ctypes.c_int), ("geometry", ctypes.c_uint32)]
 
 
 class _Robot(ctypes.Structure):
@@ -93,7 +95,9 @@ class Info(ctypes.Structure):
                 ("max_obstacles", ctypes.c_uint32), ("mask_words", ctypes.c_uint32),
                 ("tile_samples", ctypes.c_uint32), ("num_tiles", ctypes.c_uint64),
                 ("pending_boxes", ctypes.c_uint32), ("grid_ctas", ctypes.c_uint32),
-                ("open_requests", ctypes.c_uint32), ("pending_capacity", ctypes.c_uint32)]
+                ("open_requests", ctypes.c_uint32), ("pending_capacity", ctypes.c_uint32),
+                ("geometry", ctypes.c_uint32), ("grid_cells", ctypes.c_uint32),
+                ("grid_items", ctypes.c_uint64), ("spline_vertices", ctypes.c_uint64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -144,6 +148,9 @@ def _lib():
         "rgg_save": [vp, ctypes.c_char_p, vp],
         "rgg_resolve_gray": [vp, u32, vp, vp, i32, ctypes.POINTER(_ResolveStats), vp],
         "rgg_fetch_boxes": [vp, vp, vp, vp],
+        "rgg_set_obb_filter": [vp, i32],
+        "rgg_obb_work": [vp, ctypes.POINTER(u64), ctypes.POINTER(u64)],
+        "rgg_fetch_obb_records": [vp, vp, vp, vp],
         "rgg_load": [vp, ctypes.c_char_p, vp],
     }
     for name, args in sig.items():
@@ -204,9 +211,9 @@ class Roadmap:
     """One resident roadmap (wraps an rgg_roadmap_t)."""
 
     def __init__(self, num_links: int, inner_per_link: int, max_obstacles: int,
-                 margin: float = 2e-5, device: int = 0):
+                 margin: float = 2e-5, device: int = 0, geometry: int = GEOMETRY_SPHERES):
         lib = _lib()
-        desc = _Desc(num_links, inner_per_link, max_obstacles, margin, device)
+        desc = _Desc(num_links, inner_per_link, max_obstacles, margin, device, geometry)
         h = ctypes.c_void_p()
         _check("rgg_roadmap_create", lib.rgg_roadmap_create(ctypes.byref(desc), ctypes.byref(h)))
         self._h = h
@@ -215,6 +222,7 @@ class Roadmap:
         self.inner_per_link = inner_per_link
         self.max_obstacles = max_obstacles
         self.margin = margin
+        self.geometry = geometry
 
     # -- lifetime -----------------------------------------------------------
     def close(self) -> None:
@@ -379,6 +387,28 @@ class Roadmap:
 
     def check_status(self, stream=None) -> None:
         _check("rgg_check_status", _lib().rgg_check_status(self._h, _stream(stream, self.device)))
+
+    def set_obb_filter(self, enable: bool) -> None:
+        """OBB geometry: test only the grid cells the moved boxes meet (default)."""
+        _check("rgg_set_obb_filter", _lib().rgg_set_obb_filter(self._h, int(enable)))
+
+    def fetch_obb_records(self):
+        """OBB geometry: (boxes [N, L, 16], spline offsets [N*L*K + 1],
+        spline vertices [V, 4]) host copies (rgg_fetch_obb_records)."""
+        info = self.info()
+        n, L, K = info["num_edges"], self.num_links, self.inner_per_link
+        obb = np.empty((n, L, 16), dtype=np.float32)
+        off = np.empty(n * L * K + 1, dtype=np.uint64)
+        v = np.empty((max(info["spline_vertices"], 1), 4), dtype=np.float32)
+        _check("rgg_fetch_obb_records", _lib().rgg_fetch_obb_records(
+            self._h, obb.ctypes.data, off.ctypes.data, v.ctypes.data))
+        return obb, off, v[:info["spline_vertices"]]
+
+    def obb_work(self):
+        """OBB geometry: (box tests, spline-segment tests) since the last call."""
+        a, b = ctypes.c_uint64(), ctypes.c_uint64()
+        _check("rgg_obb_work", _lib().rgg_obb_work(self._h, ctypes.byref(a), ctypes.byref(b)))
+        return int(a.value), int(b.value)
 
     def resolve_gray(self, factor: int = 10, stream=None):
         """Non-lazy resolution of the gray edges (rgg_resolve_gray): returns
