@@ -556,11 +556,14 @@ __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const 
       uint32_t bits = 0;
       uint32_t any_cand = 0;
       if (act) {
-        // any active lane's sphere can centre the bounding sphere
-        const int mid = (act & 0xffff0000u) ? __ffs(act & 0xffff0000u) - 1 : 31 - __clz(act);
-        const float mx = __shfl_sync(0xffffffffu, x, mid);
-        const float my = __shfl_sync(0xffffffffu, y, mid);
-        const float mz = __shfl_sync(0xffffffffu, z, mid);
+        // the bounding sphere's centre: the midpoint of the first and the last
+        // active sphere centres (the round's spheres follow one link's path,
+        // and the chord's midpoint gave the fewest candidates of the centres
+        // tried); any centre is valid, the radius covers every sphere
+        const int lo_l = __ffs(act) - 1, hi_l = 31 - __clz(act);
+        const float mx = 0.5f * (__shfl_sync(0xffffffffu, x, lo_l) + __shfl_sync(0xffffffffu, x, hi_l));
+        const float my = 0.5f * (__shfl_sync(0xffffffffu, y, lo_l) + __shfl_sync(0xffffffffu, y, hi_l));
+        const float mz = 0.5f * (__shfl_sync(0xffffffffu, z, lo_l) + __shfl_sync(0xffffffffu, z, hi_l));
         const float dx = x - mx, dy = y - my, dz = z - mz;
         const float reach = has_next ? sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) + r : 0.0f;
         const float rw = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(reach)));
