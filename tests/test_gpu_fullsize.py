@@ -1,0 +1,94 @@
+"""Parity at the benchmark's full sizes, in the launch configuration bench.py
+times (default pipeline variant and warp count): the large roadmap (501,516
+edges, 26.8 GB of records), the 7-DOF roadmap, and the 128-roadmap batched
+launch.  After real updates, the labels of a random sample of edges are
+checked against the FP64 oracle edge by edge: identical where the clearance
+exceeds 1e-4 m, otherwise GPU gray; and the per-box sets of the sample in
+the conservative relation."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2603_28674_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+PIN = 1e-4
+
+
+@pytest.fixture(scope="module")
+def rgg():
+    from paper_2603_28674_gb300 import build
+    build.build()
+    from paper_2603_28674_gb300 import rgg as _rgg
+    return _rgg
+
+
+def f32(x):
+    return np.asarray(x, dtype=np.float32)
+
+
+def check_sample(r, sc, boxes, sample, where):
+    rm = sc.roadmap
+    got = r.fetch_labels()[sample]
+    hit, touch = r.fetch_box_sets()
+    want = oracle.classify(rm.robot, rm.q_from[sample], rm.q_to[sample], rm.step, boxes.poses(),
+                           bits=True)
+    pinned = want["kappa"] > PIN
+    bad = np.flatnonzero(pinned & (got != want["labels"]))
+    assert bad.size == 0, f"{where}: {bad.size} pinned sampled edges differ"
+    off = got != want["labels"]
+    assert np.all(got[off] == oracle.GRAY), f"{where}: disagreement other than GPU gray"
+    w = want["hit"].shape[1]
+    assert np.all((hit[sample, :w] & ~want["hit"]) == 0), f"{where}: GPU hit outside the oracle's"
+    assert np.all((want["touch"] & ~touch[sample, :w]) == 0), f"{where}: oracle touch missing"
+    return int(off.sum())
+
+
+@pytest.mark.parametrize("which", ["large", "7dof"])
+def test_full_size_roadmap_sampled_against_oracle(rgg, which):
+    sc = W.workload_large(n_updates=3) if which == "large" else W.workload_7dof(n_updates=3)
+    rm, robot = sc.roadmap, sc.roadmap.robot
+    boxes = sc.boxes.copy()
+    with rgg.Roadmap(robot.num_links, robot.inner_per_link, boxes.count) as r:
+        r.build_edges(robot, rm.q_from, rm.q_to, rm.step)
+        info = r.info()
+        assert info["tile_samples"] == 713          # the benchmark's default pipeline shape
+        r.update_obstacles(np.arange(boxes.count), f32(boxes.poses()))
+        r.classify()
+        for up in sc.updates:
+            r.update_obstacles(up.ids, f32(up.poses))
+            r.classify()
+            boxes.centre[up.ids] = up.poses[:, :3]
+        rng = np.random.default_rng(11)
+        sample = np.sort(rng.choice(rm.num_edges, size=1500, replace=False))
+        check_sample(r, sc, boxes, sample, which)
+        r.check_status()
+
+
+def test_full_size_batched_launch_sampled_against_oracle(rgg):
+    scenes = W.workload_batched(n_updates=2)
+    rms, states = [], []
+    for sc in scenes:
+        robot = sc.roadmap.robot
+        r = rgg.Roadmap(robot.num_links, robot.inner_per_link, sc.boxes.count)
+        r.build_edges(robot, sc.roadmap.q_from, sc.roadmap.q_to, sc.roadmap.step)
+        r.update_obstacles(np.arange(sc.boxes.count), f32(sc.boxes.poses()))
+        rms.append(r)
+        states.append(sc.boxes.copy())
+    rgg.classify_many(rms)
+    for step in range(2):
+        for r, sc, st in zip(rms, scenes, states):
+            up = sc.updates[step]
+            r.update_obstacles(up.ids, f32(up.poses))
+            st.centre[up.ids] = up.poses[:, :3]
+        rgg.classify_many(rms)
+    rng = np.random.default_rng(12)
+    for k in rng.choice(len(scenes), size=8, replace=False):
+        sc, r = scenes[k], rms[k]
+        sample = np.sort(rng.choice(sc.roadmap.num_edges, size=min(300, sc.roadmap.num_edges),
+                                    replace=False))
+        check_sample(r, sc, states[k], sample, f"roadmap {k}")
+    for r in rms:
+        r.check_status()
+        r.close()
