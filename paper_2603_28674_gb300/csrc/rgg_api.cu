@@ -124,7 +124,7 @@ struct EdgeState {
   uint32_t n_cells = 0;
   uint64_t n_items = 0;
   uint32_t* d_cell_off = nullptr;   // [cells + 1]
-  uint32_t* d_cell_items = nullptr;
+  float4* d_cell_items = nullptr;   // 2 per item: AABB low corner + index, high corner
   uint2* d_pairs = nullptr;         // [pair_cap]
   uint32_t pair_cap = 0;
   uint32_t* d_qcnt = nullptr;       // [2] query counters
@@ -822,7 +822,7 @@ static int build_obb(rgg_roadmap* r, EdgeState* es, const rgg_robot_desc* robot,
   }
   es->n_items = items;
   RGG_OB(es->d_cell_off, (uint64_t)es->n_cells + 1);
-  RGG_OB(es->d_cell_items, std::max<uint64_t>(items, 1));
+  RGG_OB(es->d_cell_items, 2 * std::max<uint64_t>(items, 1));
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(es->d_cell_off, coff.data(), coff.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(d_cc, 0, es->n_cells * sizeof(uint32_t), s);

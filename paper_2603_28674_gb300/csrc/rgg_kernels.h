@@ -138,7 +138,7 @@ struct ObbGridParams {
   uint32_t* cell_count;       // pass 0: incidences per cell (atomic)
   const uint32_t* cell_off;   // pass 1: offsets
   uint32_t* cell_cursor;      // pass 1: fill cursors (atomic)
-  uint32_t* cell_items;       // pass 1: OBB indices
+  float4* cell_items;         // pass 1: per item (AABB low corner, OBB index bits), (high corner, 0)
   int pass;
 };
 
@@ -150,7 +150,7 @@ struct ObbQueryParams {
   const uint64_t* spl_off;
   const float4* spl_v;
   const uint32_t* cell_off;
-  const uint32_t* cell_items;
+  const float4* cell_items;   // 2 float4 per item, see ObbGridParams
   const float* boxes;         // [C][24] derived records of the pass's boxes
   uint32_t* edge_acc;         // [N][2]
   uint2* pairs;               // (box position | chunk << 5, cell) work list

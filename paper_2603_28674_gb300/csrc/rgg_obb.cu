@@ -297,7 +297,9 @@ __global__ void __launch_bounds__(256) obb_bounds_kernel(const float4* obb, uint
 }
 
 // Pass 0 counts, per cell, the boxes whose AABB meets it; pass 1 writes each
-// box's index into every such cell's list.
+// box into every such cell's list as two float4: (AABB low corner, index
+// bits) and (AABB high corner, 0), so that a query streams the AABBs of a
+// cell's boxes contiguously and loads a box record only when the AABBs meet.
 __global__ void __launch_bounds__(256) obb_grid_kernel(const __grid_constant__ ObbGridParams p) {
   for (uint64_t o = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; o < p.n_obb;
        o += (uint64_t)gridDim.x * blockDim.x) {
@@ -314,7 +316,9 @@ __global__ void __launch_bounds__(256) obb_grid_kernel(const __grid_constant__ O
             atomicAdd(&p.cell_count[cell], 1u);
           } else {
             const uint32_t k = atomicAdd(&p.cell_cursor[cell], 1u);
-            p.cell_items[p.cell_off[cell] + k] = (uint32_t)o;
+            const size_t at = 2 * ((size_t)p.cell_off[cell] + k);
+            p.cell_items[at] = make_float4(a[0], a[1], a[2], __uint_as_float((uint32_t)o));
+            p.cell_items[at + 1] = make_float4(b[0], b[1], b[2], 0.0f);
           }
         }
   }
@@ -459,13 +463,13 @@ __global__ void __launch_bounds__(256) obb_query_kernel(const __grid_constant__ 
     const uint32_t bit = 1u << bpos;
     unsigned long long n_sat = 0, n_seg = 0;
     for (uint32_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
-      const uint32_t o = p.cell_items[k];
-      const float4* ob = p.obb + 4 * (size_t)o;
-      float lo[3], hi[3];
-      obb_aabb(ob, lo, hi);
+      const float4 ia = p.cell_items[2 * (size_t)k], ib = p.cell_items[2 * (size_t)k + 1];
+      const float lo[3] = {ia.x, ia.y, ia.z}, hi[3] = {ib.x, ib.y, ib.z};
       if (lo[0] > bhi[0] || lo[1] > bhi[1] || lo[2] > bhi[2] || blo[0] > hi[0] ||
           blo[1] > hi[1] || blo[2] > hi[2])
         continue;
+      const uint32_t o = __float_as_uint(ia.w);
+      const float4* ob = p.obb + 4 * (size_t)o;
       const uint32_t rx = cell_coord(fmaxf(lo[0], blo[0]), p.g.ox, p.g.cell, p.g.gx);
       const uint32_t ry = cell_coord(fmaxf(lo[1], blo[1]), p.g.oy, p.g.cell, p.g.gy);
       const uint32_t rz = cell_coord(fmaxf(lo[2], blo[2]), p.g.oz, p.g.cell, p.g.gz);

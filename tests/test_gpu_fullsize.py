@@ -92,3 +92,44 @@ def test_full_size_batched_launch_sampled_against_oracle(rgg):
     for r in rms:
         r.check_status()
         r.close()
+
+
+def test_full_size_serving_alone_equals_mix(rgg):
+    """The serving workload's eight resident roadmaps at full size (~50k and
+    ~200k edges), the first 0.3 s of its 2,000 requests/s stream: every
+    request's labels are bit-identical served with continuous batching and
+    one request per launch, and a few requests agree with the oracle on
+    sampled edges of the state after them."""
+    from paper_2603_28674_gb300 import serve as SV
+    scenes, reqs = W.workload_serving(duration_s=0.3)
+    requests = [SV.ServeRequest(q.arrival_s, q.roadmap, q.update.ids.astype(np.uint32),
+                                q.update.poses.astype(np.float32)) for q in reqs]
+    res = {}
+    for mode in ("batched", "one_at_a_time"):
+        srv = SV.Server(device=0, host_slots=64)
+        for sc in scenes:
+            rm = sc.roadmap
+            srv.add_roadmap(rm.robot, rm.q_from, rm.q_to, rm.step, np.arange(sc.boxes.count),
+                            sc.boxes.poses())
+        res[mode] = srv.serve(requests, mode, keep_results=True)
+        srv.close()
+    mix, alone = res["batched"], res["one_at_a_time"]
+    assert mix["mean_batch"] > 1.0
+    for i in range(len(requests)):
+        np.testing.assert_array_equal(mix["results"][i], alone["results"][i],
+                                      err_msg=f"request {i}")
+    states = [sc.boxes.copy() for sc in scenes]
+    rng = np.random.default_rng(13)
+    check = set(rng.choice(len(reqs), size=4, replace=False).tolist())
+    for i, q in enumerate(reqs):
+        states[q.roadmap].centre[q.update.ids] = q.update.poses[:, :3]
+        if i in check:
+            sc = scenes[q.roadmap]
+            rm = sc.roadmap
+            sample = np.sort(rng.choice(rm.num_edges, size=400, replace=False))
+            want = oracle.classify(rm.robot, rm.q_from[sample], rm.q_to[sample], rm.step,
+                                   states[q.roadmap].poses())
+            got = mix["results"][i][sample]
+            pinned = want["kappa"] > PIN
+            assert np.all(got[pinned] == want["labels"][pinned]), f"request {i}"
+            assert np.all(got[got != want["labels"]] == oracle.GRAY), f"request {i}"
