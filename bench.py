@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--geometry", default="spheres", choices=["spheres", "obb"],
                     help="obb: time the paper's OBB / spline geometry beside the sphere one "
                          "on the same roadmap and updates")
+    ap.add_argument("--persist", action="store_true",
+                    help="also time rgg_save / rgg_load of the roadmap through a temporary file")
     ap.add_argument("--resolve", type=int, default=0, metavar="F",
                     help="also time the non-lazy resolution of the gray edges at F-times "
                          "finer resampling (0: off)")
@@ -381,6 +383,7 @@ def run_gpu(args):
     r.check_status(stream)
     resolve = measure_resolve(r, sc, args.resolve, stream, rank == 0 and world == 1) \
         if args.resolve else None
+    persist = measure_persist(r, robot, sc.boxes.count, stream) if args.persist else None
 
     n_edges = info["num_edges"]
     value = replica_throughput(world, n_edges * args.steps, ms / 1000.0)
@@ -426,6 +429,8 @@ def run_gpu(args):
     }
     if resolve is not None:
         line["resolve"] = resolve
+    if persist is not None:
+        line["persist"] = persist
     r.close()
     if rank == 0:
         print(json.dumps(line))
@@ -433,6 +438,28 @@ def run_gpu(args):
         dist.barrier()
         dist.destroy_process_group()
     return 0
+
+
+def measure_persist(r, robot, m: int, stream) -> dict:
+    """Save the roadmap to a temporary file and load it into a second roadmap
+    (wall time of each call); the reloaded labels must equal the original's."""
+    import tempfile
+    from paper_2603_28674_gb300 import rgg
+    info = r.info()
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "roadmap.rgg")
+        t0 = time.perf_counter()
+        r.save(path, stream)
+        t_save = time.perf_counter() - t0
+        size = os.path.getsize(path)
+        with rgg.Roadmap(robot.num_links, robot.inner_per_link, m) as b:
+            t0 = time.perf_counter()
+            b.load(path, stream)
+            t_load = time.perf_counter() - t0
+            same = bool(np.array_equal(b.fetch_labels(stream=stream), r.fetch_labels(stream=stream)))
+    return {"file_gb": size / 1e9, "record_gb": info["record_bytes"] / 1e9,
+            "save_s": t_save, "load_s": t_load, "save_gbs": size / t_save / 1e9,
+            "load_gbs": size / t_load / 1e9, "labels_identical": same}
 
 
 def measure_resolve(r, sc, factor: int, stream, with_oracle: bool) -> dict:
