@@ -182,3 +182,35 @@ def test_sphere_only_calls_are_refused(rgg, tmp_path):
         with pytest.raises(rgg.RGGError) as e:
             s.set_obb_filter(False)
         assert e.value.status == rgg.RGG_ERR_STATE
+
+
+def test_obb_edge_cases(rgg):
+    """An empty roadmap; a single resting edge (every spline one segment);
+    a box that is never placed (absent: affects nothing)."""
+    robot = W.planar_arm(1, 0.3, 0.03, 4)
+    with rgg.Roadmap(1, 4, 3, geometry=rgg.GEOMETRY_OBB) as r:
+        r.build_edges(robot, np.zeros((0, 1)), np.zeros((0, 1)), 0.05)
+        r.update_obstacles([0], f32([[0.15, 0, 0, 1, 0, 0, 0, 1, 0, 0, 0, 1, 0.05, 0.05, 0.05]]))
+        r.classify()
+        assert r.fetch_labels().shape == (0,)
+        r.check_status()
+    boxes = np.array([[0.15, 0, 0, 1, 0, 0, 0, 1, 0, 0, 0, 1, 0.05, 0.05, 0.05],
+                      [0.15, 0.5, 0, 1, 0, 0, 0, 1, 0, 0, 0, 1, 0.05, 0.05, 0.05],
+                      [0.15, 0.07, 0, 1, 0, 0, 0, 1, 0, 0, 0, 1, 0.05, 0.05, 0.05]])
+    with rgg.Roadmap(1, 4, 4, geometry=rgg.GEOMETRY_OBB) as r:
+        r.build_edges(robot, np.zeros((1, 1)), np.zeros((1, 1)), 0.05)
+        obb, off, verts = r.fetch_obb_records()
+        assert np.all(np.diff(off.astype(np.int64)) == 2)      # one segment per spline
+        for b, want in ((0, rgg.RED), (1, rgg.GREEN), (2, rgg.GRAY)):
+            r.update_obstacles([b], f32(boxes[b:b + 1]))
+            r.classify()
+            got = r.fetch_labels()[0]
+            ref = oracle.classify_obb(robot, [[0.0]], [[0.0]], 0.05, boxes[b:b + 1])["labels"][0]
+            assert got == ref == want, (b, got, ref)
+            # move it far away again before the next case
+            far = boxes[b:b + 1].copy()
+            far[0, :3] = [40.0 + b, 40.0, 0.0]
+            r.update_obstacles([b], f32(far))
+            r.classify()
+            assert r.fetch_labels()[0] == rgg.GREEN
+        r.check_status()
