@@ -19,8 +19,9 @@ SRC_DIR = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "librgg.so")
-SOURCES = ["rgg_kernels.cu", "rgg_api.cu", "rgg_noalloc.cu", "rgg_obb.cu"]
-HEADERS = ["rgg_device.cuh", "rgg_kernels.h"]
+SOURCES = ["rgg_kernels.cu", "rgg_api.cu", "rgg_noalloc.cu", "rgg_obb.cu", "rgg_obb_host.cu",
+           "rgg_persist.cu", "rgg_tune.cu", "rgg_resolve_host.cu"]
+HEADERS = ["rgg_device.cuh", "rgg_kernels.h", "rgg_host.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + SRC_DIR]
 

@@ -1,0 +1,239 @@
+// Internal header of the host side: the per-roadmap state and the helpers the
+// host translation units share (not part of the C ABI).
+#pragma once
+
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <utility>
+#include <vector>
+
+#include "rgg.h"
+#include "rgg_kernels.h"
+
+namespace rgg_host {
+
+using namespace rgg;
+
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+inline int cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return RGG_OK;
+  cudaGetLastError();  // clear sticky-free errors so the next call starts clean
+  return e == cudaErrorMemoryAllocation ? RGG_ERR_OOM : RGG_ERR_CUDA;
+}
+
+#define RGG_CK(call)                         \
+  do {                                       \
+    cudaError_t e_ = (call);                 \
+    if (e_ != cudaSuccess) return cuda_status(e_); \
+  } while (0)
+
+template <class T>
+cudaError_t dalloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) return cudaSuccess;
+  return cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
+}
+
+// Smallest margin for which interpolated inner centres are used (their error
+// is below 2e-6 m, the FP32 tests' below 1e-6 m).
+constexpr float kRegularMinMargin = 1e-5f;
+
+// Streaming tile geometry of one roadmap (see the classify kernel): each
+// stage buffer holds a header, the tile's edge table, 4 inner planes and 4
+// outer planes.
+struct Tiling {
+  uint32_t S = 0, max_edges = 0;
+  uint32_t off_in = 0, off_out = 0, in_cap = 0, out_cap = 0;
+};
+
+inline uint32_t align16(uint32_t x) { return (x + 15u) & ~15u; }
+inline uint32_t round4(uint32_t x) { return (x + 3u) & ~3u; }
+
+// A window of S consecutive global samples meets at most S/(2L) + 2 edges
+// (every edge has at least 2L samples); one more entry of slack.
+inline bool tiling_for(uint32_t L, uint32_t K, uint32_t S, uint32_t stage_bytes, Tiling* t) {
+  t->S = S;
+  t->max_edges = S / (2 * L) + 3;
+  t->off_in = align16(kStageEtabOff + 16 * t->max_edges);
+  t->in_cap = round4(K * S + 8);
+  t->off_out = t->off_in + 16 * t->in_cap;
+  t->out_cap = round4(S + 1 + 8);
+  return t->max_edges <= (uint32_t)kMaxTileEdges &&
+         (uint64_t)t->off_out + 16ull * t->out_cap <= (uint64_t)stage_bytes;
+}
+
+// Tiles of 31*rounds samples (full rounds) when they fit a stage, else the
+// largest that does; smaller only for roadmaps too small to give every CTA of
+// a launch two tiles (big tiles keep the producer warp's per-tile cost low).
+inline Tiling choose_tiling(uint32_t L, uint32_t K, uint64_t G, uint32_t warps, int variant) {
+  // `warps`: how many tiles the roadmap should at least be cut into
+  const VariantShape v = variant_shape(variant);
+  uint32_t smax = 31 * v.rounds;
+  Tiling t;
+  while (smax > 1 && !tiling_for(L, K, smax, v.stage_bytes, &t)) --smax;
+  const uint64_t want = (G + warps - 1) / std::max<uint32_t>(warps, 1);
+  uint32_t s = (uint32_t)std::min<uint64_t>(smax, std::max<uint64_t>(want, 31));
+  s = std::max<uint32_t>(1, std::min(s, smax));
+  tiling_for(L, K, s, v.stage_bytes, &t);
+  return t;
+}
+
+struct EdgeState {
+  uint64_t N = 0, S_tot = 0, G = 0, n_inner = 0, n_outer = 0;
+  uint64_t in_stride = 0, out_stride = 0;
+  std::vector<uint64_t> h_soff;
+  uint64_t* d_soff = nullptr;
+  float* d_inner = nullptr;
+  float* d_outer = nullptr;
+  TileDesc* d_tiles = nullptr;
+  int4* d_etab = nullptr;
+  uint64_t T = 0, n_etab = 0;
+  Tiling tiling;
+  uint32_t* d_red = nullptr;
+  uint32_t* d_touch = nullptr;
+  uint32_t* d_counts = nullptr;
+  uint8_t* d_labels = nullptr;
+  uint32_t* d_edge_acc = nullptr;
+  uint8_t* d_hist = nullptr;   // [RGG_MAX_REQUESTS][N] request snapshots, allocated on first use
+  double* d_qa = nullptr;      // [N][L] edge endpoints (edges built by rgg_build_edges only)
+  double* d_qb = nullptr;
+  uint8_t* d_resolved = nullptr;  // [N] labels of the last gray resolution
+  float* d_clear = nullptr;       // [N] its clearances
+  // OBB / spline geometry (Sec. 4.2): boxes per (edge, body), spline CSR,
+  // the uniform grid over the boxes, and the per-pass work list
+  float4* d_obb = nullptr;        // [N * L][4]
+  uint64_t* d_spl_off = nullptr;  // [N * L * K + 1]
+  float4* d_spl_v = nullptr;      // spline vertices
+  uint64_t n_obb = 0, n_spl = 0, n_spl_v = 0;
+  GridSpec grid{};
+  uint32_t n_cells = 0;
+  uint64_t n_items = 0;
+  uint32_t* d_cell_off = nullptr;   // [cells + 1]
+  float4* d_cell_items = nullptr;   // 2 per item: AABB low corner + index, high corner
+  uint2* d_pairs = nullptr;         // [pair_cap]
+  uint32_t pair_cap = 0;
+  uint32_t* d_qcnt = nullptr;       // [2] query counters
+  uint64_t device_bytes = 0;
+  bool regular = false;        // inner spheres equally spaced with one radius per sample
+
+  void release() {
+    cudaFree(d_soff);
+    cudaFree(d_inner);
+    cudaFree(d_outer);
+    cudaFree(d_tiles);
+    cudaFree(d_etab);
+    cudaFree(d_red);
+    cudaFree(d_touch);
+    cudaFree(d_counts);
+    cudaFree(d_labels);
+    cudaFree(d_edge_acc);
+    cudaFree(d_hist);
+    cudaFree(d_qa);
+    cudaFree(d_qb);
+    cudaFree(d_resolved);
+    cudaFree(d_clear);
+    cudaFree(d_obb);
+    cudaFree(d_spl_off);
+    cudaFree(d_spl_v);
+    cudaFree(d_cell_off);
+    cudaFree(d_cell_items);
+    cudaFree(d_pairs);
+    cudaFree(d_qcnt);
+    *this = EdgeState();
+  }
+};
+
+}  // namespace rgg_host
+
+struct rgg_roadmap {
+  using EdgeState = rgg_host::EdgeState;
+  int device = 0;
+  uint32_t L = 0, K = 0, M = 0, Wm = 0;
+  float margin = 2e-5f;
+  int num_sms = 0;
+  uint32_t ctas_per_sm = 1, consumer_warps = rgg::kDefaultConsumerWarps;
+  int variant = rgg::kDefaultVariant;
+  bool has_edges = false;
+  uint64_t gen = 0;            // bumped whenever tiles or edges are replaced
+  uint32_t geometry = RGG_GEOMETRY_SPHERES;
+  bool obb_filter = true;      // spatial grid filtering of the OBB queries
+  unsigned long long* d_obbwork = nullptr;  // [2] SAT tests, spline-segment tests
+  // the robot of edges built by rgg_build_edges (for the gray resolution)
+  bool has_robot = false;
+  double dh_a[RGG_MAX_LINKS], dh_alpha[RGG_MAX_LINKS], dh_d[RGG_MAX_LINKS], dh_radius[RGG_MAX_LINKS];
+  unsigned long long* d_work = nullptr;  // [4] resolution counters
+  EdgeState es;
+  float* d_table = nullptr;    // [M][16] box poses
+  float* d_stage = nullptr;    // [stage_rows][16] staged pose of each pending entry
+  uint32_t stage_rows = 0;
+  float* d_changed = nullptr;  // [32][24] derived records of the current pass
+  int* d_status = nullptr;          // [0] status word, [1] classify work counter
+  std::vector<uint8_t> present;
+  // Pending entries in application order.  Entry i stages its pose in row
+  // `row` of d_stage; `snap` >= 0 marks the last entry of a request whose
+  // snapshot is taken right after it.  The trailing run is the entries after
+  // the last snapshot; within it a box has at most one entry (run_idx[b]).
+  struct Entry {
+    uint32_t id, row;
+    int32_t snap;
+  };
+  std::vector<Entry> pending;
+  std::vector<int32_t> run_idx;
+  size_t run_start = 0;
+  // request handles: 0 free, 1 waiting for a classify, 2 classified
+  std::vector<uint8_t> req_state;
+  // kernel timing: events before classify, between classify and merge, after merge
+  bool timing = false;
+  std::vector<std::array<cudaEvent_t, 3>> events;
+  size_t events_used = 0;
+};
+
+namespace rgg_host {
+
+// rgg_api.cu
+uint32_t launch_ctas(const rgg_roadmap* r);
+bool build_tiles(uint32_t L, uint64_t N, const std::vector<uint64_t>& soff, uint64_t G, uint32_t S,
+                 std::vector<TileDesc>* tiles, std::vector<int4>* etab);
+int set_tiles(rgg_roadmap* r, EdgeState* es, cudaStream_t s);
+int alloc_edges(rgg_roadmap* r, EdgeState* es, uint64_t N, std::vector<uint64_t>&& soff,
+                cudaStream_t s);
+void clear_pending(rgg_roadmap* r);
+int install_edges(rgg_roadmap* r, EdgeState&& es, cudaStream_t s);
+bool valid_soff(const uint64_t* soff, uint64_t N, uint32_t L);
+bool finite_planes(const float* p, uint64_t count, bool radius_plane);
+bool regular_inner(const float* inner, uint64_t n_in, uint32_t K);
+bool valid_pose(const float* p);
+cudaEvent_t* next_events(rgg_roadmap* r);
+ClassifyJob make_job(rgg_roadmap* r, uint32_t C, uint64_t tile_base);
+MergeJob make_merge_job(rgg_roadmap* r, size_t lo, uint32_t C, bool ordered, uint64_t edge_base);
+bool shape_ok(uint32_t variant, uint32_t cw);
+int apply_shape(rgg_roadmap* r, int variant, uint32_t cw);
+int check_moves(rgg_roadmap_t r, uint32_t n, const uint32_t* ids, const float* pose,
+                int src_is_device, uint32_t* new_entries);
+int stage_moves(rgg_roadmap_t r, uint32_t n, const uint32_t* ids, const float* pose,
+                int src_is_device, cudaStream_t s);
+int classify_group(rgg_roadmap_t* rs, uint32_t n, cudaStream_t s);
+int check_status_locked(rgg_roadmap_t r, cudaStream_t s);
+
+// rgg_obb_host.cu
+int build_obb(rgg_roadmap* r, EdgeState* es, const rgg_robot_desc* robot, const double* d_qa,
+              const double* d_qb, cudaStream_t s);
+int classify_group_obb(rgg_roadmap_t* rs, uint32_t n, cudaStream_t s);
+
+}  // namespace rgg_host
