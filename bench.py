@@ -150,6 +150,7 @@ class ClockSampler:
     def __init__(self, gpu: int):
         self.gpu = gpu
         self.proc = None
+        self.skip = 0     # rows written before the timed region started
         self.path = os.path.join("/tmp", f"rgg_clocks_{os.getpid()}.csv")
 
     def __enter__(self):
@@ -161,6 +162,15 @@ class ClockSampler:
                 stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            return self
+        # start timing only once the sampler is writing (at most 3 s), so a
+        # short timed region still gets its samples
+        t0 = time.time()
+        while time.time() - t0 < 3.0 and self.proc.poll() is None:
+            if os.path.getsize(self.path) > 0:
+                break
+            time.sleep(0.02)
+        self.skip = 1 if os.path.getsize(self.path) > 0 else 0
         return self
 
     def __exit__(self, *exc):
@@ -177,10 +187,11 @@ class ClockSampler:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         sm, smax, reasons, mem, power = [], [], set(), [], []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
-            f = [x.strip() for x in line.split(",")]
-            if len(f) < 9:
-                continue
+        rows = [[x.strip() for x in line.split(",")] for line in open(self.path)]
+        rows = [f for f in rows if len(f) >= 9]
+        if len(rows) > self.skip:
+            rows = rows[self.skip:]
+        for f in rows:
             try:
                 sm.append(float(f[1]))
                 smax.append(float(f[2]))
@@ -203,12 +214,21 @@ class ClockSampler:
         return out
 
 
-def algorithmic_bytes(info: dict, moved: int) -> int:
-    """Bytes one classify launch must move: every sphere record once (16 B
-    per inner and outer sphere) and each edge's pass result (hit and touch
-    words, 8 B).  Tile descriptors, edge tables and the moved boxes' records
-    are implementation overhead and not counted."""
-    return info["record_bytes"] + 8 * info["num_edges"]
+ROUND_SLOT_BYTES = 16 + 4 + 4 + 4   # per (tile, round) slot: sphere, candidates written + read, range
+
+
+def algorithmic_bytes(info: dict, record_bytes_per_launch=None) -> int:
+    """Bytes one classify launch must move: the sphere records it copies
+    (unfiltered: every record once, 16 B per inner and outer sphere;
+    with the spatial filter: the rounds some moved box may reach, as counted
+    on the device), each edge's pass result (hit and touch words, 8 B) and,
+    with the filter, its per-round data (bounding sphere read, candidate
+    mask written and read, record range read).  Tile descriptors, edge
+    tables and the moved boxes' records are overhead and not counted."""
+    if record_bytes_per_launch is None or not info.get("round_filter"):
+        return info["record_bytes"] + 8 * info["num_edges"]
+    return (int(record_bytes_per_launch) + 8 * info["num_edges"]
+            + ROUND_SLOT_BYTES * 32 * info["num_tiles"])
 
 
 # --------------------------------------------------------------------------
@@ -346,6 +366,7 @@ def run_gpu(args):
     # ---- device-timed region: inputs resident in HBM, records 27 GB >> L2
     r.set_kernel_timing(True)
     r.kernel_time()
+    r.streamed_bytes()
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
@@ -359,6 +380,7 @@ def run_gpu(args):
     ms = ev0.elapsed_time(ev1)
     k_ms, m_ms, k_launches = r.kernel_time()
     r.set_kernel_timing(False)
+    streamed = r.streamed_bytes()
     ms = max_over_ranks(dist, ms, f"cuda:{local}")
     clk = clocks.summary()
 
@@ -380,6 +402,29 @@ def run_gpu(args):
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     e2e_s = max_over_ranks(dist, e2e_s, f"cuda:{local}")
+    # ---- the same steps with the spatial filter on (after the end-to-end
+    # loop; the headline above streams every record)
+    filtered = None
+    r.set_round_filter(True)
+    if r.info()["round_filter"]:
+        n_cmp = min(args.steps, 100)
+        for i in range(3):
+            device_step(2 * args.steps + args.warmup + i)
+        torch.cuda.synchronize()
+        r.set_kernel_timing(True)
+        r.kernel_time()
+        r.streamed_bytes()
+        for i in range(n_cmp):
+            device_step(2 * args.steps + args.warmup + 3 + i)
+        torch.cuda.synchronize()
+        kf_ms, _, kf_n = r.kernel_time()
+        r.set_kernel_timing(False)
+        sf = r.streamed_bytes()
+        filtered = {"kernel_ms": kf_ms / max(1, kf_n),
+                    "record_bytes_per_launch": sf / max(1, kf_n), "launches": kf_n,
+                    "info": r.info()}
+    r.set_round_filter(False)
+
     r.check_status(stream)
     resolve = measure_resolve(r, sc, args.resolve, stream, rank == 0 and world == 1) \
         if args.resolve else None
@@ -389,10 +434,23 @@ def run_gpu(args):
     value = replica_throughput(world, n_edges * args.steps, ms / 1000.0)
     e2e_value = replica_throughput(world, n_edges * args.steps, e2e_s)
     peak, peak_kind = hbm_peak()
-    b_alg = algorithmic_bytes(info, moved)
     k_avg_ms = k_ms / max(1, k_launches)
+    rec_per_launch = streamed / max(1, k_launches)
+    b_alg = algorithmic_bytes(info, rec_per_launch)
     achieved = b_alg / (k_avg_ms / 1000.0) / 1e9
     traffic = profiled_traffic(args.workload)
+    filt = None
+    if filtered is not None:
+        b_f = algorithmic_bytes(filtered["info"], filtered["record_bytes_per_launch"])
+        filt = {"kernel_ms": filtered["kernel_ms"],
+                "record_bytes_per_launch": filtered["record_bytes_per_launch"],
+                "records_copied_frac": filtered["record_bytes_per_launch"] / info["record_bytes"],
+                "bytes_per_launch": b_f,
+                "frac": b_f / (filtered["kernel_ms"] / 1000.0) / 1e9 / peak,
+                "edges_per_s": n_edges / (filtered["kernel_ms"] / 1000.0),
+                "speedup_vs_streaming_all": k_avg_ms / filtered["kernel_ms"],
+                "note": "opt-in spatial filter (rgg_set_round_filter): kernel interval = "
+                        "round-filter kernel + classify kernel; bytes recounted as copied"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -420,9 +478,11 @@ def run_gpu(args):
                      "kernel": "classify_kernel", "bytes_per_launch": b_alg,
                      "kernel_ms": k_avg_ms,
                      "merge_kernel_ms": m_ms / max(1, k_launches)},
+        "round_filter": filt,
         "e2e": {"value": e2e_value, "unit": UNIT,
                 "h2d_bytes_per_step": moved * (4 + 60),
                 "d2h_bytes_per_step": n_edges + 4},
+        # per step: box update, box prep, classify, merge
         "gpu_launches": 4 * args.steps,
         "clocks": clk,
         "cpu_baseline": cpu,
@@ -645,6 +705,9 @@ def run_batched(args):
     def run(mode, steps, warm):
         step_ms, lat = [], []
         for i in range(warm + steps):
+            if i == warm:
+                for r in rms:
+                    r.streamed_bytes()   # count the timed steps only
             ev0 = torch.cuda.Event(enable_timing=True)
             ends = []
             ev0.record(stream)
@@ -669,7 +732,8 @@ def run_batched(args):
             if i >= warm:
                 step_ms.append(ev0.elapsed_time(ends[-1]))
                 lat.extend(ev0.elapsed_time(e) for e in ends)
-        return float(np.mean(step_ms)), np.array(lat), np.array(step_ms)
+        copied = sum(r.streamed_bytes() for r in rms)
+        return float(np.mean(step_ms)), np.array(lat), np.array(step_ms), copied / max(1, steps)
 
     out, final = {}, {}
     with ClockSampler(0) as clocks:
@@ -679,12 +743,20 @@ def run_batched(args):
                 graphs = [rgg.StepGraph(rms, [(sc.updates[k].ids, d[k])
                                               for sc, d in zip(scenes, dev)])
                           for k in range(n_up)]
-            ms, lat, st = run(mode, args.steps, args.warmup)
+            ms, lat, st, copied = run(mode, args.steps, args.warmup)
             final[mode] = [r.fetch_labels(stream=stream) for r in rms]
+            # bytes one step must move: the records the launches copied (the
+            # spatial filter skips the rest), the per-edge results and the
+            # filter's per-round data
+            b_step = copied + sum(8 * i["num_edges"] + (ROUND_SLOT_BYTES * 32 * i["num_tiles"]
+                                                        if i["round_filter"] else 0)
+                                  for i in infos)
             out[mode] = {"ms_per_step": ms, "edges_per_s": n_edges / (ms / 1e3),
                          "step_ms_min_med_max": [float(np.min(st)), float(np.median(st)),
                                                  float(np.max(st))],
-                         "record_gbs": rec / (ms / 1e3) / 1e9,
+                         "record_bytes_copied_per_step": copied,
+                         "records_copied_frac": copied / rec,
+                         "achieved_gbs": b_step / (ms / 1e3) / 1e9,
                          "latency_ms_p50": float(np.percentile(lat, 50)),
                          "latency_ms_p99": float(np.percentile(lat, 99))}
     # every mode applies the same update sequence: the final labels agree
@@ -705,8 +777,8 @@ def run_batched(args):
         "config": {"workload": f"batched {len(rms)} roadmaps", "edges": n_edges,
                    "record_gb": rec / 1e9, "dof": sorted({i["num_links"] for i in infos}),
                    "moved_per_update": "1-16 per roadmap", "l2": "records > L2; no flush needed"},
-        "roofline": {"bound": "hbm", "achieved": b["record_gbs"], "peak": peak, "unit": "GB/s",
-                     "frac": b["record_gbs"] / peak, "traffic": None,
+        "roofline": {"bound": "hbm", "achieved": b["achieved_gbs"], "peak": peak, "unit": "GB/s",
+                     "frac": b["achieved_gbs"] / peak, "traffic": None,
                      "peak_source": f"{peak_kind} HBM copy bandwidth",
                      "note": "whole step (updates + one launch per pass over all roadmaps, "
                              "replayed as one CUDA graph)"},

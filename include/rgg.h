@@ -146,6 +146,7 @@ typedef struct {
   uint32_t grid_cells;      /* OBB geometry: cells of the uniform grid            */
   uint64_t grid_items;      /* OBB geometry: (box, cell) incidences               */
   uint64_t spline_vertices; /* OBB geometry: kept spline vertices                 */
+  uint32_t round_filter;    /* 1: the spatial filter is on and active (see below)  */
 } rgg_info;
 
 /* ------------------------------------------------------------------------ */
@@ -414,6 +415,29 @@ int rgg_resolve_gray(rgg_roadmap_t r, uint32_t factor, uint8_t* labels_out, floa
  * mismatch. */
 int rgg_save(rgg_roadmap_t r, const char* path, void* stream);
 int rgg_load(rgg_roadmap_t r, const char* path, void* stream);
+
+/* Sphere geometry only: the spatial filter (Sec. 4.3, "spatially filtered
+ * many-to-many checking", here over the streamed records).  Off by default.
+ * While it is on, every round of 31 configurations of a tile
+ * (rgg_info.tile_samples configurations per tile) has a bounding sphere of
+ * its outer spheres (24 B per round slot, 32 slots per tile, computed when it
+ * is switched on and whenever the tiles change).  Before each pass a small
+ * kernel tests those spheres against the pass's moved boxes (exact box
+ * distance, radius plus margin, FP32 slack 1e-5 m); the classify kernel skips
+ * a tile no box may reach, copies only the runs of rounds some box may
+ * reach, and tests only the boxes that may reach each round.  Labels and box
+ * sets are the same with and without it (a round no box reaches holds no
+ * touch).  It applies with the default launch shape only (rgg_info.
+ * round_filter reports whether it is active); on workloads where the moved
+ * boxes reach most tiles it is slower than streaming every record.
+ * rgg_set_round_filter synchronises the device.  RGG_ERR_STATE on an
+ * OBB-geometry roadmap.
+ * rgg_streamed_bytes returns the record bytes (inner and outer planes, with
+ * the 16-byte rounding of each copy) the classify launches of this roadmap
+ * copied since the last call, and resets the count; it waits for the device.
+ * The autotuner's launches are not counted. */
+int rgg_set_round_filter(rgg_roadmap_t r, int enable);
+int rgg_streamed_bytes(rgg_roadmap_t r, uint64_t* record_bytes);
 
 /* OBB geometry only.  rgg_set_obb_filter(r, 0) makes every pass test the
  * moved boxes against the boxes of every non-empty grid cell instead of the

@@ -80,6 +80,7 @@ int set_tiles(rgg_roadmap* r, EdgeState* es, cudaStream_t s) {
     cudaFree(d_etab);
     return cuda_status(e);
   }
+  release_rounds(es);  // they describe the old tiles
   es->device_bytes -= es->T * sizeof(TileDesc) + es->n_etab * sizeof(int4);
   cudaFree(es->d_tiles);
   cudaFree(es->d_etab);
@@ -89,6 +90,56 @@ int set_tiles(rgg_roadmap* r, EdgeState* es, cudaStream_t s) {
   es->n_etab = h_etab.size();
   es->tiling = tiling;
   es->device_bytes += es->T * sizeof(TileDesc) + es->n_etab * sizeof(int4);
+  return RGG_OK;
+}
+
+void release_rounds(EdgeState* es) {
+  if (es->d_rsph) es->device_bytes -= es->T * kRoundSlots * (sizeof(float4) + 2 * sizeof(uint32_t));
+  cudaFree(es->d_rsph);
+  cudaFree(es->d_rout);
+  cudaFree(es->d_rcand);
+  es->d_rsph = nullptr;
+  es->d_rout = nullptr;
+  es->d_rcand = nullptr;
+}
+
+// The spatial filter runs with the default pipeline variant only (the one
+// its kernel instance is compiled for).
+bool filter_active(const rgg_roadmap* r) {
+  return r->round_filter && r->es.d_rcand && r->variant == kDefaultVariant;
+}
+
+// The spatial filter's per-round bounding spheres and outer ranges of the
+// current tiles, from the resident outer records (stream-ordered after them);
+// nothing while the filter is off.
+int compute_rounds(rgg_roadmap* r, EdgeState* es, cudaStream_t s) {
+  release_rounds(es);
+  if (!r->round_filter || r->geometry != RGG_GEOMETRY_SPHERES || es->T == 0) return RGG_OK;
+  const uint64_t n = es->T * kRoundSlots;
+  cudaError_t e = dalloc(&es->d_rsph, n);
+  if (e == cudaSuccess) e = dalloc(&es->d_rout, n);
+  if (e == cudaSuccess) e = dalloc(&es->d_rcand, n);
+  if (e != cudaSuccess) {
+    cudaFree(es->d_rsph);
+    cudaFree(es->d_rout);
+    cudaFree(es->d_rcand);
+    es->d_rsph = nullptr;
+    es->d_rout = nullptr;
+    es->d_rcand = nullptr;
+    return cuda_status(e);
+  }
+  es->device_bytes += n * (sizeof(float4) + 2 * sizeof(uint32_t));
+  RoundBoundsParams p;
+  p.outer = es->d_outer;
+  p.out_stride = es->out_stride;
+  p.tiles = es->d_tiles;
+  p.etab = es->d_etab;
+  p.T = es->T;
+  p.G = es->G;
+  p.S = es->tiling.S;
+  p.rsph = es->d_rsph;
+  p.rout = es->d_rout;
+  RGG_CK(launch_round_bounds(p, r->num_sms, s));
   return RGG_OK;
 }
 
@@ -163,6 +214,11 @@ void clear_pending(rgg_roadmap* r) {
 // closed, and every present box pending (its staged pose copied from the
 // box table) so that the next classify tests it against the new edges.
 int install_edges(rgg_roadmap* r, EdgeState&& es, cudaStream_t s) {
+  const int rc = compute_rounds(r, &es, s);
+  if (rc != RGG_OK) {
+    es.release();
+    return rc;
+  }
   r->es.release();
   r->es = std::move(es);
   r->has_edges = true;
@@ -291,6 +347,12 @@ ClassifyJob make_job(rgg_roadmap* r, uint32_t C, uint64_t tile_base) {
   j.regular = (es.regular && r->margin >= kRegularMinMargin) ? 1u : 0u;
   j.inv_k = 1.0f / (float)r->K;
   j.inv_km1 = r->K > 1 ? 1.0f / (float)(r->K - 1) : 0.0f;
+  if (filter_active(r)) {
+    j.rsph = es.d_rsph;
+    j.rout = es.d_rout;
+    j.rcand = es.d_rcand;
+  }
+  j.streamed = r->d_streamed;
   return j;
 }
 
@@ -344,13 +406,17 @@ int apply_shape(rgg_roadmap* r, int variant, uint32_t cw) {
   r->consumer_warps = cw;
   if (variant != old_v && r->has_edges && r->es.N && r->geometry == RGG_GEOMETRY_SPHERES) {
     cudaDeviceSynchronize();  // no launch may still read the old tiles
-    const int rc = set_tiles(r, &r->es, nullptr);
-    if (rc != RGG_OK) {
+    int rc = set_tiles(r, &r->es, nullptr);
+    if (rc != RGG_OK) {  // the old tiles stay
       r->variant = old_v;
       r->consumer_warps = old_cw;
       return rc;
     }
     ++r->gen;  // captured step graphs hold the old tiles
+    // the new tiles' round data; without them the roadmap runs unfiltered
+    rc = compute_rounds(r, &r->es, nullptr);
+    if (cudaDeviceSynchronize() != cudaSuccess && rc == RGG_OK) rc = RGG_ERR_CUDA;
+    return rc;
   }
   return RGG_OK;
 }
@@ -573,7 +639,9 @@ int rgg_roadmap_create(const rgg_roadmap_desc* desc, rgg_roadmap_t* out) {
   if (e == cudaSuccess) e = dalloc(&r->d_status, 4);
   if (e == cudaSuccess) e = dalloc(&r->d_work, 4);
   if (e == cudaSuccess) e = dalloc(&r->d_obbwork, 2);
+  if (e == cudaSuccess) e = dalloc(&r->d_streamed, 1);
   if (e == cudaSuccess) e = cudaMemset(r->d_obbwork, 0, 2 * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemset(r->d_streamed, 0, sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMemset(r->d_table, 0, (size_t)r->M * 16 * sizeof(float));
   if (e == cudaSuccess) e = cudaMemset(r->d_status, 0, 4 * sizeof(int));
   if (e != cudaSuccess) {
@@ -583,6 +651,7 @@ int rgg_roadmap_create(const rgg_roadmap_desc* desc, rgg_roadmap_t* out) {
     cudaFree(r->d_status);
     cudaFree(r->d_work);
     cudaFree(r->d_obbwork);
+    cudaFree(r->d_streamed);
     delete r;
     return cuda_status(e);
   }
@@ -601,6 +670,7 @@ int rgg_roadmap_destroy(rgg_roadmap_t r) {
   cudaFree(r->d_status);
   cudaFree(r->d_work);
   cudaFree(r->d_obbwork);
+  cudaFree(r->d_streamed);
   for (auto& ev : r->events)
     for (cudaEvent_t x : ev) cudaEventDestroy(x);
   delete r;
@@ -962,6 +1032,7 @@ int rgg_roadmap_info(rgg_roadmap_t r, rgg_info* out) {
   out->grid_cells = es.n_cells;
   out->grid_items = es.n_items;
   out->spline_vertices = es.n_spl_v;
+  out->round_filter = filter_active(r) ? 1u : 0u;
   if (r->geometry == RGG_GEOMETRY_OBB) {
     // boxes, spline vertices and spline offsets
     out->num_inner = es.n_spl_v;
@@ -969,6 +1040,38 @@ int rgg_roadmap_info(rgg_roadmap_t r, rgg_info* out) {
     out->record_bytes = 64 * es.n_obb + 16 * es.n_spl_v + 8 * (es.n_spl + 1);
   }
   out->grid_ctas = (uint32_t)std::min<uint64_t>(es.T, launch_ctas(r));
+  return RGG_OK;
+}
+
+int rgg_set_round_filter(rgg_roadmap_t r, int enable) {
+  if (!r) return RGG_ERR_INVALID;
+  if (r->geometry != RGG_GEOMETRY_SPHERES) return RGG_ERR_STATE;
+  const bool on = enable != 0;
+  if (on == r->round_filter) return RGG_OK;
+  DeviceGuard g(r->device);
+  if (!g.ok) return RGG_ERR_CUDA;
+  RGG_CK(cudaDeviceSynchronize());  // no launch may still read the round data
+  ++r->gen;                         // captured step graphs hold the old jobs
+  r->round_filter = on;
+  // the round data exist while the filter is on (computed from the records)
+  int rc = on ? compute_rounds(r, &r->es, nullptr) : (release_rounds(&r->es), RGG_OK);
+  if (cudaDeviceSynchronize() != cudaSuccess && rc == RGG_OK) rc = RGG_ERR_CUDA;
+  if (rc != RGG_OK) {
+    release_rounds(&r->es);
+    r->round_filter = false;
+  }
+  return rc;
+}
+
+int rgg_streamed_bytes(rgg_roadmap_t r, uint64_t* record_bytes) {
+  if (!r || !record_bytes) return RGG_ERR_INVALID;
+  DeviceGuard g(r->device);
+  if (!g.ok) return RGG_ERR_CUDA;
+  unsigned long long v = 0;
+  RGG_CK(cudaDeviceSynchronize());
+  RGG_CK(cudaMemcpy(&v, r->d_streamed, sizeof(v), cudaMemcpyDeviceToHost));
+  RGG_CK(cudaMemset(r->d_streamed, 0, sizeof(v)));
+  *record_bytes = v;
   return RGG_OK;
 }
 

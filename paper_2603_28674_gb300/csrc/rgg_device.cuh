@@ -16,6 +16,15 @@
 // every interval adjacent to one of them (one halo interval before the first
 // sample when the tile starts inside a link's run), and a table with one
 // entry per edge that has samples in the tile.
+//
+// Rounds: round r of a tile is its samples [31r, 31r+31) and the intervals
+// that follow its local samples 31r-1 .. 31r+30 (those a consumer warp tests
+// in one step).  Per round, computed when the tiles are set: a bounding
+// sphere of those intervals' outer spheres and their range of outer records.
+// Spatial filter (Sec. 4.3, "spatially filtered many-to-many checking"):
+// before each pass a small kernel tests every round's bounding sphere
+// against the pass's moved boxes; the producer copies only the rounds some
+// box can reach, and skips a tile none can.
 #pragma once
 
 #include <cstdint>
@@ -27,6 +36,7 @@ constexpr int kMaxJobs = 128;          // roadmaps per batched launch
 constexpr int kBoxesPerPass = 32;      // moved boxes per streaming pass (one mask word)
 constexpr int kBoxRecFloats = 24;      // derived box record, 6 x float4 = 96 B
 constexpr int kStageHdrBytes = 32;
+constexpr int kRoundSlots = 32;        // round entries per tile (rounds per tile <= 32)
 constexpr int kAccMax = 96;            // per-stage accumulator entries (edges per tile)
 constexpr int kStageAccOff = kStageHdrBytes;                 // hit[kAccMax], touch[kAccMax]
 constexpr int kStageEtabOff = kStageAccOff + 8 * kAccMax;    // edge table
@@ -71,6 +81,11 @@ struct ClassifyJob {
   // interpolate their centres from the first and the last
   uint32_t regular;
   float inv_k, inv_km1;             // 1/K and 1/(K-1) (0 when K = 1)
+  // spatial filter (all three null: every round of every tile is copied)
+  const float4* rsph;               // [T][kRoundSlots] bounding sphere (radius < 0: empty)
+  const uint32_t* rout;             // [T][kRoundSlots] outer records lo | hi << 16, tile-local
+  uint32_t* rcand;                  // [T][kRoundSlots] moved boxes that may reach the round
+  unsigned long long* streamed;     // record bytes copied (may be null)
 };
 
 template <int MAXJ>

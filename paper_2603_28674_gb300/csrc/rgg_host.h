@@ -129,6 +129,11 @@ struct EdgeState {
   uint2* d_pairs = nullptr;         // [pair_cap]
   uint32_t pair_cap = 0;
   uint32_t* d_qcnt = nullptr;       // [2] query counters
+  // spatial filter of the sphere geometry: per (tile, round) bounding sphere,
+  // outer-record range and this pass's candidate boxes (see rgg_device.cuh)
+  float4* d_rsph = nullptr;
+  uint32_t* d_rout = nullptr;
+  uint32_t* d_rcand = nullptr;
   uint64_t device_bytes = 0;
   bool regular = false;        // inner spheres equally spaced with one radius per sample
 
@@ -155,6 +160,9 @@ struct EdgeState {
     cudaFree(d_cell_items);
     cudaFree(d_pairs);
     cudaFree(d_qcnt);
+    cudaFree(d_rsph);
+    cudaFree(d_rout);
+    cudaFree(d_rcand);
     *this = EdgeState();
   }
 };
@@ -173,6 +181,8 @@ struct rgg_roadmap {
   uint64_t gen = 0;            // bumped whenever tiles or edges are replaced
   uint32_t geometry = RGG_GEOMETRY_SPHERES;
   bool obb_filter = true;      // spatial grid filtering of the OBB queries
+  bool round_filter = false;   // spatial filtering of the sphere records (opt-in)
+  unsigned long long* d_streamed = nullptr;  // [1] record bytes the classify launches copied
   unsigned long long* d_obbwork = nullptr;  // [2] SAT tests, spline-segment tests
   // the robot of edges built by rgg_build_edges (for the gray resolution)
   bool has_robot = false;
@@ -215,6 +225,9 @@ int alloc_edges(rgg_roadmap* r, EdgeState* es, uint64_t N, std::vector<uint64_t>
                 cudaStream_t s);
 void clear_pending(rgg_roadmap* r);
 int install_edges(rgg_roadmap* r, EdgeState&& es, cudaStream_t s);
+void release_rounds(EdgeState* es);
+int compute_rounds(rgg_roadmap* r, EdgeState* es, cudaStream_t s);
+bool filter_active(const rgg_roadmap* r);
 bool valid_soff(const uint64_t* soff, uint64_t N, uint32_t L);
 bool finite_planes(const float* p, uint64_t count, bool radius_plane);
 bool regular_inner(const float* inner, uint64_t n_in, uint32_t K);

@@ -6,6 +6,10 @@
 //   box_update_kernel      a1: write moved boxes' poses in place (Sec. 4.3,
 //                          "Online updates")
 //   box_prep_kernel        a1: derived per-pass box records
+//   round_bounds_kernel    per-round bounding spheres of the outer records
+//                          (when tiles are set)
+//   round_filter_kernel    spatial filter of a pass: rounds the moved boxes
+//                          may reach (Sec. 4.3, spatially filtered checking)
 //   classify_kernel        a2..a5: persistent streaming classification
 //                          (Sec. 4.1 labelling rule)
 //   merge_kernel           a6: per-edge box sets and labels (Algorithm 1)
@@ -279,6 +283,32 @@ __device__ __forceinline__ int search_le(const int* tab, int field, int n, int v
   return lo;
 }
 
+// Where local sample q of a tile sits: its edge-table entry j, the edge's
+// configuration count n, its position k in its link's run, and the local
+// index o of the interval that follows it (branch-free).  `valid`: q is one
+// of the tile's samples [0, q_end); `has_next`: an interval follows it.
+struct SampleAt {
+  int j, n, k, o;
+  bool valid, has_next;
+};
+__device__ __forceinline__ SampleAt locate_sample(const int* etab, int n_edges, int q, int q_end) {
+  SampleAt a;
+  a.j = search_le(etab, 0, n_edges, max(q, 0));
+  const int4 ej = *reinterpret_cast<const int4*>(etab + 4 * a.j);
+  a.n = ej.y;
+  const int rr = q - ej.x;
+  int li = __float2int_rz(((float)rr + 0.5f) * __int_as_float(ej.w));
+  int k = rr - li * a.n;
+  const int adj = k < 0 ? -1 : (k >= a.n ? 1 : 0);  // exact rr / n
+  li += adj;
+  k -= adj * a.n;
+  a.k = k;
+  a.valid = q < q_end && rr >= 0;
+  a.has_next = a.valid && k < a.n - 1;
+  a.o = a.has_next ? ej.z + li * (a.n - 1) + k : 0;
+  return a;
+}
+
 template <int MAXJ>
 __device__ __forceinline__ int find_job(const ClassifyParams<MAXJ>& P, uint64_t t) {
   int lo = 0, hi = (int)P.njobs - 1;
@@ -289,7 +319,134 @@ __device__ __forceinline__ int find_job(const ClassifyParams<MAXJ>& P, uint64_t 
   return lo;
 }
 
+// ---------------------------------------------------------------------------
+// Spatial filter (Sec. 4.3): per-round bounding spheres, and the per-pass test
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double warp_max_d(double v) {
+#pragma unroll
+  for (int m = 16; m; m >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, m));
+  return v;
+}
+
+// Radius of the sphere about (cx, cy, cz) that holds every active lane's
+// sphere, in FP64 from the FP32 records, rounded up to FP32.
+__device__ __forceinline__ float cover_radius(float x, float y, float z, float r, bool on,
+                                              float cx, float cy, float cz) {
+  const double dx = (double)x - cx, dy = (double)y - cy, dz = (double)z - cz;
+  const double v = on ? sqrt(dx * dx + dy * dy + dz * dz) + (double)r : 0.0;
+  return __double2float_ru(warp_max_d(v));
+}
+
+// One warp per tile.  Round r's outer spheres are those of the intervals the
+// classify kernel's consumer tests in that round (the same lane mapping).
+// The centre starts at the midpoint of the first and the last sphere centre
+// and takes 24 steps of the Badoiu-Clarkson iteration (a step of 1/(i+1)
+// towards the sphere that reaches farthest), which approaches the centre of
+// the smallest enclosing sphere; the smaller of the two radii is kept.
+__global__ void __launch_bounds__(256) round_bounds_kernel(const __grid_constant__ RoundBoundsParams p) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t t = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < p.T; t += nw) {
+    const TileDesc d = p.tiles[t];
+    const uint64_t o0 = d.packed & ((1ull << 40) - 1);
+    const int n_edges = (int)(d.packed >> 56);
+    const int* etab = reinterpret_cast<const int*>(p.etab + d.etab);
+    const uint64_t g0 = t * p.S;
+    const int n_samp = (int)(min(g0 + p.S, p.G) - g0);
+    for (int rnd = 0; rnd < kRoundSlots; ++rnd) {
+      const int base = 31 * rnd;
+      float4 sph = make_float4(0.0f, 0.0f, 0.0f, -1.0f);
+      uint32_t range = 0;
+      if (base < n_samp) {
+        const SampleAt a = locate_sample(etab, n_edges, base - 1 + lane, min(base + 31, n_samp));
+        float x = 0.0f, y = 0.0f, z = 0.0f, r = 0.0f;
+        if (a.has_next) {
+          const float* o = p.outer + o0 + a.o;
+          x = o[0];
+          y = o[p.out_stride];
+          z = o[2 * p.out_stride];
+          r = o[3 * p.out_stride];
+        }
+        const uint32_t act = __ballot_sync(0xffffffffu, a.has_next);
+        if (act) {
+          const int lo_l = __ffs(act) - 1, hi_l = 31 - __clz(act);
+          const float mx = 0.5f * (__shfl_sync(0xffffffffu, x, lo_l) + __shfl_sync(0xffffffffu, x, hi_l));
+          const float my = 0.5f * (__shfl_sync(0xffffffffu, y, lo_l) + __shfl_sync(0xffffffffu, y, hi_l));
+          const float mz = 0.5f * (__shfl_sync(0xffffffffu, z, lo_l) + __shfl_sync(0xffffffffu, z, hi_l));
+          float cx = mx, cy = my, cz = mz;
+          for (int it = 1; it <= 24; ++it) {
+            const float dx = x - cx, dy = y - cy, dz = z - cz;
+            const float f = a.has_next ? sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) + r : 0.0f;
+            const float fm = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(f)));
+            const int w0 = __ffs(__ballot_sync(0xffffffffu, a.has_next && f == fm)) - 1;
+            const int w = w0 < 0 ? lo_l : w0;
+            const float step = 1.0f / (float)(it + 1);
+            cx = fmaf(__shfl_sync(0xffffffffu, x, w) - cx, step, cx);
+            cy = fmaf(__shfl_sync(0xffffffffu, y, w) - cy, step, cy);
+            cz = fmaf(__shfl_sync(0xffffffffu, z, w) - cz, step, cz);
+          }
+          const float r_mid = cover_radius(x, y, z, r, a.has_next, mx, my, mz);
+          const float r_bc = cover_radius(x, y, z, r, a.has_next, cx, cy, cz);
+          sph = r_bc < r_mid ? make_float4(cx, cy, cz, r_bc) : make_float4(mx, my, mz, r_mid);
+          const uint32_t lo = (uint32_t)__shfl_sync(0xffffffffu, a.o, lo_l);
+          const uint32_t hi = (uint32_t)__shfl_sync(0xffffffffu, a.o, hi_l) + 1u;
+          range = lo | (hi << 16);
+        }
+      }
+      if (lane == 0) {
+        p.rsph[t * kRoundSlots + rnd] = sph;
+        p.rout[t * kRoundSlots + rnd] = range;
+      }
+    }
+  }
+}
+
+// Before a pass: per (tile, round), the moved boxes whose exact distance
+// from the round's bounding sphere centre is within its radius plus the
+// margin.  Any outer sphere of the round lies inside the bounding sphere, so
+// a box that touches one of them (distance <= r + margin) passes this test;
+// the slack covers FP32 rounding in both tests.  One warp per tile, one lane
+// per round.
+template <int MAXJ>
+__global__ void __launch_bounds__(256) round_filter_kernel(const __grid_constant__ ClassifyParams<MAXJ> P) {
+  const uint64_t t = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (t >= P.total_tiles) return;
+  const ClassifyJob& J = P.job[MAXJ == 1 ? 0 : find_job(P, t)];
+  if (J.rcand == nullptr) return;
+  const uint64_t slot = (t - J.tile_base) * kRoundSlots + lane;
+  uint32_t m = 0;
+  if (lane < kRoundSlots - 1) {
+    const float4 sph = J.rsph[slot];
+    if (sph.w >= 0.0f) {
+      const float thr = (sph.w + J.margin) * (1.0f + 1e-6f) + 1e-5f;
+      const float thr2 = thr * thr;
+      const float4* bx = reinterpret_cast<const float4*>(J.boxes);
+      for (uint32_t b = 0; b < J.C; ++b)
+        if (box_dist2(sph.x, sph.y, sph.z, bx + 6 * b) <= thr2) m |= 1u << b;
+    }
+  }
+  // the last slot (never a round: tiles have at most 31 rounds) holds the
+  // tile's rounds that some box may reach
+  const uint32_t need = __ballot_sync(0xffffffffu, m != 0u);
+  J.rcand[slot] = lane == kRoundSlots - 1 ? need : m;
+}
+
 constexpr uint64_t kWaitLimit = 4000000000ull;  // 4 s of wall time per wait
+
+__device__ __forceinline__ void write_stage_hdr(unsigned char* sb, int job, uint64_t g0, uint64_t g1,
+                                                uint32_t n_out, uint32_t n_edges, int in_shift,
+                                                int out_shift, uint32_t e_first) {
+  StageHdr* h = reinterpret_cast<StageHdr*>(sb);
+  h->job = job;
+  h->n_samp = (int)(g1 - g0);
+  h->n_out = (int)n_out;
+  h->n_edges = (int)n_edges;
+  h->in_shift = in_shift;
+  h->out_shift = out_shift;
+  h->e_first = e_first;
+  h->end = 0;
+}
 
 constexpr int kPairQueue = 64;   // (sample, box) pairs a warp compacts per round
 constexpr uint32_t kChunkTiles = 16;  // tiles a producer takes per grab (<= 32)
@@ -304,8 +461,12 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
 // whose following interval the round needs (for r = 0 that is the tile's
 // halo interval).  The warp that finishes a tile's last round flushes the
 // tile's per-edge bits and releases the stage.
-template <int MAXJ, int NSTAGE, int STAGE_BYTES, int ROUNDS, int RPI>
+// FILTER: the instance that serves spatially filtered jobs (tiles skipped,
+// rounds copied in runs, per-round candidate masks); without it the jobs'
+// filter fields are ignored and every tile is copied whole.
+template <int MAXJ, int NSTAGE, int STAGE_BYTES, int ROUNDS, int RPI, bool FILTER>
 __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const __grid_constant__ ClassifyParams<MAXJ> P) {
+  static_assert(ROUNDS < kRoundSlots, "rounds per tile");
   // Shared-memory carve-up, by integer offsets from the __shared__ base so that
   // every derived pointer stays a shared-memory pointer (plain LDS/STS).
   // Box records: one area staged once for a single-roadmap launch; one per
@@ -318,7 +479,10 @@ __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const 
   constexpr size_t kOffCnt = kOffItem + 8;
   constexpr size_t kOffDesc = (kOffCnt + 4 * ((NSTAGE + 3) & ~3) + 15) & ~(size_t)15;
   constexpr size_t kOffDjob = kOffDesc + 32 * sizeof(TileDesc);
-  constexpr size_t kOffBoxes = (kOffDjob + 32 * sizeof(int) + 127) & ~(size_t)127;
+  constexpr size_t kOffNeed = kOffDjob + 32 * sizeof(int);
+  constexpr size_t kOffCand = kOffNeed + (FILTER ? 32 * sizeof(uint32_t) : 0);  // 16-byte aligned
+  constexpr size_t kOffBoxes =
+      (kOffCand + (FILTER ? (size_t)NSTAGE * kRoundSlots * 4 : 0) + 127) & ~(size_t)127;
   constexpr size_t kOffQueues = kOffBoxes + (size_t)kBoxAreas * kBoxesPerPass * kBoxRecFloats * 4;
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char* stages = smem;
@@ -329,6 +493,10 @@ __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const 
   uint32_t* s_cnt = reinterpret_cast<uint32_t*>(smem + kOffCnt);       // items done per stage
   TileDesc* s_desc = reinterpret_cast<TileDesc*>(smem + kOffDesc);     // producer's batch
   int* s_djob = reinterpret_cast<int*>(smem + kOffDjob);
+  uint32_t* s_need = reinterpret_cast<uint32_t*>(smem + kOffNeed);  // producer's batch
+  // per stage (spatial filter): the moved boxes that may reach each round of
+  // its tile, 0 for a round that was not copied
+  uint32_t* s_cand = reinterpret_cast<uint32_t*>(smem + kOffCand);
   float4* s_boxes = reinterpret_cast<float4*>(smem + kOffBoxes);
   uint32_t* queues = reinterpret_cast<uint32_t*>(smem + kOffQueues);
 
@@ -364,6 +532,8 @@ __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const 
     uint32_t slot = 0;
     bool ok = true;
     int stage_job = -1;  // lane s < NSTAGE: job whose boxes stage s holds
+    unsigned long long streamed = 0;  // lane 0: record bytes copied for streamed_job
+    int streamed_job = -1;
     // Tiles are taken in chunks of kChunkTiles from a launch-wide counter, so
     // that CTAs finish together however unevenly the tiles' work is spread.
     for (;;) {
@@ -374,15 +544,41 @@ __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const 
       const uint64_t t_end = min(P.total_tiles, tb + kChunkTiles);
       const uint64_t t = tb + lane;
       __syncwarp();
+      // lane i: tile tb+i's descriptor, job and (spatial filter) the mask of
+      // its rounds some moved box may reach; lane r also loads round r's
+      // outer range of the chunk's first tile, and each tile prefetches the
+      // next one's, so that no tile waits on a global load of its own
+      uint32_t ro_next = 0;
       if (t < t_end) {
         const int jb = find_job(P, t);
         const ClassifyJob& J = P.job[jb];
         s_desc[lane] = J.tiles[t - J.tile_base];
         s_djob[lane] = jb;
+        if constexpr (FILTER)
+          s_need[lane] = J.rcand ? J.rcand[(t - J.tile_base) * kRoundSlots + kRoundSlots - 1] : ~0u;
+      }
+      if constexpr (FILTER) {
+        const ClassifyJob& J0 = P.job[find_job(P, tb)];
+        if (J0.rcand) ro_next = J0.rout[(tb - J0.tile_base) * kRoundSlots + lane];
       }
       __syncwarp();
       const int nb = (int)(t_end - tb);
-      for (int i = 0; i < nb; ++i, ++slot) {
+      for (int i = 0; i < nb; ++i) {
+        const int jb = s_djob[i];
+        const ClassifyJob& J = P.job[jb];
+        const TileDesc d = s_desc[i];
+        const uint64_t lt = tb + i - J.tile_base;
+        uint32_t need = ~0u, ro = 0;
+        if constexpr (FILTER) {
+          need = s_need[i];
+          ro = ro_next;
+          if (i + 1 < nb) {
+            const ClassifyJob& Jn = P.job[s_djob[i + 1]];
+            if (Jn.rcand) ro_next = Jn.rout[(tb + i + 1 - Jn.tile_base) * kRoundSlots + lane];
+          }
+          // the spatial filter found no moved box near the tile: no slot
+          if (need == 0u) continue;
+        }
         const int stage = slot % NSTAGE;
         const uint32_t round = slot / NSTAGE;
         int good = 1;
@@ -394,11 +590,7 @@ __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const 
           break;
         }
         // every lane derives the tile's copies; lane 0 writes the header and
-        // arms the barrier, then lanes 0..8 issue the 9 bulk copies together
-        const int jb = s_djob[i];
-        const ClassifyJob& J = P.job[jb];
-        const TileDesc d = s_desc[i];
-        const uint64_t lt = tb + i - J.tile_base;
+        // arms the barrier, then the lanes issue the bulk copies together
         const uint64_t K = J.K;
         const uint64_t g0 = lt * J.S;
         const uint64_t g1 = min(g0 + J.S, J.G);
@@ -408,44 +600,101 @@ __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const 
         const uint32_t n_edges = (uint32_t)(d.packed >> 56);
         const uint64_t b0 = o0 & ~3ull, b1 = (o0 + n_out + 3) & ~3ull;
         unsigned char* sb = stages + (size_t)stage * STAGE_BYTES;
-        const uint32_t in_bytes = (uint32_t)((a1 - a0) * 4);
-        const uint32_t out_bytes = (uint32_t)((b1 - b0) * 4);
         const uint32_t et_bytes = n_edges * 16;
         // the stage's box records are refreshed only when its job changes
         const int held = __shfl_sync(0xffffffffu, stage_job, stage);
         const uint32_t box_bytes =
             (MAXJ != 1 && held != jb) ? J.C * (uint32_t)(kBoxRecFloats * 4) : 0u;
         if (lane == stage) stage_job = jb;
-        if (lane == 0) {
-          StageHdr* h = reinterpret_cast<StageHdr*>(sb);
-          h->job = jb;
-          h->n_samp = (int)(g1 - g0);
-          h->n_out = (int)n_out;
-          h->n_edges = (int)n_edges;
-          h->in_shift = (int)(K * g0 - a0);
-          h->out_shift = (int)(o0 - b0);
-          h->e_first = d.e_first;
-          h->end = 0;
-          mbar_arrive_expect_tx(&full[stage], et_bytes + 4 * in_bytes + 4 * out_bytes + box_bytes);
-        }
-        __syncwarp();
-        if (lane == 0) {
-          bulk_g2s(sb + kStageEtabOff, J.etab + d.etab, et_bytes, &full[stage]);
-        } else if (lane == 9) {
-          if (box_bytes)
+        uint32_t tile_rec_bytes = 0;  // lane 0: record bytes this tile's copies move
+        if (!FILTER || J.rcand == nullptr) {
+          // the whole tile: lanes 1..4 the inner planes, 5..8 the outer ones
+          const uint32_t in_bytes = (uint32_t)((a1 - a0) * 4);
+          const uint32_t out_bytes = (uint32_t)((b1 - b0) * 4);
+          if (lane == 0) {
+            write_stage_hdr(sb, jb, g0, g1, n_out, n_edges, (int)(K * g0 - a0), (int)(o0 - b0),
+                            d.e_first);
+            mbar_arrive_expect_tx(&full[stage], et_bytes + 4 * in_bytes + 4 * out_bytes + box_bytes);
+          }
+          tile_rec_bytes = 4 * (in_bytes + out_bytes);
+          __syncwarp();
+          if (lane == 0) {
+            bulk_g2s(sb + kStageEtabOff, J.etab + d.etab, et_bytes, &full[stage]);
+          } else if (lane == 9) {
+            if (box_bytes)
+              bulk_g2s(s_boxes + (size_t)stage * kBoxesPerPass * 6, J.boxes, box_bytes, &full[stage]);
+          } else if (lane <= 4) {
+            const int pl = lane - 1;
+            bulk_g2s(sb + J.off_in + (size_t)pl * J.in_cap * 4, J.inner + pl * J.in_stride + a0,
+                     in_bytes, &full[stage]);
+          } else if (lane <= 8) {
+            const int pl = lane - 5;
+            bulk_g2s(sb + J.off_out + (size_t)pl * J.out_cap * 4, J.outer + pl * J.out_stride + b0,
+                     out_bytes, &full[stage]);
+          }
+        } else if constexpr (FILTER) {
+          // the runs of consecutive rounds in `need`: the lane of a run's
+          // first round copies the run's 4 inner and 4 outer plane pieces,
+          // at the offsets they have in a whole-tile copy; lane 10 copies the
+          // tile's candidate row for the consumers
+          const bool starts = ((need >> lane) & 1u) && (lane == 0 || !((need >> (lane - 1)) & 1u));
+          const uint32_t clear_above = ~need & ~((2u << lane) - 1u);
+          const int re = clear_above ? __ffs(clear_above) - 1 : 32;  // run = rounds [lane, re)
+          const uint32_t ro_last = __shfl_sync(0xffffffffu, ro, starts ? re - 1 : lane);
+          uint64_t ia = a0, ib = a0, oa = b0, ob = b0;
+          if (starts) {
+            ia = (K * (g0 + (uint64_t)(31 * lane))) & ~3ull;
+            ib = (K * min(g0 + (uint64_t)(31 * re), g1) + 3) & ~3ull;
+            oa = (o0 + (ro & 0xffffu)) & ~3ull;
+            ob = (o0 + (ro_last >> 16) + 3) & ~3ull;
+          }
+          // never outside the whole-tile window, whatever the round data say
+          ia = max(ia, a0);
+          ib = max(min(ib, a1), ia);
+          oa = max(oa, b0);
+          ob = max(min(ob, b1), oa);
+          const uint32_t in_bytes = (uint32_t)((ib - ia) * 4);
+          const uint32_t out_bytes = (uint32_t)((ob - oa) * 4);
+          const uint32_t tile_bytes = __reduce_add_sync(0xffffffffu, 4 * (in_bytes + out_bytes));
+          if (lane == 0) {
+            write_stage_hdr(sb, jb, g0, g1, n_out, n_edges, (int)(K * g0 - a0), (int)(o0 - b0),
+                            d.e_first);
+            mbar_arrive_expect_tx(&full[stage], et_bytes + tile_bytes + box_bytes + 4 * kRoundSlots);
+          }
+          tile_rec_bytes = tile_bytes;
+          __syncwarp();
+          if (lane == 0) bulk_g2s(sb + kStageEtabOff, J.etab + d.etab, et_bytes, &full[stage]);
+          if (lane == 9 && box_bytes)
             bulk_g2s(s_boxes + (size_t)stage * kBoxesPerPass * 6, J.boxes, box_bytes, &full[stage]);
-        } else if (lane <= 4) {
-          const int pl = lane - 1;
-          bulk_g2s(sb + J.off_in + (size_t)pl * J.in_cap * 4, J.inner + pl * J.in_stride + a0,
-                   in_bytes, &full[stage]);
-        } else if (lane <= 8) {
-          const int pl = lane - 5;
-          bulk_g2s(sb + J.off_out + (size_t)pl * J.out_cap * 4, J.outer + pl * J.out_stride + b0,
-                   out_bytes, &full[stage]);
+          if (lane == 10)
+            bulk_g2s(s_cand + stage * kRoundSlots, J.rcand + lt * kRoundSlots, 4 * kRoundSlots,
+                     &full[stage]);
+          if (in_bytes)
+            for (int pl = 0; pl < 4; ++pl)
+              bulk_g2s(sb + J.off_in + ((size_t)pl * J.in_cap + (ia - a0)) * 4,
+                       J.inner + pl * J.in_stride + ia, in_bytes, &full[stage]);
+          if (out_bytes)
+            for (int pl = 0; pl < 4; ++pl)
+              bulk_g2s(sb + J.off_out + ((size_t)pl * J.out_cap + (oa - b0)) * 4,
+                       J.outer + pl * J.out_stride + oa, out_bytes, &full[stage]);
         }
+        // record bytes are counted per job, off the copies' critical path, and
+        // added to the job's counter when the job changes (and at the end)
+        if (lane == 0) {
+          if (jb != streamed_job) {
+            if (streamed_job >= 0 && streamed && P.job[streamed_job].streamed)
+              atomicAdd(P.job[streamed_job].streamed, streamed);
+            streamed = 0;
+            streamed_job = jb;
+          }
+          streamed += tile_rec_bytes;
+        }
+        ++slot;
       }
       ok = __shfl_sync(0xffffffffu, ok, 0);
     }
+    if (lane == 0 && streamed_job >= 0 && streamed && P.job[streamed_job].streamed)
+      atomicAdd(P.job[streamed_job].streamed, streamed);
     // end markers: one slot per items-per-tile consumer warps, so that every
     // consumer warp takes one
     if (lane == 0 && ok) {
@@ -533,22 +782,16 @@ __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const 
     for (int rnd = sub * RPI; rnd < r_end; ++rnd) {
       const int base = 31 * rnd;
       if (base >= n_samp) break;
+      uint32_t rc = ~0u;
+      if constexpr (FILTER) {
+        // the spatial filter found no moved box near the round (not copied)
+        if (J.rcand) rc = s_cand[stage * kRoundSlots + rnd];
+        if (rc == 0u) continue;
+      }
       const int q = base - 1 + lane;
-      const int q_end = min(base + 31, n_samp);
-      // locate q: its edge j, its position k in its link's run, and the local
-      // index o of the interval that follows it (branch-free)
-      const int j = search_le(etab, 0, n_edges, max(q, 0));
-      const int4 ej = *reinterpret_cast<const int4*>(etab + 4 * j);
-      const int n = ej.y;
-      const int rr = q - ej.x;
-      int li = __float2int_rz(((float)rr + 0.5f) * __int_as_float(ej.w));
-      int k = rr - li * n;
-      const int adj = k < 0 ? -1 : (k >= n ? 1 : 0);  // exact rr / n
-      li += adj;
-      k -= adj * n;
-      const bool valid = q < q_end && rr >= 0;
-      const bool has_next = valid && k < n - 1;
-      const int o = has_next ? ej.z + li * (n - 1) + k : 0;
+      const SampleAt at = locate_sample(etab, n_edges, q, min(base + 31, n_samp));
+      const int j = at.j, n = at.n, k = at.k, o = at.o;
+      const bool valid = at.valid, has_next = at.has_next;
       // ---- a3: the outer sphere of the interval after q, against the moved
       // boxes that survive a warp bounding-sphere cull
       float x = ox[o], y = oy[o], z = oz[o], r = orad[o];
@@ -574,7 +817,7 @@ __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const 
           const float thr = (rw + b0.w + margin) * (1.0f + 1e-6f) + 1e-5f;
           cb = fmaf(ex, ex, fmaf(ey, ey, ez * ez)) <= thr * thr;
         }
-        uint32_t cand = __ballot_sync(0xffffffffu, cb);
+        uint32_t cand = __ballot_sync(0xffffffffu, cb) & rc;
         any_cand = cand;
         const float rt = r + margin;
         const float rt2 = rt * rt;
@@ -1011,15 +1254,17 @@ cudaError_t launch_box_prep(const BoxPrepParams& p, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template <int MAXJ, int NSTAGE, int STAGE_BYTES>
+template <int MAXJ, int NSTAGE, int STAGE_BYTES, bool FILTER>
 static size_t smem_bytes_t(uint32_t consumer_warps) {
   // mirrors the carve-up at the top of classify_kernel
   constexpr int kBoxAreas = MAXJ == 1 ? 1 : NSTAGE;
   constexpr size_t kOffFull = (size_t)NSTAGE * STAGE_BYTES;
   constexpr size_t kOffCnt = kOffFull + (2 * NSTAGE + 1) * sizeof(uint64_t) + 8;
   constexpr size_t kOffDesc = (kOffCnt + 4 * ((NSTAGE + 3) & ~3) + 15) & ~(size_t)15;
-  constexpr size_t kOffBoxes = (kOffDesc + 32 * sizeof(TileDesc) + 32 * sizeof(int) + 127) &
-                               ~(size_t)127;
+  constexpr size_t kOffBoxes =
+      (kOffDesc + 32 * sizeof(TileDesc) + 32 * sizeof(int) +
+       (FILTER ? 32 * sizeof(uint32_t) + (size_t)NSTAGE * kRoundSlots * 4 : 0) + 127) &
+      ~(size_t)127;
   constexpr size_t kOffQueues = kOffBoxes + (size_t)kBoxAreas * kBoxesPerPass * kBoxRecFloats * 4;
   return kOffQueues + (size_t)consumer_warps * 4 * kPairQueue;
 }
@@ -1028,30 +1273,50 @@ size_t classify_smem_bytes(int variant, uint32_t consumer_warps) {
   // the batched kernel's (larger) footprint, which bounds both
   switch (variant) {
 #define RGG_VARIANT(id, ns, sb, rd, rpi) \
-  case id: return smem_bytes_t<kMaxJobs, ns, sb>(consumer_warps);
+  case id: return smem_bytes_t<kMaxJobs, ns, sb, id == kDefaultVariant>(consumer_warps);
     RGG_VARIANTS(RGG_VARIANT)
 #undef RGG_VARIANT
     default: return 0;
   }
 }
 
-template <int MAXJ, int NSTAGE, int STAGE_BYTES, int ROUNDS, int RPI>
+template <int MAXJ, int NSTAGE, int STAGE_BYTES, int ROUNDS, int RPI, bool FILTER>
 static cudaError_t launch_classify_v(const ClassifyParams<MAXJ>& p, const ClassifyLaunch& lc,
                                      cudaStream_t s) {
-  auto kern = classify_kernel<MAXJ, NSTAGE, STAGE_BYTES, ROUNDS, RPI>;
-  const size_t smem = smem_bytes_t<MAXJ, NSTAGE, STAGE_BYTES>(lc.consumer_warps);
+  auto kern = classify_kernel<MAXJ, NSTAGE, STAGE_BYTES, ROUNDS, RPI, FILTER>;
+  const size_t smem = smem_bytes_t<MAXJ, NSTAGE, STAGE_BYTES, FILTER>(lc.consumer_warps);
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
   kern<<<lc.grid, 32 * (1 + lc.consumer_warps), smem, s>>>(p);
   return cudaGetLastError();
 }
 
+// The filtered instance exists for the default pipeline variant only.
+template <int MAXJ, int ID, int NS, int SB, int RD, int RPI>
+static cudaError_t launch_variant(const ClassifyParams<MAXJ>& p, const ClassifyLaunch& lc,
+                                  bool filtered, cudaStream_t s) {
+  if constexpr (ID == kDefaultVariant) {
+    if (filtered) return launch_classify_v<MAXJ, NS, SB, RD, RPI, true>(p, lc, s);
+  } else {
+    if (filtered) return cudaErrorInvalidValue;
+  }
+  return launch_classify_v<MAXJ, NS, SB, RD, RPI, false>(p, lc, s);
+}
+
 template <int MAXJ>
 static cudaError_t launch_classify_t(const ClassifyParams<MAXJ>& p, const ClassifyLaunch& lc,
                                      cudaStream_t s) {
+  // the spatial filter's per-pass test, when a job uses it
+  bool filtered = false;
+  for (uint32_t j = 0; j < p.njobs && j < (uint32_t)MAXJ; ++j) filtered |= p.job[j].rcand != nullptr;
+  if (filtered && p.total_tiles) {
+    round_filter_kernel<MAXJ><<<(unsigned)((p.total_tiles + 7) / 8), 256, 0, s>>>(p);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   switch (lc.variant) {
 #define RGG_VARIANT(id, ns, sb, rd, rpi) \
-  case id: return launch_classify_v<MAXJ, ns, sb, rd, rpi>(p, lc, s);
+  case id: return launch_variant<MAXJ, id, ns, sb, rd, rpi>(p, lc, filtered, s);
     RGG_VARIANTS(RGG_VARIANT)
 #undef RGG_VARIANT
     default: return cudaErrorInvalidValue;
@@ -1081,6 +1346,14 @@ static_assert(sizeof(MergeParams<kMaxJobs>) <= 32764, "merge parameters too larg
 static_assert(sizeof(BoxPrepParams) <= 32764, "box-prep parameters too large");
 static_assert(sizeof(BoxUpdateParams) <= 32764, "box-update parameters too large");
 static_assert(sizeof(ClassifyParams<kMaxJobs>) <= 32764, "classify parameters too large");
+
+cudaError_t launch_round_bounds(const RoundBoundsParams& p, int num_sms, cudaStream_t s) {
+  if (p.T == 0) return cudaSuccess;
+  const uint64_t want = (p.T + 7) / 8;  // a warp per tile
+  const uint64_t cap = (uint64_t)num_sms * 16;
+  round_bounds_kernel<<<(unsigned)(want < cap ? want : cap), 256, 0, s>>>(p);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_resolve_gray(const ResolveParams& p, int num_sms, cudaStream_t s) {
   if (p.n_edges == 0) return cudaSuccess;

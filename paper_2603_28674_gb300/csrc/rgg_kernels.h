@@ -12,7 +12,8 @@ namespace rgg {
 // Compiled shapes of the streaming pipeline: (id, stages in the shared-memory
 // ring, bytes per stage, rounds of 31 samples per tile, rounds per work item).
 // Each stage holds one tile: header, accumulators, edge table, inner and
-// outer record planes; beside it, 3 KB for the tile's job's box records.
+// outer record planes; beside it, the tile's round candidates and 3 KB for
+// the tile's job's box records.
 #define RGG_VARIANTS(X)             \
   X(0, 14, 10 * 1024, 3, 1)        \
   X(1, 7, 28 * 1024, 9, 1)         \
@@ -160,6 +161,19 @@ struct ObbQueryParams {
   unsigned long long* work;   // [2] SAT tests, spline-segment tests (may be null)
 };
 
+// Per-round bounding spheres and outer ranges of one roadmap's tiles (see
+// rgg_device.cuh), computed from its resident outer records.
+struct RoundBoundsParams {
+  const float* outer;
+  uint64_t out_stride;
+  const TileDesc* tiles;
+  const int4* etab;
+  uint64_t T, G;
+  uint32_t S;
+  float4* rsph;               // [T][kRoundSlots]
+  uint32_t* rout;             // [T][kRoundSlots]
+};
+
 size_t classify_smem_bytes(int variant, uint32_t consumer_warps);
 
 cudaError_t launch_count_samples(const double* qa, const double* qb, uint64_t n_edges, uint32_t L,
@@ -171,6 +185,7 @@ cudaError_t launch_classify_single(const ClassifyParams<1>& p, const ClassifyLau
                                    cudaStream_t s);
 cudaError_t launch_classify_batched(const ClassifyParams<kMaxJobs>& p, const ClassifyLaunch& lc,
                                     cudaStream_t s);
+cudaError_t launch_round_bounds(const RoundBoundsParams& p, int num_sms, cudaStream_t s);
 cudaError_t launch_merge_single(const MergeParams<1>& p, cudaStream_t s);
 cudaError_t launch_merge_batched(const MergeParams<kMaxJobs>& p, cudaStream_t s);
 cudaError_t launch_resolve_gray(const ResolveParams& p, int num_sms, cudaStream_t s);

@@ -214,6 +214,11 @@ int rgg_load(rgg_roadmap_t r, const char* path, void* stream) {
     es.release();
     return cuda_status(e);
   }
+  rc = compute_rounds(r, &es, s);
+  if (rc != RGG_OK) {
+    es.release();
+    return rc;
+  }
   for (uint32_t b = 0; b < r->M; ++b) r->present[b] = present[b] ? 1 : 0;
   r->es.release();
   r->es = std::move(es);

@@ -24,6 +24,7 @@ static int tune_launch(rgg_roadmap_t* rs, uint32_t n, const std::vector<uint32_t
     if (r->es.N == 0 || C[i] == 0) continue;
     ClassifyJob j = make_job(r, C[i], tiles);
     j.edge_acc = acc[i];
+    j.streamed = nullptr;
     if (n == 1) cp1.job[0] = j; else cpp->job[nj] = j;
     ++nj;
     tiles += r->es.T;

@@ -42,7 +42,8 @@ EXPORTS = (
     "rgg_fetch_request_labels", "rgg_release_request", "rgg_autotune",
     "rgg_step_graph_create", "rgg_step_graph_launch", "rgg_step_graph_nodes",
     "rgg_step_graph_destroy", "rgg_save", "rgg_load", "rgg_resolve_gray", "rgg_fetch_boxes",
-    "rgg_set_obb_filter", "rgg_obb_work", "rgg_fetch_obb_records",
+    "rgg_set_obb_filter", "rgg_obb_work", "rgg_fetch_obb_records", "rgg_set_round_filter",
+    "rgg_streamed_bytes",
 )
 
 
@@ -97,7 +98,8 @@ class Info(ctypes.Structure):
                 ("pending_boxes", ctypes.c_uint32), ("grid_ctas", ctypes.c_uint32),
                 ("open_requests", ctypes.c_uint32), ("pending_capacity", ctypes.c_uint32),
                 ("geometry", ctypes.c_uint32), ("grid_cells", ctypes.c_uint32),
-                ("grid_items", ctypes.c_uint64), ("spline_vertices", ctypes.c_uint64)]
+                ("grid_items", ctypes.c_uint64), ("spline_vertices", ctypes.c_uint64),
+                ("round_filter", ctypes.c_uint32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -149,6 +151,8 @@ def _lib():
         "rgg_resolve_gray": [vp, u32, vp, vp, i32, ctypes.POINTER(_ResolveStats), vp],
         "rgg_fetch_boxes": [vp, vp, vp, vp],
         "rgg_set_obb_filter": [vp, i32],
+        "rgg_set_round_filter": [vp, i32],
+        "rgg_streamed_bytes": [vp, ctypes.POINTER(u64)],
         "rgg_obb_work": [vp, ctypes.POINTER(u64), ctypes.POINTER(u64)],
         "rgg_fetch_obb_records": [vp, vp, vp, vp],
         "rgg_load": [vp, ctypes.c_char_p, vp],
@@ -387,6 +391,17 @@ class Roadmap:
 
     def check_status(self, stream=None) -> None:
         _check("rgg_check_status", _lib().rgg_check_status(self._h, _stream(stream, self.device)))
+
+    def set_round_filter(self, enable: bool) -> None:
+        """Sphere geometry: copy only the rounds of records the moved boxes may
+        reach (default); off streams every record."""
+        _check("rgg_set_round_filter", _lib().rgg_set_round_filter(self._h, int(enable)))
+
+    def streamed_bytes(self) -> int:
+        """Record bytes the classify launches copied since the last call."""
+        v = ctypes.c_uint64()
+        _check("rgg_streamed_bytes", _lib().rgg_streamed_bytes(self._h, ctypes.byref(v)))
+        return int(v.value)
 
     def set_obb_filter(self, enable: bool) -> None:
         """OBB geometry: test only the grid cells the moved boxes meet (default)."""

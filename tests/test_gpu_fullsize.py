@@ -66,6 +66,37 @@ def test_full_size_roadmap_sampled_against_oracle(rgg, which):
         r.check_status()
 
 
+def test_full_size_filter_changes_no_bit(rgg):
+    """The large roadmap with and without the spatial filter (2 x 26.8 GB):
+    identical labels and box sets after every update, fewer bytes copied."""
+    sc = W.workload_large(n_updates=3)
+    rm, robot = sc.roadmap, sc.roadmap.robot
+    m = sc.boxes.count
+    rs = []
+    for flt in (True, False):
+        r = rgg.Roadmap(robot.num_links, robot.inner_per_link, m)
+        r.build_edges(robot, rm.q_from, rm.q_to, rm.step)
+        r.set_round_filter(flt)
+        r.update_obstacles(np.arange(m), f32(sc.boxes.poses()))
+        r.classify()
+        r.streamed_bytes()
+        rs.append(r)
+    f, u = rs
+    for k, up in enumerate(sc.updates):
+        for x in rs:
+            x.update_obstacles(up.ids, f32(up.poses))
+            x.classify()
+        np.testing.assert_array_equal(f.fetch_labels(), u.fetch_labels(), err_msg=f"update {k}")
+        hf, tf = f.fetch_box_sets()
+        hu, tu = u.fetch_box_sets()
+        np.testing.assert_array_equal(hf, hu, err_msg=f"update {k}")
+        np.testing.assert_array_equal(tf, tu, err_msg=f"update {k}")
+        assert f.streamed_bytes() < u.streamed_bytes()
+    for r in rs:
+        r.check_status()
+        r.close()
+
+
 def test_full_size_batched_launch_sampled_against_oracle(rgg):
     scenes = W.workload_batched(n_updates=2)
     rms, states = [], []

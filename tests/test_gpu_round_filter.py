@@ -1,0 +1,226 @@
+"""The sphere geometry's opt-in spatial filter (Sec. 4.3, spatially filtered
+many-to-many checking, applied to the streamed records): every round of 31
+configurations of a tile has a bounding sphere of its outer spheres; before
+each pass the rounds are tested against the moved boxes and the classify
+kernel copies only the rounds some box may reach.
+
+Rules checked:
+  * labels and per-edge hit / touch sets are bit-identical with and without
+    the filter after every update: planar and 7-DOF scenes, every launch
+    shape, a batched launch mixing filtered and unfiltered roadmaps,
+    uploaded records, a reloaded roadmap;
+  * the unfiltered launch copies every record (at least record_bytes per
+    pass); the filtered one copies fewer on sparse scenes, and none for a
+    pass whose boxes are far from every edge;
+  * the filtered labels agree with the FP64 oracle (pinned edges equal,
+    other differences GPU gray).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2603_28674_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+PIN = 1e-4
+
+
+@pytest.fixture(scope="module")
+def rgg():
+    from paper_2603_28674_gb300 import build
+    build.build()
+    from paper_2603_28674_gb300 import rgg as _rgg
+    return _rgg
+
+
+def f32(x):
+    return np.asarray(x, dtype=np.float32)
+
+
+def scene(which):
+    if which == "planar":
+        sc = W.workload_planar(n_nodes=300, n_updates=4)
+        return sc.roadmap, sc.boxes, sc.updates
+    rng = np.random.default_rng(61)
+    arm = W.dh_arm(rng, 7)
+    rm = W.prm_roadmap(rng, arm, 200, 10, 0.03)
+    boxes = W.random_boxes(rng, 24)
+    return rm, boxes, W.update_stream(rng, boxes, 4, 4)
+
+
+def built(rgg, rm, m, filtered):
+    r = rgg.Roadmap(rm.robot.num_links, rm.robot.inner_per_link, m)
+    r.build_edges(rm.robot, rm.q_from, rm.q_to, rm.step)
+    r.set_round_filter(filtered)
+    return r
+
+
+def same_state(a, b, where):
+    np.testing.assert_array_equal(a.fetch_labels(), b.fetch_labels(), err_msg=where)
+    ha, ta = a.fetch_box_sets()
+    hb, tb = b.fetch_box_sets()
+    np.testing.assert_array_equal(ha, hb, err_msg=where)
+    np.testing.assert_array_equal(ta, tb, err_msg=where)
+
+
+@pytest.mark.parametrize("which", ["planar", "7dof"])
+def test_filter_changes_no_bit(rgg, which):
+    rm, boxes, ups = scene(which)
+    m = boxes.count
+    state = boxes.copy()
+    with built(rgg, rm, m, True) as f, built(rgg, rm, m, False) as u:
+        assert f.info()["round_filter"] == 1 and u.info()["round_filter"] == 0
+        with rgg.Roadmap(rm.robot.num_links, rm.robot.inner_per_link, m) as d:
+            assert d.info()["round_filter"] == 0          # off by default
+        record_bytes = u.info()["record_bytes"]
+        for x in (f, u):
+            x.update_obstacles(np.arange(m), f32(state.poses()))
+            x.classify()
+        same_state(f, u, "initial")
+        f.streamed_bytes()
+        u.streamed_bytes()
+        for k, up in enumerate(ups):
+            for x in (f, u):
+                x.update_obstacles(up.ids, f32(up.poses))
+                x.classify()
+            state.centre[up.ids] = up.poses[:, :3]
+            same_state(f, u, f"update {k}")
+            bf, bu = f.streamed_bytes(), u.streamed_bytes()
+            assert bu >= record_bytes, (bu, record_bytes)
+            assert bf < bu, (bf, bu)
+        want = oracle.classify(rm.robot, rm.q_from, rm.q_to, rm.step, state.poses())
+        got = f.fetch_labels()
+        pinned = want["kappa"] > PIN
+        assert np.all(got[pinned] == want["labels"][pinned])
+        assert np.all(got[got != want["labels"]] == oracle.GRAY)
+        f.check_status()
+        u.check_status()
+
+
+def test_every_launch_shape(rgg):
+    """The filter runs with the default launch shape only; the round data
+    follow the tiles when a launch shape changes them (3 -> 5 rebuilds
+    both)."""
+    rm, boxes, ups = scene("7dof")
+    m = boxes.count
+    with built(rgg, rm, m, False) as u:
+        u.update_obstacles(np.arange(m), f32(boxes.poses()))
+        u.classify()
+        for up in ups:
+            u.update_obstacles(up.ids, f32(up.poses))
+            u.classify()
+        want_l = u.fetch_labels()
+        want_h, want_t = u.fetch_box_sets()
+    for variant in list(range(7)) + ["3->5"]:
+        with built(rgg, rm, m, True) as f:
+            if variant == "3->5":
+                f.set_launch_shape(3, 16)
+                assert f.info()["round_filter"] == 0
+                f.set_launch_shape(5, 16)
+                assert f.info()["round_filter"] == 1
+            else:
+                f.set_launch_shape(variant, 16)
+                assert f.info()["round_filter"] == (1 if variant == 5 else 0)
+            f.update_obstacles(np.arange(m), f32(boxes.poses()))
+            f.classify()
+            for up in ups:
+                f.update_obstacles(up.ids, f32(up.poses))
+                f.classify()
+            np.testing.assert_array_equal(f.fetch_labels(), want_l, err_msg=f"variant {variant}")
+            h, t = f.fetch_box_sets()
+            np.testing.assert_array_equal(h, want_h, err_msg=f"variant {variant}")
+            np.testing.assert_array_equal(t, want_t, err_msg=f"variant {variant}")
+            f.check_status()
+
+
+def test_batched_mix_of_filtered_and_unfiltered(rgg):
+    scenes = W.workload_batched(n_roadmaps=6, edge_lo=300, edge_hi=3000, n_updates=2)
+    mixed, plain = [], []
+    for i, sc in enumerate(scenes):
+        for lst, flt in ((mixed, i % 2 == 0), (plain, False)):
+            r = built(rgg, sc.roadmap, sc.boxes.count, flt)
+            r.update_obstacles(np.arange(sc.boxes.count), f32(sc.boxes.poses()))
+            lst.append(r)
+    rgg.classify_many(mixed)
+    for r in plain:
+        r.classify()
+    for k in range(2):
+        for sc, a, b in zip(scenes, mixed, plain):
+            up = sc.updates[k]
+            a.update_obstacles(up.ids, f32(up.poses))
+            b.update_obstacles(up.ids, f32(up.poses))
+        rgg.classify_many(mixed)
+        for b in plain:
+            b.classify()
+        for i, (a, b) in enumerate(zip(mixed, plain)):
+            same_state(a, b, f"roadmap {i} step {k}")
+    for r in mixed + plain:
+        r.check_status()
+        r.close()
+
+
+def test_uploaded_and_reloaded_roadmaps(rgg, tmp_path):
+    rm, boxes, ups = scene("7dof")
+    m = boxes.count
+    robot = rm.robot
+    with built(rgg, rm, m, False) as u:
+        inner, outer, soff = u.fetch_records()
+        u.update_obstacles(np.arange(m), f32(boxes.poses()))
+        u.classify()
+        path = str(tmp_path / "r.rgg")
+        u.save(path)
+        with rgg.Roadmap(robot.num_links, robot.inner_per_link, m) as up_r, \
+                rgg.Roadmap(robot.num_links, robot.inner_per_link, m) as ld:
+            # switched on before the records arrive: computed when they do
+            up_r.set_round_filter(True)
+            ld.set_round_filter(True)
+            up_r.upload_edges(soff, inner, outer)
+            up_r.update_obstacles(np.arange(m), f32(boxes.poses()))
+            up_r.classify()
+            ld.load(path)
+            assert up_r.info()["round_filter"] == 1 and ld.info()["round_filter"] == 1
+            for k, mv in enumerate(ups):
+                for x in (u, up_r, ld):
+                    x.update_obstacles(mv.ids, f32(mv.poses))
+                    x.classify()
+                same_state(up_r, u, f"uploaded, update {k}")
+                same_state(ld, u, f"reloaded, update {k}")
+            up_r.check_status()
+            ld.check_status()
+
+
+def test_far_boxes_copy_nothing_and_clear_their_bits(rgg):
+    rm, boxes, _ = scene("planar")
+    m = boxes.count
+    state = boxes.copy()
+    with built(rgg, rm, m, True) as f, built(rgg, rm, m, False) as u:
+        for x in (f, u):
+            x.update_obstacles(np.arange(m), f32(state.poses()))
+            x.classify()
+        f.streamed_bytes()
+        _, touch0 = f.fetch_box_sets()
+        # the three boxes that touch the most edges move far away
+        per_box = np.array([np.count_nonzero((touch0[:, b >> 5] >> (b & 31)) & 1) for b in range(m)])
+        ids = np.sort(np.argsort(-per_box, kind="stable")[:3])
+        assert per_box[ids].min() > 0
+        mask = np.uint32(sum(1 << int(b) for b in ids))
+        far = state.poses()[ids].copy()
+        far[:, :3] = [[60.0, 60.0, 0.0], [61.0, 60.0, 0.0], [62.0, 60.0, 0.0]]
+        for x in (f, u):
+            x.update_obstacles(ids, f32(far))
+            x.classify()
+        state.centre[ids] = far[:, :3]
+        assert f.streamed_bytes() == 0
+        same_state(f, u, "far boxes")
+        _, touch1 = f.fetch_box_sets()
+        assert not np.any(touch1[:, 0] & mask)
+        want = oracle.classify(rm.robot, rm.q_from, rm.q_to, rm.step, state.poses())
+        got = f.fetch_labels()
+        pinned = want["kappa"] > PIN
+        assert np.all(got[pinned] == want["labels"][pinned])
+        # switching the filter is refused for the OBB geometry only
+        with rgg.Roadmap(3, 4, 4, geometry=rgg.GEOMETRY_OBB) as o:
+            with pytest.raises(rgg.RGGError) as e:
+                o.set_round_filter(False)
+            assert e.value.status == rgg.RGG_ERR_STATE
