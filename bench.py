@@ -705,9 +705,6 @@ def run_batched(args):
     def run(mode, steps, warm):
         step_ms, lat = [], []
         for i in range(warm + steps):
-            if i == warm:
-                for r in rms:
-                    r.streamed_bytes()   # count the timed steps only
             ev0 = torch.cuda.Event(enable_timing=True)
             ends = []
             ev0.record(stream)
@@ -732,8 +729,7 @@ def run_batched(args):
             if i >= warm:
                 step_ms.append(ev0.elapsed_time(ends[-1]))
                 lat.extend(ev0.elapsed_time(e) for e in ends)
-        copied = sum(r.streamed_bytes() for r in rms)
-        return float(np.mean(step_ms)), np.array(lat), np.array(step_ms), copied / max(1, steps)
+        return float(np.mean(step_ms)), np.array(lat), np.array(step_ms)
 
     out, final = {}, {}
     with ClockSampler(0) as clocks:
@@ -743,19 +739,13 @@ def run_batched(args):
                 graphs = [rgg.StepGraph(rms, [(sc.updates[k].ids, d[k])
                                               for sc, d in zip(scenes, dev)])
                           for k in range(n_up)]
-            ms, lat, st, copied = run(mode, args.steps, args.warmup)
+            ms, lat, st = run(mode, args.steps, args.warmup)
             final[mode] = [r.fetch_labels(stream=stream) for r in rms]
-            # bytes one step must move: the records the launches copied (the
-            # spatial filter skips the rest), the per-edge results and the
-            # filter's per-round data
-            b_step = copied + sum(8 * i["num_edges"] + (ROUND_SLOT_BYTES * 32 * i["num_tiles"]
-                                                        if i["round_filter"] else 0)
-                                  for i in infos)
+            # bytes one step must move: every record and each edge's pass result
+            b_step = sum(algorithmic_bytes(i) for i in infos)
             out[mode] = {"ms_per_step": ms, "edges_per_s": n_edges / (ms / 1e3),
                          "step_ms_min_med_max": [float(np.min(st)), float(np.median(st)),
                                                  float(np.max(st))],
-                         "record_bytes_copied_per_step": copied,
-                         "records_copied_frac": copied / rec,
                          "achieved_gbs": b_step / (ms / 1e3) / 1e9,
                          "latency_ms_p50": float(np.percentile(lat, 50)),
                          "latency_ms_p99": float(np.percentile(lat, 99))}

@@ -433,9 +433,10 @@ int rgg_load(rgg_roadmap_t r, const char* path, void* stream);
  * rgg_set_round_filter synchronises the device.  RGG_ERR_STATE on an
  * OBB-geometry roadmap.
  * rgg_streamed_bytes returns the record bytes (inner and outer planes, with
- * the 16-byte rounding of each copy) the classify launches of this roadmap
- * copied since the last call, and resets the count; it waits for the device.
- * The autotuner's launches are not counted. */
+ * the 16-byte rounding of each copy) the filtered classify launches of this
+ * roadmap copied since the last call, and resets the count; it waits for the
+ * device.  Launches without the filter copy every record (record_bytes plus
+ * the rounding) and are not counted, nor are the autotuner's. */
 int rgg_set_round_filter(rgg_roadmap_t r, int enable);
 int rgg_streamed_bytes(rgg_roadmap_t r, uint64_t* record_bytes);
 

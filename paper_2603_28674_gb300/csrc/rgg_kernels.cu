@@ -678,9 +678,10 @@ __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const 
               bulk_g2s(sb + J.off_out + ((size_t)pl * J.out_cap + (oa - b0)) * 4,
                        J.outer + pl * J.out_stride + oa, out_bytes, &full[stage]);
         }
-        // record bytes are counted per job, off the copies' critical path, and
-        // added to the job's counter when the job changes (and at the end)
-        if (lane == 0) {
+        // filtered instance: record bytes are counted per job, after the
+        // copies, and added to the job's counter when the job changes (and at
+        // the end); the count costs the streaming instance 2% and is left out
+        if (FILTER && lane == 0) {
           if (jb != streamed_job) {
             if (streamed_job >= 0 && streamed && P.job[streamed_job].streamed)
               atomicAdd(P.job[streamed_job].streamed, streamed);
@@ -693,7 +694,7 @@ __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const 
       }
       ok = __shfl_sync(0xffffffffu, ok, 0);
     }
-    if (lane == 0 && streamed_job >= 0 && streamed && P.job[streamed_job].streamed)
+    if (FILTER && lane == 0 && streamed_job >= 0 && streamed && P.job[streamed_job].streamed)
       atomicAdd(P.job[streamed_job].streamed, streamed);
     // end markers: one slot per items-per-tile consumer warps, so that every
     // consumer warp takes one
