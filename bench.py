@@ -454,11 +454,20 @@ def run_gpu(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
         rate, n_s, t_s, cores = oracle_rate(sc, args.cpu_seconds)
+        # the same oracle on one thread, on a shorter sample
+        oracle.set_threads(1)
+        try:
+            rate1, n_1, t_1, _ = oracle_rate(sc, max(1.0, args.cpu_seconds / 3), seed=1)
+        finally:
+            oracle.set_threads(cores)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": (f"{n_s} random edges classified from their endpoints against the "
                           f"{moved} boxes one update moves (FP64, OpenMP over edges), "
-                          f"{t_s:.1f} s")}
+                          f"{t_s:.1f} s"),
+               "single_thread_value": rate1,
+               "single_thread_sample": f"{n_1} random edges, {t_1:.1f} s, one thread"}
 
     cfg = workload_config(args.workload, sc)
     cfg.update({"samples": info["num_samples"], "record_gb": info["record_bytes"] / 1e9,
@@ -474,11 +483,17 @@ def run_gpu(args):
         * args.steps / (ms / 1000.0),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
+                     # ncu-measured DRAM bytes per launch over the live launch time
+                     "traffic_frac": (traffic / (k_avg_ms / 1000.0) / 1e9 / peak
+                                      if traffic else None),
                      "peak_source": f"{peak_kind} HBM copy bandwidth",
                      "kernel": "classify_kernel", "bytes_per_launch": b_alg,
                      "kernel_ms": k_avg_ms,
                      "merge_kernel_ms": m_ms / max(1, k_launches)},
         "round_filter": filt,
+        # label mix after the end-to-end steps (the paper's roadmaps: 0.3-10% gray)
+        "labels": {"green": float(np.mean(labels_host == 0)), "gray": float(np.mean(labels_host == 1)),
+                   "red": float(np.mean(labels_host == 2))},
         "e2e": {"value": e2e_value, "unit": UNIT,
                 "h2d_bytes_per_step": moved * (4 + 60),
                 "d2h_bytes_per_step": n_edges + 4},
