@@ -581,16 +581,10 @@ __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const 
         }
         const int stage = slot % NSTAGE;
         const uint32_t round = slot / NSTAGE;
-        int good = 1;
-        if (lane == 0) good = mbar_wait_bounded(&empty[stage], (round & 1) ^ 1, kWaitLimit);
-        good = __shfl_sync(0xffffffffu, good, 0);
-        if (!good) {
-          if (lane == 0) atomicCAS(P.status, 0, (int)kStatusTimeoutEmpty);
-          ok = false;
-          break;
-        }
-        // every lane derives the tile's copies; lane 0 writes the header and
-        // arms the barrier, then the lanes issue the bulk copies together
+        // every lane derives the tile's copies before waiting for the stage
+        // (the wait to the copies is the ring's critical path: computing them
+        // first made the launch 4% faster); then lane 0 writes the header and
+        // arms the barrier, and the lanes issue the bulk copies together
         const uint64_t K = J.K;
         const uint64_t g0 = lt * J.S;
         const uint64_t g1 = min(g0 + J.S, J.G);
@@ -606,6 +600,14 @@ __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const 
         const uint32_t box_bytes =
             (MAXJ != 1 && held != jb) ? J.C * (uint32_t)(kBoxRecFloats * 4) : 0u;
         if (lane == stage) stage_job = jb;
+        int good = 1;
+        if (lane == 0) good = mbar_wait_bounded(&empty[stage], (round & 1) ^ 1, kWaitLimit);
+        good = __shfl_sync(0xffffffffu, good, 0);
+        if (!good) {
+          if (lane == 0) atomicCAS(P.status, 0, (int)kStatusTimeoutEmpty);
+          ok = false;
+          break;
+        }
         uint32_t tile_rec_bytes = 0;  // lane 0: record bytes this tile's copies move
         if (!FILTER || J.rcand == nullptr) {
           // the whole tile: lanes 1..4 the inner planes, 5..8 the outer ones
@@ -929,19 +931,33 @@ __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const 
     done = __shfl_sync(0xffffffffu, done, 0);
     if (done == IPT - 1) {
       __threadfence_block();
-      // ---- a5: the tile's per-edge bits into the global accumulators
-      for (int jl = lane; jl < n_edges; jl += 32) {
-        const uint32_t h = *reinterpret_cast<volatile uint32_t*>(&acc_hit[jl]);
-        const uint32_t t = *reinterpret_cast<volatile uint32_t*>(&acc_touch[jl]);
-        const uint64_t e = (uint64_t)hdr.e_first + jl;
-        if (h) atomicOr(&J.edge_acc[2 * e], h);
-        if (t) atomicOr(&J.edge_acc[2 * e + 1], t);
-        acc_hit[jl] = 0;
-        acc_touch[jl] = 0;
+      // ---- a5: the tile's per-edge bits into the global accumulators.  They
+      // are taken into registers and the stage is released first: the
+      // release (a CTA-scope arrive) would otherwise wait for the global ORs,
+      // and the release is on the ring's critical path (1% of the launch)
+      static_assert(kAccMax <= 3 * 32, "accumulator entries per lane");
+      uint32_t hv[3], tv[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const int jl = lane + 32 * c;
+        hv[c] = 0;
+        tv[c] = 0;
+        if (jl < n_edges) {
+          hv[c] = *reinterpret_cast<volatile uint32_t*>(&acc_hit[jl]);
+          tv[c] = *reinterpret_cast<volatile uint32_t*>(&acc_touch[jl]);
+          acc_hit[jl] = 0;
+          acc_touch[jl] = 0;
+        }
       }
       if (lane == 0) s_cnt[stage] = 0;
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[stage]);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const uint64_t e = (uint64_t)hdr.e_first + lane + 32 * c;
+        if (hv[c]) atomicOr(&J.edge_acc[2 * e], hv[c]);
+        if (tv[c]) atomicOr(&J.edge_acc[2 * e + 1], tv[c]);
+      }
     }
   }
 }
