@@ -600,6 +600,29 @@ __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const 
         const uint32_t box_bytes =
             (MAXJ != 1 && held != jb) ? J.C * (uint32_t)(kBoxRecFloats * 4) : 0u;
         if (lane == stage) stage_job = jb;
+        // whole-tile copies (every job of the streaming instance): lane 0 the
+        // edge table, lanes 1..4 the inner planes, 5..8 the outer ones, lane 9
+        // the box records; one predicated issue after the wait
+        const uint32_t in_bytes = (uint32_t)((a1 - a0) * 4);
+        const uint32_t out_bytes = (uint32_t)((b1 - b0) * 4);
+        void* c_dst = sb + kStageEtabOff;
+        const void* c_src = J.etab + d.etab;
+        uint32_t c_bytes = et_bytes;
+        if (lane >= 1 && lane <= 4) {
+          c_dst = sb + J.off_in + (size_t)(lane - 1) * J.in_cap * 4;
+          c_src = J.inner + (lane - 1) * J.in_stride + a0;
+          c_bytes = in_bytes;
+        } else if (lane >= 5 && lane <= 8) {
+          c_dst = sb + J.off_out + (size_t)(lane - 5) * J.out_cap * 4;
+          c_src = J.outer + (lane - 5) * J.out_stride + b0;
+          c_bytes = out_bytes;
+        } else if (lane == 9) {
+          c_dst = s_boxes + (size_t)stage * kBoxesPerPass * 6;
+          c_src = J.boxes;
+          c_bytes = box_bytes;
+        } else if (lane > 9) {
+          c_bytes = 0;
+        }
         int good = 1;
         if (lane == 0) good = mbar_wait_bounded(&empty[stage], (round & 1) ^ 1, kWaitLimit);
         good = __shfl_sync(0xffffffffu, good, 0);
@@ -610,9 +633,7 @@ __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const 
         }
         uint32_t tile_rec_bytes = 0;  // lane 0: record bytes this tile's copies move
         if (!FILTER || J.rcand == nullptr) {
-          // the whole tile: lanes 1..4 the inner planes, 5..8 the outer ones
-          const uint32_t in_bytes = (uint32_t)((a1 - a0) * 4);
-          const uint32_t out_bytes = (uint32_t)((b1 - b0) * 4);
+          // the whole tile
           if (lane == 0) {
             write_stage_hdr(sb, jb, g0, g1, n_out, n_edges, (int)(K * g0 - a0), (int)(o0 - b0),
                             d.e_first);
@@ -620,20 +641,7 @@ __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const 
           }
           tile_rec_bytes = 4 * (in_bytes + out_bytes);
           __syncwarp();
-          if (lane == 0) {
-            bulk_g2s(sb + kStageEtabOff, J.etab + d.etab, et_bytes, &full[stage]);
-          } else if (lane == 9) {
-            if (box_bytes)
-              bulk_g2s(s_boxes + (size_t)stage * kBoxesPerPass * 6, J.boxes, box_bytes, &full[stage]);
-          } else if (lane <= 4) {
-            const int pl = lane - 1;
-            bulk_g2s(sb + J.off_in + (size_t)pl * J.in_cap * 4, J.inner + pl * J.in_stride + a0,
-                     in_bytes, &full[stage]);
-          } else if (lane <= 8) {
-            const int pl = lane - 5;
-            bulk_g2s(sb + J.off_out + (size_t)pl * J.out_cap * 4, J.outer + pl * J.out_stride + b0,
-                     out_bytes, &full[stage]);
-          }
+          if (c_bytes) bulk_g2s(c_dst, c_src, c_bytes, &full[stage]);
         } else if constexpr (FILTER) {
           // the runs of consecutive rounds in `need`: the lane of a run's
           // first round copies the run's 4 inner and 4 outer plane pieces,
@@ -655,9 +663,9 @@ __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const 
           ib = max(min(ib, a1), ia);
           oa = max(oa, b0);
           ob = max(min(ob, b1), oa);
-          const uint32_t in_bytes = (uint32_t)((ib - ia) * 4);
-          const uint32_t out_bytes = (uint32_t)((ob - oa) * 4);
-          const uint32_t tile_bytes = __reduce_add_sync(0xffffffffu, 4 * (in_bytes + out_bytes));
+          const uint32_t run_in = (uint32_t)((ib - ia) * 4);
+          const uint32_t run_out = (uint32_t)((ob - oa) * 4);
+          const uint32_t tile_bytes = __reduce_add_sync(0xffffffffu, 4 * (run_in + run_out));
           if (lane == 0) {
             write_stage_hdr(sb, jb, g0, g1, n_out, n_edges, (int)(K * g0 - a0), (int)(o0 - b0),
                             d.e_first);
@@ -671,14 +679,14 @@ __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const 
           if (lane == 10)
             bulk_g2s(s_cand + stage * kRoundSlots, J.rcand + lt * kRoundSlots, 4 * kRoundSlots,
                      &full[stage]);
-          if (in_bytes)
+          if (run_in)
             for (int pl = 0; pl < 4; ++pl)
               bulk_g2s(sb + J.off_in + ((size_t)pl * J.in_cap + (ia - a0)) * 4,
-                       J.inner + pl * J.in_stride + ia, in_bytes, &full[stage]);
-          if (out_bytes)
+                       J.inner + pl * J.in_stride + ia, run_in, &full[stage]);
+          if (run_out)
             for (int pl = 0; pl < 4; ++pl)
               bulk_g2s(sb + J.off_out + ((size_t)pl * J.out_cap + (oa - b0)) * 4,
-                       J.outer + pl * J.out_stride + oa, out_bytes, &full[stage]);
+                       J.outer + pl * J.out_stride + oa, run_out, &full[stage]);
         }
         // filtered instance: record bytes are counted per job, after the
         // copies, and added to the job's counter when the job changes (and at
