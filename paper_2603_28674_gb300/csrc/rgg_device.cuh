@@ -19,12 +19,12 @@
 //
 // Rounds: round r of a tile is its samples [31r, 31r+31) and the intervals
 // that follow its local samples 31r-1 .. 31r+30 (those a consumer warp tests
-// in one step).  Per round, computed when the tiles are set: a bounding
-// sphere of those intervals' outer spheres and their range of outer records.
-// Spatial filter (Sec. 4.3, "spatially filtered many-to-many checking"):
-// before each pass a small kernel tests every round's bounding sphere
-// against the pass's moved boxes; the producer copies only the rounds some
-// box can reach, and skips a tile none can.
+// in one step).  Opt-in spatial filter (Sec. 4.3, "spatially filtered
+// many-to-many checking"): while it is on, every round has a bounding
+// sphere of those intervals' outer spheres and their range of outer records
+// (recomputed whenever the tiles change); before each pass a small kernel
+// tests the spheres against the pass's moved boxes, and the producer copies
+// only the rounds some box can reach and skips a tile none can.
 #pragma once
 
 #include <cstdint>

@@ -214,17 +214,20 @@ __global__ void box_prep_kernel(const __grid_constant__ BoxPrepParams p) {
 // ===========================================================================
 // a2..a5: persistent streaming classification
 // ===========================================================================
-// One CTA per SM.  Warp 0 is the producer: it walks this CTA's contiguous
-// range of tiles and, for each, bulk-copies the tile's edge table and its 4
-// inner and 4 outer record planes into the next slot of an NSTAGE-deep ring
-// of shared-memory stages (TMA bulk copies completing on the slot's `full`
-// mbarrier).  Every other warp is a consumer that takes whole tiles on its
-// own (no CTA-wide barriers): it grabs the next slot, tests the tile's outer
-// spheres against the pass's moved boxes (a3), its inner spheres against the
-// boxes their enclosing outer spheres touched (a4), releases the slot, and
-// ORs the tile's per-edge hit / touch bits into the global per-edge
-// accumulators (a5).  The merge kernel then updates the per-edge box sets
-// and labels (a6).
+// One CTA per SM.  Warp 0 is the producer: it takes chunks of tiles from a
+// launch-wide counter and, for each tile, bulk-copies the tile's edge table
+// and its 4 inner and 4 outer record planes into the next slot of an
+// NSTAGE-deep ring of shared-memory stages (TMA bulk copies completing on
+// the slot's `full` mbarrier).  Every other warp is a consumer that takes
+// work items, rounds of 31 configurations, from a shared counter (no
+// CTA-wide barriers): it tests its round's outer spheres against the pass's
+// moved boxes (a3) and the inner spheres against the boxes their enclosing
+// outer spheres touched (a4), into per-stage accumulators.  The warp that
+// finishes a tile's last round releases the slot and ORs the tile's
+// per-edge hit / touch bits into the global per-edge accumulators (a5).  The
+// merge kernel then updates the per-edge box sets and labels (a6).  The
+// FILTER instance serves the opt-in spatial filter: it skips tiles and
+// rounds that no moved box can reach.
 __device__ __forceinline__ float box_dist2(float x, float y, float z, const float4* __restrict__ B) {
   const float4 a0 = B[1], a1 = B[2], a2 = B[3], h = B[4];
   const float p0 = fmaf(a0.x, x, fmaf(a0.y, y, fmaf(a0.z, z, -a0.w)));
