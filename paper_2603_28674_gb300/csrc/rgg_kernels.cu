@@ -1125,17 +1125,30 @@ __device__ __forceinline__ float seg_box_dist2(const float p[3], const float dlt
 // best is skipped, so the minimum is exact.  The warp stops at the first
 // clearance below -thr (RED); otherwise the edge is GREEN when the minimum
 // is at least thr, and stays GRAY in between.
+// Order-preserving map of a float onto an unsigned int (for atomicMin).
+__device__ __forceinline__ uint32_t float_key(float f) {
+  const uint32_t b = __float_as_uint(f);
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float key_float(uint32_t k) {
+  return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+
 __global__ void __launch_bounds__(256) resolve_gray_kernel(const __grid_constant__ ResolveParams p) {
-  __shared__ float s_box[8][32][16];
-  const uint32_t lane = threadIdx.x & 31;
-  const uint32_t wib = threadIdx.x >> 5;
-  const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
-  const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  // One block per gray edge at a time: its 256 threads take the edge's
+  // configurations in steps of 256 (a long edge no longer runs on one warp).
+  __shared__ float s_box[32][16];
+  __shared__ uint32_t s_best;                 // block's running minimum (float_key)
+  __shared__ float s_red_best[8];
+  __shared__ unsigned long long s_evals[8];
+  const uint32_t tid = threadIdx.x;
+  const uint32_t lane = tid & 31;
+  const uint32_t wib = tid >> 5;
   const uint32_t L = p.L, Wm = p.Wm;
-  for (uint64_t e = warp; e < p.n_edges; e += nwarps) {
+  for (uint64_t e = blockIdx.x; e < p.n_edges; e += gridDim.x) {
     const uint8_t lab = p.labels[e];
     if (lab != 1) {
-      if (lane == 0) {
+      if (tid == 0) {
         p.out[e] = lab;
         p.clearance[e] = __int_as_float(0x7fc00000);
       }
@@ -1147,13 +1160,15 @@ __global__ void __launch_bounds__(256) resolve_gray_kernel(const __grid_constant
     const double* qa = p.qa + e * L;
     const double* qb = p.qb + e * L;
     const uint32_t* tw = p.touch + e * Wm;
+    if (tid == 0) s_best = float_key(INFINITY);
     float best = INFINITY;
     unsigned long long evals = 0;
     bool red = false;
     uint32_t w = 0, word = Wm ? tw[0] : 0u;
     for (;;) {
-      // the next up to 32 boxes of the touch set (every lane walks the words)
+      // the next up to 32 boxes of the touch set (every thread walks the words)
       int cnt = 0;
+      __syncthreads();  // the previous batch's boxes are no longer read
       while (cnt < 32 && w < Wm) {
         if (word == 0u) {
           if (++w < Wm) word = tw[w];
@@ -1161,17 +1176,19 @@ __global__ void __launch_bounds__(256) resolve_gray_kernel(const __grid_constant
         }
         const uint32_t b = 32u * w + (uint32_t)(__ffs(word) - 1);
         word &= word - 1u;
-        if ((uint32_t)cnt == lane) {
+        if ((uint32_t)cnt == tid) {
           const float4* src = reinterpret_cast<const float4*>(p.table + 16 * (size_t)b);
-          float4* dst = reinterpret_cast<float4*>(s_box[wib][lane]);
+          float4* dst = reinterpret_cast<float4*>(s_box[tid]);
           for (int c = 0; c < 4; ++c) dst[c] = src[c];
         }
         ++cnt;
       }
-      __syncwarp();
+      __syncthreads();
       if (cnt == 0) break;
-      for (uint64_t c0 = 0; c0 <= m && !red; c0 += 32) {
-        const uint64_t c = c0 + lane;
+      for (uint64_t c0 = 0; c0 <= m && !red; c0 += 256) {
+        const uint64_t c = c0 + tid;
+        // prune against the block's best so far, not only this thread's
+        best = fminf(best, key_float(*reinterpret_cast<volatile uint32_t*>(&s_best)));
         if (c <= m) {
           const double tt = (double)c * inv_m;
           float R[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
@@ -1192,7 +1209,7 @@ __global__ void __launch_bounds__(256) resolve_gray_kernel(const __grid_constant
                                           (on[2] - o[2]) * (on[2] - o[2]));
             const float rad = p.radius[i];
             for (int b = 0; b < cnt; ++b) {
-              const float* B = s_box[wib][b];
+              const float* B = s_box[b];
               const float hx = B[12], hy = B[13], hz = B[14];
               const float dx = mx - B[0], dy = my - B[1], dz = mz - B[2];
               // lower bound of the pair's clearance from the two bounding spheres
@@ -1227,17 +1244,26 @@ __global__ void __launch_bounds__(256) resolve_gray_kernel(const __grid_constant
             for (int r = 0; r < 3; ++r) o[r] = on[r];
           }
         }
-        red = __any_sync(0xffffffffu, best <= -p.thr);
+        if (best < INFINITY) atomicMin(&s_best, float_key(best));
+        red = __syncthreads_or(best <= -p.thr) != 0;
       }
-      __syncwarp();
       if (red) break;
     }
-    // warp minimum of the lanes' clearances and of the evaluation counts
+    // block minimum of the clearances and sum of the evaluation counts
     for (int off = 16; off; off >>= 1) {
       best = fminf(best, __shfl_xor_sync(0xffffffffu, best, off));
       evals += __shfl_xor_sync(0xffffffffu, evals, off);
     }
     if (lane == 0) {
+      s_red_best[wib] = best;
+      s_evals[wib] = evals;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      for (int k = 1; k < 8; ++k) {
+        best = fminf(best, s_red_best[k]);
+        evals += s_evals[k];
+      }
       const uint8_t res = best <= -p.thr ? 2 : (best >= p.thr ? 0 : 1);
       p.out[e] = res;
       p.clearance[e] = best;
@@ -1246,6 +1272,7 @@ __global__ void __launch_bounds__(256) resolve_gray_kernel(const __grid_constant
       if (res == 0) atomicAdd(&p.work[2], 1ull);
       atomicAdd(&p.work[3], evals);
     }
+    __syncthreads();  // the shared results are read before the next edge
   }
 }
 
@@ -1385,8 +1412,14 @@ cudaError_t launch_round_bounds(const RoundBoundsParams& p, int num_sms, cudaStr
 
 cudaError_t launch_resolve_gray(const ResolveParams& p, int num_sms, cudaStream_t s) {
   if (p.n_edges == 0) return cudaSuccess;
-  const uint64_t want = (p.n_edges + 7) / 8;  // 8 warps per block, a warp per edge
-  const uint64_t cap = (uint64_t)num_sms * 8;
+  // a block per edge at a time; as many blocks as are resident at once, so
+  // that every block starts with the launch
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, resolve_gray_kernel, 256, 0) !=
+          cudaSuccess || per_sm < 1)
+    per_sm = 1;
+  const uint64_t want = p.n_edges;
+  const uint64_t cap = (uint64_t)num_sms * (uint64_t)per_sm;
   resolve_gray_kernel<<<(unsigned)(want < cap ? want : cap), 256, 0, s>>>(p);
   return cudaGetLastError();
 }
