@@ -39,8 +39,9 @@ METRIC = "RGG edges classified/s"
 UNIT = "edges/s"
 FALLBACK_HBM_GBS = 6800.0
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "classify_kernel_traffic.txt")
-KERNEL_SOURCES = [os.path.join(ROOT, "paper_2603_28674_gb300", "csrc", f)
-                  for f in ("rgg_kernels.cu", "rgg_device.cuh", "rgg_kernels.h")]
+KERNEL_HEADERS = [os.path.join(ROOT, "paper_2603_28674_gb300", "csrc", f)
+                  for f in ("rgg_device.cuh", "rgg_kernels.h")]
+KERNEL_FILE = os.path.join(ROOT, "paper_2603_28674_gb300", "csrc", "rgg_kernels.cu")
 
 
 def parse():
@@ -106,9 +107,16 @@ def workload_config(name: str, sc) -> dict:
 
 
 def kernel_sha() -> str:
+    """Hash of the code classify_kernel is compiled from: the two kernel
+    headers and the classify section of rgg_kernels.cu (from its a2..a5
+    banner to the a6 banner), so that edits to the other kernels do not
+    invalidate the traffic profile."""
     h = hashlib.sha256()
-    for p in KERNEL_SOURCES:
+    for p in KERNEL_HEADERS:
         h.update(open(p, "rb").read())
+    t = open(KERNEL_FILE, "rb").read()
+    a = t.index(b"// a2..a5: persistent streaming classification")
+    h.update(t[a:t.index(b"// a6: merge", a)])
     return h.hexdigest()[:16]
 
 
