@@ -110,7 +110,9 @@ struct ResolveParams {
 // splines, a uniform grid over the OBBs, and the per-pass queries.
 // ---------------------------------------------------------------------------
 // OBB record: 4 float4 = (centre, 0), (u1, h1), (u2, h2), (u3, h3).
-constexpr uint32_t kObbChunk = 4096;  // grid-cell boxes per query work item
+// Grid-cell boxes per query work item, chosen per pass between these bounds
+// from the pass's total work (obb_pairs_kernel).
+constexpr uint32_t kObbChunkMin = 256, kObbChunkMax = 4096;
 struct ObbBuildParams {
   uint32_t L, K;
   double a[kMaxBuildLinks], alpha[kMaxBuildLinks], d[kMaxBuildLinks], radius[kMaxBuildLinks];
@@ -155,7 +157,8 @@ struct ObbQueryParams {
   const float* boxes;         // [C][24] derived records of the pass's boxes
   uint32_t* edge_acc;         // [N][2]
   uint2* pairs;               // (box position | chunk << 5, cell) work list
-  uint32_t* counters;         // [0] pairs listed, [1] pairs taken
+  uint32_t* counters;         // [0] pairs listed, [1] pairs taken, [2] this pass's chunk size
+  uint32_t target_items;      // work items the chunk size aims at
   uint32_t pair_cap;
   uint32_t filter;            // 0: every non-empty cell for every box (no spatial filter)
   unsigned long long* work;   // [2] SAT tests, spline-segment tests (may be null)

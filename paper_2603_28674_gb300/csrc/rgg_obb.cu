@@ -343,35 +343,65 @@ __device__ __forceinline__ void box_aabb(const float4* B, float margin, float lo
 }
 
 // One block: the (moved box, cell, chunk) work items -- every chunk of
-// kObbChunk boxes of each non-empty cell that a moved box's AABB meets (every
-// non-empty cell without the spatial filter).  Chunks keep crowded cells (the
-// ones near the robot's base hold most edges' first bodies) from landing on
-// a single block.
+// boxes of each non-empty cell that a moved box's AABB meets (every non-empty
+// cell without the spatial filter).  Chunks keep crowded cells (the ones near
+// the robot's base hold most edges' first bodies) from landing on a single
+// block.  A first sweep sums the boxes of the pass's (box, cell) pairs and
+// picks the chunk size: the smallest power of two in [kObbChunkMin,
+// kObbChunkMax] that gives at most target_items work items.  Fixed sizes
+// showed why: on the 7-DOF roadmap chunks of 1,024 instead of 4,096 halved
+// the query time (more items balance the blocks' long test chains), and on
+// the large one chunks of 512 doubled it (per-item overhead).
 __global__ void __launch_bounds__(256) obb_pairs_kernel(const __grid_constant__ ObbQueryParams p) {
-  for (uint32_t b = 0; b < p.C; ++b) {
-    const float4* B = reinterpret_cast<const float4*>(p.boxes) + 6 * b;
-    float lo[3], hi[3];
-    box_aabb(B, p.margin, lo, hi);
-    int x0 = 0, y0 = 0, z0 = 0, x1 = (int)p.g.gx - 1, y1 = (int)p.g.gy - 1, z1 = (int)p.g.gz - 1;
-    if (p.filter) {
-      x0 = cell_coord(lo[0], p.g.ox, p.g.cell, p.g.gx);
-      x1 = cell_coord(hi[0], p.g.ox, p.g.cell, p.g.gx);
-      y0 = cell_coord(lo[1], p.g.oy, p.g.cell, p.g.gy);
-      y1 = cell_coord(hi[1], p.g.oy, p.g.cell, p.g.gy);
-      z0 = cell_coord(lo[2], p.g.oz, p.g.cell, p.g.gz);
-      z1 = cell_coord(hi[2], p.g.oz, p.g.cell, p.g.gz);
+  __shared__ unsigned long long s_total;
+  __shared__ uint32_t s_chunk;
+  if (threadIdx.x == 0) s_total = 0;
+  __syncthreads();
+  for (int sweep = 0; sweep < 2; ++sweep) {
+    const uint32_t chunk = sweep ? s_chunk : 0u;
+    unsigned long long mine = 0;
+    for (uint32_t b = 0; b < p.C; ++b) {
+      const float4* B = reinterpret_cast<const float4*>(p.boxes) + 6 * b;
+      float lo[3], hi[3];
+      box_aabb(B, p.margin, lo, hi);
+      int x0 = 0, y0 = 0, z0 = 0, x1 = (int)p.g.gx - 1, y1 = (int)p.g.gy - 1, z1 = (int)p.g.gz - 1;
+      if (p.filter) {
+        x0 = cell_coord(lo[0], p.g.ox, p.g.cell, p.g.gx);
+        x1 = cell_coord(hi[0], p.g.ox, p.g.cell, p.g.gx);
+        y0 = cell_coord(lo[1], p.g.oy, p.g.cell, p.g.gy);
+        y1 = cell_coord(hi[1], p.g.oy, p.g.cell, p.g.gy);
+        z0 = cell_coord(lo[2], p.g.oz, p.g.cell, p.g.gz);
+        z1 = cell_coord(hi[2], p.g.oz, p.g.cell, p.g.gz);
+      }
+      const uint32_t nx = (uint32_t)(x1 - x0 + 1), ny = (uint32_t)(y1 - y0 + 1);
+      const uint32_t ncell = nx * ny * (uint32_t)(z1 - z0 + 1);
+      for (uint32_t k = threadIdx.x; k < ncell; k += blockDim.x) {
+        const uint32_t x = x0 + k % nx, y = y0 + (k / nx) % ny, z = z0 + k / (nx * ny);
+        const uint32_t cell = (z * p.g.gy + y) * p.g.gx + x;
+        const uint32_t items = p.cell_off[cell + 1] - p.cell_off[cell];
+        if (items == 0) continue;
+        if (sweep == 0) {
+          mine += items;
+          continue;
+        }
+        const uint32_t chunks = (items + chunk - 1) / chunk;
+        const uint32_t slot = atomicAdd(&p.counters[0], chunks);
+        for (uint32_t c = 0; c < chunks; ++c)
+          if (slot + c < p.pair_cap) p.pairs[slot + c] = make_uint2(b | (c << 5), cell);
+      }
     }
-    const uint32_t nx = (uint32_t)(x1 - x0 + 1), ny = (uint32_t)(y1 - y0 + 1);
-    const uint32_t ncell = nx * ny * (uint32_t)(z1 - z0 + 1);
-    for (uint32_t k = threadIdx.x; k < ncell; k += blockDim.x) {
-      const uint32_t x = x0 + k % nx, y = y0 + (k / nx) % ny, z = z0 + k / (nx * ny);
-      const uint32_t cell = (z * p.g.gy + y) * p.g.gx + x;
-      const uint32_t items = p.cell_off[cell + 1] - p.cell_off[cell];
-      if (items == 0) continue;
-      const uint32_t chunks = (items + kObbChunk - 1) / kObbChunk;
-      const uint32_t slot = atomicAdd(&p.counters[0], chunks);
-      for (uint32_t c = 0; c < chunks; ++c)
-        if (slot + c < p.pair_cap) p.pairs[slot + c] = make_uint2(b | (c << 5), cell);
+    if (sweep == 0) {
+      if (mine) atomicAdd(&s_total, mine);
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        const uint64_t t = p.target_items ? p.target_items : 1u;
+        const uint64_t want = (s_total + t - 1) / t;
+        uint32_t c = kObbChunkMin;
+        while (c < kObbChunkMax && c < want) c <<= 1;
+        s_chunk = c;
+        p.counters[2] = c;
+      }
+      __syncthreads();
     }
   }
 }
@@ -442,6 +472,7 @@ __global__ void __launch_bounds__(256) obb_query_kernel(const __grid_constant__ 
   __shared__ uint2 s_pair;
   __shared__ unsigned long long s_work[2];
   const uint32_t total = min(p.counters[0], p.pair_cap);
+  const uint32_t chunk = p.counters[2];  // chosen by obb_pairs_kernel for this pass
   for (;;) {
     if (threadIdx.x == 0) {
       const uint32_t k = atomicAdd(&p.counters[1], 1u);
@@ -453,8 +484,8 @@ __global__ void __launch_bounds__(256) obb_query_kernel(const __grid_constant__ 
     __syncthreads();
     if (pr.x == 0xffffffffu) break;
     const uint32_t bpos = pr.x & 31u, cell = pr.y;
-    const uint32_t k0 = p.cell_off[cell] + (pr.x >> 5) * kObbChunk;
-    const uint32_t k1 = min(p.cell_off[cell + 1], k0 + kObbChunk);
+    const uint32_t k0 = p.cell_off[cell] + (pr.x >> 5) * chunk;
+    const uint32_t k1 = min(p.cell_off[cell + 1], k0 + chunk);
     const float4* B = reinterpret_cast<const float4*>(p.boxes) + 6 * bpos;
     float blo[3], bhi[3];
     box_aabb(B, p.margin, blo, bhi);
@@ -530,10 +561,19 @@ cudaError_t launch_obb_grid(const ObbGridParams& p, cudaStream_t s) {
 
 cudaError_t launch_obb_query(const ObbQueryParams& p, int num_sms, cudaStream_t s) {
   if (p.C == 0) return cudaSuccess;
-  obb_pairs_kernel<<<1, 256, 0, s>>>(p);
+  // the query grid: as many blocks as are resident at once; the chunk size
+  // aims at about 4 work items per block
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, obb_query_kernel, 256, 0) !=
+          cudaSuccess || per_sm < 1)
+    per_sm = 1;
+  const uint32_t blocks = (uint32_t)num_sms * (uint32_t)per_sm;
+  ObbQueryParams q = p;
+  q.target_items = 4 * blocks;
+  obb_pairs_kernel<<<1, 256, 0, s>>>(q);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  obb_query_kernel<<<(unsigned)(num_sms * 4), 256, 0, s>>>(p);
+  obb_query_kernel<<<blocks, 256, 0, s>>>(q);
   return cudaGetLastError();
 }
 

@@ -162,11 +162,11 @@ int build_obb(rgg_roadmap* r, EdgeState* es, const rgg_robot_desc* robot, const 
   if (e == cudaSuccess) e = launch_obb_grid(gp, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   cudaFree(d_cc);
-  // every moved box may list every chunk of every cell
+  // every moved box may list every chunk of every cell, at the smallest chunk
   es->pair_cap = (uint32_t)std::min<uint64_t>(
-      0xffffffffull, (uint64_t)kBoxesPerPass * (es->n_cells + items / kObbChunk + 1));
+      0xffffffffull, (uint64_t)kBoxesPerPass * (es->n_cells + items / kObbChunkMin + 1));
   RGG_OB(es->d_pairs, es->pair_cap);
-  RGG_OB(es->d_qcnt, 2);
+  RGG_OB(es->d_qcnt, 3);
 #undef RGG_OB
   if (e != cudaSuccess) return done(cuda_status(e));
   return done(RGG_OK);
@@ -220,7 +220,7 @@ int classify_group_obb(rgg_roadmap_t* rs, uint32_t n, cudaStream_t s) {
       q.pair_cap = es.pair_cap;
       q.filter = r->obb_filter ? 1u : 0u;
       q.work = r->d_obbwork;
-      RGG_CK(cudaMemsetAsync(es.d_qcnt, 0, 2 * sizeof(uint32_t), s));
+      RGG_CK(cudaMemsetAsync(es.d_qcnt, 0, 3 * sizeof(uint32_t), s));
       cudaEvent_t* ev = r->timing ? next_events(r) : nullptr;
       if (ev) RGG_CK(cudaEventRecord(ev[0], s));
       RGG_CK(launch_obb_query(q, r->num_sms, s));
