@@ -7,7 +7,7 @@
 //   obb_build_kernel    offline: FP64 kinematics, boxes, greedy shortcuts
 //   obb_bounds_kernel   offline: extent of the OBBs (grid sizing)
 //   obb_grid_kernel     offline: cell incidences (count, then fill)
-//   obb_pairs_kernel    per pass: (moved box, grid cell) work list
+//   obb_pairs_kernel    per pass: chunk size, (moved box, grid cell, chunk) work list
 //   obb_query_kernel    per pass: the tests, OR-ed into the per-edge bits
 #include <cstdio>
 
