@@ -510,6 +510,60 @@ def test_edge_obbs_hold_the_swept_capsules(oracle):
                     assert np.all(np.abs(R.T @ (p - c)) <= h + 1e-9), (e, t, i)
 
 
+def _obb_parts(ob):
+    return ob[:3], ob[3:12].reshape(3, 3), ob[12:]
+
+
+def test_edge_obbs_moving_planar_links_hand_derived(oracle):
+    """Moving edges whose boxes follow by hand (Sec. 4.2's per-body box; the
+    axes come from the motion, the growth is the outer spheres' motion bound).
+
+    Planar links of length 0.3 m and radius 0.03 m; a joint sweeps 0 -> 0.5
+    rad in 4 steps of 0.125 rad (5 configurations, the middle one at 0.25).
+    A link that rotates rigidly about a fixed point has its axis u1 along the
+    bisector (cos .25, sin .25, 0); its midpoint moves along a chord, which is
+    normal to the bisector, so u2 = (-sin .25, cos .25, 0) and u3 = +z.  A
+    link point at distance s from the pivot projects to s cos(q - .25) on u1
+    and s sin(q - .25) on u2.  Each half-extent grows by R plus half of
+    sum_{j<=i} |dq_j| rho_{j,i} with rho_{j,i} = sum_{m=j..i} l_m."""
+    c, s = math.cos(0.25), math.sin(0.25)
+    u1, u2, u3 = np.array([c, s, 0.0]), np.array([-s, c, 0.0]), np.array([0.0, 0.0, 1.0])
+    rot = np.stack([u1, u2, u3], axis=1)
+    dq = 0.5 / 4
+
+    # one link about the origin: spans [0, 0.3] on u1, +-0.3 sin .25 on u2
+    ob = oracle.edge_obbs(W.planar_arm(1, 0.3, 0.03, 4), [0.0], [0.5], 0.125)
+    ctr, R, h = _obb_parts(ob[0])
+    grow = 0.03 + 0.5 * 0.3 * dq
+    np.testing.assert_allclose(R, rot, atol=1e-12)
+    np.testing.assert_allclose(ctr, 0.15 * u1, atol=1e-12)
+    np.testing.assert_allclose(h, [0.15 + grow, 0.3 * s + grow, grow], atol=1e-12)
+
+    # two links, joint 0 turning: link 1 (from 0.3 to 0.6 m along the arm)
+    # turns rigidly about the origin; rho_{0,1} = l_0 + l_1
+    ob = oracle.edge_obbs(W.planar_arm(2, 0.3, 0.03, 4), [0.0, 0.0], [0.5, 0.0], 0.125)
+    ctr, R, h = _obb_parts(ob[1])
+    lo1 = 0.3 * c - 0.3          # the near end at the first / last configuration
+    grow = 0.03 + 0.5 * (0.3 + 0.3) * dq
+    np.testing.assert_allclose(R, rot, atol=1e-12)
+    np.testing.assert_allclose(ctr, 0.3 * u1 + 0.5 * (lo1 + 0.3) * u1, atol=1e-12)
+    np.testing.assert_allclose(h, [0.5 * (0.3 - lo1) + grow, 0.6 * s + grow, grow], atol=1e-12)
+
+    # two links, joint 1 turning: link 0 rests (no displacement: u2 is the
+    # world axis least aligned with u1 = x, i.e. y), link 1 turns about
+    # (0.3, 0, 0); rho_{1,1} = l_1 and joint 0 contributes nothing
+    ob = oracle.edge_obbs(W.planar_arm(2, 0.3, 0.03, 4), [0.0, 0.0], [0.0, 0.5], 0.125)
+    ctr, R, h = _obb_parts(ob[0])
+    np.testing.assert_allclose(R, np.eye(3), atol=1e-12)
+    np.testing.assert_allclose(ctr, [0.15, 0, 0], atol=1e-12)
+    np.testing.assert_allclose(h, [0.18, 0.03, 0.03], atol=1e-12)
+    ctr, R, h = _obb_parts(ob[1])
+    grow = 0.03 + 0.5 * 0.3 * dq
+    np.testing.assert_allclose(R, rot, atol=1e-12)
+    np.testing.assert_allclose(ctr, [0.3, 0, 0] + 0.15 * u1, atol=1e-12)
+    np.testing.assert_allclose(h, [0.15 + grow, 0.3 * s + grow, grow], atol=1e-12)
+
+
 def test_edge_splines_follow_the_shortcut_rule(oracle):
     """Kept vertices are original centres, first and last included; every
     dropped centre lies closer than R to its covering segment; and no kept
