@@ -61,8 +61,11 @@ def parse():
     ap.add_argument("--resolve", type=int, default=0, metavar="F",
                     help="also time the non-lazy resolution of the gray edges at F-times "
                          "finer resampling (0: off)")
-    ap.add_argument("--serve-seconds", type=float, default=3.0,
-                    help="serve workload: seconds of Poisson arrivals at 2000 requests/s")
+    ap.add_argument("--serve-seconds", type=float, default=10.0,
+                    help="serving: seconds of Poisson arrivals at 2000 requests/s")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="default workload: skip the mixed-label scene and the batched and "
+                         "serving measurements that follow the headline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     return ap.parse_args()
@@ -88,7 +91,9 @@ def make_scene(name: str, n_updates: int):
     return W.workload_planar(n_updates=n_updates)
 
 
-def workload_config(name: str, sc) -> dict:
+def workload_config(name: str, sc, world: int = 1) -> dict:
+    """The workload's description, the same for the GPU arm and the oracle's
+    reference arm (only what the inputs fix, nothing measured)."""
     rm = sc.roadmap
     moved = len(sc.updates[0].ids) if sc.updates else 0
     cfg = {
@@ -102,6 +107,8 @@ def workload_config(name: str, sc) -> dict:
         "boxes": sc.boxes.count,
         "moved_per_update": moved,
         "record_dtype": "fp32",
+        "l2": "records > L2 (129 MB); no flush needed",
+        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
     }
     return cfg
 
@@ -166,7 +173,7 @@ class ClockSampler:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.fh,
+                 "--format=csv,noheader,nounits", "-lms", "25"], stdout=self.fh,
                 stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -294,7 +301,7 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000 * t / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": workload_config(args.workload, sc),
+        "config": workload_config(args.workload, sc, int(os.environ.get("WORLD_SIZE", "1"))),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.max_threads(),
                          "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -477,18 +484,20 @@ def run_gpu(args):
                "single_thread_value": rate1,
                "single_thread_sample": f"{n_1} random edges, {t_1:.1f} s, one thread"}
 
-    cfg = workload_config(args.workload, sc)
-    cfg.update({"samples": info["num_samples"], "record_gb": info["record_bytes"] / 1e9,
-                "l2": "records > L2 (129 MB); no flush needed", "parallelism":
-                f"replicas x{world}" if world > 1 else "single GPU",
-                "tile_samples": info["tile_samples"], "grid_ctas": info["grid_ctas"]})
+    cfg = workload_config(args.workload, sc, world)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": cfg,
-        "sphere_box_tests_per_s": world * (info["num_inner"] + info["num_outer"]) * moved
-        * args.steps / (ms / 1000.0),
+        "sizes": {"samples": info["num_samples"], "record_gb": info["record_bytes"] / 1e9,
+                  "tile_samples": info["tile_samples"], "grid_ctas": info["grid_ctas"]},
+        # every (sphere, moved box) pair the definition asks about; the kernel
+        # culls most of them per warp before an exact test
+        "sphere_box_tests_per_s": {
+            "logical": world * (info["num_inner"] + info["num_outer"]) * moved
+            * args.steps / (ms / 1000.0),
+            "note": "(inner + outer spheres) x moved boxes per update, per second"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      # ncu-measured DRAM bytes per launch over the live launch time
@@ -514,13 +523,73 @@ def run_gpu(args):
         line["resolve"] = resolve
     if persist is not None:
         line["persist"] = persist
+    extras = (args.workload == "large" and world == 1 and not args.no_extras)
+    if extras:
+        line["mixed_scene"] = measure_mixed(r, args, stream, peak)
     r.close()
+    del dev_poses
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    if extras:
+        # the latency half of the metric: the batched form (workload 4) and
+        # the served form (workload 5) against one launch per update
+        with ClockSampler(local) as clk_b:
+            line["batched"] = measure_batched(args, args.steps, max(3, args.warmup),
+                                              args.roadmaps)
+        line["batched"]["clocks"] = clk_b.summary()
+        with ClockSampler(local) as clk_s:
+            line["serving"] = measure_serving(args, args.serve_seconds)
+        line["serving"]["clocks"] = clk_s.summary()
     if rank == 0:
         print(json.dumps(line))
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
     return 0
+
+
+def measure_mixed(r, args, stream, peak: float) -> dict:
+    """The same roadmap among the mixed-label boxes (256 small boxes spread
+    over a 4 m cube, 32 moved per update): every box is placed at its new
+    pose, then K updates are timed like the headline.  The classify kernel's
+    HBM fraction on a scene where green, gray and red edges all occur."""
+    import torch
+    boxes, ups = W.large_mixed_boxes(n_updates=max(8, args.warmup + args.steps))
+    dev = [torch.from_numpy(u.poses.astype(np.float32)).to(stream.device) for u in ups]
+    r.update_obstacles(np.arange(boxes.count), boxes.poses().astype(np.float32), stream)
+    r.classify(stream)
+
+    def step(i):
+        r.update_obstacles(ups[i % len(ups)].ids, dev[i % len(ups)], stream)
+        r.classify(stream)
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    r.set_kernel_timing(True)
+    r.kernel_time()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(args.steps):
+        step(args.warmup + i)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    k_ms, m_ms, n = r.kernel_time()
+    r.set_kernel_timing(False)
+    info = r.info()
+    lab = r.fetch_labels(stream=stream)
+    r.check_status(stream)
+    k_avg = k_ms / max(1, n)
+    b_alg = algorithmic_bytes(info)
+    mix = np.bincount(lab, minlength=3) / max(1, lab.size)
+    return {"boxes": "256, half-extents U[0.02, 0.06] m, centres in a 4 m cube",
+            "moved_per_update": 32, "steps": args.steps, "ms_per_step": ms / args.steps,
+            "edges_per_s": info["num_edges"] * args.steps / (ms / 1e3),
+            "kernel_ms": k_avg, "merge_kernel_ms": m_ms / max(1, n),
+            "bytes_per_launch": b_alg, "achieved_gbs": b_alg / (k_avg / 1e3) / 1e9,
+            "frac": b_alg / (k_avg / 1e3) / 1e9 / peak,
+            "labels": {"green": float(mix[0]), "gray": float(mix[1]), "red": float(mix[2])}}
 
 
 def measure_persist(r, robot, m: int, stream) -> dict:
@@ -686,21 +755,34 @@ def run_geometry(args):
     return 0
 
 
-def run_batched(args):
+def sjf_groups(sizes, n_groups: int):
+    """Roadmap indices in shortest-job-first order (record bytes), cut into
+    n_groups groups of (nearly) equal count: latency percentiles are taken
+    over roadmaps, so equal counts put the median roadmap at the end of the
+    middle group."""
+    order = sorted(range(len(sizes)), key=lambda k: (sizes[k], k))
+    n_groups = max(1, min(n_groups, len(order)))
+    cuts = [round(g * len(order) / n_groups) for g in range(n_groups + 1)]
+    return [order[a:b] for a, b in zip(cuts[:-1], cuts[1:]) if b > a]
+
+
+def measure_batched(args, steps: int, warmup: int, n_roadmaps: int, n_groups: int = 8):
     """Workload 4: many independent roadmaps, each with its own robot, boxes
-    and update per step.  'plain' classifies them one launch sequence per
-    roadmap; 'batched' runs every roadmap's pass in one persistent launch
-    (rgg_classify_many) at the shape the library's autotuner picked;
-    'graph' replays the whole step (every roadmap's update, then the batched
-    pass) as one captured CUDA graph.  Latency of a roadmap's update = from
-    the step's start (all updates issued together) to its labels being
-    ready."""
+    and update per step; every roadmap's update is issued at the start of the
+    step and its latency runs to its labels being ready (a CUDA event after
+    its last launch).  Modes:
+      plain        one launch sequence per roadmap, in arrival (index) order;
+      plain_sjf    the same, smallest roadmap first;
+      batched      roadmaps smallest first in n_groups persistent launches
+                   (rgg_classify_many per group), an event after each group;
+      one_launch   every roadmap's pass in one persistent launch;
+      graph        the whole step (every update, then one persistent launch)
+                   replayed as one captured CUDA graph.
+    All run at the launch shape the library's autotuner picked, and all apply
+    the same updates, so the final labels must agree."""
     import torch
-    torch.cuda.set_device(0)
-    from paper_2603_28674_gb300 import build
-    build.build()
     from paper_2603_28674_gb300 import rgg
-    scenes = W.workload_batched(n_roadmaps=args.roadmaps, n_updates=8)
+    scenes = W.workload_batched(n_roadmaps=n_roadmaps, n_updates=8)
     stream = torch.cuda.current_stream()
     rms = []
     for sc in scenes:
@@ -716,111 +798,143 @@ def run_batched(args):
     rec = sum(i["record_bytes"] for i in infos)
     dev = [[torch.from_numpy(u.poses.astype(np.float32)).cuda() for u in sc.updates]
            for sc in scenes]
+    n_up = min(len(sc.updates) for sc in scenes)
+    groups = sjf_groups([i["record_bytes"] for i in infos], n_groups)
+    sjf = [k for g in groups for k in g]
+    graphs = None
 
     def updates(step):
         for r, sc, d in zip(rms, scenes, dev):
             k = step % n_up
             r.update_obstacles(sc.updates[k].ids, d[k], stream)
 
-    n_up = min(len(sc.updates) for sc in scenes)
-    graphs = None
+    def event():
+        e = torch.cuda.Event(enable_timing=True)
+        e.record(stream)
+        return e
 
     def run(mode, steps, warm):
         step_ms, lat = [], []
         for i in range(warm + steps):
-            ev0 = torch.cuda.Event(enable_timing=True)
-            ends = []
-            ev0.record(stream)
+            ends = [None] * len(rms)
+            ev0 = event()
             if mode == "graph":
                 graphs[i % n_up].launch(stream)
             else:
                 updates(i)
-                if mode == "batched":
+                if mode == "one_launch":
                     rgg.classify_many(rms, stream)
+                elif mode == "batched":
+                    for g in groups:
+                        rgg.classify_many([rms[k] for k in g], stream)
+                        e = event()
+                        for k in g:
+                            ends[k] = e
                 else:
-                    for r in rms:
-                        r.classify(stream)
-                        e = torch.cuda.Event(enable_timing=True)
-                        e.record(stream)
-                        ends.append(e)
-            if not ends:
+                    for k in (sjf if mode == "plain_sjf" else range(len(rms))):
+                        rms[k].classify(stream)
+                        ends[k] = event()
+            if ends[0] is None:
                 # every roadmap's labels are ready when the shared launch ends
-                e = torch.cuda.Event(enable_timing=True)
-                e.record(stream)
+                e = event()
                 ends = [e] * len(rms)
+            last = event()
             torch.cuda.synchronize()
             if i >= warm:
-                step_ms.append(ev0.elapsed_time(ends[-1]))
+                step_ms.append(ev0.elapsed_time(last))
                 lat.extend(ev0.elapsed_time(e) for e in ends)
         return float(np.mean(step_ms)), np.array(lat), np.array(step_ms)
 
     out, final = {}, {}
-    with ClockSampler(0) as clocks:
-        for mode in ("plain", "batched", "graph"):
-            if mode == "graph":
-                # one graph per update index, reading the same device poses
-                graphs = [rgg.StepGraph(rms, [(sc.updates[k].ids, d[k])
-                                              for sc, d in zip(scenes, dev)])
-                          for k in range(n_up)]
-            ms, lat, st = run(mode, args.steps, args.warmup)
-            final[mode] = [r.fetch_labels(stream=stream) for r in rms]
-            # bytes one step must move: every record and each edge's pass result
-            b_step = sum(algorithmic_bytes(i) for i in infos)
-            out[mode] = {"ms_per_step": ms, "edges_per_s": n_edges / (ms / 1e3),
-                         "step_ms_min_med_max": [float(np.min(st)), float(np.median(st)),
-                                                 float(np.max(st))],
-                         "achieved_gbs": b_step / (ms / 1e3) / 1e9,
-                         "latency_ms_p50": float(np.percentile(lat, 50)),
-                         "latency_ms_p99": float(np.percentile(lat, 99))}
-    # every mode applies the same update sequence: the final labels agree
-    same = all(np.array_equal(a, b) and np.array_equal(a, c) for a, b, c in
-               zip(final["plain"], final["batched"], final["graph"]))
+    b_step = sum(algorithmic_bytes(i) for i in infos)
+    for mode in ("plain", "plain_sjf", "batched", "one_launch", "graph"):
+        if mode == "graph":
+            # one graph per update index, reading the same device poses
+            graphs = [rgg.StepGraph(rms, [(sc.updates[k].ids, d[k])
+                                          for sc, d in zip(scenes, dev)])
+                      for k in range(n_up)]
+        ms, lat, st = run(mode, steps, warmup)
+        final[mode] = [r.fetch_labels(stream=stream) for r in rms]
+        out[mode] = {"ms_per_step": ms, "edges_per_s": n_edges / (ms / 1e3),
+                     "step_ms_min_med_max": [float(np.min(st)), float(np.median(st)),
+                                             float(np.max(st))],
+                     "achieved_gbs": b_step / (ms / 1e3) / 1e9,
+                     "latency_ms_p50": float(np.percentile(lat, 50)),
+                     "latency_ms_p99": float(np.percentile(lat, 99))}
+    ref = final["plain"]
+    same = all(all(np.array_equal(a, b) for a, b in zip(ref, final[m])) for m in final)
     for r in rms:
         r.check_status(stream)
     nodes = graphs[0].nodes()
     for g in graphs:
         g.close()
+    for r in rms:
+        r.close()
+    del dev
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    b, p = out["batched"], out["plain"]
+    res = {"roadmaps": len(rms), "edges": n_edges, "record_gb": rec / 1e9,
+           "dof": sorted({i["num_links"] for i in infos}), "moved_per_update": "1-16 per roadmap",
+           "groups": len(groups), "graph_nodes": nodes,
+           "autotune": {"chosen": tuned[0] if tuned else None, "shapes_timed": len(tuned)},
+           "steps": steps, "warmup": warmup, "modes": out,
+           "batched_vs_plain": {"throughput": b["edges_per_s"] / p["edges_per_s"],
+                                "p50": p["latency_ms_p50"] / b["latency_ms_p50"],
+                                "p99": p["latency_ms_p99"] / b["latency_ms_p99"]},
+           "batched_vs_plain_sjf": {
+               "throughput": b["edges_per_s"] / out["plain_sjf"]["edges_per_s"],
+               "p50": out["plain_sjf"]["latency_ms_p50"] / b["latency_ms_p50"],
+               "p99": out["plain_sjf"]["latency_ms_p99"] / b["latency_ms_p99"]},
+           "labels_identical_across_modes": bool(same),
+           # per step: one update kernel per roadmap; per launch group box
+           # prep, classify and merge
+           "gpu_launches_per_step": {"batched": len(rms) + 3 * len(groups),
+                                     "plain": 4 * len(rms), "graph": len(rms) + 3}}
+    return res
+
+
+def run_batched(args):
+    """Workload 4 on its own line (see measure_batched); the headline value is
+    the CUDA-graph step's throughput."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2603_28674_gb300 import build
+    build.build()
     peak, peak_kind = hbm_peak()
-    b = out["graph"]
+    with ClockSampler(0) as clocks:
+        res = measure_batched(args, args.steps, args.warmup, args.roadmaps)
+    g = res["modes"]["graph"]
     line = {
-        "metric": METRIC, "value": b["edges_per_s"], "unit": UNIT, "n_gpus": 1,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": b["ms_per_step"],
+        "metric": METRIC, "value": g["edges_per_s"], "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": g["ms_per_step"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": f"batched {len(rms)} roadmaps", "edges": n_edges,
-                   "record_gb": rec / 1e9, "dof": sorted({i["num_links"] for i in infos}),
+        "config": {"workload": f"batched {res['roadmaps']} roadmaps", "edges": res["edges"],
+                   "record_gb": res["record_gb"], "dof": res["dof"],
                    "moved_per_update": "1-16 per roadmap", "l2": "records > L2; no flush needed"},
-        "roofline": {"bound": "hbm", "achieved": b["achieved_gbs"], "peak": peak, "unit": "GB/s",
-                     "frac": b["achieved_gbs"] / peak, "traffic": None,
+        "roofline": {"bound": "hbm", "achieved": g["achieved_gbs"], "peak": peak, "unit": "GB/s",
+                     "frac": g["achieved_gbs"] / peak, "traffic": None,
                      "peak_source": f"{peak_kind} HBM copy bandwidth",
                      "note": "whole step (updates + one launch per pass over all roadmaps, "
                              "replayed as one CUDA graph)"},
-        "plain": out["plain"], "batched": out["batched"], "graph": out["graph"],
-        "autotune": {"chosen": tuned[0] if tuned else None, "shapes_timed": len(tuned)},
-        "graph_nodes": nodes,
-        "labels_identical_across_modes": bool(same),
-        # per step: one update kernel per roadmap, then box prep, classify, merge
-        "gpu_launches": args.steps * (len(rms) + 3),
+        "batched": res,
+        "gpu_launches": args.steps * res["gpu_launches_per_step"]["graph"],
         "clocks": clocks.summary(),
     }
-    for r in rms:
-        r.close()
     print(json.dumps(line))
-    return 0 if same else 1
+    return 0 if res["labels_identical_across_modes"] else 1
 
 
-def run_serve(args):
+def measure_serving(args, seconds: float):
     """Workload 5: a Poisson stream of obstacle-update requests against eight
     resident roadmaps, served with continuous batching and, for comparison,
     one request per classify launch.  Each mode starts from the same box
     state; the final labels of every roadmap must agree between the modes."""
     import torch
-    torch.cuda.set_device(0)
-    from paper_2603_28674_gb300 import build
-    build.build()
     from paper_2603_28674_gb300 import serve as SV
-    scenes, reqs = W.workload_serving(duration_s=args.serve_seconds)
-    srv = SV.Server(device=0)
+    scenes, reqs = W.workload_serving(duration_s=seconds)
+    srv = SV.Server(device=torch.cuda.current_device())
     for sc in scenes:
         rm = sc.roadmap
         srv.add_roadmap(rm.robot, rm.q_from, rm.q_to, rm.step, np.arange(sc.boxes.count),
@@ -835,40 +949,57 @@ def run_serve(args):
             r.classify(srv.stream)
         srv.stream.synchronize()
 
-    n_warm = min(len(requests), 100 * max(args.warmup, 3))
+    n_warm = min(len(requests), 300)
     warm = [SV.ServeRequest(q.arrival_s - requests[0].arrival_s, q.roadmap, q.ids, q.poses)
             for q in requests[:n_warm]]
     out, final = {}, {}
-    with ClockSampler(0) as clocks:
-        for mode in ("one_at_a_time", "batched"):
-            srv.serve(warm, mode)
-            reset()
-            out[mode] = srv.serve(requests, mode)
-            final[mode] = [srv.labels(k) for k in range(len(srv.roadmaps))]
+    for mode in ("one_at_a_time", "batched"):
+        srv.serve(warm, mode)
+        reset()
+        out[mode] = srv.serve(requests, mode)
+        final[mode] = [srv.labels(k) for k in range(len(srv.roadmaps))]
     same = all(np.array_equal(a, b) for a, b in zip(final["batched"], final["one_at_a_time"]))
-    b, p = out["batched"], out["one_at_a_time"]
     infos = [r.info() for r in srv.roadmaps]
+    srv.close()
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    b, p = out["batched"], out["one_at_a_time"]
+    return {"roadmaps": len(scenes), "edges": [i["num_edges"] for i in infos],
+            "record_gb": sum(i["record_bytes"] for i in infos) / 1e9,
+            "requests": len(requests), "arrival_window_s": seconds,
+            "offered_req_s": b["offered_req_s"], "moved_per_request": "1-8",
+            "batched": b, "one_at_a_time": p,
+            "p50_speedup": p["latency_ms_p50"] / b["latency_ms_p50"],
+            "p99_speedup": p["latency_ms_p99"] / b["latency_ms_p99"],
+            "throughput_speedup": b["throughput_req_s"] / p["throughput_req_s"],
+            "final_labels_identical": bool(same)}
+
+
+def run_serve(args):
+    """Workload 5 on its own line (see measure_serving)."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2603_28674_gb300 import build
+    build.build()
+    with ClockSampler(0) as clocks:
+        res = measure_serving(args, args.serve_seconds)
+    b = res["batched"]
     line = {
         "metric": METRIC, "value": b["edges_per_s"], "unit": "request-edges/s", "n_gpus": 1,
-        "steps": len(requests), "warmup": n_warm,
+        "steps": res["requests"], "warmup": 300,
         "ms_per_step": 1e3 / b["throughput_req_s"] if b["throughput_req_s"] else None,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": f"serving {len(scenes)} resident roadmaps",
-                   "edges": [i["num_edges"] for i in infos],
-                   "record_gb": sum(i["record_bytes"] for i in infos) / 1e9,
-                   "offered_req_s": b["offered_req_s"], "boxes_per_roadmap": scenes[0].boxes.count,
+        "config": {"workload": f"serving {res['roadmaps']} resident roadmaps",
+                   "edges": res["edges"], "record_gb": res["record_gb"],
+                   "offered_req_s": res["offered_req_s"], "boxes_per_roadmap": 64,
                    "moved_per_request": "1-8", "duration_s": args.serve_seconds,
                    "l2": "records > L2; no flush needed"},
-        "serving": {"batched": b, "one_at_a_time": p,
-                    "p99_speedup": p["latency_ms_p99"] / b["latency_ms_p99"],
-                    "throughput_speedup": b["throughput_req_s"] / p["throughput_req_s"],
-                    "final_labels_identical": bool(same)},
+        "serving": res,
         "clocks": clocks.summary(),
     }
-    srv.close()
     print(json.dumps(line))
-    return 0 if same else 1
+    return 0 if res["final_labels_identical"] else 1
 
 
 def main():

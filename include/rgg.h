@@ -48,9 +48,18 @@
  *     source alive and unchanged until the stream reaches it).
  *   - Each roadmap lives on one CUDA device (rgg_roadmap_desc.device); calls
  *     switch to that device and restore the caller's current device.
- *   - Errors that only the device can see (a bounded wait that ran out)
- *     are latched in a device status word and returned by the next
- *     rgg_fetch_labels or rgg_check_status as RGG_ERR_TIMEOUT.
+ *   - Errors that only the device can see (a bounded wait that ran out,
+ *     see rgg_set_wait_limit) are latched in the roadmap's device status
+ *     word and returned by the next rgg_fetch_labels / rgg_fetch_box_sets
+ *     with a host destination or rgg_check_status as RGG_ERR_TIMEOUT.  While
+ *     an error is latched every classify pass of the roadmap is skipped on
+ *     the device (its kernels return at once and leave the box sets and
+ *     labels as they were), so a stream of enqueued passes cannot pile up
+ *     one time-out after another.  Reporting the error recovers: the word is
+ *     cleared, every present box is queued again (the next rgg_classify
+ *     re-tests all of them, so the labels become those of the current poses)
+ *     and every open request handle is marked lost (rgg_fetch_request_labels
+ *     returns RGG_ERR_TIMEOUT for it; release it).
  */
 #ifndef RGG_H_
 #define RGG_H_
@@ -326,8 +335,37 @@ int rgg_labels_device_ptr(rgg_roadmap_t r, const uint8_t** out);
 int rgg_roadmap_info(rgg_roadmap_t r, rgg_info* out);
 
 /* Wait for the stream and report any latched device-side error
- * (RGG_ERR_TIMEOUT), clearing it. */
+ * (RGG_ERR_TIMEOUT), clearing it and recovering as described at the top. */
 int rgg_check_status(rgg_roadmap_t r, void* stream);
+
+/* Limit, in nanoseconds of wall time, of every bounded wait in the classify
+ * kernel (a consumer warp waiting for its tile's records, the producer
+ * waiting for a free stage).  A wait that runs out ends the launch with
+ * RGG_ERR_TIMEOUT latched (see the top).  The default, 4 s, is far above any
+ * wait of a healthy launch (microseconds); very small limits exist to test
+ * the failure path.  RGG_ERR_INVALID for 0. */
+int rgg_set_wait_limit(rgg_roadmap_t r, uint64_t limit_ns);
+
+/* Fault injection for tests of the host's error paths: the nth device
+ * allocation the library makes from now on (any roadmap, any call) fails as
+ * if the device were out of memory, and the call that made it returns
+ * RGG_ERR_OOM with the roadmap unchanged.  0 turns it off; it also turns off
+ * by itself once it has fired.  The paper has no counterpart. */
+int rgg_inject_alloc_failure(uint64_t nth);
+
+/* Device bytes a sphere-geometry roadmap created with `desc` holds once
+ * rgg_build_edges(num_edges, q_from, q_to, step) has run: record planes,
+ * tile tables of the default launch shape, per-edge state, kept endpoints
+ * and the fixed per-roadmap tables, i.e. rgg_roadmap_info's device_bytes
+ * after the build (the first rgg_update_request adds RGG_MAX_REQUESTS x N
+ * bytes).  Host-only arithmetic: the configuration counts follow
+ * rgg_build_edges' rule; the tile size uses desc->device's SM count (152 if
+ * the device cannot be queried; it matters only for roadmaps too small to
+ * give each SM two tiles).  RGG_ERR_INVALID for bad arguments (as for
+ * rgg_roadmap_create / rgg_build_edges), RGG_ERR_STATE for the OBB geometry,
+ * whose spline sizes are only known once built. */
+int rgg_estimate_bytes(const rgg_roadmap_desc* desc, uint64_t num_edges, const double* q_from,
+                       const double* q_to, double step, uint64_t* bytes);
 
 /* Kernel timing: when enabled, rgg_classify records CUDA events on its stream
  * around each pass's streaming classify launch and its merge launch;
@@ -523,8 +561,10 @@ int rgg_step_graph_destroy(rgg_step_graph_t g);
  *
  * The caller owns the serialized records and the per-edge state, in device
  * memory, laid out as below; the call tests every edge against the given
- * moved boxes and merges the results into the per-edge state exactly as
- * rgg_classify does (same arithmetic, same labels).  It calls no cudaMalloc,
+ * moved boxes and merges the results into the per-edge state as
+ * rgg_classify does: the same kernels, and with regular_records set as
+ * rgg_classify would set it for the same records, the same labels and box
+ * sets bit for bit.  It calls no cudaMalloc,
  * cudaFree or other allocating routine: its scratch (tile tables, per-edge
  * accumulators, box records; about 3.7 MB) is a fixed array inside the
  * library, held by every device that loads the library until the process
@@ -548,6 +588,19 @@ int rgg_step_graph_destroy(rgg_step_graph_t g);
  *   counts       N uint32: hit-set size | touch-set size << 16 (in/out);
  *                zero together with the sets before the first call
  *   labels       N uint8 (out), enum rgg_label
+ *   regular_records  1 if every configuration's K inner spheres share one
+ *                radius and sit at equal steps on a segment, as
+ *                rgg_build_edges writes them (records read back with
+ *                rgg_fetch_records from such a roadmap are); the inner test
+ *                then interpolates the centres when margin_m >= 1e-5, as
+ *                rgg_classify does.  0: sphere by sphere.  The library cannot
+ *                check device records: set it only for such records.
+ *   status       optional device int (may be NULL): 0 once the pass has
+ *                finished, else the code of a bounded wait that ran out, in
+ *                which case hit, touch, counts and labels were left as they
+ *                were (run the call again)
+ *   wait_limit_ns  limit of the kernel's bounded waits (0: 4 s), as
+ *                rgg_set_wait_limit
  * Limits: N <= RGG_NOALLOC_MAX_EDGES and at most RGG_NOALLOC_MAX_TILES tiles
  * (tiles hold up to 527 configurations x links, fewer for robots with few
  * links); larger inputs return RGG_ERR_CAPACITY and nothing is launched.
@@ -570,6 +623,9 @@ typedef struct {
   uint32_t* counts;
   uint8_t* labels;
   float margin_m;
+  uint32_t regular_records;
+  int* status;
+  uint64_t wait_limit_ns;
 } rgg_noalloc_args;
 
 int rgg_classify_noalloc(const rgg_noalloc_args* args, void* stream);

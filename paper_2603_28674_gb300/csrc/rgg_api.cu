@@ -3,12 +3,39 @@
 // the classification runs in the kernels of rgg_kernels.cu.  The OBB
 // geometry, persistence, the autotuner and step graphs, and the gray
 // resolution have their own host files.
+#include <atomic>
+
 #include "rgg_host.h"
 
 using namespace rgg;
 using namespace rgg_host;
 
 namespace rgg_host {
+
+// Allocation-failure injection (a test hook, rgg_inject_alloc_failure): when
+// the countdown reaches zero the allocation fails as if the device were out
+// of memory.
+static std::atomic<uint64_t> g_fail_countdown{0};
+
+cudaError_t device_alloc(void** p, size_t bytes) {
+  uint64_t c = g_fail_countdown.load();
+  while (c != 0) {
+    if (g_fail_countdown.compare_exchange_weak(c, c - 1)) {
+      if (c == 1) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+      }
+      break;
+    }
+  }
+  return cudaMalloc(p, bytes);
+}
+
+// Device bytes every roadmap holds whatever its edges: the box table, the
+// staging rows, the pass's box records and the status words.
+uint64_t fixed_device_bytes(const rgg_roadmap* r) {
+  return (uint64_t)r->M * 64 + (uint64_t)r->stage_rows * 64 + kBoxesPerPass * kBoxRecFloats * 4 + 16;
+}
 
 uint32_t launch_ctas(const rgg_roadmap* r) { return (uint32_t)r->num_sms * r->ctas_per_sm; }
 
@@ -210,21 +237,11 @@ void clear_pending(rgg_roadmap* r) {
   r->run_start = 0;
 }
 
-// Swap in freshly built edges: labels GREEN, box sets empty, open requests
-// closed, and every present box pending (its staged pose copied from the
-// box table) so that the next classify tests it against the new edges.
-int install_edges(rgg_roadmap* r, EdgeState&& es, cudaStream_t s) {
-  const int rc = compute_rounds(r, &es, s);
-  if (rc != RGG_OK) {
-    es.release();
-    return rc;
-  }
-  r->es.release();
-  r->es = std::move(es);
-  r->has_edges = true;
-  ++r->gen;
+// Drop the pending entries and make every present box pending again, its
+// staged pose copied from the box table, so that the next classify tests
+// every present box against every edge and replaces all of their bits.
+int requeue_present(rgg_roadmap* r, cudaStream_t s) {
   clear_pending(r);
-  std::fill(r->req_state.begin(), r->req_state.end(), 0);
   BoxUpdateParams p;
   p.n = 0;
   p.table = r->d_table;
@@ -245,6 +262,23 @@ int install_edges(rgg_roadmap* r, EdgeState&& es, cudaStream_t s) {
   }
   RGG_CK(launch_box_update(p, s));
   return RGG_OK;
+}
+
+// Swap in freshly built edges: labels GREEN, box sets empty, open requests
+// closed, and every present box pending so that the next classify tests it
+// against the new edges.
+int install_edges(rgg_roadmap* r, EdgeState&& es, cudaStream_t s) {
+  const int rc = compute_rounds(r, &es, s);
+  if (rc != RGG_OK) {
+    es.release();
+    return rc;
+  }
+  r->es.release();
+  r->es = std::move(es);
+  r->has_edges = true;
+  ++r->gen;
+  std::fill(r->req_state.begin(), r->req_state.end(), 0);
+  return requeue_present(r, s);
 }
 
 // n_e >= 2 per edge; L*n_e and the edge count fit the 32-bit tile tables.
@@ -353,6 +387,7 @@ ClassifyJob make_job(rgg_roadmap* r, uint32_t C, uint64_t tile_base) {
     j.rcand = es.d_rcand;
   }
   j.streamed = r->d_streamed;
+  j.status = r->d_status;
   return j;
 }
 
@@ -373,6 +408,7 @@ MergeJob make_merge_job(rgg_roadmap* r, size_t lo, uint32_t C, bool ordered, uin
   m.C = C;
   m.ordered = ordered ? 1u : 0u;
   m.hist = es.d_hist;
+  m.status = r->d_status;
   for (uint32_t b = 0; b < C; ++b) {
     const auto& en = r->pending[lo + b];
     m.ids[b] = en.id;
@@ -543,22 +579,26 @@ int classify_group(rgg_roadmap_t* rs, uint32_t n, cudaStream_t s) {
       cp1.total_tiles = tiles;
       cp1.status = r0->d_status;
       cp1.work_counter = counter;
+      cp1.wait_ns = r0->wait_ns;
       RGG_CK(launch_classify_single(cp1, lc, s));
     } else {
       cpp->njobs = nj;
       cpp->total_tiles = tiles;
       cpp->status = r0->d_status;
       cpp->work_counter = counter;
+      cpp->wait_ns = r0->wait_ns;
       RGG_CK(launch_classify_batched(*cpp, lc, s));
     }
     if (ev) RGG_CK(cudaEventRecord(ev[1], s));
     if (n == 1) {
       mp1.njobs = 1;
       mp1.total_edges = edges;
+      mp1.status = r0->d_status;
       RGG_CK(launch_merge_single(mp1, s));
     } else {
       mpp->njobs = nj;
       mpp->total_edges = edges;
+      mpp->status = r0->d_status;
       RGG_CK(launch_merge_batched(*mpp, s));
     }
     if (ev) RGG_CK(cudaEventRecord(ev[2], s));
@@ -571,12 +611,24 @@ int classify_group(rgg_roadmap_t* rs, uint32_t n, cudaStream_t s) {
   return RGG_OK;
 }
 
+// Reports a device error latched on the roadmap (a classify launch whose
+// bounded wait ran out, or a pass skipped because of an earlier one) and
+// recovers from it: the word is cleared, every present box is queued again
+// (the box table holds the latest poses, so the next classify recomputes
+// every bit the failed passes left out), and open request handles are
+// marked lost (their snapshots may be partial).
 int check_status_locked(rgg_roadmap_t r, cudaStream_t s) {
   int st = 0;
   RGG_CK(cudaMemcpyAsync(&st, r->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
   RGG_CK(cudaStreamSynchronize(s));
   if (st != 0) {
     RGG_CK(cudaMemsetAsync(r->d_status, 0, sizeof(int), s));
+    for (auto& q : r->req_state)
+      if (q != 0) q = 3;
+    if (r->has_edges) {
+      const int rc = requeue_present(r, s);
+      if (rc != RGG_OK) return rc;
+    }
     RGG_CK(cudaStreamSynchronize(s));
     return RGG_ERR_TIMEOUT;
   }
@@ -924,6 +976,7 @@ int rgg_fetch_request_labels(rgg_roadmap_t r, uint32_t handle, uint8_t* out, uin
   if (!r || handle >= RGG_MAX_REQUESTS || (!out && count) || dst_is_device < 0 ||
       dst_is_device > 2)
     return RGG_ERR_INVALID;
+  if (r->has_edges && r->req_state[handle] == 3) return RGG_ERR_TIMEOUT;
   if (!r->has_edges || r->req_state[handle] != 2) return RGG_ERR_STATE;
   if (first > r->es.N || count > r->es.N - first) return RGG_ERR_INVALID;
   DeviceGuard g(r->device);
@@ -938,7 +991,7 @@ int rgg_fetch_request_labels(rgg_roadmap_t r, uint32_t handle, uint8_t* out, uin
 
 int rgg_release_request(rgg_roadmap_t r, uint32_t handle) {
   if (!r || handle >= RGG_MAX_REQUESTS) return RGG_ERR_INVALID;
-  if (r->req_state[handle] != 2) return RGG_ERR_STATE;
+  if (r->req_state[handle] != 2 && r->req_state[handle] != 3) return RGG_ERR_STATE;
   r->req_state[handle] = 0;
   return RGG_OK;
 }
@@ -1016,8 +1069,7 @@ int rgg_roadmap_info(rgg_roadmap_t r, rgg_info* out) {
   out->num_inner = es.n_inner;
   out->num_outer = es.n_outer;
   out->record_bytes = 16 * (es.n_inner + es.n_outer);
-  out->device_bytes = es.device_bytes + (uint64_t)r->M * 64 + (uint64_t)r->stage_rows * 64 +
-                      kBoxesPerPass * kBoxRecFloats * 4 + 16;
+  out->device_bytes = es.device_bytes + fixed_device_bytes(r);
   out->num_links = r->L;
   out->inner_per_link = r->K;
   out->max_obstacles = r->M;
@@ -1080,6 +1132,70 @@ int rgg_check_status(rgg_roadmap_t r, void* stream) {
   DeviceGuard g(r->device);
   if (!g.ok) return RGG_ERR_CUDA;
   return check_status_locked(r, static_cast<cudaStream_t>(stream));
+}
+
+int rgg_set_wait_limit(rgg_roadmap_t r, uint64_t limit_ns) {
+  if (!r || limit_ns == 0) return RGG_ERR_INVALID;
+  r->wait_ns = limit_ns;
+  return RGG_OK;
+}
+
+int rgg_inject_alloc_failure(uint64_t nth) {
+  g_fail_countdown.store(nth);
+  return RGG_OK;
+}
+
+int rgg_estimate_bytes(const rgg_roadmap_desc* desc, uint64_t num_edges, const double* q_from,
+                       const double* q_to, double step, uint64_t* bytes) {
+  if (!desc || !bytes || desc->num_links < 1 || desc->num_links > RGG_MAX_LINKS ||
+      desc->inner_per_link < 1 || desc->inner_per_link > RGG_MAX_INNER ||
+      desc->max_obstacles < 1 || desc->max_obstacles > RGG_MAX_OBSTACLES ||
+      !(step > 0.0) || !std::isfinite(step) || (num_edges && (!q_from || !q_to)) ||
+      num_edges >= 0xffffffffull)
+    return RGG_ERR_INVALID;
+  if (desc->geometry != RGG_GEOMETRY_SPHERES) return RGG_ERR_STATE;
+  const uint32_t L = desc->num_links, K = desc->inner_per_link, M = desc->max_obstacles;
+  const uint32_t Wm = (M + 31) / 32;
+  // rgg_build_edges' configuration counts, on the host
+  std::vector<uint64_t> soff(num_edges + 1, 0);
+  for (uint64_t e = 0; e < num_edges; ++e) {
+    double m = 0.0;
+    for (uint32_t j = 0; j < L; ++j) {
+      const double a = q_from[e * L + j], b = q_to[e * L + j];
+      if (!std::isfinite(a) || !std::isfinite(b)) return RGG_ERR_INVALID;
+      m = std::max(m, std::fabs(b - a));
+    }
+    const double c = std::ceil(m / step);
+    if (!(c < 2147483647.0)) return RGG_ERR_INVALID;
+    soff[e + 1] = soff[e] + std::max<uint64_t>(2, (uint64_t)c + 1);
+  }
+  const uint64_t N = num_edges, S = soff[N], G = (uint64_t)L * S;
+  if (N && !valid_soff(soff.data(), N, L)) return RGG_ERR_INVALID;
+  // the tiles of the default launch shape (their size depends on the SM
+  // count only for roadmaps too small to give every CTA two tiles)
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, desc->device) != cudaSuccess ||
+      sms <= 0) {
+    cudaGetLastError();
+    sms = 152;
+  }
+  uint64_t tile_bytes = 0;
+  if (N) {
+    const Tiling t = choose_tiling(L, K, G, 2 * (uint32_t)sms, kDefaultVariant);
+    std::vector<TileDesc> tiles;
+    std::vector<int4> etab;
+    if (!build_tiles(L, N, soff, G, t.S, &tiles, &etab)) return RGG_ERR_INVALID;
+    tile_bytes = tiles.size() * sizeof(TileDesc) + etab.size() * sizeof(int4);
+  }
+  const uint64_t n_in = (uint64_t)K * G, n_out = (uint64_t)L * (S - N);
+  const uint64_t in_stride = ((n_in + 4 + 63) / 64) * 64, out_stride = ((n_out + 4 + 63) / 64) * 64;
+  uint64_t b = (N + 1) * 8 + 16 * in_stride + 16 * out_stride;  // offsets and record planes
+  b += N * (2ull * Wm * 4 + 4 + 1 + 8);                         // box sets, counts, labels, pass bits
+  b += tile_bytes;
+  b += 2 * N * L * sizeof(double);                              // endpoints (gray resolution)
+  b += (uint64_t)M * 64 + (uint64_t)(M + RGG_PENDING_EXTRA) * 64 + kBoxesPerPass * kBoxRecFloats * 4 + 16;
+  *bytes = b;
+  return RGG_OK;
 }
 
 int rgg_set_kernel_timing(rgg_roadmap_t r, int enable) {

@@ -86,6 +86,7 @@ struct ClassifyJob {
   const uint32_t* rout;             // [T][kRoundSlots] outer records lo | hi << 16, tile-local
   uint32_t* rcand;                  // [T][kRoundSlots] moved boxes that may reach the round
   unsigned long long* streamed;     // record bytes copied (may be null)
+  const int* status = nullptr;      // the roadmap's own status word (may be null)
 };
 
 template <int MAXJ>
@@ -93,8 +94,9 @@ struct ClassifyParams {
   ClassifyJob job[MAXJ];
   uint32_t njobs;
   uint64_t total_tiles;
-  int* status;                      // device status word (0 = ok)
+  int* status;                      // device status word of the launch (0 = ok)
   uint32_t* work_counter;           // tile-chunk counter, zero at launch
+  uint64_t wait_ns = 4000000000ull; // limit of every bounded wait, ns of wall time
 };
 
 // Per-stage header written by the producer warp.
@@ -128,6 +130,7 @@ struct MergeJob {
   uint32_t snap_mask;
   uint8_t* hist;
   uint8_t snap_slot[kBoxesPerPass];
+  int* status = nullptr;  // the roadmap's status word: a failed launch's code is copied here
 };
 
 template <int MAXJ>
@@ -135,6 +138,11 @@ struct MergeParams {
   MergeJob job[MAXJ];
   uint32_t njobs;
   uint64_t total_edges;
+  // status word of the classify launch whose bits are merged (may be null):
+  // when it is set, the launch did not finish its tiles, so the per-edge
+  // sets and labels are left as they were and only the accumulators are
+  // cleared
+  const int* status = nullptr;
 };
 
 enum StatusCode : int {
@@ -142,6 +150,9 @@ enum StatusCode : int {
   kStatusTimeoutFull = 1,
   kStatusTimeoutEmpty = 2,
   kStatusTimeoutBoxes = 3,
+  // the launch found an error already latched (by an earlier launch) and
+  // did no work: its pass still has to be run again
+  kStatusSkipped = 4,
 };
 
 // ---------------------------------------------------------------------------

@@ -43,11 +43,15 @@ inline int cuda_status(cudaError_t e) {
     if (e_ != cudaSuccess) return cuda_status(e_); \
   } while (0)
 
+// Every device allocation of the library goes through here, so that a test
+// can make the n-th one fail (rgg_inject_alloc_failure).
+cudaError_t device_alloc(void** p, size_t bytes);
+
 template <class T>
 cudaError_t dalloc(T** p, size_t count) {
   *p = nullptr;
   if (count == 0) return cudaSuccess;
-  return cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
+  return device_alloc(reinterpret_cast<void**>(p), count * sizeof(T));
 }
 
 // Smallest margin for which interpolated inner centres are used (their error
@@ -194,6 +198,7 @@ struct rgg_roadmap {
   uint32_t stage_rows = 0;
   float* d_changed = nullptr;  // [32][24] derived records of the current pass
   int* d_status = nullptr;          // [0] status word, [1] classify work counter
+  uint64_t wait_ns = 4000000000ull; // limit of the classify kernel's bounded waits
   std::vector<uint8_t> present;
   // Pending entries in application order.  Entry i stages its pose in row
   // `row` of d_stage; `snap` >= 0 marks the last entry of a request whose
@@ -206,7 +211,8 @@ struct rgg_roadmap {
   std::vector<Entry> pending;
   std::vector<int32_t> run_idx;
   size_t run_start = 0;
-  // request handles: 0 free, 1 waiting for a classify, 2 classified
+  // request handles: 0 free, 1 waiting for a classify, 2 classified, 3 lost
+  // to a device error (its snapshot is not valid; release it)
   std::vector<uint8_t> req_state;
   // kernel timing: events before classify, between classify and merge, after merge
   bool timing = false;
@@ -224,6 +230,8 @@ int set_tiles(rgg_roadmap* r, EdgeState* es, cudaStream_t s);
 int alloc_edges(rgg_roadmap* r, EdgeState* es, uint64_t N, std::vector<uint64_t>&& soff,
                 cudaStream_t s);
 void clear_pending(rgg_roadmap* r);
+int requeue_present(rgg_roadmap* r, cudaStream_t s);
+uint64_t fixed_device_bytes(const rgg_roadmap* r);
 int install_edges(rgg_roadmap* r, EdgeState&& es, cudaStream_t s);
 void release_rounds(EdgeState* es);
 int compute_rounds(rgg_roadmap* r, EdgeState* es, cudaStream_t s);

@@ -435,7 +435,9 @@ __global__ void __launch_bounds__(256) round_filter_kernel(const __grid_constant
   J.rcand[slot] = lane == kRoundSlots - 1 ? need : m;
 }
 
-constexpr uint64_t kWaitLimit = 4000000000ull;  // 4 s of wall time per wait
+// Bound of the producer's final wait for its own bulk copies before the CTA
+// exits (copies always land; the bound only keeps the wait finite).
+constexpr uint64_t kDrainLimit = 500000000ull;
 
 __device__ __forceinline__ void write_stage_hdr(unsigned char* sb, int job, uint64_t g0, uint64_t g1,
                                                 uint32_t n_out, uint32_t n_edges, int in_shift,
@@ -506,6 +508,20 @@ __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
   const int ncw = (blockDim.x >> 5) - 1;
+
+  // An error latched by an earlier launch (on the launch's word or on one of
+  // its roadmaps' own words) stops the launch before it issues anything: its
+  // pass is marked skipped, so the merge leaves every per-edge set alone and
+  // the host re-queues the boxes when it collects the error.
+  {
+    int bad = threadIdx.x == 0 ? *reinterpret_cast<volatile const int*>(P.status) : 0;
+    for (uint32_t j = threadIdx.x; j < P.njobs && j < (uint32_t)MAXJ; j += blockDim.x)
+      if (P.job[j].status) bad |= *reinterpret_cast<volatile const int*>(P.job[j].status);
+    if (__syncthreads_or(bad != 0)) {
+      if (threadIdx.x == 0) atomicCAS(P.status, 0, (int)kStatusSkipped);
+      return;
+    }
+  }
 
   // zero the stages (their accumulators must start at zero) and counters
   for (uint32_t i = threadIdx.x; i < NSTAGE * STAGE_BYTES / 16; i += blockDim.x)
@@ -627,7 +643,7 @@ __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const 
           c_bytes = 0;
         }
         int good = 1;
-        if (lane == 0) good = mbar_wait_bounded(&empty[stage], (round & 1) ^ 1, kWaitLimit);
+        if (lane == 0) good = mbar_wait_bounded(&empty[stage], (round & 1) ^ 1, P.wait_ns);
         good = __shfl_sync(0xffffffffu, good, 0);
         if (!good) {
           if (lane == 0) atomicCAS(P.status, 0, (int)kStatusTimeoutEmpty);
@@ -717,7 +733,7 @@ __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const 
       for (int i = 0; i < n_end; ++i, ++slot) {
         const int stage = slot % NSTAGE;
         const uint32_t round = slot / NSTAGE;
-        if (!mbar_wait_bounded(&empty[stage], (round & 1) ^ 1, kWaitLimit)) {
+        if (!mbar_wait_bounded(&empty[stage], (round & 1) ^ 1, P.wait_ns)) {
           atomicCAS(P.status, 0, (int)kStatusTimeoutEmpty);
           break;
         }
@@ -727,11 +743,14 @@ __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const 
       }
     }
     // Before leaving, make sure none of this CTA's bulk copies is still in
-    // flight (bounded; immediate when every issued slot has landed).
+    // flight (bounded; immediate when every issued slot has landed): the
+    // slots armed last, and the box records copied at the start, which
+    // consumers that gave up early never waited for.
     if (lane == 0) {
       const uint32_t first = slot > (uint32_t)NSTAGE ? slot - NSTAGE : 0;
       for (uint32_t k = first; k < slot; ++k)
-        mbar_wait_bounded(&full[k % NSTAGE], (k / NSTAGE) & 1, 500000000ull);
+        mbar_wait_bounded(&full[k % NSTAGE], (k / NSTAGE) & 1, kDrainLimit);
+      mbar_wait_bounded(boxbar, 0, kDrainLimit);
     }
     return;
   }
@@ -740,13 +759,13 @@ __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const 
   uint32_t* queue = queues + (size_t)(warp - 1) * kPairQueue;
   {
     int ok = 1;
-    if (lane == 0) ok = mbar_wait_bounded(boxbar, 0, kWaitLimit);
+    if (lane == 0) ok = mbar_wait_bounded(boxbar, 0, P.wait_ns);
     ok = __shfl_sync(0xffffffffu, ok, 0);
     if (!ok) {
       if (lane == 0) atomicCAS(P.status, 0, (int)kStatusTimeoutBoxes);
       return;
     }
-    mbar_wait_bounded(boxbar, 0, kWaitLimit);
+    mbar_wait_bounded(boxbar, 0, P.wait_ns);
   }
   constexpr int IPT = (ROUNDS + RPI - 1) / RPI;  // work items per tile
   for (;;) {
@@ -758,14 +777,14 @@ __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const 
     const int stage = slot % NSTAGE;
     const uint32_t parity = (slot / NSTAGE) & 1;
     int ok = 1;
-    if (lane == 0) ok = mbar_wait_bounded(&full[stage], parity, kWaitLimit);
+    if (lane == 0) ok = mbar_wait_bounded(&full[stage], parity, P.wait_ns);
     ok = __shfl_sync(0xffffffffu, ok, 0);
     if (!ok) {
       if (lane == 0) atomicCAS(P.status, 0, (int)kStatusTimeoutFull);
       break;
     }
     // completed phase: returns at once and orders the stage's data for this lane
-    mbar_wait_bounded(&full[stage], parity, kWaitLimit);
+    mbar_wait_bounded(&full[stage], parity, P.wait_ns);
     unsigned char* sb = stages + (size_t)stage * STAGE_BYTES;
     const StageHdr hdr = *reinterpret_cast<const StageHdr*>(sb);
     if (hdr.end) break;
@@ -997,6 +1016,16 @@ __global__ void __launch_bounds__(256) merge_kernel(const __grid_constant__ Merg
   uint2* accp = reinterpret_cast<uint2*>(J.edge_acc) + e;
   const uint2 acc = *accp;
   if (acc.x | acc.y) *accp = make_uint2(0u, 0u);
+  if (P.status) {
+    // the classify launch gave up or was skipped: its bits are partial, so
+    // the sets, counts and labels stay; each roadmap of the launch latches
+    // the error for the host
+    const int st = *reinterpret_cast<volatile const int*>(P.status);
+    if (st != 0) {
+      if (e == 0 && J.status) atomicCAS(J.status, 0, st);
+      return;
+    }
+  }
   uint32_t cnt = J.counts[e];
   int rc = (int)(cnt & 0xffffu), tc = (int)(cnt >> 16);
   uint32_t* red = J.red + e * J.Wm;

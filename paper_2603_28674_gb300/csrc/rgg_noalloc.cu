@@ -256,8 +256,12 @@ extern "C" int rgg_classify_noalloc(const rgg_noalloc_args* a, void* stream) {
   float* boxes = reinterpret_cast<float*>(base + kNaBoxOff);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
 
-  // the accumulators must start at zero; the array keeps the last call's bits
-  if (cudaMemsetAsync(acc, 0, 2 * N * sizeof(uint32_t), s) != cudaSuccess) return RGG_ERR_CUDA;
+  int* st = reinterpret_cast<int*>(base + kNaStatusOff);
+  // the accumulators and the status word must start at zero; the array keeps
+  // the last call's contents
+  if (cudaMemsetAsync(acc, 0, 2 * N * sizeof(uint32_t), s) != cudaSuccess ||
+      cudaMemsetAsync(st, 0, sizeof(int), s) != cudaSuccess)
+    return RGG_ERR_CUDA;
   noalloc_tiles_kernel<<<(unsigned)((T + 127) / 128), 128, 0, s>>>(a->sample_off, N, a->num_samples,
                                                                    L, tl.S, T, tiles, etab);
   pp.out = boxes;
@@ -287,12 +291,16 @@ extern "C" int rgg_classify_noalloc(const rgg_noalloc_args* a, void* stream) {
   j.in_cap = tl.in_cap;
   j.out_cap = tl.out_cap;
   j.margin = a->margin_m;
+  // the same rule as rgg_classify: interpolated inner centres only for
+  // regular records and a margin that covers their error
+  j.regular = (a->regular_records && a->margin_m >= 1e-5f) ? 1u : 0u;
   j.inv_k = 1.0f / (float)K;
   j.inv_km1 = K > 1 ? 1.0f / (float)(K - 1) : 0.0f;
   cp.njobs = 1;
   cp.total_tiles = T;
-  cp.status = reinterpret_cast<int*>(base + kNaStatusOff);
+  cp.status = st;
   cp.work_counter = reinterpret_cast<uint32_t*>(base + kNaStatusOff + 16);
+  cp.wait_ns = a->wait_limit_ns ? a->wait_limit_ns : 4000000000ull;
   if (cudaMemsetAsync(cp.work_counter, 0, sizeof(uint32_t), s) != cudaSuccess) return RGG_ERR_CUDA;
   ClassifyLaunch lc;
   lc.consumer_warps = kDefaultConsumerWarps;
@@ -315,6 +323,11 @@ extern "C" int rgg_classify_noalloc(const rgg_noalloc_args* a, void* stream) {
   for (uint32_t i = 0; i < C; ++i) m.ids[i] = pp.ids[i];
   mp.njobs = 1;
   mp.total_edges = N;
+  // a launch whose bounded wait ran out leaves the caller's state untouched
+  mp.status = st;
   if (launch_merge_single(mp, s) != cudaSuccess) return RGG_ERR_CUDA;
+  if (a->status &&
+      cudaMemcpyAsync(a->status, st, sizeof(int), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    return RGG_ERR_CUDA;
   return RGG_OK;
 }

@@ -42,12 +42,14 @@ static int tune_launch(rgg_roadmap_t* rs, uint32_t n, const std::vector<uint32_t
     cp1.total_tiles = tiles;
     cp1.status = r0->d_status;
     cp1.work_counter = counter;
+    cp1.wait_ns = r0->wait_ns;
     RGG_CK(launch_classify_single(cp1, lc, s));
   } else {
     cpp->njobs = nj;
     cpp->total_tiles = tiles;
     cpp->status = r0->d_status;
     cpp->work_counter = counter;
+    cpp->wait_ns = r0->wait_ns;
     RGG_CK(launch_classify_batched(*cpp, lc, s));
   }
   return RGG_OK;

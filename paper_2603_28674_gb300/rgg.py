@@ -43,7 +43,7 @@ EXPORTS = (
     "rgg_step_graph_create", "rgg_step_graph_launch", "rgg_step_graph_nodes",
     "rgg_step_graph_destroy", "rgg_save", "rgg_load", "rgg_resolve_gray", "rgg_fetch_boxes",
     "rgg_set_obb_filter", "rgg_obb_work", "rgg_fetch_obb_records", "rgg_set_round_filter",
-    "rgg_streamed_bytes",
+    "rgg_streamed_bytes", "rgg_set_wait_limit", "rgg_inject_alloc_failure", "rgg_estimate_bytes",
 )
 
 
@@ -75,7 +75,9 @@ class _NoallocArgs(ctypes.Structure):
                 ("box_ids", ctypes.c_void_p), ("box_poses", ctypes.c_void_p),
                 ("mask_words", ctypes.c_uint32), ("hit", ctypes.c_void_p),
                 ("touch", ctypes.c_void_p), ("counts", ctypes.c_void_p),
-                ("labels", ctypes.c_void_p), ("margin_m", ctypes.c_float)]
+                ("labels", ctypes.c_void_p), ("margin_m", ctypes.c_float),
+                ("regular_records", ctypes.c_uint32), ("status", ctypes.c_void_p),
+                ("wait_limit_ns", ctypes.c_uint64)]
 
 
 class _TuneResult(ctypes.Structure):
@@ -156,6 +158,9 @@ def _lib():
         "rgg_obb_work": [vp, ctypes.POINTER(u64), ctypes.POINTER(u64)],
         "rgg_fetch_obb_records": [vp, vp, vp, vp],
         "rgg_load": [vp, ctypes.c_char_p, vp],
+        "rgg_set_wait_limit": [vp, u64],
+        "rgg_inject_alloc_failure": [u64],
+        "rgg_estimate_bytes": [ctypes.POINTER(_Desc), u64, vp, vp, dbl, ctypes.POINTER(u64)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -392,6 +397,10 @@ class Roadmap:
     def check_status(self, stream=None) -> None:
         _check("rgg_check_status", _lib().rgg_check_status(self._h, _stream(stream, self.device)))
 
+    def set_wait_limit(self, limit_ns: int) -> None:
+        """Limit of the classify kernel's bounded waits, ns (rgg_set_wait_limit)."""
+        _check("rgg_set_wait_limit", _lib().rgg_set_wait_limit(self._h, int(limit_ns)))
+
     def set_round_filter(self, enable: bool) -> None:
         """Sphere geometry: copy only the rounds of records the moved boxes may
         reach (default); off streams every record."""
@@ -474,16 +483,41 @@ def classify_many(roadmaps: Sequence[Roadmap], stream=None) -> None:
                                                          _stream(stream, roadmaps[0].device)))
 
 
+def inject_alloc_failure(nth: int) -> None:
+    """Make the nth device allocation of the library from now fail (0: off);
+    a test hook (rgg_inject_alloc_failure)."""
+    _check("rgg_inject_alloc_failure", _lib().rgg_inject_alloc_failure(int(nth)))
+
+
+def estimate_bytes(num_links: int, inner_per_link: int, max_obstacles: int, q_from, q_to,
+                   step: float, margin: float = 2e-5, device: int = 0) -> int:
+    """Device bytes a sphere-geometry roadmap holds after build_edges with
+    these edges (rgg_estimate_bytes; host arithmetic, no GPU needed)."""
+    desc = _Desc(num_links, inner_per_link, max_obstacles, margin, device, GEOMETRY_SPHERES)
+    qa = _host(q_from, np.float64).reshape(-1, num_links)
+    qb = _host(q_to, np.float64).reshape(-1, num_links)
+    if qa.shape != qb.shape:
+        raise ValueError("q_from and q_to differ in shape")
+    out = ctypes.c_uint64()
+    _check("rgg_estimate_bytes", _lib().rgg_estimate_bytes(
+        ctypes.byref(desc), qa.shape[0], qa.ctypes.data, qb.ctypes.data, float(step),
+        ctypes.byref(out)))
+    return int(out.value)
+
+
 def classify_noalloc(*, num_links: int, inner_per_link: int, sample_off, num_samples: int,
                      inner, outer, box_ids, box_poses, mask_words: int, hit, touch, counts,
-                     labels, margin: float = 2e-5, stream=None) -> None:
+                     labels, margin: float = 2e-5, regular_records: bool = False, status=None,
+                     wait_limit_ns: int = 0, stream=None) -> None:
     """One pass of rgg_classify_noalloc on caller-owned device buffers.
 
     ``sample_off`` (int64/uint64), ``inner`` / ``outer`` ([4, stride] float32
     planes), ``hit`` / ``touch`` ([N, mask_words] int32/uint32), ``counts``
-    ([N] int32/uint32) and ``labels`` ([N] uint8) are CUDA tensors on the
-    current device; ``box_ids`` / ``box_poses`` are host arrays.  The call
-    itself allocates nothing on the device."""
+    ([N] int32/uint32), ``labels`` ([N] uint8) and the optional ``status``
+    ([1] int32) are CUDA tensors on the current device; ``box_ids`` /
+    ``box_poses`` are host arrays.  ``regular_records``: the records are
+    rgg_build_edges' (see include/rgg.h).  The call itself allocates nothing
+    on the device."""
     ids = _host(box_ids, np.uint32).reshape(-1)
     poses = _host(box_poses, np.float32).reshape(-1, 15)
     if poses.shape[0] != ids.shape[0]:
@@ -492,7 +526,8 @@ def classify_noalloc(*, num_links: int, inner_per_link: int, sample_off, num_sam
         num_links, inner_per_link, int(labels.shape[0]), int(num_samples), _ptr(sample_off),
         _ptr(inner), int(inner.stride(0)), _ptr(outer), int(outer.stride(0)), ids.shape[0],
         ids.ctypes.data, poses.ctypes.data, mask_words, _ptr(hit), _ptr(touch), _ptr(counts),
-        _ptr(labels), margin)
+        _ptr(labels), margin, int(bool(regular_records)),
+        _ptr(status) if status is not None else None, int(wait_limit_ns))
     dev = inner.device.index if hasattr(inner, "device") else 0
     _check("rgg_classify_noalloc", _lib().rgg_classify_noalloc(ctypes.byref(args),
                                                                _stream(stream, dev)))

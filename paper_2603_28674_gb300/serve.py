@@ -21,7 +21,13 @@ continuous batching:
     freed as iterations complete.
 
 Roadmaps are admitted by device memory: a roadmap whose records, per-edge
-state and snapshot memory would not fit in the memory budget is refused.
+state and snapshot memory (the library's own estimate, rgg_estimate_bytes)
+would not fit in the memory budget is refused.
+
+Requests are admitted by queue length: with `max_queue` set, a request that
+arrives while that many requests already wait is refused at once.  A request
+may carry a cancellation time: if it is still waiting then, it leaves the
+queue without being staged (a request already on the GPU completes).
 
 The `one_at_a_time` mode serves the same stream with one request per
 classify launch (the update-then-classify loop of a plain caller), with the
@@ -47,6 +53,43 @@ class ServeRequest:
     roadmap: int          # index returned by Server.add_roadmap
     ids: np.ndarray       # [m] uint32 box ids
     poses: np.ndarray     # [m, 15] float32 absolute poses
+    cancel_s: Optional[float] = None  # withdrawn at this time if not yet admitted
+
+
+class RequestQueue:
+    """Waiting requests in arrival order (host logic only).
+
+    ``arrive`` refuses a request when ``max_len`` requests already wait;
+    ``sweep`` drops the waiting requests whose cancellation time has come.
+    Refused and cancelled requests are recorded."""
+
+    def __init__(self, max_len: Optional[int] = None):
+        self.items: collections.deque = collections.deque()
+        self.max_len = max_len
+        self.refused: list = []
+        self.cancelled: list = []
+
+    def __len__(self) -> int:
+        return len(self.items)
+
+    def arrive(self, item) -> bool:
+        if self.max_len is not None and len(self.items) >= self.max_len:
+            self.refused.append(item)
+            return False
+        self.items.append(item)
+        return True
+
+    def sweep(self, now: float, cancel_at) -> None:
+        if not self.items:
+            return
+        keep = collections.deque()
+        for item in self.items:
+            t = cancel_at(item)
+            if t is not None and t <= now:
+                self.cancelled.append(item)
+            else:
+                keep.append(item)
+        self.items = keep
 
 
 class Planner:
@@ -84,17 +127,13 @@ class Planner:
 
 
 def roadmap_bytes(num_links: int, inner_per_link: int, max_obstacles: int, q_from, q_to,
-                  step: float, max_requests: int) -> int:
-    """Device bytes a roadmap will hold: records, per-edge state and request
-    snapshots (rgg_build_edges' sample-count rule)."""
-    dq = np.abs(np.asarray(q_to, np.float64) - np.asarray(q_from, np.float64))
-    n_e = np.maximum(2, np.ceil(dq.max(axis=1) / step) + 1) if dq.size else np.zeros(0)
-    N, S = len(n_e), int(n_e.sum())
-    L, K = num_links, inner_per_link
-    wm = (max_obstacles + 31) // 32
-    records = 16 * (K * L * S + L * (S - N)) + 2 * 4 * 256
-    per_edge = N * (8 * wm + 4 + 1 + 8 + 8 + max_requests)
-    return int(records + per_edge + 64 * max_obstacles * 3 + (1 << 20))
+                  step: float, device: int = 0) -> int:
+    """Device bytes a roadmap will hold once built and serving requests: the
+    library's estimate of the built roadmap plus the request snapshots."""
+    from . import rgg
+    n = int(np.asarray(q_from).reshape(-1, num_links).shape[0])
+    return rgg.estimate_bytes(num_links, inner_per_link, max_obstacles, q_from, q_to, step,
+                              device=device) + rgg.MAX_REQUESTS * n
 
 
 class Server:
@@ -127,7 +166,7 @@ class Server:
         rgg = self.rgg
         M = int(max_obstacles if max_obstacles is not None else len(box_ids))
         need = roadmap_bytes(robot.num_links, robot.inner_per_link, M, q_from, q_to, step,
-                             rgg.MAX_REQUESTS)
+                             self.device)
         if self.memory_used + need > self.memory_budget:
             raise MemoryError(f"roadmap needs {need} B; {self.memory_budget - self.memory_used}"
                               " B of the budget left")
@@ -162,10 +201,13 @@ class Server:
         return self._slots
 
     def serve(self, requests: Sequence[ServeRequest], mode: str = "batched",
-              keep_results: bool = False) -> Dict:
+              keep_results: bool = False, max_queue: Optional[int] = None) -> Dict:
         """Serve `requests` (arrival times relative to the start of the call)
-        and return latency and throughput statistics; with keep_results the
-        labels of every request are returned under "results"."""
+        and return latency and throughput statistics over the requests that
+        completed; with keep_results the labels of every completed request
+        are returned under "results" (None for refused or cancelled ones).
+        With max_queue, arrivals beyond that many waiting requests are
+        refused."""
         if mode not in ("batched", "one_at_a_time"):
             raise ValueError(f"unknown mode {mode}")
         torch, rgg = self.torch, self.rgg
@@ -178,7 +220,7 @@ class Server:
         limit = 1 if mode == "one_at_a_time" else None
         done_s = np.full(n, np.nan)
         results: List[Optional[np.ndarray]] = [None] * n if keep_results else []
-        queue: collections.deque = collections.deque()
+        rq_queue = RequestQueue(max_queue)
         inflight: collections.deque = collections.deque()
         batch_sizes, passes_roadmaps = [], []
         launches = 0
@@ -201,11 +243,16 @@ class Server:
                 planner.release(k)
                 completed += 1
 
-        while completed < n:
+        def settled():
+            return completed + len(rq_queue.refused) + len(rq_queue.cancelled)
+
+        while settled() < n:
             now = time.perf_counter() - t0
             while nxt < n and requests[order[nxt]].arrival_s <= now:
-                queue.append(order[nxt])
+                rq_queue.arrive(order[nxt])
                 nxt += 1
+            rq_queue.sweep(now, lambda i: requests[i].cancel_s)
+            queue = rq_queue.items
             while inflight and inflight[0][0].query():
                 retire(*inflight.popleft())
             if queue and len(inflight) < self.max_inflight:
@@ -239,24 +286,28 @@ class Server:
             if inflight and (len(inflight) >= self.max_inflight or queue or nxt >= n):
                 inflight[0][0].synchronize()
                 continue
-            if not inflight and nxt < n:
+            if not inflight and nxt < n and not queue:
                 wait = requests[order[nxt]].arrival_s - (time.perf_counter() - t0)
                 if wait > 3e-4:
                     time.sleep(wait - 2e-4)
         for r in rms:
             r.check_status(s)
         arrivals = np.array([rq.arrival_s for rq in requests])
-        lat = (done_s - arrivals) * 1e3
-        span = float(np.nanmax(done_s) - arrivals.min()) if n else 0.0
-        edges = sum(self.num_edges[rq.roadmap] for rq in requests)
+        ok = ~np.isnan(done_s)
+        n_ok = int(ok.sum())
+        lat = (done_s[ok] - arrivals[ok]) * 1e3
+        span = float(np.nanmax(done_s) - arrivals.min()) if n_ok else 0.0
+        edges = sum(self.num_edges[requests[i].roadmap] for i in np.flatnonzero(ok))
         out = {
-            "mode": mode, "requests": n,
-            "latency_ms_p50": float(np.percentile(lat, 50)) if n else 0.0,
-            "latency_ms_p99": float(np.percentile(lat, 99)) if n else 0.0,
-            "latency_ms_max": float(lat.max()) if n else 0.0,
-            "latency_ms_mean": float(lat.mean()) if n else 0.0,
-            "throughput_req_s": n / span if span > 0 else 0.0,
-            "offered_req_s": n / float(arrivals.max() - arrivals.min()) if n > 1 else 0.0,
+            "mode": mode, "requests": n, "completed": n_ok,
+            "refused": len(rq_queue.refused), "cancelled": len(rq_queue.cancelled),
+            "latency_ms_p50": float(np.percentile(lat, 50)) if n_ok else 0.0,
+            "latency_ms_p99": float(np.percentile(lat, 99)) if n_ok else 0.0,
+            "latency_ms_max": float(lat.max()) if n_ok else 0.0,
+            "latency_ms_mean": float(lat.mean()) if n_ok else 0.0,
+            "throughput_req_s": n_ok / span if span > 0 else 0.0,
+            "offered_req_s": (n / float(arrivals.max() - arrivals.min())
+                              if n > 1 and arrivals.max() > arrivals.min() else 0.0),
             "edges_per_s": edges / span if span > 0 else 0.0,
             "span_s": span,
             "batches": len(batch_sizes),

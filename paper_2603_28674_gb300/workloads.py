@@ -15,7 +15,8 @@ build the roadmap as a PRM without obstacles; the recipes below follow that.
 Workloads (sizes as in the project's five configurations):
   1  planar 3-link arm, 500-node k=6 PRM, 0.05 rad step, 16 AABBs, 2 moved
   2  7-DOF DH arm, 10k-node k=10 PRM, 0.02 rad step, 64 OBBs, 8 moved
-  3  same arm, ~500k-edge PRM, ~80 samples/edge, 256 OBBs, 32 moved
+  3  same arm, ~500k-edge PRM, ~80 samples/edge, 256 OBBs, 32 moved (and a
+     mixed-label variant: the same roadmap among 256 small boxes in a 4 m cube)
   4  128 roadmaps (3/6/7-DOF), log-uniform edge and sample counts, own boxes
   5  8 resident roadmaps (4x ~50k, 4x ~200k edges) and a Poisson stream of
      obstacle-move requests
@@ -274,6 +275,25 @@ def workload_7dof(n_nodes: int = 10_000, n_boxes: int = 64, n_moved: int = 8,
 def workload_large(n_nodes: int = LARGE_NODES, n_updates: int = 8) -> Scene:
     return workload_7dof(n_nodes=n_nodes, n_boxes=256, n_moved=32, step=LARGE_STEP,
                          n_updates=n_updates, index=3, name=f"dh7_large_{n_nodes}n")
+
+
+def large_mixed_boxes(n_updates: int = 8):
+    """Boxes and updates of the mixed-label variant of the large roadmap:
+    the same 256 boxes and 32 moves per update as workload 3, but small
+    (half-extents U[0.02, 0.06] m) and spread over a 4 m cube, so that green,
+    gray and red edges all occur (the surveyed scene leaves every edge red).
+    Returns (boxes, updates); the roadmap is workload 3's."""
+    rb, ru = [np.random.Generator(np.random.PCG64(s)) for s in
+              np.random.SeedSequence([BASE_SEED + 3, 1]).spawn(2)]
+    boxes = random_boxes(rb, 256, extent=2.0, half_lo=0.02, half_hi=0.06)
+    return boxes, update_stream(ru, boxes, n_updates, 32)
+
+
+def workload_large_mixed(n_nodes: int = LARGE_NODES, n_updates: int = 8) -> Scene:
+    """Workload 3's roadmap (same seed and edges) among large_mixed_boxes."""
+    sc = workload_large(n_nodes=n_nodes, n_updates=0)
+    boxes, ups = large_mixed_boxes(n_updates)
+    return Scene(f"dh7_large_mixed_{n_nodes}n", sc.roadmap, boxes, ups)
 
 
 def workload_batched(n_roadmaps: int = 128, edge_lo: int = 1_000, edge_hi: int = 100_000,

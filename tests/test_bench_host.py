@@ -70,3 +70,14 @@ def test_clock_sampler_summary(tmp_path):
 def test_clock_sampler_without_nvidia_smi():
     s = bench.ClockSampler(0)
     assert s.summary()["reasons"] == ["nvidia-smi unavailable"]
+
+
+def test_sjf_groups_order_and_counts():
+    sizes = [50, 10, 40, 10, 30, 20, 60, 5]
+    g = bench.sjf_groups(sizes, 3)
+    flat = [k for grp in g for k in grp]
+    assert sorted(flat) == list(range(len(sizes)))               # each roadmap once
+    assert [sizes[k] for k in flat] == sorted(sizes)             # smallest first
+    assert [len(x) for x in g] == [3, 2, 3]                      # (nearly) equal counts
+    assert bench.sjf_groups(sizes, 100) == [[k] for k in flat]   # at most one per roadmap
+    assert bench.sjf_groups([7], 8) == [[0]]

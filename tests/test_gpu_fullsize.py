@@ -66,6 +66,31 @@ def test_full_size_roadmap_sampled_against_oracle(rgg, which):
         r.check_status()
 
 
+def test_full_size_mixed_label_scene_sampled_against_oracle(rgg):
+    """The large roadmap among the mixed-label boxes (256 small boxes spread
+    over a 4 m cube): green, gray and red edges all occur at full size, and a
+    sample holding all three meets the oracle rule after every update."""
+    sc = W.workload_large_mixed(n_updates=3)
+    rm, robot = sc.roadmap, sc.roadmap.robot
+    boxes = sc.boxes.copy()
+    rng = np.random.default_rng(13)
+    sample = np.sort(rng.choice(rm.num_edges, size=1500, replace=False))
+    with rgg.Roadmap(robot.num_links, robot.inner_per_link, boxes.count) as r:
+        r.build_edges(robot, rm.q_from, rm.q_to, rm.step)
+        assert r.info()["tile_samples"] == 713
+        r.update_obstacles(np.arange(boxes.count), f32(boxes.poses()))
+        r.classify()
+        for k, up in enumerate(sc.updates):
+            r.update_obstacles(up.ids, f32(up.poses))
+            r.classify()
+            boxes.centre[up.ids] = up.poses[:, :3]
+            check_sample(r, sc, boxes, sample, f"mixed, update {k}")
+            mix = np.bincount(r.fetch_labels(), minlength=3) / rm.num_edges
+            assert np.all(mix > 0.05), f"mixed scene lost a label: {mix}"
+            assert np.all(np.bincount(r.fetch_labels()[sample], minlength=3) > 50)
+        r.check_status()
+
+
 def test_full_size_filter_changes_no_bit(rgg):
     """The large roadmap with and without the spatial filter (2 x 26.8 GB):
     identical labels and box sets after every update, fewer record bytes

@@ -247,11 +247,26 @@ def test_serving_alone_equals_mix(rgg):
     torch.cuda.synchronize()
 
 
+def test_library_estimate_equals_the_built_roadmap(rgg):
+    """rgg_estimate_bytes (host arithmetic) equals the device bytes the built
+    roadmap reports, and the first request adds the snapshot rows."""
+    for seed, nodes in ((4, 200), (5, 30)):
+        rm, boxes, _ = small_scene(n_nodes=nodes, seed=seed)
+        L, K = rm.robot.num_links, rm.robot.inner_per_link
+        est = rgg.estimate_bytes(L, K, boxes.count, rm.q_from, rm.q_to, rm.step)
+        with new_roadmap(rgg, rm, boxes) as r:
+            assert r.info()["device_bytes"] == est
+            h = r.update_request([0], boxes.poses()[:1].astype(np.float32))
+            assert r.info()["device_bytes"] == est + rgg.MAX_REQUESTS * rm.num_edges
+            r.classify()
+            r.release_request(h)
+
+
 def test_serving_admits_roadmaps_by_memory(rgg):
     from paper_2603_28674_gb300 import serve as SV
     rm, boxes, _ = small_scene(n_nodes=200, seed=4)
     need = SV.roadmap_bytes(rm.robot.num_links, rm.robot.inner_per_link, boxes.count,
-                            rm.q_from, rm.q_to, rm.step, rgg.MAX_REQUESTS)
+                            rm.q_from, rm.q_to, rm.step)
     srv = SV.Server(device=0, memory_budget=int(1.5 * need))
     srv.add_roadmap(rm.robot, rm.q_from, rm.q_to, rm.step, np.arange(boxes.count),
                     boxes.poses())
@@ -260,3 +275,43 @@ def test_serving_admits_roadmaps_by_memory(rgg):
                         boxes.poses())
     assert len(srv.roadmaps) == 1
     srv.close()
+
+
+def test_serving_refuses_beyond_the_queue_and_drops_cancelled_requests(rgg):
+    """Admission control on the request queue and cancellation of waiting
+    requests: every request is completed, refused or cancelled exactly once,
+    and the completed ones get the labels of the same stream served without
+    the withdrawn requests, one request per launch."""
+    from paper_2603_28674_gb300 import serve as SV
+    scenes, reqs = W.workload_serving(node_counts=(300, 500), rate_hz=200_000.0,
+                                      duration_s=0.0004, n_boxes=16)
+    assert len(reqs) >= 40
+    burst = [SV.ServeRequest(0.0, q.roadmap, q.update.ids.astype(np.uint32),
+                             q.update.poses.astype(np.float32),
+                             cancel_s=0.0 if i % 7 == 3 else None)
+             for i, q in enumerate(reqs)]
+    srv = SV.Server(device=0, max_inflight=1, host_slots=8)
+    for sc in scenes:
+        rm = sc.roadmap
+        srv.add_roadmap(rm.robot, rm.q_from, rm.q_to, rm.step, np.arange(sc.boxes.count),
+                        sc.boxes.poses())
+    out = srv.serve(burst, "batched", keep_results=True, max_queue=24)
+    n = len(burst)
+    assert out["completed"] + out["refused"] + out["cancelled"] == n
+    assert out["refused"] == n - 24                  # a burst: all arrive at once
+    assert out["cancelled"] >= 1
+    done = [i for i in range(n) if out["results"][i] is not None]
+    assert len(done) == out["completed"]
+    # the completed requests, replayed alone in order, give the same labels
+    states = [sc.boxes.copy() for sc in scenes]
+    srv2 = SV.Server(device=0)
+    for sc in scenes:
+        rm = sc.roadmap
+        srv2.add_roadmap(rm.robot, rm.q_from, rm.q_to, rm.step, np.arange(sc.boxes.count),
+                         sc.boxes.poses())
+    replay = [SV.ServeRequest(0.0, burst[i].roadmap, burst[i].ids, burst[i].poses) for i in done]
+    ref = srv2.serve(replay, "one_at_a_time", keep_results=True)
+    for j, i in enumerate(done):
+        np.testing.assert_array_equal(out["results"][i], ref["results"][j], err_msg=f"request {i}")
+    srv.close()
+    srv2.close()

@@ -1,11 +1,13 @@
-"""Host logic of the serving loop: admission and the memory estimate."""
+"""Host logic of the serving loop: admission, refusal, cancellation and the
+library's memory estimate (no GPU needed)."""
 import collections
 
 import numpy as np
+import pytest
 
 import oracle
 from paper_2603_28674_gb300 import workloads as W
-from paper_2603_28674_gb300.serve import Planner, roadmap_bytes
+from paper_2603_28674_gb300.serve import Planner, RequestQueue, roadmap_bytes
 
 
 def test_admission_keeps_per_roadmap_order_and_capacities():
@@ -50,8 +52,16 @@ def test_one_at_a_time_limit():
     assert order == list(range(6))
 
 
-def test_memory_estimate_covers_the_records():
-    # the estimate's configuration count follows the sample-count rule
+@pytest.fixture(scope="module")
+def built():
+    from paper_2603_28674_gb300 import build
+    build.build()
+
+
+def test_memory_estimate_covers_the_records(built):
+    # the library's estimate (host arithmetic) counts the configurations by
+    # the sample-count rule, which the oracle pins
+    from paper_2603_28674_gb300 import rgg
     sc = W.workload_7dof(n_nodes=300, n_updates=0)
     rm, robot = sc.roadmap, sc.roadmap.robot
     n_e = np.array([oracle.num_samples(rm.q_from[e], rm.q_to[e], rm.step)
@@ -59,6 +69,36 @@ def test_memory_estimate_covers_the_records():
     S, N = int(n_e.sum()), rm.num_edges
     L, K = robot.num_links, robot.inner_per_link
     records = 16 * (K * L * S + L * (S - N))
-    est = roadmap_bytes(L, K, sc.boxes.count, rm.q_from, rm.q_to, rm.step, 64)
-    assert est >= records + 64 * N
-    assert est <= records + 200 * N + (2 << 20)
+    est = rgg.estimate_bytes(L, K, sc.boxes.count, rm.q_from, rm.q_to, rm.step)
+    # per edge at least the offsets, box sets, counts, label, pass bits and endpoints
+    assert est >= records + N * (8 + 8 + 4 + 1 + 8 + 16 * L)
+    assert est <= records + N * (64 + 16 * L) + (1 << 20)
+    assert roadmap_bytes(L, K, sc.boxes.count, rm.q_from, rm.q_to, rm.step) == est + 64 * N
+
+
+def test_memory_estimate_rejects_bad_arguments(built):
+    from paper_2603_28674_gb300 import rgg
+    q = np.zeros((2, 3))
+    with pytest.raises(rgg.RGGError):
+        rgg.estimate_bytes(3, 4, 16, q, q, 0.0)          # step must be positive
+    with pytest.raises(rgg.RGGError):
+        rgg.estimate_bytes(3, 4, 16, q, q + np.inf, 0.05)
+    assert rgg.estimate_bytes(3, 4, 16, q[:0], q[:0], 0.05) > 0   # no edges: fixed tables
+
+
+def test_request_queue_refuses_beyond_its_length_and_cancels_waiting_requests():
+    q = RequestQueue(max_len=2)
+    assert q.arrive(0) and q.arrive(1)
+    assert not q.arrive(2)                   # full: refused at once
+    assert q.refused == [2] and list(q.items) == [0, 1]
+    cancel = {0: 5.0, 1: None, 3: 1.0}
+    q.sweep(1.0, cancel.get)                 # nothing due yet among the waiting
+    assert list(q.items) == [0, 1]
+    assert q.arrive(3) is False              # still full
+    q.sweep(5.0, cancel.get)                 # request 0 withdraws while waiting
+    assert q.cancelled == [0] and list(q.items) == [1]
+    assert q.arrive(3)
+    q.sweep(6.0, cancel.get)                 # 3's time has passed: it leaves too
+    assert q.cancelled == [0, 3] and list(q.items) == [1]
+    unbounded = RequestQueue()
+    assert all(unbounded.arrive(i) for i in range(1000))
