@@ -96,6 +96,19 @@ enum rgg_status {
  *             the moved boxes meet (Sec. 4.3, spatial filtering). */
 enum rgg_geometry { RGG_GEOMETRY_SPHERES = 0, RGG_GEOMETRY_OBB = 1 };
 
+/* How rgg_build_edges stores a sphere-geometry roadmap's inner spheres
+ * (rgg_roadmap_desc.record_format):
+ *   LINK_ENDS  per (edge, link, configuration) only the far end of the link
+ *              (12 B); the near end is the previous link's far end (the base,
+ *              the world origin, for link 0) and the K inner spheres are
+ *              interpolated on the GPU at fractions (j + 1/2)/K of the
+ *              segment, radius R_i.  The default; it needs margin_m >= 1e-5 m
+ *              (the interpolation adds under 1e-6 m of error), and a roadmap
+ *              with a smaller margin stores SPHERES.
+ *   SPHERES    every inner sphere (16 B each, K per link and configuration).
+ * Uploaded records are always SPHERES. */
+enum rgg_record_format { RGG_RECORDS_LINK_ENDS = 0, RGG_RECORDS_SPHERES = 1 };
+
 /* Edge labels (Sec. 4.1): valid, unknown, invalid. */
 enum rgg_label { RGG_GREEN = 0, RGG_GRAY = 1, RGG_RED = 2 };
 
@@ -122,6 +135,7 @@ typedef struct {
                             /* default; it must exceed the FP32 rounding error)   */
   int device;               /* CUDA device ordinal                                */
   uint32_t geometry;        /* enum rgg_geometry (0 = spheres)                    */
+  uint32_t record_format;   /* enum rgg_record_format (0 = link ends)             */
 } rgg_roadmap_desc;
 
 /* A serial arm in standard Denavit-Hartenberg form, for rgg_build_edges.
@@ -142,7 +156,8 @@ typedef struct {
   uint64_t num_samples;     /* S = sum over edges of n_e (configurations)         */
   uint64_t num_inner;       /* K * L * S inner spheres                            */
   uint64_t num_outer;       /* L * (S - N) outer spheres                          */
-  uint64_t record_bytes;    /* 16 * (num_inner + num_outer)                       */
+  uint64_t record_bytes;    /* 16 * (num_inner + num_outer), or with link-end     */
+                            /* records 12 * L * S + 16 * num_outer                */
   uint64_t device_bytes;    /* all device memory held by the roadmap              */
   uint32_t num_links, inner_per_link, max_obstacles, mask_words;
   uint32_t tile_samples;    /* configurations per streaming tile                  */
@@ -156,6 +171,7 @@ typedef struct {
   uint64_t grid_items;      /* OBB geometry: (box, cell) incidences               */
   uint64_t spline_vertices; /* OBB geometry: kept spline vertices                 */
   uint32_t round_filter;    /* 1: the spatial filter is on and active (see below)  */
+  uint32_t record_format;   /* enum rgg_record_format of the resident records     */
 } rgg_info;
 
 /* ------------------------------------------------------------------------ */
@@ -203,8 +219,9 @@ int rgg_upload_edges(rgg_roadmap_t r, uint64_t num_edges, const uint64_t* sample
 
 /* Build the serialized approximations on the GPU from the edges themselves
  * (the offline preprocessing of Sec. 4.2 / 4.3), in FP64, stored as FP32
- * (inner radii rounded down, outer radii rounded up).  Same effect on the
- * roadmap state as rgg_upload_edges.
+ * (inner radii rounded down, outer radii rounded up; link ends rounded to
+ * nearest), in the roadmap's record format.  Same effect on the roadmap
+ * state as rgg_upload_edges.
  *
  *   robot        the arm; robot->num_links must equal the roadmap's L.
  *   q_from, q_to N x L host doubles (row-major): edge e goes from q_from[e]
@@ -317,7 +334,9 @@ int rgg_fetch_box_sets(rgg_roadmap_t r, uint32_t* hit, uint32_t* touch, uint64_t
  * the rgg_upload_edges layout restricted to that range (inner: 4 planes of
  * K*L*(sample_off[first+count]-sample_off[first]) floats; outer: 4 planes of
  * L*(samples - count) floats), and the N+1 sample offsets (host, may be NULL).
- * Synchronous.  For inspection and tests. */
+ * With link-end records the inner spheres are the ones the records stand
+ * for: centres interpolated in FP64 from the stored FP32 link ends, then
+ * rounded; radii R_i rounded down.  Synchronous.  For inspection and tests. */
 int rgg_fetch_records(rgg_roadmap_t r, uint64_t first, uint64_t count, float* inner_xyzr,
                       float* outer_xyzr, uint64_t* sample_off);
 
@@ -444,10 +463,12 @@ int rgg_resolve_gray(rgg_roadmap_t r, uint32_t factor, uint8_t* labels_out, floa
  *
  * File layout (little-endian): a 96-byte header ("RGGSAVE1", version, L, K,
  * M, mask words, margin, flags, N, S, inner and outer counts), then
- * sample_off[N+1] (uint64), inner planes (4 x K*L*S float), outer planes
- * (4 x L*(S-N) float), hit and touch sets (2 x N x mask words uint32),
- * counts[N] (uint32), labels[N] (uint8), box table (M x 16 float),
- * present[M] (uint8), and a 64-bit checksum of everything before it.
+ * sample_off[N+1] (uint64), inner planes (4 x K*L*S float; with link-end
+ * records, flag bit 1, 3 x L*S float followed by 32 link radii), outer
+ * planes (4 x L*(S-N) float), hit and touch sets (2 x N x mask words
+ * uint32), counts[N] (uint32), labels[N] (uint8), box table (M x 16 float),
+ * present[M] (uint8), and a 64-bit checksum of everything before it.  A
+ * roadmap loads either record format.
  * RGG_ERR_IO if the file cannot be opened, read or written; RGG_ERR_INVALID
  * for a header that does not match, a truncated file or a checksum
  * mismatch. */

@@ -34,7 +34,30 @@ cudaError_t device_alloc(void** p, size_t bytes) {
 // Device bytes every roadmap holds whatever its edges: the box table, the
 // staging rows, the pass's box records and the status words.
 uint64_t fixed_device_bytes(const rgg_roadmap* r) {
-  return (uint64_t)r->M * 64 + (uint64_t)r->stage_rows * 64 + kBoxesPerPass * kBoxRecFloats * 4 + 16;
+  return (uint64_t)r->M * 64 + (uint64_t)r->stage_rows * 64 + kBoxAreaFloats * 4 + 16;
+}
+
+// Built sphere-geometry edges get link-end records unless the roadmap asked
+// for sphere records or its margin is too small to cover the interpolated
+// centres' error.
+bool use_joints(const rgg_roadmap* r) {
+  return r->geometry == RGG_GEOMETRY_SPHERES && r->record_format == 0 &&
+         r->margin >= kRegularMinMargin;
+}
+
+// The link radii R_i, rounded down to FP32, behind the pass's box records
+// (link-end records take their inner radius from there).
+int set_link_radii(rgg_roadmap* r, const double* radius, cudaStream_t s) {
+  float lr[kLinkRadiiFloats] = {};
+  for (uint32_t i = 0; i < r->L && i < (uint32_t)kLinkRadiiFloats; ++i) {
+    float f = (float)radius[i];
+    if ((double)f > radius[i]) f = std::nextafter(f, 0.0f);
+    lr[i] = f;
+  }
+  RGG_CK(cudaMemcpyAsync(r->d_changed + kBoxesPerPass * kBoxRecFloats, lr, sizeof(lr),
+                         cudaMemcpyHostToDevice, s));
+  RGG_CK(cudaStreamSynchronize(s));  // lr lives on this stack frame
+  return RGG_OK;
 }
 
 uint32_t launch_ctas(const rgg_roadmap* r) { return (uint32_t)r->num_sms * r->ctas_per_sm; }
@@ -42,9 +65,11 @@ uint32_t launch_ctas(const rgg_roadmap* r) { return (uint32_t)r->num_sms * r->ct
 // Tile descriptors and per-tile edge tables of a roadmap (see
 // rgg_device.cuh): tile t covers global samples [t*S, min((t+1)*S, G)).
 bool build_tiles(uint32_t L, uint64_t N, const std::vector<uint64_t>& soff, uint64_t G,
-                 uint32_t S, std::vector<TileDesc>* tiles, std::vector<int4>* etab) {
+                 uint32_t S, std::vector<TileDesc>* tiles, std::vector<int4>* etab,
+                 std::vector<uint32_t>* halo) {
   const uint64_t T = (G + S - 1) / S;
   tiles->resize(T);
+  if (halo) halo->resize(T);
   etab->clear();
   etab->reserve(N + T);
   uint64_t ef = 0;  // edge holding the tile's first sample
@@ -69,6 +94,9 @@ bool build_tiles(uint32_t L, uint64_t N, const std::vector<uint64_t>& soff, uint
     (*tiles)[t].packed = o0 | ((o1 - o0) << 40) | (n_edges << 56);
     (*tiles)[t].etab = (uint32_t)etab->size();
     (*tiles)[t].e_first = (uint32_t)ef;
+    // link-end records: the entries before the tile that belong to its first
+    // edge, up to one link's run (they hold its first samples' near ends)
+    if (halo) (*halo)[t] = (uint32_t)std::min<uint64_t>(n_f, rf);
     for (uint64_t e = ef; e <= el; ++e) {
       const int64_t estart = (int64_t)(L * soff[e]) - (int64_t)g0;
       const int64_t ostart = (int64_t)(L * (soff[e] - e)) - (int64_t)o0;
@@ -85,15 +113,24 @@ bool build_tiles(uint32_t L, uint64_t N, const std::vector<uint64_t>& soff, uint
 // (Re)build the tile descriptors and edge tables of `es` for the roadmap's
 // current launch shape and copy them to the device (synchronous).
 int set_tiles(rgg_roadmap* r, EdgeState* es, cudaStream_t s) {
-  Tiling tiling = choose_tiling(r->L, r->K, es->G, 2 * launch_ctas(r), r->variant);
+  Tiling tiling = choose_tiling(r->L, r->K, es->G, 2 * launch_ctas(r), r->variant, es->joints,
+                                es->max_n);
+  if (tiling.S == 0) return RGG_ERR_INVALID;
   std::vector<TileDesc> h_tiles;
   std::vector<int4> h_etab;
-  if (es->N && !build_tiles(r->L, es->N, es->h_soff, es->G, tiling.S, &h_tiles, &h_etab))
+  std::vector<uint32_t> h_halo;
+  if (es->N && !build_tiles(r->L, es->N, es->h_soff, es->G, tiling.S, &h_tiles, &h_etab,
+                            es->joints ? &h_halo : nullptr))
     return RGG_ERR_INVALID;
   TileDesc* d_tiles = nullptr;
   int4* d_etab = nullptr;
+  uint32_t* d_halo = nullptr;
   cudaError_t e = dalloc(&d_tiles, h_tiles.size());
   if (e == cudaSuccess) e = dalloc(&d_etab, h_etab.size());
+  if (e == cudaSuccess) e = dalloc(&d_halo, h_halo.size());
+  if (e == cudaSuccess && !h_halo.empty())
+    e = cudaMemcpyAsync(d_halo, h_halo.data(), h_halo.size() * sizeof(uint32_t),
+                        cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess && !h_tiles.empty())
     e = cudaMemcpyAsync(d_tiles, h_tiles.data(), h_tiles.size() * sizeof(TileDesc),
                         cudaMemcpyHostToDevice, s);
@@ -105,18 +142,23 @@ int set_tiles(rgg_roadmap* r, EdgeState* es, cudaStream_t s) {
   if (e != cudaSuccess) {
     cudaFree(d_tiles);
     cudaFree(d_etab);
+    cudaFree(d_halo);
     return cuda_status(e);
   }
   release_rounds(es);  // they describe the old tiles
-  es->device_bytes -= es->T * sizeof(TileDesc) + es->n_etab * sizeof(int4);
+  es->device_bytes -= es->T * sizeof(TileDesc) + es->n_etab * sizeof(int4) +
+                      (es->d_tile_halo ? es->T * sizeof(uint32_t) : 0);
   cudaFree(es->d_tiles);
   cudaFree(es->d_etab);
+  cudaFree(es->d_tile_halo);
   es->d_tiles = d_tiles;
   es->d_etab = d_etab;
+  es->d_tile_halo = d_halo;
   es->T = h_tiles.size();
   es->n_etab = h_etab.size();
   es->tiling = tiling;
-  es->device_bytes += es->T * sizeof(TileDesc) + es->n_etab * sizeof(int4);
+  es->device_bytes += es->T * sizeof(TileDesc) + es->n_etab * sizeof(int4) +
+                      (d_halo ? es->T * sizeof(uint32_t) : 0);
   return RGG_OK;
 }
 
@@ -173,13 +215,18 @@ int compute_rounds(rgg_roadmap* r, EdgeState* es, cudaStream_t s) {
 // Allocate the per-edge state and record planes for N edges with per-edge
 // sample offsets h_soff (host), into `es` (not yet visible to the roadmap).
 int alloc_edges(rgg_roadmap* r, EdgeState* es, uint64_t N, std::vector<uint64_t>&& soff,
-                cudaStream_t s) {
+                cudaStream_t s, bool joints) {
   const bool spheres = r->geometry == RGG_GEOMETRY_SPHERES;
   es->N = N;
   es->h_soff = std::move(soff);
   es->S_tot = es->h_soff[N];
   es->G = (uint64_t)r->L * es->S_tot;
-  es->n_inner = spheres ? (uint64_t)r->K * es->G : 0;
+  es->joints = spheres && joints;
+  es->max_n = 0;
+  for (uint64_t e = 0; e < N; ++e)
+    es->max_n = std::max<uint64_t>(es->max_n, es->h_soff[e + 1] - es->h_soff[e]);
+  // link-end records: one entry per (edge, link, configuration), 3 planes
+  es->n_inner = spheres ? (es->joints ? es->G : (uint64_t)r->K * es->G) : 0;
   es->n_outer = spheres ? (uint64_t)r->L * (es->S_tot - N) : 0;
   // plane stride: count + 4 floats of tail slack for 16-byte rounding of the
   // bulk copies, rounded to 64 floats (256 B) to keep planes aligned
@@ -193,7 +240,7 @@ int alloc_edges(rgg_roadmap* r, EdgeState* es, uint64_t N, std::vector<uint64_t>
   }
   RGG_AL(es->d_soff, N + 1);
   if (spheres) {
-    RGG_AL(es->d_inner, 4 * es->in_stride);
+    RGG_AL(es->d_inner, (es->joints ? 3 : 4) * es->in_stride);
     RGG_AL(es->d_outer, 4 * es->out_stride);
   }
   RGG_AL(es->d_red, N * r->Wm);
@@ -221,7 +268,7 @@ int alloc_edges(rgg_roadmap* r, EdgeState* es, uint64_t N, std::vector<uint64_t>
   }
   if (e == cudaSuccess && N && spheres) {
     // zero the padded tails so that the rounded bulk copies read defined data
-    e = cudaMemsetAsync(es->d_inner, 0, 4 * es->in_stride * sizeof(float), s);
+    e = cudaMemsetAsync(es->d_inner, 0, (es->joints ? 3 : 4) * es->in_stride * sizeof(float), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(es->d_outer, 0, 4 * es->out_stride * sizeof(float), s);
   }
   if (e != cudaSuccess) {
@@ -379,6 +426,8 @@ ClassifyJob make_job(rgg_roadmap* r, uint32_t C, uint64_t tile_base) {
   // interpolated inner centres add up to ~2e-6 m of error on top of the FP32
   // rounding; the margin must cover both
   j.regular = (es.regular && r->margin >= kRegularMinMargin) ? 1u : 0u;
+  j.joints = es.joints ? 1u : 0u;
+  j.tile_halo = es.d_tile_halo;
   j.inv_k = 1.0f / (float)r->K;
   j.inv_km1 = r->K > 1 ? 1.0f / (float)(r->K - 1) : 0.0f;
   if (filter_active(r)) {
@@ -661,7 +710,8 @@ int rgg_roadmap_create(const rgg_roadmap_desc* desc, rgg_roadmap_t* out) {
   if (desc->num_links < 1 || desc->num_links > RGG_MAX_LINKS || desc->inner_per_link < 1 ||
       desc->inner_per_link > RGG_MAX_INNER || desc->max_obstacles < 1 ||
       desc->max_obstacles > RGG_MAX_OBSTACLES || !(desc->margin_m >= 0.0f) ||
-      !std::isfinite(desc->margin_m) || desc->geometry > RGG_GEOMETRY_OBB)
+      !std::isfinite(desc->margin_m) || desc->geometry > RGG_GEOMETRY_OBB ||
+      desc->record_format > RGG_RECORDS_SPHERES)
     return RGG_ERR_INVALID;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess) {
@@ -680,6 +730,7 @@ int rgg_roadmap_create(const rgg_roadmap_desc* desc, rgg_roadmap_t* out) {
   r->Wm = (r->M + 31) / 32;
   r->margin = desc->margin_m;
   r->geometry = desc->geometry;
+  r->record_format = desc->record_format;
   r->present.assign(r->M, 0);
   r->run_idx.assign(r->M, -1);
   r->req_state.assign(RGG_MAX_REQUESTS, 0);
@@ -687,7 +738,8 @@ int rgg_roadmap_create(const rgg_roadmap_desc* desc, rgg_roadmap_t* out) {
   cudaError_t e = cudaDeviceGetAttribute(&r->num_sms, cudaDevAttrMultiProcessorCount, r->device);
   if (e == cudaSuccess) e = dalloc(&r->d_table, (size_t)r->M * 16);
   if (e == cudaSuccess) e = dalloc(&r->d_stage, (size_t)r->stage_rows * 16);
-  if (e == cudaSuccess) e = dalloc(&r->d_changed, (size_t)kBoxesPerPass * kBoxRecFloats);
+  if (e == cudaSuccess) e = dalloc(&r->d_changed, (size_t)kBoxAreaFloats);
+  if (e == cudaSuccess) e = cudaMemset(r->d_changed, 0, (size_t)kBoxAreaFloats * sizeof(float));
   if (e == cudaSuccess) e = dalloc(&r->d_status, 4);
   if (e == cudaSuccess) e = dalloc(&r->d_work, 4);
   if (e == cudaSuccess) e = dalloc(&r->d_obbwork, 2);
@@ -820,7 +872,8 @@ int rgg_build_edges(rgg_roadmap_t r, const rgg_robot_desc* robot, uint64_t num_e
   std::vector<uint64_t> soff(num_edges + 1, 0);
   for (uint64_t i = 0; i < num_edges; ++i) soff[i + 1] = soff[i] + counts[i];
   EdgeState es;
-  int rc = alloc_edges(r, &es, num_edges, std::move(soff), s);
+  const bool joints = use_joints(r);
+  int rc = alloc_edges(r, &es, num_edges, std::move(soff), s, joints);
   if (rc != RGG_OK) {
     cleanup();
     return rc;
@@ -850,6 +903,7 @@ int rgg_build_edges(rgg_roadmap_t r, const rgg_robot_desc* robot, uint64_t num_e
     bp.in_stride = es.in_stride;
     bp.out_stride = es.out_stride;
     bp.n_edges = num_edges;
+    bp.joints = joints ? 1u : 0u;
     e = launch_build_records(bp, r->num_sms, s);
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -865,7 +919,15 @@ int rgg_build_edges(rgg_roadmap_t r, const rgg_robot_desc* robot, uint64_t num_e
   es.d_qa = d_qa;
   es.d_qb = d_qb;
   es.device_bytes += 2 * qn * sizeof(double);
-  es.regular = r->geometry == RGG_GEOMETRY_SPHERES;  // centres at (j + 1/2)/K, one radius per link
+  // sphere records: centres at (j + 1/2)/K, one radius per link
+  es.regular = r->geometry == RGG_GEOMETRY_SPHERES && !joints;
+  if (joints) {
+    rc = set_link_radii(r, robot->radius, s);
+    if (rc != RGG_OK) {
+      es.release();
+      return rc;
+    }
+  }
   rc = install_edges(r, std::move(es), s);
   if (rc == RGG_OK) {
     r->has_robot = true;
@@ -1026,8 +1088,38 @@ int rgg_fetch_records(rgg_roadmap_t r, uint64_t first, uint64_t count, float* in
   const uint64_t s0 = es.h_soff[first], s1 = es.h_soff[first + count];
   const uint64_t i0 = (uint64_t)r->K * r->L * s0, ni = (uint64_t)r->K * r->L * (s1 - s0);
   const uint64_t o0 = (uint64_t)r->L * (s0 - first), no = (uint64_t)r->L * (s1 - s0 - count);
+  if (inner_xyzr && es.joints) {
+    // link-end records: the inner spheres they stand for, centres
+    // interpolated in FP64 from the stored FP32 ends and rounded, radii R_i
+    const uint32_t L = r->L, K = r->K;
+    const uint64_t g0 = (uint64_t)L * s0, ng = (uint64_t)L * (s1 - s0);
+    std::vector<float> J(3 * ng);
+    float lr[kLinkRadiiFloats];
+    for (int p = 0; p < 3; ++p)
+      RGG_CK(cudaMemcpy(J.data() + p * ng, es.d_inner + p * es.in_stride + g0, ng * 4,
+                        cudaMemcpyDeviceToHost));
+    RGG_CK(cudaMemcpy(lr, r->d_changed + kBoxesPerPass * kBoxRecFloats, sizeof(lr),
+                      cudaMemcpyDeviceToHost));
+    for (uint64_t e = first; e < first + count; ++e) {
+      const uint64_t n = es.h_soff[e + 1] - es.h_soff[e];
+      const uint64_t ge = (uint64_t)L * es.h_soff[e] - g0;
+      for (uint32_t i = 0; i < L; ++i)
+        for (uint64_t k = 0; k < n; ++k) {
+          const uint64_t g = ge + i * n + k;
+          for (uint32_t j = 0; j < K; ++j) {
+            const double f = ((double)j + 0.5) / (double)K;
+            const uint64_t out = (uint64_t)K * g + j;
+            for (int c = 0; c < 3; ++c) {
+              const double b = J[c * ng + g], a = i > 0 ? J[c * ng + g - n] : 0.0;
+              inner_xyzr[c * ni + out] = (float)(a + f * (b - a));
+            }
+            inner_xyzr[3 * ni + out] = lr[i];
+          }
+        }
+    }
+  }
   for (int p = 0; p < 4; ++p) {
-    if (inner_xyzr)
+    if (inner_xyzr && !es.joints)
       RGG_CK(cudaMemcpy(inner_xyzr + p * ni, es.d_inner + p * es.in_stride + i0, ni * 4,
                         cudaMemcpyDeviceToHost));
     if (outer_xyzr && no)
@@ -1066,9 +1158,10 @@ int rgg_roadmap_info(rgg_roadmap_t r, rgg_info* out) {
   const EdgeState& es = r->es;
   out->num_edges = es.N;
   out->num_samples = es.S_tot;
-  out->num_inner = es.n_inner;
+  out->num_inner = es.joints ? (uint64_t)r->K * es.G : es.n_inner;
   out->num_outer = es.n_outer;
-  out->record_bytes = 16 * (es.n_inner + es.n_outer);
+  out->record_bytes = es.joints ? 12 * es.n_inner + 16 * es.n_outer : 16 * (es.n_inner + es.n_outer);
+  out->record_format = es.joints ? RGG_RECORDS_LINK_ENDS : RGG_RECORDS_SPHERES;
   out->device_bytes = es.device_bytes + fixed_device_bytes(r);
   out->num_links = r->L;
   out->inner_per_link = r->K;
@@ -1153,8 +1246,11 @@ int rgg_estimate_bytes(const rgg_roadmap_desc* desc, uint64_t num_edges, const d
       !(step > 0.0) || !std::isfinite(step) || (num_edges && (!q_from || !q_to)) ||
       num_edges >= 0xffffffffull)
     return RGG_ERR_INVALID;
-  if (desc->geometry != RGG_GEOMETRY_SPHERES) return RGG_ERR_STATE;
+  if (desc->geometry != RGG_GEOMETRY_SPHERES || desc->record_format > RGG_RECORDS_SPHERES)
+    return desc->geometry != RGG_GEOMETRY_SPHERES ? RGG_ERR_STATE : RGG_ERR_INVALID;
   const uint32_t L = desc->num_links, K = desc->inner_per_link, M = desc->max_obstacles;
+  const bool joints = desc->record_format == RGG_RECORDS_LINK_ENDS &&
+                      desc->margin_m >= kRegularMinMargin;
   const uint32_t Wm = (M + 31) / 32;
   // rgg_build_edges' configuration counts, on the host
   std::vector<uint64_t> soff(num_edges + 1, 0);
@@ -1180,20 +1276,24 @@ int rgg_estimate_bytes(const rgg_roadmap_desc* desc, uint64_t num_edges, const d
     sms = 152;
   }
   uint64_t tile_bytes = 0;
+  uint32_t max_n = 0;
+  for (uint64_t e = 0; e < N; ++e) max_n = std::max<uint64_t>(max_n, soff[e + 1] - soff[e]);
   if (N) {
-    const Tiling t = choose_tiling(L, K, G, 2 * (uint32_t)sms, kDefaultVariant);
+    const Tiling t = choose_tiling(L, K, G, 2 * (uint32_t)sms, kDefaultVariant, joints, max_n);
+    if (t.S == 0) return RGG_ERR_INVALID;
     std::vector<TileDesc> tiles;
     std::vector<int4> etab;
     if (!build_tiles(L, N, soff, G, t.S, &tiles, &etab)) return RGG_ERR_INVALID;
-    tile_bytes = tiles.size() * sizeof(TileDesc) + etab.size() * sizeof(int4);
+    tile_bytes = tiles.size() * (sizeof(TileDesc) + (joints ? sizeof(uint32_t) : 0)) +
+                 etab.size() * sizeof(int4);
   }
-  const uint64_t n_in = (uint64_t)K * G, n_out = (uint64_t)L * (S - N);
+  const uint64_t n_in = joints ? G : (uint64_t)K * G, n_out = (uint64_t)L * (S - N);
   const uint64_t in_stride = ((n_in + 4 + 63) / 64) * 64, out_stride = ((n_out + 4 + 63) / 64) * 64;
-  uint64_t b = (N + 1) * 8 + 16 * in_stride + 16 * out_stride;  // offsets and record planes
+  uint64_t b = (N + 1) * 8 + (joints ? 12 : 16) * in_stride + 16 * out_stride;  // offsets, records
   b += N * (2ull * Wm * 4 + 4 + 1 + 8);                         // box sets, counts, labels, pass bits
   b += tile_bytes;
   b += 2 * N * L * sizeof(double);                              // endpoints (gray resolution)
-  b += (uint64_t)M * 64 + (uint64_t)(M + RGG_PENDING_EXTRA) * 64 + kBoxesPerPass * kBoxRecFloats * 4 + 16;
+  b += (uint64_t)M * 64 + (uint64_t)(M + RGG_PENDING_EXTRA) * 64 + kBoxAreaFloats * 4 + 16;
   *bytes = b;
   return RGG_OK;
 }

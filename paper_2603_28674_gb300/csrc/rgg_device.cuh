@@ -1,10 +1,20 @@
 // Device-side structures and PTX helpers shared by the RGG kernels.
 //
-// Record layout on the device (one roadmap):
-//   inner spheres  4 FP32 planes (x, y, z, r), plane p at inner + p*in_stride;
-//                  sphere (edge e, link i, sample k, sphere j) at
-//                  K*(L*soff[e] + i*n_e + k) + j   (Sec. 4.3's E^- tensor,
-//                  unpadded: edge, body, configuration, sphere)
+// Record layout on the device (one roadmap), in one of two formats:
+//   sphere records (uploaded edges, or built ones on request)
+//     inner spheres  4 FP32 planes (x, y, z, r), plane p at inner + p*in_stride;
+//                    sphere (edge e, link i, sample k, sphere j) at
+//                    K*(L*soff[e] + i*n_e + k) + j   (Sec. 4.3's E^- tensor,
+//                    unpadded: edge, body, configuration, sphere)
+//   link-end records (built edges, the default)
+//     link ends      3 FP32 planes (x, y, z); entry L*soff[e] + i*n_e + k holds
+//                    the far end o_{i+1} of link i at configuration k.  The
+//                    near end of link i is entry - n_e (the far end of link
+//                    i-1), or the base (the world origin) for link 0.  The K
+//                    inner spheres of (e, i, k) sit at fractions (j + 1/2)/K of
+//                    the segment between the two ends, radius R_i (a per-
+//                    roadmap table), so only 12 B per (edge, link,
+//                    configuration) are stored instead of 16*K.
 //   outer spheres  4 FP32 planes; sphere (e, i, interval k) at
 //                  L*(soff[e] - e) + i*(n_e - 1) + k
 // A "global sample" g indexes the concatenation over edges and links of the
@@ -15,7 +25,10 @@
 // Streaming tiles: tile t covers the global samples [t*S, min((t+1)*S, G)),
 // every interval adjacent to one of them (one halo interval before the first
 // sample when the tile starts inside a link's run), and a table with one
-// entry per edge that has samples in the tile.
+// entry per edge that has samples in the tile.  With link-end records the
+// tile also copies the h_t entries before its first sample that belong to
+// its first edge (h_t = min(n_e, offset of the tile in that edge), at most
+// one link's run), which hold the near ends of its first samples.
 //
 // Rounds: round r of a tile is its samples [31r, 31r+31) and the intervals
 // that follow its local samples 31r-1 .. 31r+30 (those a consumer warp tests
@@ -42,6 +55,10 @@ constexpr int kStageAccOff = kStageHdrBytes;                 // hit[kAccMax], to
 constexpr int kStageEtabOff = kStageAccOff + 8 * kAccMax;    // edge table
 constexpr int kMaxTileEdges = kAccMax;
 constexpr int kBoxSlots = 2;           // jobs whose box records a CTA stages in shared memory
+// The pass's box area: 32 derived box records, then the link radii R_i of the
+// roadmap (link-end records take their inner radius from there).
+constexpr int kLinkRadiiFloats = 32;
+constexpr int kBoxAreaFloats = kBoxesPerPass * kBoxRecFloats + kLinkRadiiFloats;
 
 // Derived record of one moved box, built by the box-prep kernel:
 //   r0 = (centre.xyz, bounding radius |h| rounded up)
@@ -62,12 +79,12 @@ struct TileDesc {
 
 // One roadmap's part of a classify launch.
 struct ClassifyJob {
-  const float* inner;
+  const float* inner;               // inner-sphere planes, or link-end planes (joints)
   const float* outer;
   uint64_t in_stride, out_stride;   // floats between planes
   const TileDesc* tiles;            // [T]
   const int4* etab;                 // edge tables of all tiles
-  const float* boxes;               // [C][24] derived records of this pass's boxes
+  const float* boxes;               // box area: [32][24] derived records, then link radii
   uint32_t* edge_acc;               // [N][2] (hit, touch) bits of this pass, kept zero between passes
   uint64_t G;                       // L * soff[N] global samples
   uint64_t tile_base;               // first queue index of this job's tiles
@@ -80,6 +97,10 @@ struct ClassifyJob {
   // along a segment (the records rgg_build_edges writes), so the kernel may
   // interpolate their centres from the first and the last
   uint32_t regular;
+  // 1: link-end records (see above); the inner spheres are interpolated from
+  // the two ends of their link, always (the margin covers it)
+  uint32_t joints;
+  const uint32_t* tile_halo;        // [T] link-end entries copied before a tile's first sample
   float inv_k, inv_km1;             // 1/K and 1/(K-1) (0 when K = 1)
   // spatial filter (all three null: every round of every tile is copied)
   const float4* rsph;               // [T][kRoundSlots] bounding sphere (radius < 0: empty)

@@ -59,8 +59,8 @@ cudaError_t dalloc(T** p, size_t count) {
 constexpr float kRegularMinMargin = 1e-5f;
 
 // Streaming tile geometry of one roadmap (see the classify kernel): each
-// stage buffer holds a header, the tile's edge table, 4 inner planes and 4
-// outer planes.
+// stage buffer holds a header, the tile's edge table, 4 inner planes (or 3
+// link-end planes) and 4 outer planes.
 struct Tiling {
   uint32_t S = 0, max_edges = 0;
   uint32_t off_in = 0, off_out = 0, in_cap = 0, out_cap = 0;
@@ -70,13 +70,17 @@ inline uint32_t align16(uint32_t x) { return (x + 15u) & ~15u; }
 inline uint32_t round4(uint32_t x) { return (x + 3u) & ~3u; }
 
 // A window of S consecutive global samples meets at most S/(2L) + 2 edges
-// (every edge has at least 2L samples); one more entry of slack.
-inline bool tiling_for(uint32_t L, uint32_t K, uint32_t S, uint32_t stage_bytes, Tiling* t) {
+// (every edge has at least 2L samples); one more entry of slack.  Link-end
+// planes hold the tile's S entries, up to max_n halo entries before them
+// (the longest edge's configuration count bounds a link's run) and the
+// 16-byte rounding of the copy.
+inline bool tiling_for(uint32_t L, uint32_t K, uint32_t S, uint32_t stage_bytes, bool joints,
+                       uint32_t max_n, Tiling* t) {
   t->S = S;
   t->max_edges = S / (2 * L) + 3;
   t->off_in = align16(kStageEtabOff + 16 * t->max_edges);
-  t->in_cap = round4(K * S + 8);
-  t->off_out = t->off_in + 16 * t->in_cap;
+  t->in_cap = joints ? round4(S + max_n + 8) : round4(K * S + 8);
+  t->off_out = t->off_in + (joints ? 12 : 16) * t->in_cap;
   t->out_cap = round4(S + 1 + 8);
   return t->max_edges <= (uint32_t)kMaxTileEdges &&
          (uint64_t)t->off_out + 16ull * t->out_cap <= (uint64_t)stage_bytes;
@@ -85,16 +89,19 @@ inline bool tiling_for(uint32_t L, uint32_t K, uint32_t S, uint32_t stage_bytes,
 // Tiles of 31*rounds samples (full rounds) when they fit a stage, else the
 // largest that does; smaller only for roadmaps too small to give every CTA of
 // a launch two tiles (big tiles keep the producer warp's per-tile cost low).
-inline Tiling choose_tiling(uint32_t L, uint32_t K, uint64_t G, uint32_t warps, int variant) {
+// S = 0 when nothing fits (link-end records of an edge longer than a stage).
+inline Tiling choose_tiling(uint32_t L, uint32_t K, uint64_t G, uint32_t warps, int variant,
+                            bool joints = false, uint32_t max_n = 0) {
   // `warps`: how many tiles the roadmap should at least be cut into
   const VariantShape v = variant_shape(variant);
   uint32_t smax = 31 * v.rounds;
   Tiling t;
-  while (smax > 1 && !tiling_for(L, K, smax, v.stage_bytes, &t)) --smax;
+  while (smax > 1 && !tiling_for(L, K, smax, v.stage_bytes, joints, max_n, &t)) --smax;
+  if (!tiling_for(L, K, smax, v.stage_bytes, joints, max_n, &t)) return Tiling();
   const uint64_t want = (G + warps - 1) / std::max<uint32_t>(warps, 1);
   uint32_t s = (uint32_t)std::min<uint64_t>(smax, std::max<uint64_t>(want, 31));
   s = std::max<uint32_t>(1, std::min(s, smax));
-  tiling_for(L, K, s, v.stage_bytes, &t);
+  tiling_for(L, K, s, v.stage_bytes, joints, max_n, &t);
   return t;
 }
 
@@ -140,6 +147,11 @@ struct EdgeState {
   uint32_t* d_rcand = nullptr;
   uint64_t device_bytes = 0;
   bool regular = false;        // inner spheres equally spaced with one radius per sample
+  // link-end records (3 planes, see rgg_device.cuh) instead of inner spheres,
+  // with per-tile halo counts; max_n = the longest edge's configurations
+  bool joints = false;
+  uint32_t* d_tile_halo = nullptr;
+  uint32_t max_n = 0;
 
   void release() {
     cudaFree(d_soff);
@@ -167,6 +179,7 @@ struct EdgeState {
     cudaFree(d_rsph);
     cudaFree(d_rout);
     cudaFree(d_rcand);
+    cudaFree(d_tile_halo);
     *this = EdgeState();
   }
 };
@@ -196,7 +209,8 @@ struct rgg_roadmap {
   float* d_table = nullptr;    // [M][16] box poses
   float* d_stage = nullptr;    // [stage_rows][16] staged pose of each pending entry
   uint32_t stage_rows = 0;
-  float* d_changed = nullptr;  // [32][24] derived records of the current pass
+  float* d_changed = nullptr;  // box area: [32][24] derived records of the pass, link radii
+  uint32_t record_format = 0;  // 0: link-end records for built edges when the margin allows
   int* d_status = nullptr;          // [0] status word, [1] classify work counter
   uint64_t wait_ns = 4000000000ull; // limit of the classify kernel's bounded waits
   std::vector<uint8_t> present;
@@ -225,10 +239,13 @@ namespace rgg_host {
 // rgg_api.cu
 uint32_t launch_ctas(const rgg_roadmap* r);
 bool build_tiles(uint32_t L, uint64_t N, const std::vector<uint64_t>& soff, uint64_t G, uint32_t S,
-                 std::vector<TileDesc>* tiles, std::vector<int4>* etab);
+                 std::vector<TileDesc>* tiles, std::vector<int4>* etab,
+                 std::vector<uint32_t>* halo = nullptr);
 int set_tiles(rgg_roadmap* r, EdgeState* es, cudaStream_t s);
 int alloc_edges(rgg_roadmap* r, EdgeState* es, uint64_t N, std::vector<uint64_t>&& soff,
-                cudaStream_t s);
+                cudaStream_t s, bool joints = false);
+bool use_joints(const rgg_roadmap* r);
+int set_link_radii(rgg_roadmap* r, const double* radius, cudaStream_t s);
 void clear_pending(rgg_roadmap* r);
 int requeue_present(rgg_roadmap* r, cudaStream_t s);
 uint64_t fixed_device_bytes(const rgg_roadmap* r);

@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(256) build_records_kernel(const __grid_constan
   float* ix = p.inner;
   float* iy = p.inner + p.in_stride;
   float* iz = p.inner + 2 * p.in_stride;
-  float* ir = p.inner + 3 * p.in_stride;
+  float* ir = p.joints ? nullptr : p.inner + 3 * p.in_stride;
   float* ox = p.outer;
   float* oy = p.outer + p.out_stride;
   float* oz = p.outer + 2 * p.out_stride;
@@ -99,14 +99,22 @@ __global__ void __launch_bounds__(256) build_records_kernel(const __grid_constan
           const double v0 = p.a[i] * ct, v1 = p.a[i] * st, v2 = p.d[i];
           double on[3];
           for (int r = 0; r < 3; ++r) on[r] = o[r] + R[3 * r] * v0 + R[3 * r + 1] * v1 + R[3 * r + 2] * v2;
-          const float rad = __double2float_rd(p.radius[i]);
-          const uint64_t base = in_base + (uint64_t)K * ((uint64_t)i * n + k);
-          for (uint32_t j = 0; j < K; ++j) {
-            const double f = ((double)j + 0.5) / (double)K;
-            ix[base + j] = (float)(o[0] + f * (on[0] - o[0]));
-            iy[base + j] = (float)(o[1] + f * (on[1] - o[1]));
-            iz[base + j] = (float)(o[2] + f * (on[2] - o[2]));
-            ir[base + j] = rad;
+          if (p.joints) {
+            // link-end records: the far end of link i at q_k
+            const uint64_t g = (uint64_t)L * so + (uint64_t)i * n + k;
+            ix[g] = (float)on[0];
+            iy[g] = (float)on[1];
+            iz[g] = (float)on[2];
+          } else {
+            const float rad = __double2float_rd(p.radius[i]);
+            const uint64_t base = in_base + (uint64_t)K * ((uint64_t)i * n + k);
+            for (uint32_t j = 0; j < K; ++j) {
+              const double f = ((double)j + 0.5) / (double)K;
+              ix[base + j] = (float)(o[0] + f * (on[0] - o[0]));
+              iy[base + j] = (float)(o[1] + f * (on[1] - o[1]));
+              iz[base + j] = (float)(o[2] + f * (on[2] - o[2]));
+              ir[base + j] = rad;
+            }
           }
           // R <- R * Rz(q) Rx(alpha)
           const double A[9] = {ct, -st * ca, st * sa, st, ct * ca, -ct * sa, 0.0, sa, ca};
@@ -276,6 +284,42 @@ __device__ __forceinline__ bool inner_hit_regular(const float* __restrict__ ix,
   return false;
 }
 
+// a4 for link-end records: does one of the K inner spheres of a link at one
+// configuration (centres at fractions (j + 1/2)/K of the segment from its near
+// end a to its far end b, common radius R_i - margin = rr > 0) lie within rr
+// of box B?  Both ends are transformed into the box frame once and the
+// centres interpolated there; a link whose spheres' box-frame bounding box
+// is farther than rr from the box is rejected first.
+__device__ __forceinline__ bool inner_hit_joints(float ax, float ay, float az, float bx, float by,
+                                                 float bz, int K, float inv_k, float rr,
+                                                 const float4* __restrict__ B) {
+  const float4 a0 = B[1], a1 = B[2], a2 = B[3], h = B[4];
+  const float p0 = fmaf(a0.x, ax, fmaf(a0.y, ay, fmaf(a0.z, az, -a0.w)));
+  const float p1 = fmaf(a1.x, ax, fmaf(a1.y, ay, fmaf(a1.z, az, -a1.w)));
+  const float p2 = fmaf(a2.x, ax, fmaf(a2.y, ay, fmaf(a2.z, az, -a2.w)));
+  const float q0 = fmaf(a0.x, bx, fmaf(a0.y, by, fmaf(a0.z, bz, -a0.w)));
+  const float q1 = fmaf(a1.x, bx, fmaf(a1.y, by, fmaf(a1.z, bz, -a1.w)));
+  const float q2 = fmaf(a2.x, bx, fmaf(a2.y, by, fmaf(a2.z, bz, -a2.w)));
+  // step between consecutive centres, and the first and the last centre
+  const float d0 = (q0 - p0) * inv_k, d1 = (q1 - p1) * inv_k, d2 = (q2 - p2) * inv_k;
+  const float tl = (float)K - 0.5f;
+  const float f0 = fmaf(0.5f, d0, p0), f1 = fmaf(0.5f, d1, p1), f2 = fmaf(0.5f, d2, p2);
+  const float l0 = fmaf(tl, d0, p0), l1 = fmaf(tl, d1, p1), l2 = fmaf(tl, d2, p2);
+  const float rr2 = rr * rr;
+  const float g0 = fmaxf(fmaxf(fminf(f0, l0) - h.x, -h.x - fmaxf(f0, l0)), 0.0f);
+  const float g1 = fmaxf(fmaxf(fminf(f1, l1) - h.y, -h.y - fmaxf(f1, l1)), 0.0f);
+  const float g2 = fmaxf(fmaxf(fminf(f2, l2) - h.z, -h.z - fmaxf(f2, l2)), 0.0f);
+  if (fmaf(g0, g0, fmaf(g1, g1, g2 * g2)) > rr2) return false;
+  for (int j = 0; j < K; ++j) {
+    const float t = (float)j + 0.5f;
+    const float e0 = fmaxf(fabsf(fmaf(t, d0, p0)) - h.x, 0.0f);
+    const float e1 = fmaxf(fabsf(fmaf(t, d1, p1)) - h.y, 0.0f);
+    const float e2 = fmaxf(fabsf(fmaf(t, d2, p2)) - h.z, 0.0f);
+    if (fmaf(e0, e0, fmaf(e1, e1, e2 * e2)) <= rr2) return true;
+  }
+  return false;
+}
+
 // largest j in [0, n) with tab[4*j + field] <= v (tab[field] <= v holds)
 __device__ __forceinline__ int search_le(const int* tab, int field, int n, int v) {
   int lo = 0, hi = n - 1;
@@ -287,11 +331,11 @@ __device__ __forceinline__ int search_le(const int* tab, int field, int n, int v
 }
 
 // Where local sample q of a tile sits: its edge-table entry j, the edge's
-// configuration count n, its position k in its link's run, and the local
-// index o of the interval that follows it (branch-free).  `valid`: q is one
+// configuration count n, its link li and position k in that link's run, and
+// the local index o of the interval that follows it (branch-free).  `valid`: q is one
 // of the tile's samples [0, q_end); `has_next`: an interval follows it.
 struct SampleAt {
-  int j, n, k, o;
+  int j, n, k, o, li;
   bool valid, has_next;
 };
 __device__ __forceinline__ SampleAt locate_sample(const int* etab, int n_edges, int q, int q_end) {
@@ -306,6 +350,7 @@ __device__ __forceinline__ SampleAt locate_sample(const int* etab, int n_edges, 
   li += adj;
   k -= adj * a.n;
   a.k = k;
+  a.li = li;
   a.valid = q < q_end && rr >= 0;
   a.has_next = a.valid && k < a.n - 1;
   a.o = a.has_next ? ej.z + li * (a.n - 1) + k : 0;
@@ -484,11 +529,12 @@ __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const 
   constexpr size_t kOffCnt = kOffItem + 8;
   constexpr size_t kOffDesc = (kOffCnt + 4 * ((NSTAGE + 3) & ~3) + 15) & ~(size_t)15;
   constexpr size_t kOffDjob = kOffDesc + 32 * sizeof(TileDesc);
-  constexpr size_t kOffNeed = kOffDjob + 32 * sizeof(int);
+  constexpr size_t kOffHalo = kOffDjob + 32 * sizeof(int);
+  constexpr size_t kOffNeed = kOffHalo + 32 * sizeof(uint32_t);
   constexpr size_t kOffCand = kOffNeed + (FILTER ? 32 * sizeof(uint32_t) : 0);  // 16-byte aligned
   constexpr size_t kOffBoxes =
       (kOffCand + (FILTER ? (size_t)NSTAGE * kRoundSlots * 4 : 0) + 127) & ~(size_t)127;
-  constexpr size_t kOffQueues = kOffBoxes + (size_t)kBoxAreas * kBoxesPerPass * kBoxRecFloats * 4;
+  constexpr size_t kOffQueues = kOffBoxes + (size_t)kBoxAreas * kBoxAreaFloats * 4;
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char* stages = smem;
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + kOffFull);
@@ -498,6 +544,7 @@ __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const 
   uint32_t* s_cnt = reinterpret_cast<uint32_t*>(smem + kOffCnt);       // items done per stage
   TileDesc* s_desc = reinterpret_cast<TileDesc*>(smem + kOffDesc);     // producer's batch
   int* s_djob = reinterpret_cast<int*>(smem + kOffDjob);
+  uint32_t* s_halo = reinterpret_cast<uint32_t*>(smem + kOffHalo);  // producer's batch
   uint32_t* s_need = reinterpret_cast<uint32_t*>(smem + kOffNeed);  // producer's batch
   // per stage (spatial filter): the moved boxes that may reach each round of
   // its tile, 0 for a round that was not copied
@@ -537,9 +584,10 @@ __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const 
     *s_item = 0;
     fence_mbar_init();
     if (MAXJ == 1) {
-      const uint32_t bytes = P.job[0].C * (uint32_t)(kBoxRecFloats * 4);
+      // the whole box area: the pass's box records and the link radii
+      const uint32_t bytes = (uint32_t)(kBoxAreaFloats * 4);
       mbar_arrive_expect_tx(boxbar, bytes);
-      if (bytes) bulk_g2s(s_boxes, P.job[0].boxes, bytes, boxbar);
+      bulk_g2s(s_boxes, P.job[0].boxes, bytes, boxbar);
     } else {
       mbar_arrive(boxbar);
     }
@@ -573,6 +621,7 @@ __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const 
         const ClassifyJob& J = P.job[jb];
         s_desc[lane] = J.tiles[t - J.tile_base];
         s_djob[lane] = jb;
+        s_halo[lane] = J.joints ? J.tile_halo[t - J.tile_base] : 0u;
         if constexpr (FILTER)
           s_need[lane] = J.rcand ? J.rcand[(t - J.tile_base) * kRoundSlots + kRoundSlots - 1] : ~0u;
       }
@@ -586,6 +635,7 @@ __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const 
         const int jb = s_djob[i];
         const ClassifyJob& J = P.job[jb];
         const TileDesc d = s_desc[i];
+        const uint32_t halo = s_halo[i];
         const uint64_t lt = tb + i - J.tile_base;
         uint32_t need = ~0u, ro = 0;
         if constexpr (FILTER) {
@@ -607,7 +657,13 @@ __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const 
         const uint64_t K = J.K;
         const uint64_t g0 = lt * J.S;
         const uint64_t g1 = min(g0 + J.S, J.G);
-        const uint64_t a0 = (K * g0) & ~3ull, a1 = (K * g1 + 3) & ~3ull;
+        // inner window: the tile's K spheres per sample, or its link ends and
+        // the h_t ends before it that hold its first samples' near ends
+        const bool jt = J.joints != 0;
+        const uint64_t w0 = jt ? g0 - halo : K * g0;
+        const uint64_t a0 = w0 & ~3ull, a1 = ((jt ? g1 : K * g1) + 3) & ~3ull;
+        const int in_shift = (int)((jt ? g0 : K * g0) - a0);
+        const uint32_t n_in = jt ? 3u : 4u;
         const uint64_t o0 = d.packed & ((1ull << 40) - 1);
         const uint32_t n_out = (uint32_t)((d.packed >> 40) & 0xffff);
         const uint32_t n_edges = (uint32_t)(d.packed >> 56);
@@ -617,11 +673,12 @@ __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const 
         // the stage's box records are refreshed only when its job changes
         const int held = __shfl_sync(0xffffffffu, stage_job, stage);
         const uint32_t box_bytes =
-            (MAXJ != 1 && held != jb) ? J.C * (uint32_t)(kBoxRecFloats * 4) : 0u;
+            (MAXJ != 1 && held != jb) ? (uint32_t)(kBoxAreaFloats * 4) : 0u;
         if (lane == stage) stage_job = jb;
         // whole-tile copies (every job of the streaming instance): lane 0 the
-        // edge table, lanes 1..4 the inner planes, 5..8 the outer ones, lane 9
-        // the box records; one predicated issue after the wait
+        // edge table, lanes 1..4 the inner planes (1..3 the link-end planes),
+        // 5..8 the outer ones, lane 9 the box area; one predicated issue after
+        // the wait
         const uint32_t in_bytes = (uint32_t)((a1 - a0) * 4);
         const uint32_t out_bytes = (uint32_t)((b1 - b0) * 4);
         void* c_dst = sb + kStageEtabOff;
@@ -630,13 +687,13 @@ __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const 
         if (lane >= 1 && lane <= 4) {
           c_dst = sb + J.off_in + (size_t)(lane - 1) * J.in_cap * 4;
           c_src = J.inner + (lane - 1) * J.in_stride + a0;
-          c_bytes = in_bytes;
+          c_bytes = (uint32_t)(lane - 1) < n_in ? in_bytes : 0u;
         } else if (lane >= 5 && lane <= 8) {
           c_dst = sb + J.off_out + (size_t)(lane - 5) * J.out_cap * 4;
           c_src = J.outer + (lane - 5) * J.out_stride + b0;
           c_bytes = out_bytes;
         } else if (lane == 9) {
-          c_dst = s_boxes + (size_t)stage * kBoxesPerPass * 6;
+          c_dst = s_boxes + (size_t)stage * (kBoxAreaFloats / 4);
           c_src = J.boxes;
           c_bytes = box_bytes;
         } else if (lane > 9) {
@@ -654,26 +711,30 @@ __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const 
         if (!FILTER || J.rcand == nullptr) {
           // the whole tile
           if (lane == 0) {
-            write_stage_hdr(sb, jb, g0, g1, n_out, n_edges, (int)(K * g0 - a0), (int)(o0 - b0),
-                            d.e_first);
-            mbar_arrive_expect_tx(&full[stage], et_bytes + 4 * in_bytes + 4 * out_bytes + box_bytes);
+            write_stage_hdr(sb, jb, g0, g1, n_out, n_edges, in_shift, (int)(o0 - b0), d.e_first);
+            mbar_arrive_expect_tx(&full[stage],
+                                  et_bytes + n_in * in_bytes + 4 * out_bytes + box_bytes);
           }
-          tile_rec_bytes = 4 * (in_bytes + out_bytes);
+          tile_rec_bytes = n_in * in_bytes + 4 * out_bytes;
           __syncwarp();
           if (c_bytes) bulk_g2s(c_dst, c_src, c_bytes, &full[stage]);
         } else if constexpr (FILTER) {
           // the runs of consecutive rounds in `need`: the lane of a run's
           // first round copies the run's 4 inner and 4 outer plane pieces,
-          // at the offsets they have in a whole-tile copy; lane 10 copies the
-          // tile's candidate row for the consumers
+          // at the offsets they have in a whole-tile copy (link-end planes,
+          // 12 B per sample, are copied whole by lanes 1..3, since a run's
+          // near ends may lie in rounds the run does not cover); lane 10
+          // copies the tile's candidate row for the consumers
           const bool starts = ((need >> lane) & 1u) && (lane == 0 || !((need >> (lane - 1)) & 1u));
           const uint32_t clear_above = ~need & ~((2u << lane) - 1u);
           const int re = clear_above ? __ffs(clear_above) - 1 : 32;  // run = rounds [lane, re)
           const uint32_t ro_last = __shfl_sync(0xffffffffu, ro, starts ? re - 1 : lane);
           uint64_t ia = a0, ib = a0, oa = b0, ob = b0;
           if (starts) {
-            ia = (K * (g0 + (uint64_t)(31 * lane))) & ~3ull;
-            ib = (K * min(g0 + (uint64_t)(31 * re), g1) + 3) & ~3ull;
+            if (!jt) {
+              ia = (K * (g0 + (uint64_t)(31 * lane))) & ~3ull;
+              ib = (K * min(g0 + (uint64_t)(31 * re), g1) + 3) & ~3ull;
+            }
             oa = (o0 + (ro & 0xffffu)) & ~3ull;
             ob = (o0 + (ro_last >> 16) + 3) & ~3ull;
           }
@@ -684,17 +745,21 @@ __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const 
           ob = max(min(ob, b1), oa);
           const uint32_t run_in = (uint32_t)((ib - ia) * 4);
           const uint32_t run_out = (uint32_t)((ob - oa) * 4);
-          const uint32_t tile_bytes = __reduce_add_sync(0xffffffffu, 4 * (run_in + run_out));
+          const uint32_t tile_bytes = __reduce_add_sync(0xffffffffu, 4 * (run_in + run_out)) +
+                                      (jt ? 3 * in_bytes : 0u);
           if (lane == 0) {
-            write_stage_hdr(sb, jb, g0, g1, n_out, n_edges, (int)(K * g0 - a0), (int)(o0 - b0),
-                            d.e_first);
+            write_stage_hdr(sb, jb, g0, g1, n_out, n_edges, in_shift, (int)(o0 - b0), d.e_first);
             mbar_arrive_expect_tx(&full[stage], et_bytes + tile_bytes + box_bytes + 4 * kRoundSlots);
           }
           tile_rec_bytes = tile_bytes;
           __syncwarp();
           if (lane == 0) bulk_g2s(sb + kStageEtabOff, J.etab + d.etab, et_bytes, &full[stage]);
           if (lane == 9 && box_bytes)
-            bulk_g2s(s_boxes + (size_t)stage * kBoxesPerPass * 6, J.boxes, box_bytes, &full[stage]);
+            bulk_g2s(s_boxes + (size_t)stage * (kBoxAreaFloats / 4), J.boxes, box_bytes,
+                     &full[stage]);
+          if (jt && lane >= 1 && lane <= 3)
+            bulk_g2s(sb + J.off_in + (size_t)(lane - 1) * J.in_cap * 4,
+                     J.inner + (lane - 1) * J.in_stride + a0, in_bytes, &full[stage]);
           if (lane == 10)
             bulk_g2s(s_cand + stage * kRoundSlots, J.rcand + lt * kRoundSlots, 4 * kRoundSlots,
                      &full[stage]);
@@ -810,7 +875,10 @@ __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const 
     const float* oy = ox + J.out_cap;
     const float* oz = oy + J.out_cap;
     const float* orad = oz + J.out_cap;
-    const float4* bx = MAXJ == 1 ? s_boxes : s_boxes + (size_t)stage * kBoxesPerPass * 6;
+    const float4* bx = MAXJ == 1 ? s_boxes : s_boxes + (size_t)stage * (kBoxAreaFloats / 4);
+    // link radii of the roadmap, after its box records (link-end records)
+    const float* link_r = reinterpret_cast<const float*>(bx + kBoxesPerPass * 6);
+    const bool joints = J.joints != 0;
     const int r_end = min((sub + 1) * RPI, ROUNDS);
     for (int rnd = sub * RPI; rnd < r_end; ++rnd) {
       const int base = 31 * rnd;
@@ -823,7 +891,7 @@ __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const 
       }
       const int q = base - 1 + lane;
       const SampleAt at = locate_sample(etab, n_edges, q, min(base + 31, n_samp));
-      const int j = at.j, n = at.n, k = at.k, o = at.o;
+      const int j = at.j, n = at.n, k = at.k, o = at.o, li = at.li;
       const bool valid = at.valid, has_next = at.has_next;
       // ---- a3: the outer sphere of the interval after q, against the moved
       // boxes that survive a warp bounding-sphere cull
@@ -885,29 +953,66 @@ __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const 
         if (lane >= d) incl += v;
       }
       const int total = __shfl_sync(0xffffffffu, incl, 31);
-      if (J.regular && total > 0) {
-        // one (sample, box) pair per lane, compacted when they fit the queue
+      // a (sample, box) pair packs the box (bits 0..4), the edge-table entry
+      // (5..12), the local sample (13..26) and its link (27..31)
+      if ((J.regular || joints) && total > 0) {
+        // interpolated inner centres: one (sample, box) pair per lane,
+        // compacted when the pairs fit the queue
         if (total <= kPairQueue) {
           int pos = incl - cnt;
           for (uint32_t m = need; m; m &= m - 1)
-            queue[pos++] = ((uint32_t)q << 13) | ((uint32_t)j << 5) | (uint32_t)(__ffs(m) - 1);
+            queue[pos++] = ((uint32_t)li << 27) | ((uint32_t)q << 13) | ((uint32_t)j << 5) |
+                           (uint32_t)(__ffs(m) - 1);
           __syncwarp();
           for (int it = lane; it < total; it += 32) {
             const uint32_t e = queue[it];
-            const int s0 = K * (int)(e >> 13);
-            const float rr = ir[s0] - margin;
-            if (rr > 0.0f && inner_hit_regular(ix, iy, iz, s0, K, inv_km1, rr, bx + 6 * (int)(e & 31u)))
-              atomicOr(&acc_hit[(e >> 5) & 255u], 1u << (e & 31u));
+            const int qq = (int)((e >> 13) & 0x3fffu), jj = (int)((e >> 5) & 255u);
+            const float4* B = bx + 6 * (int)(e & 31u);
+            bool hit;
+            if (joints) {
+              const int le = (int)(e >> 27);
+              const float rr = link_r[le] - margin;
+              float ax = 0.0f, ay = 0.0f, az = 0.0f;  // link 0 starts at the base
+              if (le > 0) {
+                const int qn = qq - etab[4 * jj + 1];
+                ax = ix[qn];
+                ay = iy[qn];
+                az = iz[qn];
+              }
+              hit = rr > 0.0f && inner_hit_joints(ax, ay, az, ix[qq], iy[qq], iz[qq], K, inv_k, rr, B);
+            } else {
+              const int s0 = K * qq;
+              const float rr = ir[s0] - margin;
+              hit = rr > 0.0f && inner_hit_regular(ix, iy, iz, s0, K, inv_km1, rr, B);
+            }
+            if (hit) atomicOr(&acc_hit[jj], 1u << (e & 31u));
           }
           __syncwarp();
         } else {
+          // many pairs in one round: each lane tests its own
           uint32_t hits = 0;
-          const float rr = need ? ir[K * q] - margin : 0.0f;
-          if (rr > 0.0f)
-            for (uint32_t m = need; m; m &= m - 1) {
-              const int b = __ffs(m) - 1;
-              if (inner_hit_regular(ix, iy, iz, K * q, K, inv_km1, rr, bx + 6 * b)) hits |= 1u << b;
+          if (need) {
+            if (joints) {
+              const float rr = link_r[li] - margin;
+              const float ax = li > 0 ? ix[q - n] : 0.0f, ay = li > 0 ? iy[q - n] : 0.0f,
+                          az = li > 0 ? iz[q - n] : 0.0f;
+              const float fx = ix[q], fy = iy[q], fz = iz[q];
+              if (rr > 0.0f)
+                for (uint32_t m = need; m; m &= m - 1) {
+                  const int b = __ffs(m) - 1;
+                  if (inner_hit_joints(ax, ay, az, fx, fy, fz, K, inv_k, rr, bx + 6 * b))
+                    hits |= 1u << b;
+                }
+            } else {
+              const float rr = ir[K * q] - margin;
+              if (rr > 0.0f)
+                for (uint32_t m = need; m; m &= m - 1) {
+                  const int b = __ffs(m) - 1;
+                  if (inner_hit_regular(ix, iy, iz, K * q, K, inv_km1, rr, bx + 6 * b))
+                    hits |= 1u << b;
+                }
             }
+          }
           if (hits) atomicOr(&acc_hit[j], hits);
           __syncwarp();
         }
@@ -924,8 +1029,8 @@ __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const 
           const int p0 = __float2int_rz(((float)it + 0.5f) * inv_k);
           const int p1 = __float2int_rz(((float)it2 + 0.5f) * inv_k);
           const uint32_t e0 = queue[p0], e1 = queue[p1];
-          const int s0 = K * (int)(e0 >> 13) + (it - p0 * K);
-          const int s1 = K * (int)(e1 >> 13) + (it2 - p1 * K);
+          const int s0 = K * (int)((e0 >> 13) & 0x3fffu) + (it - p0 * K);
+          const int s1 = K * (int)((e1 >> 13) & 0x3fffu) + (it2 - p1 * K);
           const float r0 = ir[s0] - margin, r1 = ir[s1] - margin;
           const float d0 = box_dist2(ix[s0], iy[s0], iz[s0], bx + 6 * (int)(e0 & 31u));
           const float d1 = box_dist2(ix[s1], iy[s1], iz[s1], bx + 6 * (int)(e1 & 31u));
@@ -1346,10 +1451,10 @@ static size_t smem_bytes_t(uint32_t consumer_warps) {
   constexpr size_t kOffCnt = kOffFull + (2 * NSTAGE + 1) * sizeof(uint64_t) + 8;
   constexpr size_t kOffDesc = (kOffCnt + 4 * ((NSTAGE + 3) & ~3) + 15) & ~(size_t)15;
   constexpr size_t kOffBoxes =
-      (kOffDesc + 32 * sizeof(TileDesc) + 32 * sizeof(int) +
+      (kOffDesc + 32 * sizeof(TileDesc) + 32 * sizeof(int) + 32 * sizeof(uint32_t) +
        (FILTER ? 32 * sizeof(uint32_t) + (size_t)NSTAGE * kRoundSlots * 4 : 0) + 127) &
       ~(size_t)127;
-  constexpr size_t kOffQueues = kOffBoxes + (size_t)kBoxAreas * kBoxesPerPass * kBoxRecFloats * 4;
+  constexpr size_t kOffQueues = kOffBoxes + (size_t)kBoxAreas * kBoxAreaFloats * 4;
   return kOffQueues + (size_t)consumer_warps * 4 * kPairQueue;
 }
 

@@ -51,6 +51,7 @@ struct BuildParams {
   float* outer;
   uint64_t in_stride, out_stride;
   uint64_t n_edges;
+  uint32_t joints;   // 1: write link-end records (3 planes) instead of inner spheres
 };
 
 // Writes boxes' poses into the box table and into the staging rows of their

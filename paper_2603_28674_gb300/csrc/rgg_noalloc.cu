@@ -32,7 +32,8 @@ constexpr size_t kNaTilesOff = 0;
 constexpr size_t kNaEtabOff = kNaTilesOff + kNaMaxTiles * sizeof(TileDesc);
 constexpr size_t kNaAccOff = kNaEtabOff + kNaEtabEntries * sizeof(int4);
 constexpr size_t kNaBoxOff = kNaAccOff + 2 * kNaMaxEdges * sizeof(uint32_t);
-constexpr size_t kNaStatusOff = kNaBoxOff + kBoxesPerPass * kBoxRecFloats * sizeof(float);
+// the box area the classify kernel copies: box records and link radii
+constexpr size_t kNaStatusOff = kNaBoxOff + ((kBoxAreaFloats * sizeof(float) + 255) & ~(size_t)255);
 constexpr size_t kNaBytes = kNaStatusOff + 256;
 constexpr int kNaMaxDevices = 64;
 

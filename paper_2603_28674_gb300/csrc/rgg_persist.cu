@@ -13,7 +13,7 @@ struct SaveHeader {
   char magic[8];
   uint32_t version, L, K, M, Wm;
   float margin;
-  uint32_t flags;  // bit 0: regular inner records
+  uint32_t flags;  // bit 0: regular inner records; bit 1: link-end records
   uint32_t pad;
   uint64_t N, S, n_inner, n_outer;
   uint64_t reserved[3];
@@ -121,13 +121,13 @@ int rgg_save(rgg_roadmap_t r, const char* path, void* stream) {
   if (!io.f) return RGG_ERR_IO;
   SaveHeader h{};
   std::memcpy(h.magic, kSaveMagic, 8);
-  h.version = 1;
+  h.version = 2;
   h.L = r->L;
   h.K = r->K;
   h.M = r->M;
   h.Wm = r->Wm;
   h.margin = r->margin;
-  h.flags = es.regular ? 1u : 0u;
+  h.flags = (es.regular ? 1u : 0u) | (es.joints ? 2u : 0u);
   h.N = es.N;
   h.S = es.S_tot;
   h.n_inner = es.n_inner;
@@ -135,8 +135,11 @@ int rgg_save(rgg_roadmap_t r, const char* path, void* stream) {
   if (!io.put(&h, sizeof(h)) || !io.put(es.h_soff.data(), (es.N + 1) * sizeof(uint64_t)))
     return RGG_ERR_IO;
   int rc = RGG_OK;
-  for (int p = 0; p < 4 && rc == RGG_OK; ++p)
+  for (int p = 0; p < (es.joints ? 3 : 4) && rc == RGG_OK; ++p)
     rc = save_device(io, es.d_inner + p * es.in_stride, es.n_inner * 4, s);
+  if (rc == RGG_OK && es.joints)
+    rc = save_device(io, r->d_changed + kBoxesPerPass * kBoxRecFloats,
+                     kLinkRadiiFloats * sizeof(float), s);
   for (int p = 0; p < 4 && rc == RGG_OK; ++p)
     rc = save_device(io, es.d_outer + p * es.out_stride, es.n_outer * 4, s);
   const size_t set_bytes = es.N * r->Wm * sizeof(uint32_t);
@@ -165,9 +168,12 @@ int rgg_load(rgg_roadmap_t r, const char* path, void* stream) {
   if (!io.f) return RGG_ERR_IO;
   SaveHeader h{};
   if (!io.get(&h, sizeof(h))) return ferror(io.f) ? RGG_ERR_IO : RGG_ERR_INVALID;
-  if (std::memcmp(h.magic, kSaveMagic, 8) != 0 || h.version != 1 || h.L != r->L || h.K != r->K ||
-      h.M != r->M || h.Wm != r->Wm || h.N >= 0xffffffffull || h.S < 2 * h.N ||
-      h.n_inner != (uint64_t)h.K * h.L * h.S || h.n_outer != (uint64_t)h.L * (h.S - h.N))
+  const bool joints = (h.flags & 2u) != 0;
+  if (std::memcmp(h.magic, kSaveMagic, 8) != 0 || (h.version != 1 && h.version != 2) ||
+      (h.version == 1 && joints) || h.L != r->L || h.K != r->K || h.M != r->M || h.Wm != r->Wm ||
+      h.N >= 0xffffffffull || h.S < 2 * h.N ||
+      h.n_inner != (joints ? 1ull : (uint64_t)h.K) * h.L * h.S ||
+      h.n_outer != (uint64_t)h.L * (h.S - h.N))
     return RGG_ERR_INVALID;
   std::vector<uint64_t> soff(h.N + 1);
   if (!io.get(soff.data(), soff.size() * sizeof(uint64_t)))
@@ -175,8 +181,9 @@ int rgg_load(rgg_roadmap_t r, const char* path, void* stream) {
   if (!valid_soff(soff.data(), h.N, r->L) || soff[h.N] != h.S) return RGG_ERR_INVALID;
   RGG_CK(cudaMallocHost(reinterpret_cast<void**>(&io.staging), kStagingBytes));
   EdgeState es;
-  int rc = alloc_edges(r, &es, h.N, std::move(soff), s);
+  int rc = alloc_edges(r, &es, h.N, std::move(soff), s, joints);
   if (rc != RGG_OK) return rc;
+  float link_r[kLinkRadiiFloats] = {};
   float* d_table = nullptr;
   cudaError_t e = dalloc(&d_table, (size_t)r->M * 16);
   if (e != cudaSuccess) {
@@ -184,8 +191,10 @@ int rgg_load(rgg_roadmap_t r, const char* path, void* stream) {
     return cuda_status(e);
   }
   std::vector<uint8_t> present(r->M);
-  for (int p = 0; p < 4 && rc == RGG_OK; ++p)
+  for (int p = 0; p < (joints ? 3 : 4) && rc == RGG_OK; ++p)
     rc = load_device(io, es.d_inner + p * es.in_stride, es.n_inner * 4, s);
+  if (rc == RGG_OK && joints && !io.get(link_r, sizeof(link_r)))
+    rc = ferror(io.f) ? RGG_ERR_IO : RGG_ERR_INVALID;
   for (int p = 0; p < 4 && rc == RGG_OK; ++p)
     rc = load_device(io, es.d_outer + p * es.out_stride, es.n_outer * 4, s);
   const size_t set_bytes = es.N * r->Wm * sizeof(uint32_t);
@@ -208,6 +217,9 @@ int rgg_load(rgg_roadmap_t r, const char* path, void* stream) {
   es.regular = (h.flags & 1u) != 0;
   e = cudaMemcpyAsync(r->d_table, d_table, (size_t)r->M * 16 * sizeof(float),
                       cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess && joints)
+    e = cudaMemcpyAsync(r->d_changed + kBoxesPerPass * kBoxRecFloats, link_r, sizeof(link_r),
+                        cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   cudaFree(d_table);
   if (e != cudaSuccess) {

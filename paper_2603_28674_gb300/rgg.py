@@ -18,6 +18,7 @@ import numpy as np
 
 GREEN, GRAY, RED = 0, 1, 2
 GEOMETRY_SPHERES, GEOMETRY_OBB = 0, 1
+RECORDS_LINK_ENDS, RECORDS_SPHERES = 0, 1
 RGG_OK, RGG_ERR_INVALID, RGG_ERR_OOM, RGG_ERR_CUDA, RGG_ERR_TIMEOUT, RGG_ERR_STATE = \
     0, -1, -2, -3, -4, -5
 RGG_ERR_CAPACITY = -6
@@ -57,7 +58,8 @@ class RGGError(RuntimeError):
 class _Desc(ctypes.Structure):
     _fields_ = [("num_links", ctypes.c_uint32), ("inner_per_link", ctypes.c_uint32),
                 ("max_obstacles", ctypes.c_uint32), ("margin_m", ctypes.c_float),
-                ("device", ctypes.c_int), ("geometry", ctypes.c_uint32)]
+                ("device", ctypes.c_int), ("geometry", ctypes.c_uint32),
+                ("record_format", ctypes.c_uint32)]
 
 
 class _Robot(ctypes.Structure):
@@ -101,7 +103,7 @@ class Info(ctypes.Structure):
                 ("open_requests", ctypes.c_uint32), ("pending_capacity", ctypes.c_uint32),
                 ("geometry", ctypes.c_uint32), ("grid_cells", ctypes.c_uint32),
                 ("grid_items", ctypes.c_uint64), ("spline_vertices", ctypes.c_uint64),
-                ("round_filter", ctypes.c_uint32)]
+                ("round_filter", ctypes.c_uint32), ("record_format", ctypes.c_uint32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -220,9 +222,11 @@ class Roadmap:
     """One resident roadmap (wraps an rgg_roadmap_t)."""
 
     def __init__(self, num_links: int, inner_per_link: int, max_obstacles: int,
-                 margin: float = 2e-5, device: int = 0, geometry: int = GEOMETRY_SPHERES):
+                 margin: float = 2e-5, device: int = 0, geometry: int = GEOMETRY_SPHERES,
+                 record_format: int = RECORDS_LINK_ENDS):
         lib = _lib()
-        desc = _Desc(num_links, inner_per_link, max_obstacles, margin, device, geometry)
+        desc = _Desc(num_links, inner_per_link, max_obstacles, margin, device, geometry,
+                     record_format)
         h = ctypes.c_void_p()
         _check("rgg_roadmap_create", lib.rgg_roadmap_create(ctypes.byref(desc), ctypes.byref(h)))
         self._h = h
@@ -490,10 +494,12 @@ def inject_alloc_failure(nth: int) -> None:
 
 
 def estimate_bytes(num_links: int, inner_per_link: int, max_obstacles: int, q_from, q_to,
-                   step: float, margin: float = 2e-5, device: int = 0) -> int:
+                   step: float, margin: float = 2e-5, device: int = 0,
+                   record_format: int = RECORDS_LINK_ENDS) -> int:
     """Device bytes a sphere-geometry roadmap holds after build_edges with
     these edges (rgg_estimate_bytes; host arithmetic, no GPU needed)."""
-    desc = _Desc(num_links, inner_per_link, max_obstacles, margin, device, GEOMETRY_SPHERES)
+    desc = _Desc(num_links, inner_per_link, max_obstacles, margin, device, GEOMETRY_SPHERES,
+                 record_format)
     qa = _host(q_from, np.float64).reshape(-1, num_links)
     qb = _host(q_to, np.float64).reshape(-1, num_links)
     if qa.shape != qb.shape:

@@ -31,11 +31,16 @@ def rgg():
     return _rgg
 
 
-def make_roadmap(rgg, rm, n_boxes, margin=MARGIN):
+def make_roadmap(rgg, rm, n_boxes, margin=MARGIN, record_format=0):
     robot = rm.robot
-    r = rgg.Roadmap(robot.num_links, robot.inner_per_link, n_boxes, margin)
+    r = rgg.Roadmap(robot.num_links, robot.inner_per_link, n_boxes, margin,
+                    record_format=record_format)
     r.build_edges(robot, rm.q_from, rm.q_to, rm.step)
     return r
+
+
+# built roadmaps store link ends (the default) or every inner sphere
+FORMATS = pytest.mark.parametrize("fmt", [0, 1], ids=["link_ends", "spheres"])
 
 
 def f32(poses):
@@ -63,7 +68,13 @@ def check_sets(hit, touch, want):
 # records (a0)
 # --------------------------------------------------------------------------
 @pytest.mark.parametrize("which", ["planar", "7dof"])
-def test_records_match_oracle_spheres(rgg, which):
+@FORMATS
+def test_records_match_oracle_spheres(rgg, which, fmt):
+    """Sample counts are exact; the records stand for the oracle's spheres
+    within FP32 rounding: sphere records are the FP64 spheres rounded once;
+    link-end records keep each link end rounded once, so the centres read
+    back (interpolated in FP64 and rounded again) carry up to two end
+    roundings at |coordinate| <= 2 m besides their own."""
     if which == "planar":
         sc = W.workload_planar(n_updates=0)
     else:
@@ -71,8 +82,12 @@ def test_records_match_oracle_spheres(rgg, which):
     rm = sc.roadmap
     robot = rm.robot
     L, K = robot.num_links, robot.inner_per_link
-    with make_roadmap(rgg, rm, sc.boxes.count) as r:
+    with make_roadmap(rgg, rm, sc.boxes.count, record_format=fmt) as r:
         inner, outer, soff = r.fetch_records()
+        info = r.info()
+    assert info["record_format"] == fmt
+    per_g = 12 if fmt == 0 else 16 * K
+    assert info["record_bytes"] == per_g * L * int(soff[-1]) + 16 * L * (int(soff[-1]) - rm.num_edges)
     n_e = np.diff(soff.astype(np.int64))
     want_n = np.array([oracle.num_samples(rm.q_from[e], rm.q_to[e], rm.step)
                        for e in range(rm.num_edges)])
@@ -88,7 +103,7 @@ def test_records_match_oracle_spheres(rgg, which):
         go = outer[:, L * (s0 - e): L * (s0 - e + n - 1)].reshape(4, L, n - 1)
         wi = oi.transpose(3, 1, 0, 2)            # [4, L, n, K]
         wo = oo.transpose(2, 1, 0)               # [4, L, n-1]
-        tol_i = 1.2e-7 * np.abs(wi[:3]) + 1e-12
+        tol_i = 1.2e-7 * np.abs(wi[:3]) + (1e-12 if fmt == 1 else 2.4e-7)
         tol_o = 1.2e-7 * np.abs(wo[:3]) + 1e-12
         assert np.all(np.abs(gi[:3] - wi[:3]) <= tol_i)
         assert np.all(np.abs(go[:3] - wo[:3]) <= tol_o)
@@ -99,12 +114,12 @@ def test_records_match_oracle_spheres(rgg, which):
 # --------------------------------------------------------------------------
 # labels (a1..a6)
 # --------------------------------------------------------------------------
-def run_updates(rgg, sc, n_updates=None, check_every=True):
+def run_updates(rgg, sc, n_updates=None, check_every=True, fmt=0):
     """Place every box, classify, then apply the update stream; compare with
     the oracle from scratch after each step.  Returns the roadmap handle."""
     rm, robot = sc.roadmap, sc.roadmap.robot
     boxes = sc.boxes.copy()
-    r = make_roadmap(rgg, rm, boxes.count)
+    r = make_roadmap(rgg, rm, boxes.count, record_format=fmt)
     r.update_obstacles(np.arange(boxes.count), f32(boxes.poses()))
     r.classify()
     ups = sc.updates if n_updates is None else sc.updates[:n_updates]
@@ -125,20 +140,22 @@ def run_updates(rgg, sc, n_updates=None, check_every=True):
     return r, boxes, stats
 
 
-def test_planar_update_stream(rgg):
+@FORMATS
+def test_planar_update_stream(rgg, fmt):
     sc = W.workload_planar(n_updates=8)
-    r, _, stats = run_updates(rgg, sc)
+    r, _, stats = run_updates(rgg, sc, fmt=fmt)
     info = r.info()
     assert info["num_tiles"] > 4
     r.close()
     assert max(stats) <= 0.01 * sc.roadmap.num_edges
 
 
-def test_7dof_update_stream_two_passes(rgg):
+@FORMATS
+def test_7dof_update_stream_two_passes(rgg, fmt):
     """64 boxes: the first classification runs two 32-box passes and uses
     the second mask word."""
     sc = W.workload_7dof(n_nodes=1200, n_updates=4)
-    r, _, stats = run_updates(rgg, sc)
+    r, _, stats = run_updates(rgg, sc, fmt=fmt)
     assert r.info()["mask_words"] == 2
     r.close()
 
@@ -159,16 +176,18 @@ def test_incremental_equals_from_scratch(rgg):
     r.close()
 
 
-def test_long_edges_span_tiles(rgg):
+@FORMATS
+def test_long_edges_span_tiles(rgg, fmt):
     """Edges with ~1500 configurations per link run across several streaming
-    tiles (halo intervals and cross-tile merges)."""
+    tiles (halo intervals, link-end halos reaching one link's run back, and
+    cross-tile merges)."""
     rng = np.random.default_rng(3)
     robot = W.planar_arm()
     qa = rng.uniform(-np.pi, np.pi, (60, 3))
     qb = qa + rng.uniform(-3.0, 3.0, (60, 3))
     rm = W.Roadmap(robot, qa, qb, 0.002)
     boxes = W.random_boxes(rng, 12, planar=True, oriented=False, half_hi=0.08)
-    with make_roadmap(rgg, rm, boxes.count) as r:
+    with make_roadmap(rgg, rm, boxes.count, record_format=fmt) as r:
         info = r.info()
         assert info["num_samples"] / rm.num_edges > info["tile_samples"]
         r.update_obstacles(np.arange(boxes.count), f32(boxes.poses()))
@@ -248,14 +267,15 @@ def test_many_boxes_in_one_update(rgg):
 
 
 def test_upload_of_fetched_records_and_device_poses(rgg):
-    """Records uploaded by the caller (host and device) classify the same as
-    records built in place; device-side poses equal host poses."""
+    """Sphere records uploaded by the caller (host and device) classify the
+    same as the sphere records built in place; device-side poses equal host
+    poses."""
     import torch
     sc = W.workload_planar(n_nodes=200, n_updates=1)
     rm, robot = sc.roadmap, sc.roadmap.robot
     poses = f32(sc.boxes.poses())
     ids = np.arange(sc.boxes.count)
-    with make_roadmap(rgg, rm, sc.boxes.count) as a:
+    with make_roadmap(rgg, rm, sc.boxes.count, record_format=1) as a:
         inner, outer, soff = a.fetch_records()
         a.update_obstacles(ids, poses)
         a.classify()

@@ -30,9 +30,9 @@ def scene():
     return W.workload_7dof(n_nodes=800, n_boxes=40, n_updates=4)
 
 
-def prepared(rgg, sc, n_updates=2):
+def prepared(rgg, sc, n_updates=2, fmt=0):
     rm, robot = sc.roadmap, sc.roadmap.robot
-    r = rgg.Roadmap(robot.num_links, robot.inner_per_link, sc.boxes.count)
+    r = rgg.Roadmap(robot.num_links, robot.inner_per_link, sc.boxes.count, record_format=fmt)
     r.build_edges(robot, rm.q_from, rm.q_to, rm.step)
     r.update_obstacles(np.arange(sc.boxes.count), f32(sc.boxes.poses()))
     r.classify()
@@ -55,15 +55,20 @@ def same_roadmap(a, b):
     np.testing.assert_array_equal(ta, tb)
 
 
-def test_save_load_round_trip_and_later_updates(rgg, tmp_path):
+@pytest.mark.parametrize("fmt", [0, 1], ids=["link_ends", "spheres"])
+def test_save_load_round_trip_and_later_updates(rgg, tmp_path, fmt):
+    """Either record format reloads bit for bit, into a roadmap created with
+    either format (the file's format wins)."""
     sc = scene()
     rm, robot = sc.roadmap, sc.roadmap.robot
     path = str(tmp_path / "roadmap.rgg")
-    with prepared(rgg, sc) as a, rgg.Roadmap(robot.num_links, robot.inner_per_link,
-                                             sc.boxes.count) as b:
+    with prepared(rgg, sc, fmt=fmt) as a, rgg.Roadmap(robot.num_links, robot.inner_per_link,
+                                                      sc.boxes.count, record_format=1 - fmt) as b:
         a.save(path)
         b.load(path)
         assert b.info()["num_edges"] == a.info()["num_edges"]
+        assert b.info()["record_format"] == fmt
+        assert b.info()["record_bytes"] == a.info()["record_bytes"]
         assert b.info()["pending_boxes"] == 0
         same_roadmap(a, b)
         # the reloaded roadmap continues exactly like the original

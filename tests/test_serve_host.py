@@ -68,12 +68,21 @@ def test_memory_estimate_covers_the_records(built):
                     for e in range(rm.num_edges)])
     S, N = int(n_e.sum()), rm.num_edges
     L, K = robot.num_links, robot.inner_per_link
-    records = 16 * (K * L * S + L * (S - N))
+    # link-end records (the default): 12 B per (edge, link, configuration);
+    # sphere records: 16 B per inner sphere; 16 B per outer sphere in both
+    for fmt, records in ((rgg.RECORDS_LINK_ENDS, 12 * L * S + 16 * L * (S - N)),
+                         (rgg.RECORDS_SPHERES, 16 * (K * L * S + L * (S - N)))):
+        est = rgg.estimate_bytes(L, K, sc.boxes.count, rm.q_from, rm.q_to, rm.step,
+                                 record_format=fmt)
+        # per edge at least the offsets, box sets, counts, label, pass bits and endpoints
+        assert est >= records + N * (8 + 8 + 4 + 1 + 8 + 16 * L)
+        assert est <= records + N * (64 + 16 * L) + (1 << 20)
     est = rgg.estimate_bytes(L, K, sc.boxes.count, rm.q_from, rm.q_to, rm.step)
-    # per edge at least the offsets, box sets, counts, label, pass bits and endpoints
-    assert est >= records + N * (8 + 8 + 4 + 1 + 8 + 16 * L)
-    assert est <= records + N * (64 + 16 * L) + (1 << 20)
     assert roadmap_bytes(L, K, sc.boxes.count, rm.q_from, rm.q_to, rm.step) == est + 64 * N
+    # a margin below 1e-5 m keeps sphere records
+    assert rgg.estimate_bytes(L, K, sc.boxes.count, rm.q_from, rm.q_to, rm.step, margin=0.0) == \
+        rgg.estimate_bytes(L, K, sc.boxes.count, rm.q_from, rm.q_to, rm.step, margin=0.0,
+                           record_format=rgg.RECORDS_SPHERES)
 
 
 def test_memory_estimate_rejects_bad_arguments(built):

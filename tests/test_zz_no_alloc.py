@@ -100,7 +100,9 @@ def test_noalloc_two_calls_match_classify_and_the_oracle(which):
               boxes.poses()[a:a + 32].astype(np.float32)) for a in range(0, n_boxes, 32)]
     steps.append((up.ids, up.poses.astype(np.float32)))
 
-    with rgg.Roadmap(robot.num_links, robot.inner_per_link, n_boxes) as r:
+    # sphere records: the layout the allocation-free pass reads
+    with rgg.Roadmap(robot.num_links, robot.inner_per_link, n_boxes,
+                     record_format=rgg.RECORDS_SPHERES) as r:
         r.build_edges(robot, rm.q_from, rm.q_to, rm.step)
         regular = _Caller(torch, r, rm)
         exact = _Caller(torch, r, rm)
@@ -141,7 +143,8 @@ def test_noalloc_wait_that_runs_out_leaves_the_callers_state():
     rm, robot = sc.roadmap, sc.roadmap.robot
     ids = np.arange(sc.boxes.count, dtype=np.uint32)
     poses = sc.boxes.poses().astype(np.float32)
-    with rgg.Roadmap(robot.num_links, robot.inner_per_link, sc.boxes.count) as r:
+    with rgg.Roadmap(robot.num_links, robot.inner_per_link, sc.boxes.count,
+                     record_format=rgg.RECORDS_SPHERES) as r:
         r.build_edges(robot, rm.q_from, rm.q_to, rm.step)
         c = _Caller(torch, r, rm)
         r.update_obstacles(ids, poses)
