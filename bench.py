@@ -583,13 +583,45 @@ def measure_mixed(r, args, stream, peak: float) -> dict:
     k_avg = k_ms / max(1, n)
     b_alg = algorithmic_bytes(info)
     mix = np.bincount(lab, minlength=3) / max(1, lab.size)
-    return {"boxes": "256, half-extents U[0.02, 0.06] m, centres in a 4 m cube",
-            "moved_per_update": 32, "steps": args.steps, "ms_per_step": ms / args.steps,
-            "edges_per_s": info["num_edges"] * args.steps / (ms / 1e3),
-            "kernel_ms": k_avg, "merge_kernel_ms": m_ms / max(1, n),
-            "bytes_per_launch": b_alg, "achieved_gbs": b_alg / (k_avg / 1e3) / 1e9,
-            "frac": b_alg / (k_avg / 1e3) / 1e9 / peak,
-            "labels": {"green": float(mix[0]), "gray": float(mix[1]), "red": float(mix[2])}}
+    out = {"boxes": "256, half-extents U[0.02, 0.06] m, centres in a 4 m cube",
+           "moved_per_update": 32, "steps": args.steps, "ms_per_step": ms / args.steps,
+           "edges_per_s": info["num_edges"] * args.steps / (ms / 1e3),
+           "kernel_ms": k_avg, "merge_kernel_ms": m_ms / max(1, n),
+           "bytes_per_launch": b_alg, "achieved_gbs": b_alg / (k_avg / 1e3) / 1e9,
+           "frac": b_alg / (k_avg / 1e3) / 1e9 / peak,
+           "labels": {"green": float(mix[0]), "gray": float(mix[1]), "red": float(mix[2])}}
+    # the same steps with the opt-in spatial filter: on this scene most
+    # rounds have no moved box near them
+    r.set_round_filter(True)
+    if r.info()["round_filter"]:
+        # the updates of the timed steps again (absolute poses, so the final
+        # state, and the labels, are those of the streaming run)
+        for i in range(min(3, args.steps)):
+            step(args.warmup + i)
+        torch.cuda.synchronize()
+        r.set_kernel_timing(True)
+        r.kernel_time()
+        r.streamed_bytes()
+        for i in range(args.steps):
+            step(args.warmup + i)
+        torch.cuda.synchronize()
+        kf, _, nf = r.kernel_time()
+        r.set_kernel_timing(False)
+        sf = r.streamed_bytes() / max(1, nf)
+        fi = r.info()
+        lab_f = r.fetch_labels(stream=stream)
+        b_f = algorithmic_bytes(fi, sf)
+        kf_avg = kf / max(1, nf)
+        out["round_filter"] = {
+            "kernel_ms": kf_avg, "record_bytes_per_launch": sf,
+            "records_copied_frac": sf / info["record_bytes"], "bytes_per_launch": b_f,
+            "frac": b_f / (kf_avg / 1e3) / 1e9 / peak,
+            "speedup_vs_streaming_all": k_avg / kf_avg,
+            "labels_identical": bool(np.array_equal(lab_f, lab)),
+            "note": "kernel interval = round-filter kernel + classify kernel"}
+    r.set_round_filter(False)
+    r.check_status(stream)
+    return out
 
 
 def measure_persist(r, robot, m: int, stream) -> dict:

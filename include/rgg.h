@@ -118,7 +118,7 @@ enum {
   RGG_MAX_INNER = 16,          /* inner_per_link                               */
   RGG_MAX_OBSTACLES = 4096,    /* max_obstacles                                */
   RGG_BOXES_PER_PASS = 32,     /* moved boxes tested per streaming pass        */
-  RGG_NUM_VARIANTS = 7,        /* compiled pipeline shapes (rgg_set_launch_shape) */
+  RGG_NUM_VARIANTS = 10,       /* compiled pipeline shapes (rgg_set_launch_shape) */
   RGG_MAX_REQUESTS = 64,       /* open requests per roadmap (rgg_update_request) */
   RGG_PENDING_EXTRA = 4096,    /* pending entries beyond max_obstacles          */
   RGG_MAX_RESOLVE_FACTOR = 100, /* rgg_resolve_gray: resampling factor           */

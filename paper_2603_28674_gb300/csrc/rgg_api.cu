@@ -45,6 +45,31 @@ bool use_joints(const rgg_roadmap* r) {
          r->margin >= kRegularMinMargin;
 }
 
+// The default launch shape of the record format, unless the caller or the
+// autotuner chose one.
+void default_shape(rgg_roadmap* r, bool joints) {
+  if (r->shape_set) return;
+  r->variant = joints ? kDefaultVariantLinkEnds : kDefaultVariant;
+  r->consumer_warps = joints ? kDefaultConsumerWarpsLinkEnds : kDefaultConsumerWarps;
+}
+
+ShapeRestore::ShapeRestore(rgg_roadmap* rm) : r(rm), variant(rm->variant), warps(rm->consumer_warps) {}
+ShapeRestore::~ShapeRestore() {
+  if (!keep) {
+    r->variant = variant;
+    r->consumer_warps = warps;
+  }
+}
+
+// A roadmap's tiles can run in a launch of another variant when that
+// variant's tiles are at least as long and its stages hold the tile's data.
+bool tiles_fit(const rgg_roadmap* r, int variant) {
+  const VariantShape v = variant_shape(variant);
+  const Tiling& t = r->es.tiling;
+  if (filter_active(r) && !filter_variant(variant)) return false;
+  return t.S <= 31u * (uint32_t)v.rounds && (uint64_t)t.off_out + 16ull * t.out_cap <= (uint64_t)v.stage_bytes;
+}
+
 // The link radii R_i, rounded down to FP32, behind the pass's box records
 // (link-end records take their inner radius from there).
 int set_link_radii(rgg_roadmap* r, const double* radius, cudaStream_t s) {
@@ -175,7 +200,7 @@ void release_rounds(EdgeState* es) {
 // The spatial filter runs with the default pipeline variant only (the one
 // its kernel instance is compiled for).
 bool filter_active(const rgg_roadmap* r) {
-  return r->round_filter && r->es.d_rcand && r->variant == kDefaultVariant;
+  return r->round_filter && r->es.d_rcand && filter_variant(r->variant);
 }
 
 // The spatial filter's per-round bounding spheres and outer ranges of the
@@ -802,6 +827,8 @@ int rgg_upload_edges(rgg_roadmap_t r, uint64_t num_edges, const uint64_t* sample
   }
   EdgeState es;
   std::vector<uint64_t> soff(sample_off, sample_off + num_edges + 1);
+  ShapeRestore shape(r);
+  default_shape(r, false);
   int rc = alloc_edges(r, &es, num_edges, std::move(soff), s);
   if (rc != RGG_OK) return rc;
   const cudaMemcpyKind kind = src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
@@ -818,8 +845,12 @@ int rgg_upload_edges(rgg_roadmap_t r, uint64_t num_edges, const uint64_t* sample
   // device-resident uploads are not inspected: they take the exact
   // per-sphere path
   es.regular = !src_is_device && num_edges && regular_inner(inner_xyzr, n_in, r->K);
-  r->has_robot = false;
-  return install_edges(r, std::move(es), s);
+  rc = install_edges(r, std::move(es), s);
+  if (rc == RGG_OK) {
+    shape.keep = true;
+    r->has_robot = false;
+  }
+  return rc;
 }
 
 int rgg_build_edges(rgg_roadmap_t r, const rgg_robot_desc* robot, uint64_t num_edges,
@@ -873,6 +904,8 @@ int rgg_build_edges(rgg_roadmap_t r, const rgg_robot_desc* robot, uint64_t num_e
   for (uint64_t i = 0; i < num_edges; ++i) soff[i + 1] = soff[i] + counts[i];
   EdgeState es;
   const bool joints = use_joints(r);
+  ShapeRestore shape(r);
+  default_shape(r, joints);
   int rc = alloc_edges(r, &es, num_edges, std::move(soff), s, joints);
   if (rc != RGG_OK) {
     cleanup();
@@ -930,6 +963,7 @@ int rgg_build_edges(rgg_roadmap_t r, const rgg_robot_desc* robot, uint64_t num_e
   }
   rc = install_edges(r, std::move(es), s);
   if (rc == RGG_OK) {
+    shape.keep = true;
     r->has_robot = true;
     for (uint32_t i = 0; i < r->L; ++i) {
       r->dh_a[i] = robot->a[i];
@@ -1000,8 +1034,9 @@ int rgg_classify_many(rgg_roadmap_t* rs, uint32_t n, void* stream) {
   for (uint32_t i = 0; i < n; ++i) {
     if (!rs[i]) return RGG_ERR_INVALID;
     if (!rs[i]->has_edges) return RGG_ERR_STATE;
-    if (rs[i]->device != rs[0]->device || rs[i]->variant != rs[0]->variant ||
-        rs[i]->geometry != rs[0]->geometry)
+    // one launch runs every roadmap's tiles at the first roadmap's shape
+    if (rs[i]->device != rs[0]->device || rs[i]->geometry != rs[0]->geometry ||
+        (rs[i]->geometry == RGG_GEOMETRY_SPHERES && rs[i]->es.N && !tiles_fit(rs[i], rs[0]->variant)))
       return RGG_ERR_INVALID;
     for (uint32_t j = 0; j < i; ++j)
       if (rs[j] == rs[i]) return RGG_ERR_INVALID;
@@ -1328,11 +1363,15 @@ int rgg_kernel_time(rgg_roadmap_t r, double* classify_ms, double* merge_ms,
 
 int rgg_set_launch_shape(rgg_roadmap_t r, uint32_t variant, uint32_t consumer_warps) {
   if (!r) return RGG_ERR_INVALID;
-  const uint32_t cw = consumer_warps ? consumer_warps : kDefaultConsumerWarps;
+  const uint32_t cw = consumer_warps ? consumer_warps
+                                     : (r->es.joints ? kDefaultConsumerWarpsLinkEnds
+                                                     : kDefaultConsumerWarps);
   if (!shape_ok(variant, cw)) return RGG_ERR_INVALID;
   DeviceGuard g(r->device);
   if (!g.ok) return RGG_ERR_CUDA;
-  return apply_shape(r, (int)variant, cw);
+  const int rc = apply_shape(r, (int)variant, cw);
+  if (rc == RGG_OK) r->shape_set = true;
+  return rc;
 }
 
 }  // extern "C"

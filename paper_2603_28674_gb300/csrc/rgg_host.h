@@ -194,6 +194,7 @@ struct rgg_roadmap {
   int num_sms = 0;
   uint32_t ctas_per_sm = 1, consumer_warps = rgg::kDefaultConsumerWarps;
   int variant = rgg::kDefaultVariant;
+  bool shape_set = false;      // the caller or the autotuner chose the launch shape
   bool has_edges = false;
   uint64_t gen = 0;            // bumped whenever tiles or edges are replaced
   uint32_t geometry = RGG_GEOMETRY_SPHERES;
@@ -245,6 +246,19 @@ int set_tiles(rgg_roadmap* r, EdgeState* es, cudaStream_t s);
 int alloc_edges(rgg_roadmap* r, EdgeState* es, uint64_t N, std::vector<uint64_t>&& soff,
                 cudaStream_t s, bool joints = false);
 bool use_joints(const rgg_roadmap* r);
+void default_shape(rgg_roadmap* r, bool joints);
+// Puts the launch shape back unless `keep` is set: new edges take their
+// format's default shape, but a call that fails keeps the old edges, whose
+// tiles belong to the old shape.
+struct ShapeRestore {
+  rgg_roadmap* r;
+  int variant;
+  uint32_t warps;
+  bool keep = false;
+  explicit ShapeRestore(rgg_roadmap* rm);
+  ~ShapeRestore();
+};
+bool tiles_fit(const rgg_roadmap* r, int variant);
 int set_link_radii(rgg_roadmap* r, const double* radius, cudaStream_t s);
 void clear_pending(rgg_roadmap* r);
 int requeue_present(rgg_roadmap* r, cudaStream_t s);

@@ -454,14 +454,21 @@ __global__ void __launch_bounds__(256) round_bounds_kernel(const __grid_constant
 // margin.  Any outer sphere of the round lies inside the bounding sphere, so
 // a box that touches one of them (distance <= r + margin) passes this test;
 // the slack covers FP32 rounding in both tests.  One warp per tile, one lane
-// per round.
+// per round.  Each warp stages its roadmap's box records in shared memory,
+// and a box whose bounding sphere is out of reach skips the exact distance.
 template <int MAXJ>
 __global__ void __launch_bounds__(256) round_filter_kernel(const __grid_constant__ ClassifyParams<MAXJ> P) {
+  __shared__ float4 s_bx[8][kBoxesPerPass * 6];
   const uint64_t t = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  if (t >= P.total_tiles) return;
+  if (t >= P.total_tiles) return;  // whole warps: t is the same on every lane
   const ClassifyJob& J = P.job[MAXJ == 1 ? 0 : find_job(P, t)];
   if (J.rcand == nullptr) return;
+  float4* bx = s_bx[threadIdx.x >> 5];
+  const int C = (int)J.C;
+  if (lane < C)
+    for (int c = 0; c < 6; ++c) bx[6 * lane + c] = reinterpret_cast<const float4*>(J.boxes)[6 * lane + c];
+  __syncwarp();
   const uint64_t slot = (t - J.tile_base) * kRoundSlots + lane;
   uint32_t m = 0;
   if (lane < kRoundSlots - 1) {
@@ -469,9 +476,13 @@ __global__ void __launch_bounds__(256) round_filter_kernel(const __grid_constant
     if (sph.w >= 0.0f) {
       const float thr = (sph.w + J.margin) * (1.0f + 1e-6f) + 1e-5f;
       const float thr2 = thr * thr;
-      const float4* bx = reinterpret_cast<const float4*>(J.boxes);
-      for (uint32_t b = 0; b < J.C; ++b)
+      for (int b = 0; b < C; ++b) {
+        const float4 b0 = bx[6 * b];
+        const float ex = sph.x - b0.x, ey = sph.y - b0.y, ez = sph.z - b0.z;
+        const float reach = thr + b0.w;  // the box lies in the sphere of radius |h|
+        if (fmaf(ex, ex, fmaf(ey, ey, ez * ez)) > reach * reach * (1.0f + 1e-6f)) continue;
         if (box_dist2(sph.x, sph.y, sph.z, bx + 6 * b) <= thr2) m |= 1u << b;
+      }
     }
   }
   // the last slot (never a round: tiles have at most 31 rounds) holds the
@@ -938,11 +949,17 @@ __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const 
       // no moved box near the round: nothing touched, so no inner test either
       if (!any_cand) continue;
       // ---- a4: inner spheres of q against the boxes touched by the
-      // intervals before and after it
+      // intervals next to it.  Built records (link ends): each of those outer
+      // spheres holds q's capsule, so a box an inner sphere of q hits is
+      // touched by both, and only boxes touched on both sides (on the one
+      // side at an edge's ends) are tested.  Uploaded sphere records promise
+      // only that the two together hold q's spheres: boxes touched on either
       const uint32_t prev = __shfl_up_sync(0xffffffffu, bits, 1);
       uint32_t need = 0;
       if (valid && q >= base) {
-        need = (k < n - 1 ? bits : 0u) | (k > 0 ? prev : 0u);
+        const uint32_t after = k < n - 1 ? bits : (joints ? ~0u : 0u);
+        const uint32_t before = k > 0 ? prev : (joints ? ~0u : 0u);
+        need = joints ? (after & before) : (after | before);
         if (need) need &= ~*reinterpret_cast<volatile uint32_t*>(&acc_hit[j]);
       }
       const int cnt = __popc(need);
@@ -1462,7 +1479,7 @@ size_t classify_smem_bytes(int variant, uint32_t consumer_warps) {
   // the batched kernel's (larger) footprint, which bounds both
   switch (variant) {
 #define RGG_VARIANT(id, ns, sb, rd, rpi) \
-  case id: return smem_bytes_t<kMaxJobs, ns, sb, id == kDefaultVariant>(consumer_warps);
+  case id: return smem_bytes_t<kMaxJobs, ns, sb, filter_variant(id)>(consumer_warps);
     RGG_VARIANTS(RGG_VARIANT)
 #undef RGG_VARIANT
     default: return 0;
@@ -1480,11 +1497,11 @@ static cudaError_t launch_classify_v(const ClassifyParams<MAXJ>& p, const Classi
   return cudaGetLastError();
 }
 
-// The filtered instance exists for the default pipeline variant only.
+// The filtered instance exists for the two default pipeline variants only.
 template <int MAXJ, int ID, int NS, int SB, int RD, int RPI>
 static cudaError_t launch_variant(const ClassifyParams<MAXJ>& p, const ClassifyLaunch& lc,
                                   bool filtered, cudaStream_t s) {
-  if constexpr (ID == kDefaultVariant) {
+  if constexpr (filter_variant(ID)) {
     if (filtered) return launch_classify_v<MAXJ, NS, SB, RD, RPI, true>(p, lc, s);
   } else {
     if (filtered) return cudaErrorInvalidValue;

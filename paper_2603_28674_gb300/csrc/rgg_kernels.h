@@ -14,6 +14,9 @@ namespace rgg {
 // Each stage holds one tile: header, accumulators, edge table, inner and
 // outer record planes; beside it, the tile's round candidates and 3 KB for
 // the tile's job's box records.
+// Variants 7..9 keep big tiles but hold more of them in flight: link-end
+// records need 12 B per sample instead of 16*K, so a 23..31-round tile fits
+// a 27..38 KB stage.
 #define RGG_VARIANTS(X)             \
   X(0, 14, 10 * 1024, 3, 1)        \
   X(1, 7, 28 * 1024, 9, 1)         \
@@ -21,10 +24,21 @@ namespace rgg {
   X(3, 5, 40 * 1024, 13, 1)        \
   X(4, 4, 51 * 1024, 17, 1)        \
   X(5, 3, 69 * 1024, 23, 1)        \
-  X(6, 4, 51 * 1024, 16, 2)
-constexpr int kNumVariants = 7;
+  X(6, 4, 51 * 1024, 16, 2)        \
+  X(7, 7, 27 * 1024, 23, 1)        \
+  X(8, 6, 32 * 1024, 27, 1)        \
+  X(9, 5, 38 * 1024, 31, 1)
+constexpr int kNumVariants = 10;
+// Default shapes: sphere records take variant 5 with 24 consumer warps;
+// link-end records (a third of the bytes per tile) variant 7, whose deeper
+// ring keeps more tiles in flight, with 27 (measured by the autotuner on the
+// large, mixed-label and 7-DOF roadmaps).
 constexpr int kDefaultVariant = 5;
 constexpr uint32_t kDefaultConsumerWarps = 24;
+constexpr int kDefaultVariantLinkEnds = 7;
+constexpr uint32_t kDefaultConsumerWarpsLinkEnds = 27;
+// The spatial filter's kernel instance exists for the two default variants.
+constexpr bool filter_variant(int v) { return v == kDefaultVariant || v == kDefaultVariantLinkEnds; }
 constexpr int kMaxClassifyThreads = 896;  // producer warp + up to 27 consumer warps
 struct VariantShape {
   int stages, stage_bytes, rounds, rounds_per_item;

@@ -181,6 +181,8 @@ int rgg_load(rgg_roadmap_t r, const char* path, void* stream) {
   if (!valid_soff(soff.data(), h.N, r->L) || soff[h.N] != h.S) return RGG_ERR_INVALID;
   RGG_CK(cudaMallocHost(reinterpret_cast<void**>(&io.staging), kStagingBytes));
   EdgeState es;
+  ShapeRestore shape(r);
+  default_shape(r, joints);
   int rc = alloc_edges(r, &es, h.N, std::move(soff), s, joints);
   if (rc != RGG_OK) return rc;
   float link_r[kLinkRadiiFloats] = {};
@@ -232,6 +234,7 @@ int rgg_load(rgg_roadmap_t r, const char* path, void* stream) {
     return rc;
   }
   for (uint32_t b = 0; b < r->M; ++b) r->present[b] = present[b] ? 1 : 0;
+  shape.keep = true;
   r->es.release();
   r->es = std::move(es);
   r->has_edges = true;

@@ -152,6 +152,7 @@ int rgg_autotune(rgg_roadmap_t* rs, uint32_t n, uint32_t reps, rgg_tune_result* 
   if (!res.empty()) {
     for (uint32_t i = 0; i < n; ++i) {
       const int rc2 = apply_shape(rs[i], (int)res[0].variant, res[0].consumer_warps);
+      if (rc2 == RGG_OK) rs[i]->shape_set = true;
       if (rc == RGG_OK) rc = rc2;
     }
   }

@@ -21,8 +21,8 @@ def run(workload: str = "7dof", reps: int = 3, log=print):
     from . import workloads as W
 
     build.build()
-    sc = {"large": W.workload_large, "7dof": W.workload_7dof,
-          "planar": W.workload_planar}[workload](n_updates=0)
+    sc = {"large": W.workload_large, "large_mixed": W.workload_large_mixed,
+          "7dof": W.workload_7dof, "planar": W.workload_planar}[workload](n_updates=0)
     rm, robot = sc.roadmap, sc.roadmap.robot
     with rgg.Roadmap(robot.num_links, robot.inner_per_link, sc.boxes.count) as r:
         r.build_edges(robot, rm.q_from, rm.q_to, rm.step)
@@ -41,7 +41,7 @@ def run(workload: str = "7dof", reps: int = 3, log=print):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="7dof", choices=["large", "7dof", "planar"])
+    ap.add_argument("--workload", default="7dof", choices=["large", "large_mixed", "7dof", "planar"])
     ap.add_argument("--reps", type=int, default=3)
     a = ap.parse_args()
     run(a.workload, a.reps)

@@ -334,6 +334,35 @@ def test_batched_equals_alone(rgg):
         r.close()
 
 
+def test_batched_launch_of_both_record_formats(rgg):
+    """One launch runs every roadmap at the first roadmap's shape: a sphere-
+    record roadmap first (69 KB stages) also runs link-end tiles, with the
+    labels of classifying each alone; link-end first (27 KB stages) cannot
+    hold sphere tiles and is refused before anything runs."""
+    sc = W.workload_7dof(n_nodes=300, n_boxes=20, n_updates=1)
+    rm = sc.roadmap
+    rs = [make_roadmap(rgg, rm, 20, record_format=f) for f in (1, 0)]
+    alone = [make_roadmap(rgg, rm, 20, record_format=f) for f in (1, 0)]
+    for r in rs + alone:
+        r.update_obstacles(np.arange(20), f32(sc.boxes.poses()))
+    with pytest.raises(rgg.RGGError) as e:
+        rgg.classify_many(rs[::-1])
+    assert e.value.status == rgg.RGG_ERR_INVALID
+    assert all(r.info()["pending_boxes"] == 20 for r in rs)
+    rgg.classify_many(rs)
+    for r in alone:
+        r.classify()
+    for a, b in zip(rs, alone):
+        np.testing.assert_array_equal(a.fetch_labels(), b.fetch_labels())
+        ha, ta = a.fetch_box_sets()
+        hb, tb = b.fetch_box_sets()
+        np.testing.assert_array_equal(ha, hb)
+        np.testing.assert_array_equal(ta, tb)
+    for r in rs + alone:
+        r.check_status()
+        r.close()
+
+
 def test_kernel_timing_counts_launches(rgg):
     sc = W.workload_planar(n_nodes=100, n_updates=1)
     with make_roadmap(rgg, sc.roadmap, sc.boxes.count) as r:

@@ -49,8 +49,8 @@ def scene(which):
     return rm, boxes, W.update_stream(rng, boxes, 4, 4)
 
 
-def built(rgg, rm, m, filtered):
-    r = rgg.Roadmap(rm.robot.num_links, rm.robot.inner_per_link, m)
+def built(rgg, rm, m, filtered, fmt=0):
+    r = rgg.Roadmap(rm.robot.num_links, rm.robot.inner_per_link, m, record_format=fmt)
     r.build_edges(rm.robot, rm.q_from, rm.q_to, rm.step)
     r.set_round_filter(filtered)
     return r
@@ -98,13 +98,15 @@ def test_filter_changes_no_bit(rgg, which):
         u.check_status()
 
 
-def test_every_launch_shape(rgg):
-    """The filter runs with the default launch shape only; the round data
-    follow the tiles when a launch shape changes them (3 -> 5 rebuilds
-    both)."""
+@pytest.mark.parametrize("fmt", [0, 1], ids=["link_ends", "spheres"])
+def test_every_launch_shape(rgg, fmt):
+    """The filter runs with the two default launch shapes only (variants 5
+    and 7); the round data follow the tiles when a launch shape changes them
+    (3 -> 5 rebuilds both).  Every shape gives the same bits, for either
+    record format."""
     rm, boxes, ups = scene("7dof")
     m = boxes.count
-    with built(rgg, rm, m, False) as u:
+    with built(rgg, rm, m, False, fmt) as u:
         u.update_obstacles(np.arange(m), f32(boxes.poses()))
         u.classify()
         for up in ups:
@@ -112,8 +114,8 @@ def test_every_launch_shape(rgg):
             u.classify()
         want_l = u.fetch_labels()
         want_h, want_t = u.fetch_box_sets()
-    for variant in list(range(7)) + ["3->5"]:
-        with built(rgg, rm, m, True) as f:
+    for variant in list(range(rgg.NUM_VARIANTS)) + ["3->5"]:
+        with built(rgg, rm, m, True, fmt) as f:
             if variant == "3->5":
                 f.set_launch_shape(3, 16)
                 assert f.info()["round_filter"] == 0
@@ -121,7 +123,7 @@ def test_every_launch_shape(rgg):
                 assert f.info()["round_filter"] == 1
             else:
                 f.set_launch_shape(variant, 16)
-                assert f.info()["round_filter"] == (1 if variant == 5 else 0)
+                assert f.info()["round_filter"] == (1 if variant in (5, 7) else 0)
             f.update_obstacles(np.arange(m), f32(boxes.poses()))
             f.classify()
             for up in ups:
@@ -164,7 +166,8 @@ def test_uploaded_and_reloaded_roadmaps(rgg, tmp_path):
     rm, boxes, ups = scene("7dof")
     m = boxes.count
     robot = rm.robot
-    with built(rgg, rm, m, False) as u:
+    # sphere records, so that the uploaded copy makes the same decisions
+    with built(rgg, rm, m, False, 1) as u:
         inner, outer, soff = u.fetch_records()
         u.update_obstacles(np.arange(m), f32(boxes.poses()))
         u.classify()
