@@ -503,7 +503,9 @@ bool shape_ok(uint32_t variant, uint32_t cw) {
     return false;
   if (classify_smem_bytes((int)variant, cw) > 232448) return false;
   const VariantShape vs = variant_shape((int)variant);
-  return (uint64_t)cw <=
+  // every warp of the launch must find an end marker among the first
+  // `stages` slots past the last tile
+  return (uint64_t)cw + 1 <=
          (uint64_t)vs.stages * ((vs.rounds + vs.rounds_per_item - 1) / vs.rounds_per_item);
 }
 
@@ -644,22 +646,18 @@ int classify_group(rgg_roadmap_t* rs, uint32_t n, cudaStream_t s) {
     lc.variant = r0->variant;
     lc.grid = (uint32_t)std::min<uint64_t>((tiles + 1) / 2, launch_ctas(r0));
     lc.grid = std::max<uint32_t>(lc.grid, 1);
-    uint32_t* counter = reinterpret_cast<uint32_t*>(r0->d_status + 1);
-    RGG_CK(cudaMemsetAsync(counter, 0, sizeof(uint32_t), s));
     cudaEvent_t* ev = timed ? next_events(timed) : nullptr;
     if (ev) RGG_CK(cudaEventRecord(ev[0], s));
     if (n == 1) {
       cp1.njobs = 1;
       cp1.total_tiles = tiles;
       cp1.status = r0->d_status;
-      cp1.work_counter = counter;
       cp1.wait_ns = r0->wait_ns;
       RGG_CK(launch_classify_single(cp1, lc, s));
     } else {
       cpp->njobs = nj;
       cpp->total_tiles = tiles;
       cpp->status = r0->d_status;
-      cpp->work_counter = counter;
       cpp->wait_ns = r0->wait_ns;
       RGG_CK(launch_classify_batched(*cpp, lc, s));
     }

@@ -116,7 +116,6 @@ struct ClassifyParams {
   uint32_t njobs;
   uint64_t total_tiles;
   int* status;                      // device status word of the launch (0 = ok)
-  uint32_t* work_counter;           // tile-chunk counter, zero at launch
   uint64_t wait_ns = 4000000000ull; // limit of every bounded wait, ns of wall time
 };
 

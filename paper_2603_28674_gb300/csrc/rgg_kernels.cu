@@ -510,18 +510,196 @@ __device__ __forceinline__ void write_stage_hdr(unsigned char* sb, int job, uint
 }
 
 constexpr int kPairQueue = 64;   // (sample, box) pairs a warp compacts per round
-constexpr uint32_t kChunkTiles = 16;  // tiles a producer takes per grab (<= 32)
 
 __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
+// Full barriers per stage.  Slot m of a CTA completes on barrier m % (B*NSTAGE)
+// with phase parity (m / (B*NSTAGE)) & 1.  Slots are refilled out of order (a
+// stage is refilled as soon as its own tile is done), so a worker may reach
+// slot m while the stage's earlier slots are still unfilled; the parity test
+// is unambiguous as long as the barrier's previous use, slot m - B*NSTAGE, is
+// filled.  If it were not, the B slots of that stage from m - B*NSTAGE on
+// would all be unfilled with every item taken, i.e. B*IPT waiting workers,
+// plus one on the slot before them and the one at slot m: so B*IPT + 1 >= the
+// launch's warps keeps every wait exact.
+constexpr int kMaxWorkers = kMaxClassifyThreads / 32;
+__host__ __device__ constexpr int full_barriers_per_stage(int ipt) { return ipt >= kMaxWorkers - 1 ? 1 : (kMaxWorkers - 2) / ipt + 1; }
+
+// Fill ring slot `slot` of this CTA (stage slot % NSTAGE) with its tile,
+// blockIdx.x + slot * gridDim.x, or with an end marker once past the last
+// tile.  The slot's tile is fixed by its number, so every worker sees the
+// tiles in slot order and every end marker after the last tile.  Called by
+// one whole warp: lanes derive the copies, lane 0 writes the header and arms
+// the stage's barrier, and the lanes issue the bulk copies together.
+template <int MAXJ, int NSTAGE, int STAGE_BYTES, int NBAR, bool FILTER>
+__device__ __forceinline__ void fill_slot(const ClassifyParams<MAXJ>& P, uint32_t slot,
+                                          unsigned char* stages, uint64_t* full_bars, int* s_sjob,
+                                          uint32_t* s_last, uint32_t* s_cand, float4* s_boxes,
+                                          int lane) {
+  const int stage = (int)(slot % NSTAGE);
+  uint64_t* bar = &full_bars[slot % NBAR];
+  unsigned char* sb = stages + (size_t)stage * STAGE_BYTES;
+  const uint64_t t = blockIdx.x + (uint64_t)slot * gridDim.x;
+  if (t >= P.total_tiles) {
+    if (lane == 0) {
+      reinterpret_cast<StageHdr*>(sb)->end = 1;
+      s_last[stage] = slot;
+      mbar_arrive(bar);
+    }
+    __syncwarp();
+    return;
+  }
+  const int jb = MAXJ == 1 ? 0 : find_job(P, t);
+  const ClassifyJob& J = P.job[jb];
+  const uint64_t lt = t - J.tile_base;
+  const TileDesc d = J.tiles[lt];
+  const uint32_t halo = J.joints ? J.tile_halo[lt] : 0u;
+  uint32_t need = ~0u, ro = 0;
+  if constexpr (FILTER) {
+    if (J.rcand) {
+      need = J.rcand[lt * kRoundSlots + kRoundSlots - 1];
+      ro = J.rout[lt * kRoundSlots + lane];
+    }
+  }
+  const uint64_t K = J.K;
+  const uint64_t g0 = lt * J.S;
+  const uint64_t g1 = min(g0 + J.S, J.G);
+  // inner window: the tile's K spheres per sample, or its link ends and the
+  // h_t ends before it that hold its first samples' near ends
+  const bool jt = J.joints != 0;
+  const uint64_t w0 = jt ? g0 - halo : K * g0;
+  const uint64_t a0 = w0 & ~3ull, a1 = ((jt ? g1 : K * g1) + 3) & ~3ull;
+  const int in_shift = (int)((jt ? g0 : K * g0) - a0);
+  const uint32_t n_in = jt ? 3u : 4u;
+  const uint64_t o0 = d.packed & ((1ull << 40) - 1);
+  const uint32_t n_out = (uint32_t)((d.packed >> 40) & 0xffff);
+  const uint32_t n_edges = (uint32_t)(d.packed >> 56);
+  const uint64_t b0 = o0 & ~3ull, b1 = (o0 + n_out + 3) & ~3ull;
+  const uint32_t et_bytes = n_edges * 16;
+  const uint32_t in_bytes = (uint32_t)((a1 - a0) * 4);
+  const uint32_t out_bytes = (uint32_t)((b1 - b0) * 4);
+  if (FILTER && need == 0u) {
+    // the spatial filter found no moved box near the tile: no data, no
+    // rounds (the workers take its items and find nothing to do)
+    if (lane == 0) {
+      write_stage_hdr(sb, jb, g0, g0, 0, 0, 0, 0, d.e_first);
+      s_last[stage] = slot;
+      mbar_arrive(bar);
+    }
+    __syncwarp();
+    return;
+  }
+  // the stage's box records are refreshed only when its roadmap changes
+  const int held = s_sjob[stage];
+  const uint32_t box_bytes = (MAXJ != 1 && held != jb) ? (uint32_t)(kBoxAreaFloats * 4) : 0u;
+  __syncwarp();
+  uint32_t tile_rec_bytes = 0;  // record bytes this tile's copies move
+  if (!FILTER || J.rcand == nullptr) {
+    // whole-tile copies: lane 0 the edge table, lanes 1..4 the inner planes
+    // (1..3 the link-end planes), 5..8 the outer ones, lane 9 the box area;
+    // one predicated issue
+    void* c_dst = sb + kStageEtabOff;
+    const void* c_src = J.etab + d.etab;
+    uint32_t c_bytes = et_bytes;
+    if (lane >= 1 && lane <= 4) {
+      c_dst = sb + J.off_in + (size_t)(lane - 1) * J.in_cap * 4;
+      c_src = J.inner + (lane - 1) * J.in_stride + a0;
+      c_bytes = (uint32_t)(lane - 1) < n_in ? in_bytes : 0u;
+    } else if (lane >= 5 && lane <= 8) {
+      c_dst = sb + J.off_out + (size_t)(lane - 5) * J.out_cap * 4;
+      c_src = J.outer + (lane - 5) * J.out_stride + b0;
+      c_bytes = out_bytes;
+    } else if (lane == 9) {
+      c_dst = s_boxes + (size_t)stage * (kBoxAreaFloats / 4);
+      c_src = J.boxes;
+      c_bytes = box_bytes;
+    } else if (lane > 9) {
+      c_bytes = 0;
+    }
+    if (lane == 0) {
+      write_stage_hdr(sb, jb, g0, g1, n_out, n_edges, in_shift, (int)(o0 - b0), d.e_first);
+      mbar_arrive_expect_tx(bar, et_bytes + n_in * in_bytes + 4 * out_bytes + box_bytes);
+      s_sjob[stage] = jb;
+      s_last[stage] = slot;
+    }
+    tile_rec_bytes = n_in * in_bytes + 4 * out_bytes;
+    __syncwarp();
+    fence_proxy_async_smem();
+    if (c_bytes) bulk_g2s(c_dst, c_src, c_bytes, bar);
+  } else if constexpr (FILTER) {
+    // the runs of consecutive rounds in `need`: the lane of a run's first
+    // round copies the run's 4 inner and 4 outer plane pieces, at the offsets
+    // they have in a whole-tile copy (link-end planes, 12 B per sample, are
+    // copied whole by lanes 1..3, since a run's near ends may lie in rounds
+    // the run does not cover); lane 10 copies the tile's candidate row
+    const bool starts = ((need >> lane) & 1u) && (lane == 0 || !((need >> (lane - 1)) & 1u));
+    const uint32_t clear_above = ~need & ~((2u << lane) - 1u);
+    const int re = clear_above ? __ffs(clear_above) - 1 : 32;  // run = rounds [lane, re)
+    const uint32_t ro_last = __shfl_sync(0xffffffffu, ro, starts ? re - 1 : lane);
+    uint64_t ia = a0, ib = a0, oa = b0, ob = b0;
+    if (starts) {
+      if (!jt) {
+        ia = (K * (g0 + (uint64_t)(31 * lane))) & ~3ull;
+        ib = (K * min(g0 + (uint64_t)(31 * re), g1) + 3) & ~3ull;
+      }
+      oa = (o0 + (ro & 0xffffu)) & ~3ull;
+      ob = (o0 + (ro_last >> 16) + 3) & ~3ull;
+    }
+    // never outside the whole-tile window, whatever the round data say
+    ia = max(ia, a0);
+    ib = max(min(ib, a1), ia);
+    oa = max(oa, b0);
+    ob = max(min(ob, b1), oa);
+    const uint32_t run_in = (uint32_t)((ib - ia) * 4);
+    const uint32_t run_out = (uint32_t)((ob - oa) * 4);
+    const uint32_t tile_bytes = __reduce_add_sync(0xffffffffu, 4 * (run_in + run_out)) +
+                                (jt ? 3 * in_bytes : 0u);
+    if (lane == 0) {
+      write_stage_hdr(sb, jb, g0, g1, n_out, n_edges, in_shift, (int)(o0 - b0), d.e_first);
+      mbar_arrive_expect_tx(bar, et_bytes + tile_bytes + box_bytes + 4 * kRoundSlots);
+      s_sjob[stage] = jb;
+      s_last[stage] = slot;
+    }
+    tile_rec_bytes = tile_bytes;
+    __syncwarp();
+    fence_proxy_async_smem();
+    if (lane == 0) bulk_g2s(sb + kStageEtabOff, J.etab + d.etab, et_bytes, bar);
+    if (lane == 9 && box_bytes)
+      bulk_g2s(s_boxes + (size_t)stage * (kBoxAreaFloats / 4), J.boxes, box_bytes, bar);
+    if (jt && lane >= 1 && lane <= 3)
+      bulk_g2s(sb + J.off_in + (size_t)(lane - 1) * J.in_cap * 4,
+               J.inner + (lane - 1) * J.in_stride + a0, in_bytes, bar);
+    if (lane == 10)
+      bulk_g2s(s_cand + stage * kRoundSlots, J.rcand + lt * kRoundSlots, 4 * kRoundSlots,
+               bar);
+    if (run_in)
+      for (int pl = 0; pl < 4; ++pl)
+        bulk_g2s(sb + J.off_in + ((size_t)pl * J.in_cap + (ia - a0)) * 4,
+                 J.inner + pl * J.in_stride + ia, run_in, bar);
+    if (run_out)
+      for (int pl = 0; pl < 4; ++pl)
+        bulk_g2s(sb + J.off_out + ((size_t)pl * J.out_cap + (oa - b0)) * 4,
+                 J.outer + pl * J.out_stride + oa, run_out, bar);
+  }
+  // filtered instance: the record bytes this tile copied (the streaming
+  // instance copies every record and does not count)
+  if (FILTER && lane == 0 && J.streamed) atomicAdd(J.streamed, (unsigned long long)tile_rec_bytes);
+  __syncwarp();
+}
+
 // Work items: tile t of this CTA has ROUNDS rounds of 31 samples, grouped
-// RPI rounds per work item; warps take items in order from a shared counter.  Round r of a tile covers
-// the samples q = 31r .. 31r+30 on lanes 1..31; lane 0 takes sample 31r-1,
-// whose following interval the round needs (for r = 0 that is the tile's
-// halo interval).  The warp that finishes a tile's last round flushes the
-// tile's per-edge bits and releases the stage.
+// RPI rounds per work item; warps take items in order from a shared counter.
+// Round r of a tile covers the samples q = 31r .. 31r+30 on lanes 1..31;
+// lane 0 takes sample 31r-1, whose following interval the round needs (for
+// r = 0 that is the tile's halo interval).
+//
+// The ring refills itself.  Every warp is a worker.  The warp that finishes
+// a tile's last item flushes the tile's per-edge bits and loads the stage
+// with the tile NSTAGE slots ahead, so no warp waits for a free stage and no
+// single warp issues every tile's copies.  The first NSTAGE slots are filled
+// at the start.
 // FILTER: the instance that serves spatially filtered jobs (tiles skipped,
 // rounds copied in runs, per-round candidate masks); without it the jobs'
 // filter fields are ignored and every tile is copied whole.
@@ -533,30 +711,26 @@ __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const 
   // Box records: one area staged once for a single-roadmap launch; one per
   // stage, refilled when the stage's roadmap changes, for batched launches.
   constexpr int kBoxAreas = MAXJ == 1 ? 1 : NSTAGE;
+  constexpr int IPT = (ROUNDS + RPI - 1) / RPI;  // work items per tile
+  constexpr int NBAR = NSTAGE * full_barriers_per_stage(IPT);
   constexpr size_t kOffFull = (size_t)NSTAGE * STAGE_BYTES;
-  constexpr size_t kOffEmpty = kOffFull + NSTAGE * sizeof(uint64_t);
-  constexpr size_t kOffBoxBar = kOffEmpty + NSTAGE * sizeof(uint64_t);
+  constexpr size_t kOffBoxBar = kOffFull + NBAR * sizeof(uint64_t);
   constexpr size_t kOffItem = kOffBoxBar + sizeof(uint64_t);
   constexpr size_t kOffCnt = kOffItem + 8;
-  constexpr size_t kOffDesc = (kOffCnt + 4 * ((NSTAGE + 3) & ~3) + 15) & ~(size_t)15;
-  constexpr size_t kOffDjob = kOffDesc + 32 * sizeof(TileDesc);
-  constexpr size_t kOffHalo = kOffDjob + 32 * sizeof(int);
-  constexpr size_t kOffNeed = kOffHalo + 32 * sizeof(uint32_t);
-  constexpr size_t kOffCand = kOffNeed + (FILTER ? 32 * sizeof(uint32_t) : 0);  // 16-byte aligned
+  constexpr size_t kOffSjob = kOffCnt + 4 * ((NSTAGE + 3) & ~3);
+  constexpr size_t kOffLast = kOffSjob + 4 * ((NSTAGE + 3) & ~3);
+  constexpr size_t kOffCand = (kOffLast + 4 * ((NSTAGE + 3) & ~3) + 15) & ~(size_t)15;
   constexpr size_t kOffBoxes =
       (kOffCand + (FILTER ? (size_t)NSTAGE * kRoundSlots * 4 : 0) + 127) & ~(size_t)127;
   constexpr size_t kOffQueues = kOffBoxes + (size_t)kBoxAreas * kBoxAreaFloats * 4;
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char* stages = smem;
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + kOffFull);
-  uint64_t* empty = reinterpret_cast<uint64_t*>(smem + kOffEmpty);
   uint64_t* boxbar = reinterpret_cast<uint64_t*>(smem + kOffBoxBar);
   uint32_t* s_item = reinterpret_cast<uint32_t*>(smem + kOffItem);     // next work item
   uint32_t* s_cnt = reinterpret_cast<uint32_t*>(smem + kOffCnt);       // items done per stage
-  TileDesc* s_desc = reinterpret_cast<TileDesc*>(smem + kOffDesc);     // producer's batch
-  int* s_djob = reinterpret_cast<int*>(smem + kOffDjob);
-  uint32_t* s_halo = reinterpret_cast<uint32_t*>(smem + kOffHalo);  // producer's batch
-  uint32_t* s_need = reinterpret_cast<uint32_t*>(smem + kOffNeed);  // producer's batch
+  int* s_sjob = reinterpret_cast<int*>(smem + kOffSjob);              // job whose boxes a stage holds
+  uint32_t* s_last = reinterpret_cast<uint32_t*>(smem + kOffLast);     // last slot a stage was filled with
   // per stage (spatial filter): the moved boxes that may reach each round of
   // its tile, 0 for a round that was not copied
   uint32_t* s_cand = reinterpret_cast<uint32_t*>(smem + kOffCand);
@@ -565,7 +739,7 @@ __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const 
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
-  const int ncw = (blockDim.x >> 5) - 1;
+  const int nw = blockDim.x >> 5;
 
   // An error latched by an earlier launch (on the launch's word or on one of
   // its roadmaps' own words) stops the launch before it issues anything: its
@@ -584,13 +758,14 @@ __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const 
   // zero the stages (their accumulators must start at zero) and counters
   for (uint32_t i = threadIdx.x; i < NSTAGE * STAGE_BYTES / 16; i += blockDim.x)
     reinterpret_cast<uint4*>(stages)[i] = make_uint4(0, 0, 0, 0);
-  for (uint32_t i = threadIdx.x; i < NSTAGE; i += blockDim.x) s_cnt[i] = 0;
+  for (uint32_t i = threadIdx.x; i < NSTAGE; i += blockDim.x) {
+    s_cnt[i] = 0;
+    s_sjob[i] = -1;
+    s_last[i] = 0xffffffffu;
+  }
   fence_proxy_async_smem();
   if (threadIdx.x == 0) {
-    for (int s = 0; s < NSTAGE; ++s) {
-      mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 1);
-    }
+    for (int b = 0; b < NBAR; ++b) mbar_init(&full[b], 1);
     mbar_init(boxbar, 1);
     *s_item = 0;
     fence_mbar_init();
@@ -604,263 +779,43 @@ __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const 
     }
   }
   __syncthreads();
+  // the first NSTAGE slots, one warp each
+  for (int s = warp; s < NSTAGE; s += nw)
+    fill_slot<MAXJ, NSTAGE, STAGE_BYTES, NBAR, FILTER>(P, (uint32_t)s, stages, full, s_sjob,
+                                                       s_last, s_cand, s_boxes, lane);
 
-  if (warp == 0) {
-    // ------------------------------------------------------------ producer
-    uint32_t slot = 0;
-    bool ok = true;
-    int stage_job = -1;  // lane s < NSTAGE: job whose boxes stage s holds
-    unsigned long long streamed = 0;  // lane 0: record bytes copied for streamed_job
-    int streamed_job = -1;
-    // Tiles are taken in chunks of kChunkTiles from a launch-wide counter, so
-    // that CTAs finish together however unevenly the tiles' work is spread.
-    for (;;) {
-      uint64_t tb = 0;
-      if (lane == 0) tb = (uint64_t)atomicAdd(P.work_counter, 1u) * kChunkTiles;
-      tb = __shfl_sync(0xffffffffu, tb, 0);
-      if (tb >= P.total_tiles || !ok) break;
-      const uint64_t t_end = min(P.total_tiles, tb + kChunkTiles);
-      const uint64_t t = tb + lane;
-      __syncwarp();
-      // lane i: tile tb+i's descriptor, job and (spatial filter) the mask of
-      // its rounds some moved box may reach; lane r also loads round r's
-      // outer range of the chunk's first tile, and each tile prefetches the
-      // next one's, so that no tile waits on a global load of its own
-      uint32_t ro_next = 0;
-      if (t < t_end) {
-        const int jb = find_job(P, t);
-        const ClassifyJob& J = P.job[jb];
-        s_desc[lane] = J.tiles[t - J.tile_base];
-        s_djob[lane] = jb;
-        s_halo[lane] = J.joints ? J.tile_halo[t - J.tile_base] : 0u;
-        if constexpr (FILTER)
-          s_need[lane] = J.rcand ? J.rcand[(t - J.tile_base) * kRoundSlots + kRoundSlots - 1] : ~0u;
-      }
-      if constexpr (FILTER) {
-        const ClassifyJob& J0 = P.job[find_job(P, tb)];
-        if (J0.rcand) ro_next = J0.rout[(tb - J0.tile_base) * kRoundSlots + lane];
-      }
-      __syncwarp();
-      const int nb = (int)(t_end - tb);
-      for (int i = 0; i < nb; ++i) {
-        const int jb = s_djob[i];
-        const ClassifyJob& J = P.job[jb];
-        const TileDesc d = s_desc[i];
-        const uint32_t halo = s_halo[i];
-        const uint64_t lt = tb + i - J.tile_base;
-        uint32_t need = ~0u, ro = 0;
-        if constexpr (FILTER) {
-          need = s_need[i];
-          ro = ro_next;
-          if (i + 1 < nb) {
-            const ClassifyJob& Jn = P.job[s_djob[i + 1]];
-            if (Jn.rcand) ro_next = Jn.rout[(tb + i + 1 - Jn.tile_base) * kRoundSlots + lane];
-          }
-          // the spatial filter found no moved box near the tile: no slot
-          if (need == 0u) continue;
-        }
-        const int stage = slot % NSTAGE;
-        const uint32_t round = slot / NSTAGE;
-        // every lane derives the tile's copies before waiting for the stage
-        // (the wait to the copies is the ring's critical path: computing them
-        // first made the launch 4% faster); then lane 0 writes the header and
-        // arms the barrier, and the lanes issue the bulk copies together
-        const uint64_t K = J.K;
-        const uint64_t g0 = lt * J.S;
-        const uint64_t g1 = min(g0 + J.S, J.G);
-        // inner window: the tile's K spheres per sample, or its link ends and
-        // the h_t ends before it that hold its first samples' near ends
-        const bool jt = J.joints != 0;
-        const uint64_t w0 = jt ? g0 - halo : K * g0;
-        const uint64_t a0 = w0 & ~3ull, a1 = ((jt ? g1 : K * g1) + 3) & ~3ull;
-        const int in_shift = (int)((jt ? g0 : K * g0) - a0);
-        const uint32_t n_in = jt ? 3u : 4u;
-        const uint64_t o0 = d.packed & ((1ull << 40) - 1);
-        const uint32_t n_out = (uint32_t)((d.packed >> 40) & 0xffff);
-        const uint32_t n_edges = (uint32_t)(d.packed >> 56);
-        const uint64_t b0 = o0 & ~3ull, b1 = (o0 + n_out + 3) & ~3ull;
-        unsigned char* sb = stages + (size_t)stage * STAGE_BYTES;
-        const uint32_t et_bytes = n_edges * 16;
-        // the stage's box records are refreshed only when its job changes
-        const int held = __shfl_sync(0xffffffffu, stage_job, stage);
-        const uint32_t box_bytes =
-            (MAXJ != 1 && held != jb) ? (uint32_t)(kBoxAreaFloats * 4) : 0u;
-        if (lane == stage) stage_job = jb;
-        // whole-tile copies (every job of the streaming instance): lane 0 the
-        // edge table, lanes 1..4 the inner planes (1..3 the link-end planes),
-        // 5..8 the outer ones, lane 9 the box area; one predicated issue after
-        // the wait
-        const uint32_t in_bytes = (uint32_t)((a1 - a0) * 4);
-        const uint32_t out_bytes = (uint32_t)((b1 - b0) * 4);
-        void* c_dst = sb + kStageEtabOff;
-        const void* c_src = J.etab + d.etab;
-        uint32_t c_bytes = et_bytes;
-        if (lane >= 1 && lane <= 4) {
-          c_dst = sb + J.off_in + (size_t)(lane - 1) * J.in_cap * 4;
-          c_src = J.inner + (lane - 1) * J.in_stride + a0;
-          c_bytes = (uint32_t)(lane - 1) < n_in ? in_bytes : 0u;
-        } else if (lane >= 5 && lane <= 8) {
-          c_dst = sb + J.off_out + (size_t)(lane - 5) * J.out_cap * 4;
-          c_src = J.outer + (lane - 5) * J.out_stride + b0;
-          c_bytes = out_bytes;
-        } else if (lane == 9) {
-          c_dst = s_boxes + (size_t)stage * (kBoxAreaFloats / 4);
-          c_src = J.boxes;
-          c_bytes = box_bytes;
-        } else if (lane > 9) {
-          c_bytes = 0;
-        }
-        int good = 1;
-        if (lane == 0) good = mbar_wait_bounded(&empty[stage], (round & 1) ^ 1, P.wait_ns);
-        good = __shfl_sync(0xffffffffu, good, 0);
-        if (!good) {
-          if (lane == 0) atomicCAS(P.status, 0, (int)kStatusTimeoutEmpty);
-          ok = false;
-          break;
-        }
-        uint32_t tile_rec_bytes = 0;  // lane 0: record bytes this tile's copies move
-        if (!FILTER || J.rcand == nullptr) {
-          // the whole tile
-          if (lane == 0) {
-            write_stage_hdr(sb, jb, g0, g1, n_out, n_edges, in_shift, (int)(o0 - b0), d.e_first);
-            mbar_arrive_expect_tx(&full[stage],
-                                  et_bytes + n_in * in_bytes + 4 * out_bytes + box_bytes);
-          }
-          tile_rec_bytes = n_in * in_bytes + 4 * out_bytes;
-          __syncwarp();
-          if (c_bytes) bulk_g2s(c_dst, c_src, c_bytes, &full[stage]);
-        } else if constexpr (FILTER) {
-          // the runs of consecutive rounds in `need`: the lane of a run's
-          // first round copies the run's 4 inner and 4 outer plane pieces,
-          // at the offsets they have in a whole-tile copy (link-end planes,
-          // 12 B per sample, are copied whole by lanes 1..3, since a run's
-          // near ends may lie in rounds the run does not cover); lane 10
-          // copies the tile's candidate row for the consumers
-          const bool starts = ((need >> lane) & 1u) && (lane == 0 || !((need >> (lane - 1)) & 1u));
-          const uint32_t clear_above = ~need & ~((2u << lane) - 1u);
-          const int re = clear_above ? __ffs(clear_above) - 1 : 32;  // run = rounds [lane, re)
-          const uint32_t ro_last = __shfl_sync(0xffffffffu, ro, starts ? re - 1 : lane);
-          uint64_t ia = a0, ib = a0, oa = b0, ob = b0;
-          if (starts) {
-            if (!jt) {
-              ia = (K * (g0 + (uint64_t)(31 * lane))) & ~3ull;
-              ib = (K * min(g0 + (uint64_t)(31 * re), g1) + 3) & ~3ull;
-            }
-            oa = (o0 + (ro & 0xffffu)) & ~3ull;
-            ob = (o0 + (ro_last >> 16) + 3) & ~3ull;
-          }
-          // never outside the whole-tile window, whatever the round data say
-          ia = max(ia, a0);
-          ib = max(min(ib, a1), ia);
-          oa = max(oa, b0);
-          ob = max(min(ob, b1), oa);
-          const uint32_t run_in = (uint32_t)((ib - ia) * 4);
-          const uint32_t run_out = (uint32_t)((ob - oa) * 4);
-          const uint32_t tile_bytes = __reduce_add_sync(0xffffffffu, 4 * (run_in + run_out)) +
-                                      (jt ? 3 * in_bytes : 0u);
-          if (lane == 0) {
-            write_stage_hdr(sb, jb, g0, g1, n_out, n_edges, in_shift, (int)(o0 - b0), d.e_first);
-            mbar_arrive_expect_tx(&full[stage], et_bytes + tile_bytes + box_bytes + 4 * kRoundSlots);
-          }
-          tile_rec_bytes = tile_bytes;
-          __syncwarp();
-          if (lane == 0) bulk_g2s(sb + kStageEtabOff, J.etab + d.etab, et_bytes, &full[stage]);
-          if (lane == 9 && box_bytes)
-            bulk_g2s(s_boxes + (size_t)stage * (kBoxAreaFloats / 4), J.boxes, box_bytes,
-                     &full[stage]);
-          if (jt && lane >= 1 && lane <= 3)
-            bulk_g2s(sb + J.off_in + (size_t)(lane - 1) * J.in_cap * 4,
-                     J.inner + (lane - 1) * J.in_stride + a0, in_bytes, &full[stage]);
-          if (lane == 10)
-            bulk_g2s(s_cand + stage * kRoundSlots, J.rcand + lt * kRoundSlots, 4 * kRoundSlots,
-                     &full[stage]);
-          if (run_in)
-            for (int pl = 0; pl < 4; ++pl)
-              bulk_g2s(sb + J.off_in + ((size_t)pl * J.in_cap + (ia - a0)) * 4,
-                       J.inner + pl * J.in_stride + ia, run_in, &full[stage]);
-          if (run_out)
-            for (int pl = 0; pl < 4; ++pl)
-              bulk_g2s(sb + J.off_out + ((size_t)pl * J.out_cap + (oa - b0)) * 4,
-                       J.outer + pl * J.out_stride + oa, run_out, &full[stage]);
-        }
-        // filtered instance: record bytes are counted per job, after the
-        // copies, and added to the job's counter when the job changes (and at
-        // the end); the count costs the streaming instance 2% and is left out
-        if (FILTER && lane == 0) {
-          if (jb != streamed_job) {
-            if (streamed_job >= 0 && streamed && P.job[streamed_job].streamed)
-              atomicAdd(P.job[streamed_job].streamed, streamed);
-            streamed = 0;
-            streamed_job = jb;
-          }
-          streamed += tile_rec_bytes;
-        }
-        ++slot;
-      }
-      ok = __shfl_sync(0xffffffffu, ok, 0);
-    }
-    if (FILTER && lane == 0 && streamed_job >= 0 && streamed && P.job[streamed_job].streamed)
-      atomicAdd(P.job[streamed_job].streamed, streamed);
-    // end markers: one slot per items-per-tile consumer warps, so that every
-    // consumer warp takes one
-    if (lane == 0 && ok) {
-      constexpr int IPT = (ROUNDS + RPI - 1) / RPI;
-      const int n_end = (ncw + IPT - 1) / IPT;
-      for (int i = 0; i < n_end; ++i, ++slot) {
-        const int stage = slot % NSTAGE;
-        const uint32_t round = slot / NSTAGE;
-        if (!mbar_wait_bounded(&empty[stage], (round & 1) ^ 1, P.wait_ns)) {
-          atomicCAS(P.status, 0, (int)kStatusTimeoutEmpty);
-          break;
-        }
-        StageHdr* h = reinterpret_cast<StageHdr*>(stages + (size_t)stage * STAGE_BYTES);
-        h->end = 1;
-        mbar_arrive(&full[stage]);
-      }
-    }
-    // Before leaving, make sure none of this CTA's bulk copies is still in
-    // flight (bounded; immediate when every issued slot has landed): the
-    // slots armed last, and the box records copied at the start, which
-    // consumers that gave up early never waited for.
-    if (lane == 0) {
-      const uint32_t first = slot > (uint32_t)NSTAGE ? slot - NSTAGE : 0;
-      for (uint32_t k = first; k < slot; ++k)
-        mbar_wait_bounded(&full[k % NSTAGE], (k / NSTAGE) & 1, kDrainLimit);
-      mbar_wait_bounded(boxbar, 0, kDrainLimit);
-    }
-    return;
-  }
-
-  // -------------------------------------------------------------- consumers
-  uint32_t* queue = queues + (size_t)(warp - 1) * kPairQueue;
+  // ------------------------------------------------------------- workers
+  uint32_t* queue = queues + (size_t)warp * kPairQueue;
+  bool run = true;
   {
     int ok = 1;
     if (lane == 0) ok = mbar_wait_bounded(boxbar, 0, P.wait_ns);
     ok = __shfl_sync(0xffffffffu, ok, 0);
     if (!ok) {
       if (lane == 0) atomicCAS(P.status, 0, (int)kStatusTimeoutBoxes);
-      return;
+      run = false;
+    } else {
+      mbar_wait_bounded(boxbar, 0, P.wait_ns);
     }
-    mbar_wait_bounded(boxbar, 0, P.wait_ns);
   }
-  constexpr int IPT = (ROUNDS + RPI - 1) / RPI;  // work items per tile
-  for (;;) {
+  while (run) {
     uint32_t item = 0;
     if (lane == 0) item = atomicAdd(s_item, 1u);
     item = __shfl_sync(0xffffffffu, item, 0);
     const uint32_t slot = item / IPT;
     const int sub = (int)(item - slot * IPT);
     const int stage = slot % NSTAGE;
-    const uint32_t parity = (slot / NSTAGE) & 1;
+    uint64_t* bar = &full[slot % NBAR];
+    const uint32_t parity = (slot / NBAR) & 1;
     int ok = 1;
-    if (lane == 0) ok = mbar_wait_bounded(&full[stage], parity, P.wait_ns);
+    if (lane == 0) ok = mbar_wait_bounded(bar, parity, P.wait_ns);
     ok = __shfl_sync(0xffffffffu, ok, 0);
     if (!ok) {
       if (lane == 0) atomicCAS(P.status, 0, (int)kStatusTimeoutFull);
       break;
     }
     // completed phase: returns at once and orders the stage's data for this lane
-    mbar_wait_bounded(&full[stage], parity, P.wait_ns);
+    mbar_wait_bounded(bar, parity, P.wait_ns);
     unsigned char* sb = stages + (size_t)stage * STAGE_BYTES;
     const StageHdr hdr = *reinterpret_cast<const StageHdr*>(sb);
     if (hdr.end) break;
@@ -1073,7 +1028,8 @@ __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const 
         __syncwarp();
       }
     }
-    // ---- item done; the tile's last item flushes and releases the stage
+    // ---- item done; the tile's last item flushes the tile's bits and refills
+    // the stage
     __syncwarp();
     uint32_t done = 0;
     if (lane == 0) {
@@ -1084,9 +1040,8 @@ __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const 
     if (done == IPT - 1) {
       __threadfence_block();
       // ---- a5: the tile's per-edge bits into the global accumulators.  They
-      // are taken into registers and the stage is released first: the
-      // release (a CTA-scope arrive) would otherwise wait for the global ORs,
-      // and the release is on the ring's critical path (1% of the launch)
+      // are taken into registers and the stage is refilled first: the refill
+      // is on the ring's critical path, the global ORs are not
       static_assert(kAccMax <= 3 * 32, "accumulator entries per lane");
       uint32_t hv[3], tv[3];
 #pragma unroll
@@ -1103,7 +1058,9 @@ __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const 
       }
       if (lane == 0) s_cnt[stage] = 0;
       __syncwarp();
-      if (lane == 0) mbar_arrive(&empty[stage]);
+      // the stage is free: this warp loads it with the slot NSTAGE ahead
+      fill_slot<MAXJ, NSTAGE, STAGE_BYTES, NBAR, FILTER>(P, slot + NSTAGE, stages, full, s_sjob,
+                                                         s_last, s_cand, s_boxes, lane);
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         const uint64_t e = (uint64_t)hdr.e_first + lane + 32 * c;
@@ -1112,7 +1069,22 @@ __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const 
       }
     }
   }
+  // Before the CTA exits, no bulk copy of it may still be in flight.  Every
+  // warp has stopped issuing once all are here; then one thread waits
+  // (bounded; at once when every filled slot has landed) for the phase of
+  // each stage's last fill, whatever it was (normally an end marker, whose
+  // phase is complete), and for the box records copied at the start: after
+  // a wait that ran out, a slot may have been filled that no worker waited
+  // for.  A stage's earlier fills were all waited for by its workers.
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NSTAGE; ++s)
+      if (s_last[s] != 0xffffffffu)
+        mbar_wait_bounded(&full[s_last[s] % NBAR], (s_last[s] / NBAR) & 1, kDrainLimit);
+    mbar_wait_bounded(boxbar, 0, kDrainLimit);
+  }
 }
+
 
 // ===========================================================================
 // a6: merge the pass's bits into the per-edge box sets (Algorithm 1's
@@ -1460,26 +1432,26 @@ cudaError_t launch_box_prep(const BoxPrepParams& p, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template <int MAXJ, int NSTAGE, int STAGE_BYTES, bool FILTER>
+template <int MAXJ, int NSTAGE, int STAGE_BYTES, int IPT, bool FILTER>
 static size_t smem_bytes_t(uint32_t consumer_warps) {
-  // mirrors the carve-up at the top of classify_kernel
+  // mirrors the carve-up at the top of classify_kernel; every warp is a
+  // worker with its own pair queue
   constexpr int kBoxAreas = MAXJ == 1 ? 1 : NSTAGE;
+  constexpr int NBAR = NSTAGE * full_barriers_per_stage(IPT);
   constexpr size_t kOffFull = (size_t)NSTAGE * STAGE_BYTES;
-  constexpr size_t kOffCnt = kOffFull + (2 * NSTAGE + 1) * sizeof(uint64_t) + 8;
-  constexpr size_t kOffDesc = (kOffCnt + 4 * ((NSTAGE + 3) & ~3) + 15) & ~(size_t)15;
+  constexpr size_t kOffCnt = kOffFull + (NBAR + 1) * sizeof(uint64_t) + 8;
+  constexpr size_t kOffCand = (kOffCnt + 3 * 4 * ((NSTAGE + 3) & ~3) + 15) & ~(size_t)15;
   constexpr size_t kOffBoxes =
-      (kOffDesc + 32 * sizeof(TileDesc) + 32 * sizeof(int) + 32 * sizeof(uint32_t) +
-       (FILTER ? 32 * sizeof(uint32_t) + (size_t)NSTAGE * kRoundSlots * 4 : 0) + 127) &
-      ~(size_t)127;
+      (kOffCand + (FILTER ? (size_t)NSTAGE * kRoundSlots * 4 : 0) + 127) & ~(size_t)127;
   constexpr size_t kOffQueues = kOffBoxes + (size_t)kBoxAreas * kBoxAreaFloats * 4;
-  return kOffQueues + (size_t)consumer_warps * 4 * kPairQueue;
+  return kOffQueues + (size_t)(consumer_warps + 1) * 4 * kPairQueue;
 }
 
 size_t classify_smem_bytes(int variant, uint32_t consumer_warps) {
   // the batched kernel's (larger) footprint, which bounds both
   switch (variant) {
 #define RGG_VARIANT(id, ns, sb, rd, rpi) \
-  case id: return smem_bytes_t<kMaxJobs, ns, sb, filter_variant(id)>(consumer_warps);
+  case id: return smem_bytes_t<kMaxJobs, ns, sb, (rd + rpi - 1) / rpi, filter_variant(id)>(consumer_warps);
     RGG_VARIANTS(RGG_VARIANT)
 #undef RGG_VARIANT
     default: return 0;
@@ -1490,7 +1462,7 @@ template <int MAXJ, int NSTAGE, int STAGE_BYTES, int ROUNDS, int RPI, bool FILTE
 static cudaError_t launch_classify_v(const ClassifyParams<MAXJ>& p, const ClassifyLaunch& lc,
                                      cudaStream_t s) {
   auto kern = classify_kernel<MAXJ, NSTAGE, STAGE_BYTES, ROUNDS, RPI, FILTER>;
-  const size_t smem = smem_bytes_t<MAXJ, NSTAGE, STAGE_BYTES, FILTER>(lc.consumer_warps);
+  const size_t smem = smem_bytes_t<MAXJ, NSTAGE, STAGE_BYTES, (ROUNDS + RPI - 1) / RPI, FILTER>(lc.consumer_warps);
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
   kern<<<lc.grid, 32 * (1 + lc.consumer_warps), smem, s>>>(p);

@@ -300,9 +300,7 @@ extern "C" int rgg_classify_noalloc(const rgg_noalloc_args* a, void* stream) {
   cp.njobs = 1;
   cp.total_tiles = T;
   cp.status = st;
-  cp.work_counter = reinterpret_cast<uint32_t*>(base + kNaStatusOff + 16);
   cp.wait_ns = a->wait_limit_ns ? a->wait_limit_ns : 4000000000ull;
-  if (cudaMemsetAsync(cp.work_counter, 0, sizeof(uint32_t), s) != cudaSuccess) return RGG_ERR_CUDA;
   ClassifyLaunch lc;
   lc.consumer_warps = kDefaultConsumerWarps;
   lc.variant = kDefaultVariant;

@@ -35,20 +35,16 @@ static int tune_launch(rgg_roadmap_t* rs, uint32_t n, const std::vector<uint32_t
   lc.consumer_warps = r0->consumer_warps;
   lc.variant = r0->variant;
   lc.grid = std::max<uint32_t>(1, (uint32_t)std::min<uint64_t>((tiles + 1) / 2, launch_ctas(r0)));
-  uint32_t* counter = reinterpret_cast<uint32_t*>(r0->d_status + 1);
-  RGG_CK(cudaMemsetAsync(counter, 0, sizeof(uint32_t), s));
   if (n == 1) {
     cp1.njobs = 1;
     cp1.total_tiles = tiles;
     cp1.status = r0->d_status;
-    cp1.work_counter = counter;
     cp1.wait_ns = r0->wait_ns;
     RGG_CK(launch_classify_single(cp1, lc, s));
   } else {
     cpp->njobs = nj;
     cpp->total_tiles = tiles;
     cpp->status = r0->d_status;
-    cpp->work_counter = counter;
     cpp->wait_ns = r0->wait_ns;
     RGG_CK(launch_classify_batched(*cpp, lc, s));
   }
