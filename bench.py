@@ -417,11 +417,14 @@ def run_gpu(args):
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     e2e_s = max_over_ranks(dist, e2e_s, f"cuda:{local}")
-    # ---- the same steps with the spatial filter on (after the end-to-end
-    # loop; the headline above streams every record)
+    # ---- the same steps with the spatial filter in its other state (after
+    # the end-to-end loop): the headline runs the library's default (the
+    # filter on for link-end records), this one streams every record, or the
+    # other way round
     filtered = None
-    r.set_round_filter(True)
-    if r.info()["round_filter"]:
+    default_on = bool(info["round_filter"])
+    r.set_round_filter(not default_on)
+    if bool(r.info()["round_filter"]) != default_on:
         n_cmp = min(args.steps, 100)
         for i in range(3):
             device_step(2 * args.steps + args.warmup + i)
@@ -438,7 +441,17 @@ def run_gpu(args):
         filtered = {"kernel_ms": kf_ms / max(1, kf_n),
                     "record_bytes_per_launch": sf / max(1, kf_n), "launches": kf_n,
                     "info": r.info()}
-    r.set_round_filter(False)
+    r.set_round_filter(default_on)
+
+    # ---- the work the kernel executed, from its counting instance, over a
+    # few more of the same steps (the headline instance counts nothing)
+    r.set_work_counting(True)
+    r.work_counts()
+    n_cnt = 3
+    for i in range(n_cnt):
+        device_step(2 * args.steps + args.warmup + i)
+    executed = r.work_counts()
+    r.set_work_counting(False)
 
     r.check_status(stream)
     resolve = measure_resolve(r, sc, args.resolve, stream, rank == 0 and world == 1) \
@@ -456,16 +469,19 @@ def run_gpu(args):
     traffic = profiled_traffic(args.workload)
     filt = None
     if filtered is not None:
+        on = bool(filtered["info"]["round_filter"])
+        rb = filtered["record_bytes_per_launch"] if on else info["record_bytes"]
         b_f = algorithmic_bytes(filtered["info"], filtered["record_bytes_per_launch"])
-        filt = {"kernel_ms": filtered["kernel_ms"],
-                "record_bytes_per_launch": filtered["record_bytes_per_launch"],
-                "records_copied_frac": filtered["record_bytes_per_launch"] / info["record_bytes"],
+        filt = {"round_filter": on, "kernel_ms": filtered["kernel_ms"],
+                "record_bytes_per_launch": rb,
+                "records_copied_frac": rb / info["record_bytes"],
                 "bytes_per_launch": b_f,
                 "frac": b_f / (filtered["kernel_ms"] / 1000.0) / 1e9 / peak,
                 "edges_per_s": n_edges / (filtered["kernel_ms"] / 1000.0),
-                "speedup_vs_streaming_all": k_avg_ms / filtered["kernel_ms"],
-                "note": "opt-in spatial filter (rgg_set_round_filter): kernel interval = "
-                        "round-filter kernel + classify kernel; bytes recounted as copied"}
+                "headline_speedup": filtered["kernel_ms"] / k_avg_ms,
+                "note": "the same steps with the spatial filter (rgg_set_round_filter) in the "
+                        "state the headline does not use; with the filter the kernel interval "
+                        "holds the round-filter kernel and the bytes are those copied"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -497,7 +513,16 @@ def run_gpu(args):
         "sphere_box_tests_per_s": {
             "logical": world * (info["num_inner"] + info["num_outer"]) * moved
             * args.steps / (ms / 1000.0),
-            "note": "(inner + outer spheres) x moved boxes per update, per second"},
+            "note": "(inner + outer spheres) x moved boxes per update, per second; the "
+                    "kernel culls most of them per warp, see executed_per_launch"},
+        "executed_per_launch": {
+            "rounds": executed["rounds"] / n_cnt,
+            "outer_sphere_box_tests": executed["outer_tests"] / n_cnt,
+            "inner_pairs": executed["inner_pairs"] / n_cnt,
+            "inner_sphere_box_tests_max": executed["inner_pairs"] * info["inner_per_link"] / n_cnt,
+            "logical_sphere_box_tests": (info["num_inner"] + info["num_outer"]) * moved,
+            "note": "from the classify kernel's counting instance over %d further steps; an "
+                    "inner pair is one (configuration, box) pair, up to K sphere tests" % n_cnt},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      # ncu-measured DRAM bytes per launch over the live launch time
@@ -507,15 +532,16 @@ def run_gpu(args):
                      "kernel": "classify_kernel", "bytes_per_launch": b_alg,
                      "kernel_ms": k_avg_ms,
                      "merge_kernel_ms": m_ms / max(1, k_launches)},
-        "round_filter": filt,
+        "round_filter_used": bool(info["round_filter"]),
+        "other_filter_state": filt,
         # label mix after the end-to-end steps (the paper's roadmaps: 0.3-10% gray)
         "labels": {"green": float(np.mean(labels_host == 0)), "gray": float(np.mean(labels_host == 1)),
                    "red": float(np.mean(labels_host == 2))},
         "e2e": {"value": e2e_value, "unit": UNIT,
                 "h2d_bytes_per_step": moved * (4 + 60),
                 "d2h_bytes_per_step": n_edges + 4},
-        # per step: box update, box prep, classify, merge
-        "gpu_launches": 4 * args.steps,
+        # per step: box update, box prep, (round filter,) classify, merge
+        "gpu_launches": (5 if info["round_filter"] else 4) * args.steps,
         "clocks": clk,
         "cpu_baseline": cpu,
     }
@@ -551,8 +577,9 @@ def run_gpu(args):
 def measure_mixed(r, args, stream, peak: float) -> dict:
     """The same roadmap among the mixed-label boxes (256 small boxes spread
     over a 4 m cube, 32 moved per update): every box is placed at its new
-    pose, then K updates are timed like the headline.  The classify kernel's
-    HBM fraction on a scene where green, gray and red edges all occur."""
+    pose, then K updates are timed like the headline, with the library's
+    default configuration and again with the spatial filter in its other
+    state.  The labels must be the same both ways."""
     import torch
     boxes, ups = W.large_mixed_boxes(n_updates=max(8, args.warmup + args.steps))
     dev = [torch.from_numpy(u.poses.astype(np.float32)).to(stream.device) for u in ups]
@@ -563,63 +590,50 @@ def measure_mixed(r, args, stream, peak: float) -> dict:
         r.update_obstacles(ups[i % len(ups)].ids, dev[i % len(ups)], stream)
         r.classify(stream)
 
-    for i in range(args.warmup):
-        step(i)
-    torch.cuda.synchronize()
-    r.set_kernel_timing(True)
-    r.kernel_time()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for i in range(args.steps):
-        step(args.warmup + i)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
-    k_ms, m_ms, n = r.kernel_time()
-    r.set_kernel_timing(False)
-    info = r.info()
-    lab = r.fetch_labels(stream=stream)
-    r.check_status(stream)
-    k_avg = k_ms / max(1, n)
-    b_alg = algorithmic_bytes(info)
-    mix = np.bincount(lab, minlength=3) / max(1, lab.size)
-    out = {"boxes": "256, half-extents U[0.02, 0.06] m, centres in a 4 m cube",
-           "moved_per_update": 32, "steps": args.steps, "ms_per_step": ms / args.steps,
-           "edges_per_s": info["num_edges"] * args.steps / (ms / 1e3),
-           "kernel_ms": k_avg, "merge_kernel_ms": m_ms / max(1, n),
-           "bytes_per_launch": b_alg, "achieved_gbs": b_alg / (k_avg / 1e3) / 1e9,
-           "frac": b_alg / (k_avg / 1e3) / 1e9 / peak,
-           "labels": {"green": float(mix[0]), "gray": float(mix[1]), "red": float(mix[2])}}
-    # the same steps with the opt-in spatial filter: on this scene most
-    # rounds have no moved box near them
-    r.set_round_filter(True)
-    if r.info()["round_filter"]:
-        # the updates of the timed steps again (absolute poses, so the final
-        # state, and the labels, are those of the streaming run)
-        for i in range(min(3, args.steps)):
+    def timed(n_warm):
+        # the updates of the timed steps (absolute poses: the final state,
+        # and the labels, are the same whichever run came first)
+        for i in range(n_warm):
             step(args.warmup + i)
         torch.cuda.synchronize()
         r.set_kernel_timing(True)
         r.kernel_time()
         r.streamed_bytes()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
         for i in range(args.steps):
             step(args.warmup + i)
+        e1.record(stream)
         torch.cuda.synchronize()
-        kf, _, nf = r.kernel_time()
+        k_ms, m_ms, n = r.kernel_time()
         r.set_kernel_timing(False)
-        sf = r.streamed_bytes() / max(1, nf)
-        fi = r.info()
-        lab_f = r.fetch_labels(stream=stream)
-        b_f = algorithmic_bytes(fi, sf)
-        kf_avg = kf / max(1, nf)
-        out["round_filter"] = {
-            "kernel_ms": kf_avg, "record_bytes_per_launch": sf,
-            "records_copied_frac": sf / info["record_bytes"], "bytes_per_launch": b_f,
-            "frac": b_f / (kf_avg / 1e3) / 1e9 / peak,
-            "speedup_vs_streaming_all": k_avg / kf_avg,
-            "labels_identical": bool(np.array_equal(lab_f, lab)),
-            "note": "kernel interval = round-filter kernel + classify kernel"}
-    r.set_round_filter(False)
+        info = r.info()
+        rec = r.streamed_bytes() / max(1, n) if info["round_filter"] else info["record_bytes"]
+        lab = r.fetch_labels(stream=stream)
+        k_avg = k_ms / max(1, n)
+        b_alg = algorithmic_bytes(info, rec)
+        mix = np.bincount(lab, minlength=3) / max(1, lab.size)
+        return {"round_filter": bool(info["round_filter"]), "ms_per_step": e0.elapsed_time(e1) / args.steps,
+                "edges_per_s": info["num_edges"] * args.steps / (e0.elapsed_time(e1) / 1e3),
+                "kernel_ms": k_avg, "merge_kernel_ms": m_ms / max(1, n),
+                "record_bytes_per_launch": rec, "records_copied_frac": rec / info["record_bytes"],
+                "bytes_per_launch": b_alg, "achieved_gbs": b_alg / (k_avg / 1e3) / 1e9,
+                "frac": b_alg / (k_avg / 1e3) / 1e9 / peak,
+                "labels": {"green": float(mix[0]), "gray": float(mix[1]), "red": float(mix[2])}}, lab
+
+    out, lab = timed(args.warmup)
+    out.update({"boxes": "256, half-extents U[0.02, 0.06] m, centres in a 4 m cube",
+                "moved_per_update": 32, "steps": args.steps})
+    default_on = out["round_filter"]
+    r.set_round_filter(not default_on)
+    if r.info()["round_filter"] != default_on:
+        other, lab_o = timed(min(3, args.steps))
+        other["labels_identical"] = bool(np.array_equal(lab_o, lab))
+        other["headline_speedup"] = other["kernel_ms"] / out["kernel_ms"]
+        other["note"] = ("the same steps with the spatial filter in the state the headline "
+                         "does not use")
+        out["other_filter_state"] = other
+    r.set_round_filter(default_on)
     r.check_status(stream)
     return out
 

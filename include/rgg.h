@@ -375,7 +375,8 @@ int rgg_inject_alloc_failure(uint64_t nth);
 /* Device bytes a sphere-geometry roadmap created with `desc` holds once
  * rgg_build_edges(num_edges, q_from, q_to, step) has run: record planes,
  * tile tables of the default launch shape, per-edge state, kept endpoints
- * and the fixed per-roadmap tables, i.e. rgg_roadmap_info's device_bytes
+ * the default spatial filter's round data (link-end records) and the fixed
+ * per-roadmap tables, i.e. rgg_roadmap_info's device_bytes
  * after the build (the first rgg_update_request adds RGG_MAX_REQUESTS x N
  * bytes).  Host-only arithmetic: the configuration counts follow
  * rgg_build_edges' rule; the tile size uses desc->device's SM count (152 if
@@ -393,6 +394,23 @@ int rgg_estimate_bytes(const rgg_roadmap_desc* desc, uint64_t num_edges, const d
  * the events). */
 int rgg_set_kernel_timing(rgg_roadmap_t r, int enable);
 int rgg_kernel_time(rgg_roadmap_t r, double* classify_ms, double* merge_ms, uint64_t* launches);
+
+/* Work counting: while enabled, rgg_classify runs the classify kernel's
+ * counting instance (compiled for the two default launch shapes; other
+ * shapes and rgg_classify_many count nothing), which adds up the work it
+ * executes.  rgg_work_counts returns the totals since the last call (each
+ * pointer may be NULL), waits for the device and resets them:
+ *   rounds       rounds of 31 configurations examined (the spatial filter
+ *                skips the others)
+ *   outer_tests  outer sphere-box tests executed after the warp's bounding-
+ *                sphere cull (the logical count is outer spheres x moved
+ *                boxes)
+ *   inner_pairs  (configuration, box) pairs given the inner test, each up to
+ *                K sphere-box tests
+ * The paper has no counterpart; it measures what the culling saves. */
+int rgg_set_work_counting(rgg_roadmap_t r, int enable);
+int rgg_work_counts(rgg_roadmap_t r, uint64_t* rounds, uint64_t* outer_tests,
+                    uint64_t* inner_pairs);
 
 /* Launch shape of the streaming classify kernel: `variant` picks one of the
  * compiled pipeline shapes (shared-memory ring depth x stage size x rounds of
@@ -476,7 +494,10 @@ int rgg_save(rgg_roadmap_t r, const char* path, void* stream);
 int rgg_load(rgg_roadmap_t r, const char* path, void* stream);
 
 /* Sphere geometry only: the spatial filter (Sec. 4.3, "spatially filtered
- * many-to-many checking", here over the streamed records).  Off by default.
+ * many-to-many checking", here over the streamed records).  By default it is
+ * on for link-end records (where the classify kernel is bound by its work per
+ * round, and skipping rounds no moved box can reach pays) and off for sphere
+ * records; rgg_set_round_filter(r, 0 or 1) overrides the default.
  * While it is on, every round of 31 configurations of a tile
  * (rgg_info.tile_samples configurations per tile) has a bounding sphere of
  * its outer spheres (24 B per round slot, 32 slots per tile, computed when it
@@ -487,8 +508,8 @@ int rgg_load(rgg_roadmap_t r, const char* path, void* stream);
  * reach, and tests only the boxes that may reach each round.  Labels and box
  * sets are the same with and without it (a round no box reaches holds no
  * touch).  It applies with the default launch shape only (rgg_info.
- * round_filter reports whether it is active); on workloads where the moved
- * boxes reach most tiles it is slower than streaming every record.
+ * round_filter reports whether it is active).  Its round data take 24 B per
+ * round slot (32 per tile).
  * rgg_set_round_filter synchronises the device.  RGG_ERR_STATE on an
  * OBB-geometry roadmap.
  * rgg_streamed_bytes returns the record bytes (inner and outer planes, with

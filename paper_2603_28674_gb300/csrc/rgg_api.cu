@@ -200,7 +200,14 @@ void release_rounds(EdgeState* es) {
 // The spatial filter runs with the default pipeline variant only (the one
 // its kernel instance is compiled for).
 bool filter_active(const rgg_roadmap* r) {
-  return r->round_filter && r->es.d_rcand && filter_variant(r->variant);
+  return filter_wanted(r, &r->es) && r->es.d_rcand && filter_variant(r->variant);
+}
+
+// The spatial filter is on by default for link-end records, where the
+// kernel is bound by its per-round work and the filter skips rounds and
+// tiles no moved box can reach, and off for sphere records.
+bool filter_wanted(const rgg_roadmap* r, const EdgeState* es) {
+  return r->round_filter_mode == 1 || (r->round_filter_mode < 0 && es->joints);
 }
 
 // The spatial filter's per-round bounding spheres and outer ranges of the
@@ -208,7 +215,7 @@ bool filter_active(const rgg_roadmap* r) {
 // nothing while the filter is off.
 int compute_rounds(rgg_roadmap* r, EdgeState* es, cudaStream_t s) {
   release_rounds(es);
-  if (!r->round_filter || r->geometry != RGG_GEOMETRY_SPHERES || es->T == 0) return RGG_OK;
+  if (!filter_wanted(r, es) || r->geometry != RGG_GEOMETRY_SPHERES || es->T == 0) return RGG_OK;
   const uint64_t n = es->T * kRoundSlots;
   cudaError_t e = dalloc(&es->d_rsph, n);
   if (e == cudaSuccess) e = dalloc(&es->d_rout, n);
@@ -653,6 +660,7 @@ int classify_group(rgg_roadmap_t* rs, uint32_t n, cudaStream_t s) {
       cp1.total_tiles = tiles;
       cp1.status = r0->d_status;
       cp1.wait_ns = r0->wait_ns;
+      cp1.work = r0->counting ? r0->d_count : nullptr;
       RGG_CK(launch_classify_single(cp1, lc, s));
     } else {
       cpp->njobs = nj;
@@ -765,6 +773,8 @@ int rgg_roadmap_create(const rgg_roadmap_desc* desc, rgg_roadmap_t* out) {
   if (e == cudaSuccess) e = cudaMemset(r->d_changed, 0, (size_t)kBoxAreaFloats * sizeof(float));
   if (e == cudaSuccess) e = dalloc(&r->d_status, 4);
   if (e == cudaSuccess) e = dalloc(&r->d_work, 4);
+  if (e == cudaSuccess) e = dalloc(&r->d_count, 3);
+  if (e == cudaSuccess) e = cudaMemset(r->d_count, 0, 3 * sizeof(unsigned long long));
   if (e == cudaSuccess) e = dalloc(&r->d_obbwork, 2);
   if (e == cudaSuccess) e = dalloc(&r->d_streamed, 1);
   if (e == cudaSuccess) e = cudaMemset(r->d_obbwork, 0, 2 * sizeof(unsigned long long));
@@ -777,6 +787,7 @@ int rgg_roadmap_create(const rgg_roadmap_desc* desc, rgg_roadmap_t* out) {
     cudaFree(r->d_changed);
     cudaFree(r->d_status);
     cudaFree(r->d_work);
+    cudaFree(r->d_count);
     cudaFree(r->d_obbwork);
     cudaFree(r->d_streamed);
     delete r;
@@ -796,6 +807,7 @@ int rgg_roadmap_destroy(rgg_roadmap_t r) {
   cudaFree(r->d_changed);
   cudaFree(r->d_status);
   cudaFree(r->d_work);
+  cudaFree(r->d_count);
   cudaFree(r->d_obbwork);
   cudaFree(r->d_streamed);
   for (auto& ev : r->events)
@@ -1224,19 +1236,28 @@ int rgg_roadmap_info(rgg_roadmap_t r, rgg_info* out) {
 int rgg_set_round_filter(rgg_roadmap_t r, int enable) {
   if (!r) return RGG_ERR_INVALID;
   if (r->geometry != RGG_GEOMETRY_SPHERES) return RGG_ERR_STATE;
-  const bool on = enable != 0;
-  if (on == r->round_filter) return RGG_OK;
+  const int mode = enable ? 1 : 0;
+  const bool was = filter_wanted(r, &r->es);
+  const int old_mode = r->round_filter_mode;
+  r->round_filter_mode = mode;
+  if (filter_wanted(r, &r->es) == was) return RGG_OK;
   DeviceGuard g(r->device);
-  if (!g.ok) return RGG_ERR_CUDA;
-  RGG_CK(cudaDeviceSynchronize());  // no launch may still read the round data
-  ++r->gen;                         // captured step graphs hold the old jobs
-  r->round_filter = on;
+  if (!g.ok) {
+    r->round_filter_mode = old_mode;
+    return RGG_ERR_CUDA;
+  }
+  if (cudaDeviceSynchronize() != cudaSuccess) {  // no launch may still read the round data
+    cudaGetLastError();
+    r->round_filter_mode = old_mode;
+    return RGG_ERR_CUDA;
+  }
+  ++r->gen;                                    // captured step graphs hold the old jobs
   // the round data exist while the filter is on (computed from the records)
-  int rc = on ? compute_rounds(r, &r->es, nullptr) : (release_rounds(&r->es), RGG_OK);
+  int rc = mode ? compute_rounds(r, &r->es, nullptr) : (release_rounds(&r->es), RGG_OK);
   if (cudaDeviceSynchronize() != cudaSuccess && rc == RGG_OK) rc = RGG_ERR_CUDA;
   if (rc != RGG_OK) {
     release_rounds(&r->es);
-    r->round_filter = false;
+    r->round_filter_mode = 0;
   }
   return rc;
 }
@@ -1258,6 +1279,27 @@ int rgg_check_status(rgg_roadmap_t r, void* stream) {
   DeviceGuard g(r->device);
   if (!g.ok) return RGG_ERR_CUDA;
   return check_status_locked(r, static_cast<cudaStream_t>(stream));
+}
+
+int rgg_set_work_counting(rgg_roadmap_t r, int enable) {
+  if (!r) return RGG_ERR_INVALID;
+  r->counting = enable != 0;
+  return RGG_OK;
+}
+
+int rgg_work_counts(rgg_roadmap_t r, uint64_t* rounds, uint64_t* outer_tests,
+                    uint64_t* inner_pairs) {
+  if (!r) return RGG_ERR_INVALID;
+  DeviceGuard g(r->device);
+  if (!g.ok) return RGG_ERR_CUDA;
+  unsigned long long v[3] = {0, 0, 0};
+  RGG_CK(cudaDeviceSynchronize());
+  RGG_CK(cudaMemcpy(v, r->d_count, sizeof(v), cudaMemcpyDeviceToHost));
+  RGG_CK(cudaMemset(r->d_count, 0, sizeof(v)));
+  if (rounds) *rounds = v[0];
+  if (outer_tests) *outer_tests = v[1];
+  if (inner_pairs) *inner_pairs = v[2];
+  return RGG_OK;
 }
 
 int rgg_set_wait_limit(rgg_roadmap_t r, uint64_t limit_ns) {
@@ -1317,8 +1359,12 @@ int rgg_estimate_bytes(const rgg_roadmap_desc* desc, uint64_t num_edges, const d
     std::vector<TileDesc> tiles;
     std::vector<int4> etab;
     if (!build_tiles(L, N, soff, G, t.S, &tiles, &etab)) return RGG_ERR_INVALID;
+    // link-end records also keep the spatial filter's round data (on by
+    // default for them): a bounding sphere, an outer range and a candidate
+    // mask per round slot
     tile_bytes = tiles.size() * (sizeof(TileDesc) + (joints ? sizeof(uint32_t) : 0)) +
-                 etab.size() * sizeof(int4);
+                 etab.size() * sizeof(int4) +
+                 (joints ? tiles.size() * kRoundSlots * (sizeof(float4) + 2 * sizeof(uint32_t)) : 0);
   }
   const uint64_t n_in = joints ? G : (uint64_t)K * G, n_out = (uint64_t)L * (S - N);
   const uint64_t in_stride = ((n_in + 4 + 63) / 64) * 64, out_stride = ((n_out + 4 + 63) / 64) * 64;

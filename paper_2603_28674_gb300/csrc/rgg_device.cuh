@@ -116,6 +116,7 @@ struct ClassifyParams {
   uint32_t njobs;
   uint64_t total_tiles;
   int* status;                      // device status word of the launch (0 = ok)
+  unsigned long long* work = nullptr;  // [3] work counters (counting launches only)
   uint64_t wait_ns = 4000000000ull; // limit of every bounded wait, ns of wall time
 };
 

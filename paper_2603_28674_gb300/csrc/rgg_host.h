@@ -199,13 +199,17 @@ struct rgg_roadmap {
   uint64_t gen = 0;            // bumped whenever tiles or edges are replaced
   uint32_t geometry = RGG_GEOMETRY_SPHERES;
   bool obb_filter = true;      // spatial grid filtering of the OBB queries
-  bool round_filter = false;   // spatial filtering of the sphere records (opt-in)
+  // spatial filtering of the sphere geometry's records: -1 the default (on
+  // for link-end records, off for sphere records), 0 off, 1 on
+  int round_filter_mode = -1;
   unsigned long long* d_streamed = nullptr;  // [1] record bytes the classify launches copied
   unsigned long long* d_obbwork = nullptr;  // [2] SAT tests, spline-segment tests
   // the robot of edges built by rgg_build_edges (for the gray resolution)
   bool has_robot = false;
   double dh_a[RGG_MAX_LINKS], dh_alpha[RGG_MAX_LINKS], dh_d[RGG_MAX_LINKS], dh_radius[RGG_MAX_LINKS];
   unsigned long long* d_work = nullptr;  // [4] resolution counters
+  unsigned long long* d_count = nullptr; // [3] classify work counters (rgg_work_counts)
+  bool counting = false;
   EdgeState es;
   float* d_table = nullptr;    // [M][16] box poses
   float* d_stage = nullptr;    // [stage_rows][16] staged pose of each pending entry
@@ -267,6 +271,7 @@ int install_edges(rgg_roadmap* r, EdgeState&& es, cudaStream_t s);
 void release_rounds(EdgeState* es);
 int compute_rounds(rgg_roadmap* r, EdgeState* es, cudaStream_t s);
 bool filter_active(const rgg_roadmap* r);
+bool filter_wanted(const rgg_roadmap* r, const EdgeState* es);
 bool valid_soff(const uint64_t* soff, uint64_t N, uint32_t L);
 bool finite_planes(const float* p, uint64_t count, bool radius_plane);
 bool regular_inner(const float* inner, uint64_t n_in, uint32_t K);

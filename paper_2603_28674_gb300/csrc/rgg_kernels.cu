@@ -703,7 +703,9 @@ __device__ __forceinline__ void fill_slot(const ClassifyParams<MAXJ>& P, uint32_
 // FILTER: the instance that serves spatially filtered jobs (tiles skipped,
 // rounds copied in runs, per-round candidate masks); without it the jobs'
 // filter fields are ignored and every tile is copied whole.
-template <int MAXJ, int NSTAGE, int STAGE_BYTES, int ROUNDS, int RPI, bool FILTER>
+// COUNT: the instance that also counts the work it executes (rounds, outer
+// sphere-box tests, inner (sample, box) pairs) into P.work.
+template <int MAXJ, int NSTAGE, int STAGE_BYTES, int ROUNDS, int RPI, bool FILTER, bool COUNT = false>
 __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const __grid_constant__ ClassifyParams<MAXJ> P) {
   static_assert(ROUNDS < kRoundSlots, "rounds per tile");
   // Shared-memory carve-up, by integer offsets from the __shared__ base so that
@@ -786,6 +788,7 @@ __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const 
 
   // ------------------------------------------------------------- workers
   uint32_t* queue = queues + (size_t)warp * kPairQueue;
+  unsigned long long n_rounds = 0, n_outer = 0, n_pairs = 0;  // COUNT instance only
   bool run = true;
   {
     int ok = 1;
@@ -855,6 +858,7 @@ __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const 
         if (J.rcand) rc = s_cand[stage * kRoundSlots + rnd];
         if (rc == 0u) continue;
       }
+      if constexpr (COUNT) ++n_rounds;
       const int q = base - 1 + lane;
       const SampleAt at = locate_sample(etab, n_edges, q, min(base + 31, n_samp));
       const int j = at.j, n = at.n, k = at.k, o = at.o, li = at.li;
@@ -900,6 +904,7 @@ __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const 
         }
         if (!has_next) bits = 0;
         if (bits) atomicOr(&acc_touch[j], bits);
+        if constexpr (COUNT) n_outer += (unsigned long long)__popc(any_cand) * __popc(act);
       }
       // no moved box near the round: nothing touched, so no inner test either
       if (!any_cand) continue;
@@ -925,6 +930,7 @@ __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const 
         if (lane >= d) incl += v;
       }
       const int total = __shfl_sync(0xffffffffu, incl, 31);
+      if constexpr (COUNT) n_pairs += (unsigned long long)total;
       // a (sample, box) pair packs the box (bits 0..4), the edge-table entry
       // (5..12), the local sample (13..26) and its link (27..31)
       if ((J.regular || joints) && total > 0) {
@@ -1068,6 +1074,11 @@ __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const 
         if (tv[c]) atomicOr(&J.edge_acc[2 * e + 1], tv[c]);
       }
     }
+  }
+  if (COUNT && lane == 0 && P.work) {
+    atomicAdd(&P.work[0], n_rounds);
+    atomicAdd(&P.work[1], n_outer);
+    atomicAdd(&P.work[2], n_pairs);
   }
   // Before the CTA exits, no bulk copy of it may still be in flight.  Every
   // warp has stopped issuing once all are here; then one thread waits
@@ -1458,10 +1469,10 @@ size_t classify_smem_bytes(int variant, uint32_t consumer_warps) {
   }
 }
 
-template <int MAXJ, int NSTAGE, int STAGE_BYTES, int ROUNDS, int RPI, bool FILTER>
+template <int MAXJ, int NSTAGE, int STAGE_BYTES, int ROUNDS, int RPI, bool FILTER, bool COUNT = false>
 static cudaError_t launch_classify_v(const ClassifyParams<MAXJ>& p, const ClassifyLaunch& lc,
                                      cudaStream_t s) {
-  auto kern = classify_kernel<MAXJ, NSTAGE, STAGE_BYTES, ROUNDS, RPI, FILTER>;
+  auto kern = classify_kernel<MAXJ, NSTAGE, STAGE_BYTES, ROUNDS, RPI, FILTER, COUNT>;
   const size_t smem = smem_bytes_t<MAXJ, NSTAGE, STAGE_BYTES, (ROUNDS + RPI - 1) / RPI, FILTER>(lc.consumer_warps);
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
@@ -1474,6 +1485,14 @@ template <int MAXJ, int ID, int NS, int SB, int RD, int RPI>
 static cudaError_t launch_variant(const ClassifyParams<MAXJ>& p, const ClassifyLaunch& lc,
                                   bool filtered, cudaStream_t s) {
   if constexpr (filter_variant(ID)) {
+    // the counting instances exist for single-roadmap launches of the
+    // default shapes
+    if constexpr (MAXJ == 1) {
+      if (p.work) {
+        if (filtered) return launch_classify_v<MAXJ, NS, SB, RD, RPI, true, true>(p, lc, s);
+        return launch_classify_v<MAXJ, NS, SB, RD, RPI, false, true>(p, lc, s);
+      }
+    }
     if (filtered) return launch_classify_v<MAXJ, NS, SB, RD, RPI, true>(p, lc, s);
   } else {
     if (filtered) return cudaErrorInvalidValue;

@@ -45,6 +45,7 @@ EXPORTS = (
     "rgg_step_graph_destroy", "rgg_save", "rgg_load", "rgg_resolve_gray", "rgg_fetch_boxes",
     "rgg_set_obb_filter", "rgg_obb_work", "rgg_fetch_obb_records", "rgg_set_round_filter",
     "rgg_streamed_bytes", "rgg_set_wait_limit", "rgg_inject_alloc_failure", "rgg_estimate_bytes",
+    "rgg_set_work_counting", "rgg_work_counts",
 )
 
 
@@ -161,6 +162,8 @@ def _lib():
         "rgg_fetch_obb_records": [vp, vp, vp, vp],
         "rgg_load": [vp, ctypes.c_char_p, vp],
         "rgg_set_wait_limit": [vp, u64],
+        "rgg_set_work_counting": [vp, i32],
+        "rgg_work_counts": [vp, ctypes.POINTER(u64), ctypes.POINTER(u64), ctypes.POINTER(u64)],
         "rgg_inject_alloc_failure": [u64],
         "rgg_estimate_bytes": [ctypes.POINTER(_Desc), u64, vp, vp, dbl, ctypes.POINTER(u64)],
     }
@@ -400,6 +403,18 @@ class Roadmap:
 
     def check_status(self, stream=None) -> None:
         _check("rgg_check_status", _lib().rgg_check_status(self._h, _stream(stream, self.device)))
+
+    def set_work_counting(self, enable: bool) -> None:
+        """Count the classify kernel's executed work (rgg_set_work_counting)."""
+        _check("rgg_set_work_counting", _lib().rgg_set_work_counting(self._h, int(enable)))
+
+    def work_counts(self) -> dict:
+        """Rounds examined, outer sphere-box tests and inner (configuration,
+        box) pairs executed since the last call (rgg_work_counts)."""
+        a, b, c = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+        _check("rgg_work_counts", _lib().rgg_work_counts(self._h, ctypes.byref(a), ctypes.byref(b),
+                                                         ctypes.byref(c)))
+        return {"rounds": int(a.value), "outer_tests": int(b.value), "inner_pairs": int(c.value)}
 
     def set_wait_limit(self, limit_ns: int) -> None:
         """Limit of the classify kernel's bounded waits, ns (rgg_set_wait_limit)."""

@@ -451,3 +451,36 @@ def test_fetch_boxes_returns_the_table(rgg):
         want[up.ids] = f32(up.poses)
         assert present.all()
         np.testing.assert_array_equal(poses, want)
+
+
+def test_work_counting_changes_no_bit(rgg):
+    """The counting instance makes the same decisions and counts what it
+    executed: rounds, outer tests after the cull, inner pairs."""
+    sc = W.workload_7dof(n_nodes=400, n_updates=2)
+    rm = sc.roadmap
+    a = make_roadmap(rgg, rm, sc.boxes.count)
+    b = make_roadmap(rgg, rm, sc.boxes.count)
+    b.set_work_counting(True)
+    for r in (a, b):
+        r.update_obstacles(np.arange(sc.boxes.count), f32(sc.boxes.poses()))
+        r.classify()
+    for up in sc.updates:
+        for r in (a, b):
+            r.update_obstacles(up.ids, f32(up.poses))
+            r.classify()
+    np.testing.assert_array_equal(a.fetch_labels(), b.fetch_labels())
+    ha, ta = a.fetch_box_sets()
+    hb, tb = b.fetch_box_sets()
+    np.testing.assert_array_equal(ha, hb)
+    np.testing.assert_array_equal(ta, tb)
+    c = b.work_counts()
+    info = b.info()
+    assert 0 < c["rounds"] <= 4 * info["num_tiles"] * 32
+    assert 0 < c["outer_tests"]
+    assert c["outer_tests"] < 4 * info["num_outer"] * 32    # the cull leaves a fraction
+    assert 0 < c["inner_pairs"]
+    assert b.work_counts() == {"rounds": 0, "outer_tests": 0, "inner_pairs": 0}
+    assert a.work_counts()["rounds"] == 0                  # not counting
+    for r in (a, b):
+        r.check_status()
+        r.close()

@@ -74,9 +74,12 @@ def test_memory_estimate_covers_the_records(built):
                          (rgg.RECORDS_SPHERES, 16 * (K * L * S + L * (S - N)))):
         est = rgg.estimate_bytes(L, K, sc.boxes.count, rm.q_from, rm.q_to, rm.step,
                                  record_format=fmt)
-        # per edge at least the offsets, box sets, counts, label, pass bits and endpoints
+        # per edge at least the offsets, box sets, counts, label, pass bits and endpoints;
+        # link-end records also hold the spatial filter's round data, 24 B per
+        # round slot, 32 slots per tile of at least 31 configurations
+        rounds = 24 * 32 * (L * S // 31 + 1) if fmt == rgg.RECORDS_LINK_ENDS else 0
         assert est >= records + N * (8 + 8 + 4 + 1 + 8 + 16 * L)
-        assert est <= records + N * (64 + 16 * L) + (1 << 20)
+        assert est <= records + N * (64 + 16 * L) + rounds + (1 << 20)
     est = rgg.estimate_bytes(L, K, sc.boxes.count, rm.q_from, rm.q_to, rm.step)
     assert roadmap_bytes(L, K, sc.boxes.count, rm.q_from, rm.q_to, rm.step) == est + 64 * N
     # a margin below 1e-5 m keeps sphere records
