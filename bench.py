@@ -230,20 +230,22 @@ class ClockSampler:
 
 
 ROUND_SLOT_BYTES = 16 + 4 + 4 + 4   # per (tile, round) slot: sphere, candidates written + read, range
+TILE_LIST_BYTES = 4 + 4             # per tile: its entry in the pass's tile list, written and read
 
 
 def algorithmic_bytes(info: dict, record_bytes_per_launch=None) -> int:
-    """Bytes one classify launch must move: the sphere records it copies
-    (unfiltered: every record once, 16 B per inner and outer sphere;
-    with the spatial filter: the rounds some moved box may reach, as counted
-    on the device), each edge's pass result (hit and touch words, 8 B) and,
+    """Bytes one classify launch must move: the records it copies
+    (unfiltered: every record once, 12 B per link end or 16 B per inner
+    sphere, 16 B per outer sphere; with the spatial filter: the rounds some
+    moved box may reach, as counted on the device), each edge's pass result (hit and touch words, 8 B) and,
     with the filter, its per-round data (bounding sphere read, candidate
-    mask written and read, record range read).  Tile descriptors, edge
-    tables and the moved boxes' records are overhead and not counted."""
+    mask written and read, record range read) and its tile list.  Tile
+    descriptors, edge tables and the moved boxes' records are overhead and
+    not counted."""
     if record_bytes_per_launch is None or not info.get("round_filter"):
         return info["record_bytes"] + 8 * info["num_edges"]
     return (int(record_bytes_per_launch) + 8 * info["num_edges"]
-            + ROUND_SLOT_BYTES * 32 * info["num_tiles"])
+            + (ROUND_SLOT_BYTES * 32 + TILE_LIST_BYTES) * info["num_tiles"])
 
 
 # --------------------------------------------------------------------------

@@ -187,14 +187,23 @@ int set_tiles(rgg_roadmap* r, EdgeState* es, cudaStream_t s) {
   return RGG_OK;
 }
 
+// Bytes of the spatial filter's data for T tiles: per round slot a bounding
+// sphere, an outer range and a candidate mask; per tile a list entry; the
+// list's count.
+uint64_t round_data_bytes(uint64_t T) {
+  return T * kRoundSlots * (sizeof(float4) + 2 * sizeof(uint32_t)) + (T + 1) * sizeof(uint32_t);
+}
+
 void release_rounds(EdgeState* es) {
-  if (es->d_rsph) es->device_bytes -= es->T * kRoundSlots * (sizeof(float4) + 2 * sizeof(uint32_t));
+  if (es->d_rsph) es->device_bytes -= round_data_bytes(es->T);
   cudaFree(es->d_rsph);
   cudaFree(es->d_rout);
   cudaFree(es->d_rcand);
+  cudaFree(es->d_tlist);
   es->d_rsph = nullptr;
   es->d_rout = nullptr;
   es->d_rcand = nullptr;
+  es->d_tlist = nullptr;
 }
 
 // The spatial filter runs with the default pipeline variant only (the one
@@ -220,16 +229,22 @@ int compute_rounds(rgg_roadmap* r, EdgeState* es, cudaStream_t s) {
   cudaError_t e = dalloc(&es->d_rsph, n);
   if (e == cudaSuccess) e = dalloc(&es->d_rout, n);
   if (e == cudaSuccess) e = dalloc(&es->d_rcand, n);
+  // the per-pass tile list and its count, zeroed so that no entry is ever
+  // outside the tile table
+  if (e == cudaSuccess) e = dalloc(&es->d_tlist, es->T + 1);
+  if (e == cudaSuccess) e = cudaMemsetAsync(es->d_tlist, 0, (es->T + 1) * sizeof(uint32_t), s);
   if (e != cudaSuccess) {
     cudaFree(es->d_rsph);
     cudaFree(es->d_rout);
     cudaFree(es->d_rcand);
+    cudaFree(es->d_tlist);
     es->d_rsph = nullptr;
     es->d_rout = nullptr;
     es->d_rcand = nullptr;
+    es->d_tlist = nullptr;
     return cuda_status(e);
   }
-  es->device_bytes += n * (sizeof(float4) + 2 * sizeof(uint32_t));
+  es->device_bytes += round_data_bytes(es->T);
   RoundBoundsParams p;
   p.outer = es->d_outer;
   p.out_stride = es->out_stride;
@@ -466,6 +481,8 @@ ClassifyJob make_job(rgg_roadmap* r, uint32_t C, uint64_t tile_base) {
     j.rsph = es.d_rsph;
     j.rout = es.d_rout;
     j.rcand = es.d_rcand;
+    j.tlist = es.d_tlist;
+    j.tcount = es.d_tlist + es.T;
   }
   j.streamed = r->d_streamed;
   j.status = r->d_status;
@@ -625,6 +642,7 @@ int classify_group(rgg_roadmap_t* rs, uint32_t n, cudaStream_t s) {
       BoxPrepJob& pj = bp.job[bp.njobs++];
       pj.stage = r->d_stage;
       pj.out = r->d_changed;
+      pj.tcount = filter_active(r) ? r->es.d_tlist + r->es.T : nullptr;
       pj.C = C;
       for (uint32_t b = 0; b < C; ++b) {
         pj.ids[b] = r->pending[lo + b].id;
@@ -1360,11 +1378,9 @@ int rgg_estimate_bytes(const rgg_roadmap_desc* desc, uint64_t num_edges, const d
     std::vector<int4> etab;
     if (!build_tiles(L, N, soff, G, t.S, &tiles, &etab)) return RGG_ERR_INVALID;
     // link-end records also keep the spatial filter's round data (on by
-    // default for them): a bounding sphere, an outer range and a candidate
-    // mask per round slot
+    // default for them)
     tile_bytes = tiles.size() * (sizeof(TileDesc) + (joints ? sizeof(uint32_t) : 0)) +
-                 etab.size() * sizeof(int4) +
-                 (joints ? tiles.size() * kRoundSlots * (sizeof(float4) + 2 * sizeof(uint32_t)) : 0);
+                 etab.size() * sizeof(int4) + (joints ? round_data_bytes(tiles.size()) : 0);
   }
   const uint64_t n_in = joints ? G : (uint64_t)K * G, n_out = (uint64_t)L * (S - N);
   const uint64_t in_stride = ((n_in + 4 + 63) / 64) * 64, out_stride = ((n_out + 4 + 63) / 64) * 64;

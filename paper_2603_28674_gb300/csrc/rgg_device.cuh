@@ -106,6 +106,12 @@ struct ClassifyJob {
   const float4* rsph;               // [T][kRoundSlots] bounding sphere (radius < 0: empty)
   const uint32_t* rout;             // [T][kRoundSlots] outer records lo | hi << 16, tile-local
   uint32_t* rcand;                  // [T][kRoundSlots] moved boxes that may reach the round
+  // the pass's tiles that some moved box may reach: local tile indices in no
+  // particular order, appended by the filter kernel, and their count (zeroed
+  // by the box-prep kernel at the start of each pass).  With a list the
+  // classify kernel's ring slots take only these tiles.  Null: every tile.
+  uint32_t* tlist = nullptr;        // [T]
+  uint32_t* tcount = nullptr;
   unsigned long long* streamed;     // record bytes copied (may be null)
   const int* status = nullptr;      // the roadmap's own status word (may be null)
 };

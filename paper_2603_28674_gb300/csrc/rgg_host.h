@@ -145,6 +145,7 @@ struct EdgeState {
   float4* d_rsph = nullptr;
   uint32_t* d_rout = nullptr;
   uint32_t* d_rcand = nullptr;
+  uint32_t* d_tlist = nullptr;   // [T] this pass's listed tiles, then their count
   uint64_t device_bytes = 0;
   bool regular = false;        // inner spheres equally spaced with one radius per sample
   // link-end records (3 planes, see rgg_device.cuh) instead of inner spheres,
@@ -179,6 +180,7 @@ struct EdgeState {
     cudaFree(d_rsph);
     cudaFree(d_rout);
     cudaFree(d_rcand);
+    cudaFree(d_tlist);
     cudaFree(d_tile_halo);
     *this = EdgeState();
   }
@@ -268,6 +270,7 @@ void clear_pending(rgg_roadmap* r);
 int requeue_present(rgg_roadmap* r, cudaStream_t s);
 uint64_t fixed_device_bytes(const rgg_roadmap* r);
 int install_edges(rgg_roadmap* r, EdgeState&& es, cudaStream_t s);
+uint64_t round_data_bytes(uint64_t T);
 void release_rounds(EdgeState* es);
 int compute_rounds(rgg_roadmap* r, EdgeState* es, cudaStream_t s);
 bool filter_active(const rgg_roadmap* r);

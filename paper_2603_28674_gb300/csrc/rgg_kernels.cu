@@ -191,6 +191,7 @@ __global__ void box_update_kernel(const __grid_constant__ BoxUpdateParams p) {
 __global__ void box_prep_kernel(const __grid_constant__ BoxPrepParams p) {
   const BoxPrepJob& J = p.job[blockIdx.x];
   const uint32_t b = threadIdx.x;
+  if (b == 0 && J.tcount) *J.tcount = 0u;
   if (b >= J.C) return;
   const uint32_t id = J.ids[b];
   const float* row = J.stage + 16 * (size_t)J.rows[b];
@@ -222,20 +223,20 @@ __global__ void box_prep_kernel(const __grid_constant__ BoxPrepParams p) {
 // ===========================================================================
 // a2..a5: persistent streaming classification
 // ===========================================================================
-// One CTA per SM.  Warp 0 is the producer: it takes chunks of tiles from a
-// launch-wide counter and, for each tile, bulk-copies the tile's edge table
-// and its 4 inner and 4 outer record planes into the next slot of an
-// NSTAGE-deep ring of shared-memory stages (TMA bulk copies completing on
-// the slot's `full` mbarrier).  Every other warp is a consumer that takes
-// work items, rounds of 31 configurations, from a shared counter (no
-// CTA-wide barriers): it tests its round's outer spheres against the pass's
-// moved boxes (a3) and the inner spheres against the boxes their enclosing
-// outer spheres touched (a4), into per-stage accumulators.  The warp that
-// finishes a tile's last round releases the slot and ORs the tile's
-// per-edge hit / touch bits into the global per-edge accumulators (a5).  The
+// One CTA per SM, every warp a worker.  A CTA's shared memory holds an
+// NSTAGE-deep ring of stages; each stage holds one tile: its edge table and
+// its record planes, brought in by TMA bulk copies that complete on the
+// stage's `full` mbarriers.  Warps take work items (RPI rounds of 31
+// configurations of a tile) from a shared counter, with no CTA-wide barrier:
+// a round tests its outer spheres against the pass's moved boxes (a3) and
+// the inner spheres against the boxes their enclosing outer spheres touched
+// (a4), into per-stage accumulators.  The warp that finishes a tile's last
+// item ORs the tile's per-edge hit / touch bits into the global per-edge
+// accumulators (a5) and refills the stage with the CTA's next tile.  The
 // merge kernel then updates the per-edge box sets and labels (a6).  The
-// FILTER instance serves the opt-in spatial filter: it skips tiles and
-// rounds that no moved box can reach.
+// FILTER instance serves the spatial filter: its ring takes only the tiles
+// the filter kernel listed, and it copies and tests only the rounds some
+// moved box may reach, against those boxes.
 __device__ __forceinline__ float box_dist2(float x, float y, float z, const float4* __restrict__ B) {
   const float4 a0 = B[1], a1 = B[2], a2 = B[3], h = B[4];
   const float p0 = fmaf(a0.x, x, fmaf(a0.y, y, fmaf(a0.z, z, -a0.w)));
@@ -453,42 +454,70 @@ __global__ void __launch_bounds__(256) round_bounds_kernel(const __grid_constant
 // from the round's bounding sphere centre is within its radius plus the
 // margin.  Any outer sphere of the round lies inside the bounding sphere, so
 // a box that touches one of them (distance <= r + margin) passes this test;
-// the slack covers FP32 rounding in both tests.  One warp per tile, one lane
-// per round.  Each warp stages its roadmap's box records in shared memory,
+// the slack covers FP32 rounding in both tests.  One warp per 32 consecutive
+// tiles, taken one after the other, one lane per round.  The warp stages its
+// roadmap's box records in shared memory (again when the roadmap changes),
 // and a box whose bounding sphere is out of reach skips the exact distance.
+// The tiles with a round to test are appended to their roadmap's tile list,
+// one atomic per roadmap and warp; the list's order is arbitrary.
 template <int MAXJ>
 __global__ void __launch_bounds__(256) round_filter_kernel(const __grid_constant__ ClassifyParams<MAXJ> P) {
   __shared__ float4 s_bx[8][kBoxesPerPass * 6];
-  const uint64_t t = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  if (t >= P.total_tiles) return;  // whole warps: t is the same on every lane
-  const ClassifyJob& J = P.job[MAXJ == 1 ? 0 : find_job(P, t)];
-  if (J.rcand == nullptr) return;
+  const uint64_t t0 = (((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32;
+  if (t0 >= P.total_tiles) return;  // whole warps: t0 is the same on every lane
   float4* bx = s_bx[threadIdx.x >> 5];
-  const int C = (int)J.C;
-  if (lane < C)
-    for (int c = 0; c < 6; ++c) bx[6 * lane + c] = reinterpret_cast<const float4*>(J.boxes)[6 * lane + c];
-  __syncwarp();
-  const uint64_t slot = (t - J.tile_base) * kRoundSlots + lane;
-  uint32_t m = 0;
-  if (lane < kRoundSlots - 1) {
-    const float4 sph = J.rsph[slot];
-    if (sph.w >= 0.0f) {
-      const float thr = (sph.w + J.margin) * (1.0f + 1e-6f) + 1e-5f;
-      const float thr2 = thr * thr;
-      for (int b = 0; b < C; ++b) {
-        const float4 b0 = bx[6 * b];
-        const float ex = sph.x - b0.x, ey = sph.y - b0.y, ez = sph.z - b0.z;
-        const float reach = thr + b0.w;  // the box lies in the sphere of radius |h|
-        if (fmaf(ex, ex, fmaf(ey, ey, ez * ez)) > reach * reach * (1.0f + 1e-6f)) continue;
-        if (box_dist2(sph.x, sph.y, sph.z, bx + 6 * b) <= thr2) m |= 1u << b;
+  const int nt = (int)min((uint64_t)32, P.total_tiles - t0);
+  int staged = -1;
+  bool listed = false;  // lane i: tile t0 + i goes on its roadmap's list
+  for (int i = 0; i < nt; ++i) {
+    const uint64_t t = t0 + (uint64_t)i;
+    const int jb = MAXJ == 1 ? 0 : find_job(P, t);
+    const ClassifyJob& J = P.job[jb];
+    if (J.rcand == nullptr) continue;
+    const int C = (int)J.C;
+    if (jb != staged) {
+      __syncwarp();
+      if (lane < C)
+        for (int c = 0; c < 6; ++c) bx[6 * lane + c] = reinterpret_cast<const float4*>(J.boxes)[6 * lane + c];
+      __syncwarp();
+      staged = jb;
+    }
+    const uint64_t slot = (t - J.tile_base) * kRoundSlots + lane;
+    uint32_t m = 0;
+    if (lane < kRoundSlots - 1) {
+      const float4 sph = J.rsph[slot];
+      if (sph.w >= 0.0f) {
+        const float thr = (sph.w + J.margin) * (1.0f + 1e-6f) + 1e-5f;
+        const float thr2 = thr * thr;
+        for (int b = 0; b < C; ++b) {
+          const float4 b0 = bx[6 * b];
+          const float ex = sph.x - b0.x, ey = sph.y - b0.y, ez = sph.z - b0.z;
+          const float reach = thr + b0.w;  // the box lies in the sphere of radius |h|
+          if (fmaf(ex, ex, fmaf(ey, ey, ez * ez)) > reach * reach * (1.0f + 1e-6f)) continue;
+          if (box_dist2(sph.x, sph.y, sph.z, bx + 6 * b) <= thr2) m |= 1u << b;
+        }
       }
     }
+    // the last slot (never a round: tiles have at most 31 rounds) holds the
+    // tile's rounds that some box may reach
+    const uint32_t need = __ballot_sync(0xffffffffu, m != 0u);
+    J.rcand[slot] = lane == kRoundSlots - 1 ? need : m;
+    if (lane == i && need != 0u && J.tlist != nullptr) listed = true;
   }
-  // the last slot (never a round: tiles have at most 31 rounds) holds the
-  // tile's rounds that some box may reach
-  const uint32_t need = __ballot_sync(0xffffffffu, m != 0u);
-  J.rcand[slot] = lane == kRoundSlots - 1 ? need : m;
+  // the listed tiles, grouped by roadmap: one atomic per group
+  const int jl = (listed && MAXJ != 1) ? find_job(P, t0 + (uint64_t)lane) : 0;
+  const uint32_t peers = __match_any_sync(0xffffffffu, listed ? jl : -1);
+  const int leader = __ffs(peers) - 1;
+  uint32_t base = 0;
+  if (listed && lane == leader) base = atomicAdd(P.job[jl].tcount, (uint32_t)__popc(peers));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  if (listed) {
+    // bounded by the list's size whatever the count holds
+    const ClassifyJob& J = P.job[jl];
+    const uint32_t at = base + __popc(peers & ((1u << lane) - 1u));
+    if (at < J.num_tiles) J.tlist[at] = (uint32_t)(t0 + (uint64_t)lane - J.tile_base);
+  }
 }
 
 // Bound of the producer's final wait for its own bulk copies before the CTA
@@ -537,12 +566,13 @@ template <int MAXJ, int NSTAGE, int STAGE_BYTES, int NBAR, bool FILTER>
 __device__ __forceinline__ void fill_slot(const ClassifyParams<MAXJ>& P, uint32_t slot,
                                           unsigned char* stages, uint64_t* full_bars, int* s_sjob,
                                           uint32_t* s_last, uint32_t* s_cand, float4* s_boxes,
-                                          int lane) {
+                                          const uint32_t* s_pref, int lane) {
   const int stage = (int)(slot % NSTAGE);
   uint64_t* bar = &full_bars[slot % NBAR];
   unsigned char* sb = stages + (size_t)stage * STAGE_BYTES;
   const uint64_t t = blockIdx.x + (uint64_t)slot * gridDim.x;
-  if (t >= P.total_tiles) {
+  const uint32_t nj = MAXJ == 1 ? 1u : min(P.njobs, (uint32_t)MAXJ);
+  if (t >= s_pref[nj]) {
     if (lane == 0) {
       reinterpret_cast<StageHdr*>(sb)->end = 1;
       s_last[stage] = slot;
@@ -551,9 +581,21 @@ __device__ __forceinline__ void fill_slot(const ClassifyParams<MAXJ>& P, uint32_
     __syncwarp();
     return;
   }
-  const int jb = MAXJ == 1 ? 0 : find_job(P, t);
+  // the job whose range of the launch's tiles holds t (the last with
+  // s_pref[jb] <= t; jobs without tiles have empty ranges)
+  int jb = 0;
+  if (MAXJ != 1) {
+    int hi = (int)nj - 1;
+    while (jb < hi) {
+      const int mid = (jb + hi + 1) >> 1;
+      if (s_pref[mid] <= t) jb = mid; else hi = mid - 1;
+    }
+  }
   const ClassifyJob& J = P.job[jb];
-  const uint64_t lt = t - J.tile_base;
+  const uint64_t u = t - s_pref[jb];
+  // a listed job's slots take its listed tiles (entries are below num_tiles;
+  // the bound only keeps a stale entry inside the tile table)
+  const uint64_t lt = (FILTER && J.tlist) ? min((uint64_t)J.tlist[u], J.num_tiles - 1) : u;
   const TileDesc d = J.tiles[lt];
   const uint32_t halo = J.joints ? J.tile_halo[lt] : 0u;
   uint32_t need = ~0u, ro = 0;
@@ -689,8 +731,10 @@ __device__ __forceinline__ void fill_slot(const ClassifyParams<MAXJ>& P, uint32_
   __syncwarp();
 }
 
-// Work items: tile t of this CTA has ROUNDS rounds of 31 samples, grouped
-// RPI rounds per work item; warps take items in order from a shared counter.
+// Work items: a tile has ROUNDS rounds of 31 samples, grouped RPI rounds per
+// work item; warps take items in order from a shared counter.  Slot m of a
+// CTA holds the launch's tile blockIdx + m * gridDim (counting, for a job
+// with the spatial filter's list, only its listed tiles).
 // Round r of a tile covers the samples q = 31r .. 31r+30 on lanes 1..31;
 // lane 0 takes sample 31r-1, whose following interval the round needs (for
 // r = 0 that is the tile's halo interval).
@@ -700,9 +744,10 @@ __device__ __forceinline__ void fill_slot(const ClassifyParams<MAXJ>& P, uint32_
 // with the tile NSTAGE slots ahead, so no warp waits for a free stage and no
 // single warp issues every tile's copies.  The first NSTAGE slots are filled
 // at the start.
-// FILTER: the instance that serves spatially filtered jobs (tiles skipped,
-// rounds copied in runs, per-round candidate masks); without it the jobs'
-// filter fields are ignored and every tile is copied whole.
+// FILTER: the instance that serves spatially filtered jobs (listed tiles
+// only, rounds copied in runs, per-round candidate masks instead of the warp
+// cull); without it the jobs' filter fields are ignored and every tile is
+// copied whole.
 // COUNT: the instance that also counts the work it executes (rounds, outer
 // sphere-box tests, inner (sample, box) pairs) into P.work.
 template <int MAXJ, int NSTAGE, int STAGE_BYTES, int ROUNDS, int RPI, bool FILTER, bool COUNT = false>
@@ -721,7 +766,8 @@ __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const 
   constexpr size_t kOffCnt = kOffItem + 8;
   constexpr size_t kOffSjob = kOffCnt + 4 * ((NSTAGE + 3) & ~3);
   constexpr size_t kOffLast = kOffSjob + 4 * ((NSTAGE + 3) & ~3);
-  constexpr size_t kOffCand = (kOffLast + 4 * ((NSTAGE + 3) & ~3) + 15) & ~(size_t)15;
+  constexpr size_t kOffPref = kOffLast + 4 * ((NSTAGE + 3) & ~3);
+  constexpr size_t kOffCand = (kOffPref + 4 * (MAXJ + 1) + 15) & ~(size_t)15;
   constexpr size_t kOffBoxes =
       (kOffCand + (FILTER ? (size_t)NSTAGE * kRoundSlots * 4 : 0) + 127) & ~(size_t)127;
   constexpr size_t kOffQueues = kOffBoxes + (size_t)kBoxAreas * kBoxAreaFloats * 4;
@@ -733,6 +779,9 @@ __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const 
   uint32_t* s_cnt = reinterpret_cast<uint32_t*>(smem + kOffCnt);       // items done per stage
   int* s_sjob = reinterpret_cast<int*>(smem + kOffSjob);              // job whose boxes a stage holds
   uint32_t* s_last = reinterpret_cast<uint32_t*>(smem + kOffLast);     // last slot a stage was filled with
+  // s_pref[j]: the launch's tiles before job j (the filter's listed tiles
+  // for a job with a list); s_pref[njobs] = tiles of the launch
+  uint32_t* s_pref = reinterpret_cast<uint32_t*>(smem + kOffPref);
   // per stage (spatial filter): the moved boxes that may reach each round of
   // its tile, 0 for a round that was not copied
   uint32_t* s_cand = reinterpret_cast<uint32_t*>(smem + kOffCand);
@@ -780,11 +829,34 @@ __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const 
       mbar_arrive(boxbar);
     }
   }
+  if (warp == nw - 1) {
+    // tiles per job: the spatial filter's list for a job that has one (its
+    // count bounded by the job's tiles), else every tile; prefix sums
+    const uint32_t nj = MAXJ == 1 ? 1u : min(P.njobs, (uint32_t)MAXJ);
+    uint32_t carry = 0;
+    if (lane == 0) s_pref[0] = 0;
+    for (uint32_t j0 = 0; j0 < nj; j0 += 32) {
+      const uint32_t jj = j0 + (uint32_t)lane;
+      uint32_t c = 0;
+      if (jj < nj) {
+        const ClassifyJob& J = P.job[MAXJ == 1 ? 0 : jj];
+        c = (FILTER && J.tlist) ? min(*J.tcount, (uint32_t)J.num_tiles) : (uint32_t)J.num_tiles;
+      }
+      uint32_t incl = c;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += v;
+      }
+      if (jj < nj) s_pref[jj + 1] = carry + incl;
+      carry += __shfl_sync(0xffffffffu, incl, 31);
+    }
+  }
   __syncthreads();
   // the first NSTAGE slots, one warp each
   for (int s = warp; s < NSTAGE; s += nw)
     fill_slot<MAXJ, NSTAGE, STAGE_BYTES, NBAR, FILTER>(P, (uint32_t)s, stages, full, s_sjob,
-                                                       s_last, s_cand, s_boxes, lane);
+                                                       s_last, s_cand, s_boxes, s_pref, lane);
 
   // ------------------------------------------------------------- workers
   uint32_t* queue = queues + (size_t)warp * kPairQueue;
@@ -864,31 +936,37 @@ __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const 
       const int j = at.j, n = at.n, k = at.k, o = at.o, li = at.li;
       const bool valid = at.valid, has_next = at.has_next;
       // ---- a3: the outer sphere of the interval after q, against the moved
-      // boxes that survive a warp bounding-sphere cull
+      // boxes that may reach the round: the spatial filter's candidates for
+      // the round, or those that survive a warp bounding-sphere cull
       float x = ox[o], y = oy[o], z = oz[o], r = orad[o];
       const uint32_t act = __ballot_sync(0xffffffffu, has_next);
       uint32_t bits = 0;
       uint32_t any_cand = 0;
       if (act) {
-        // the bounding sphere's centre: the midpoint of the first and the last
-        // active sphere centres (the round's spheres follow one link's path,
-        // and the chord's midpoint gave the fewest candidates of the centres
-        // tried); any centre is valid, the radius covers every sphere
-        const int lo_l = __ffs(act) - 1, hi_l = 31 - __clz(act);
-        const float mx = 0.5f * (__shfl_sync(0xffffffffu, x, lo_l) + __shfl_sync(0xffffffffu, x, hi_l));
-        const float my = 0.5f * (__shfl_sync(0xffffffffu, y, lo_l) + __shfl_sync(0xffffffffu, y, hi_l));
-        const float mz = 0.5f * (__shfl_sync(0xffffffffu, z, lo_l) + __shfl_sync(0xffffffffu, z, hi_l));
-        const float dx = x - mx, dy = y - my, dz = z - mz;
-        const float reach = has_next ? sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) + r : 0.0f;
-        const float rw = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(reach)));
-        bool cb = false;
-        if (lane < C) {
-          const float4 b0 = bx[6 * lane];
-          const float ex = b0.x - mx, ey = b0.y - my, ez = b0.z - mz;
-          const float thr = (rw + b0.w + margin) * (1.0f + 1e-6f) + 1e-5f;
-          cb = fmaf(ex, ex, fmaf(ey, ey, ez * ez)) <= thr * thr;
+        uint32_t cand = rc;
+        // the filter's test (exact box distance from a near-smallest sphere
+        // about the round) is tighter than the cull, which then only costs
+        if (!FILTER || J.rcand == nullptr) {
+          // the bounding sphere's centre: the midpoint of the first and the
+          // last active sphere centres (the round's spheres follow one link's
+          // path, and the chord's midpoint gave the fewest candidates of the
+          // centres tried); any centre is valid, the radius covers every sphere
+          const int lo_l = __ffs(act) - 1, hi_l = 31 - __clz(act);
+          const float mx = 0.5f * (__shfl_sync(0xffffffffu, x, lo_l) + __shfl_sync(0xffffffffu, x, hi_l));
+          const float my = 0.5f * (__shfl_sync(0xffffffffu, y, lo_l) + __shfl_sync(0xffffffffu, y, hi_l));
+          const float mz = 0.5f * (__shfl_sync(0xffffffffu, z, lo_l) + __shfl_sync(0xffffffffu, z, hi_l));
+          const float dx = x - mx, dy = y - my, dz = z - mz;
+          const float reach = has_next ? sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) + r : 0.0f;
+          const float rw = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(reach)));
+          bool cb = false;
+          if (lane < C) {
+            const float4 b0 = bx[6 * lane];
+            const float ex = b0.x - mx, ey = b0.y - my, ez = b0.z - mz;
+            const float thr = (rw + b0.w + margin) * (1.0f + 1e-6f) + 1e-5f;
+            cb = fmaf(ex, ex, fmaf(ey, ey, ez * ez)) <= thr * thr;
+          }
+          cand = __ballot_sync(0xffffffffu, cb) & rc;
         }
-        uint32_t cand = __ballot_sync(0xffffffffu, cb) & rc;
         any_cand = cand;
         const float rt = r + margin;
         const float rt2 = rt * rt;
@@ -922,14 +1000,23 @@ __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const 
         need = joints ? (after & before) : (after | before);
         if (need) need &= ~*reinterpret_cast<volatile uint32_t*>(&acc_hit[j]);
       }
-      const int cnt = __popc(need);
-      int incl = cnt;
-#pragma unroll
-      for (int d = 1; d < 32; d <<= 1) {
-        const int v = __shfl_up_sync(0xffffffffu, incl, d);
-        if (lane >= d) incl += v;
+      // the round's (sample, box) pairs into the warp's queue, box by box: a
+      // ballot per box gives each lane its place (when the pairs outnumber
+      // the queue, each lane tests its own below)
+      const uint32_t need_or = __reduce_or_sync(0xffffffffu, need);
+      int total = 0;
+      if (need_or) {
+        const uint32_t lt = (1u << lane) - 1u;
+        const uint32_t ent = ((uint32_t)li << 27) | ((uint32_t)q << 13) | ((uint32_t)j << 5);
+        for (uint32_t m = need_or; m; m &= m - 1) {
+          const int b = __ffs(m) - 1;
+          const bool mine = (need >> b) & 1u;
+          const uint32_t mb = __ballot_sync(0xffffffffu, mine);
+          const int pos = total + __popc(mb & lt);
+          if (mine && pos < kPairQueue) queue[pos] = ent | (uint32_t)b;
+          total += __popc(mb);
+        }
       }
-      const int total = __shfl_sync(0xffffffffu, incl, 31);
       if constexpr (COUNT) n_pairs += (unsigned long long)total;
       // a (sample, box) pair packs the box (bits 0..4), the edge-table entry
       // (5..12), the local sample (13..26) and its link (27..31)
@@ -937,10 +1024,6 @@ __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const 
         // interpolated inner centres: one (sample, box) pair per lane,
         // compacted when the pairs fit the queue
         if (total <= kPairQueue) {
-          int pos = incl - cnt;
-          for (uint32_t m = need; m; m &= m - 1)
-            queue[pos++] = ((uint32_t)li << 27) | ((uint32_t)q << 13) | ((uint32_t)j << 5) |
-                           (uint32_t)(__ffs(m) - 1);
           __syncwarp();
           for (int it = lane; it < total; it += 32) {
             const uint32_t e = queue[it];
@@ -997,9 +1080,6 @@ __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const 
       } else if (total > 0 && total <= kPairQueue) {
         // compact the (sample, box) pairs, then test (pair, sphere) items on
         // all lanes, two items per lane per iteration
-        int pos = incl - cnt;
-        for (uint32_t m = need; m; m &= m - 1)
-          queue[pos++] = ((uint32_t)q << 13) | ((uint32_t)j << 5) | (uint32_t)(__ffs(m) - 1);
         __syncwarp();
         const int n_items = total * K;
         for (int it = lane; it < n_items; it += 64) {
@@ -1066,7 +1146,7 @@ __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const 
       __syncwarp();
       // the stage is free: this warp loads it with the slot NSTAGE ahead
       fill_slot<MAXJ, NSTAGE, STAGE_BYTES, NBAR, FILTER>(P, slot + NSTAGE, stages, full, s_sjob,
-                                                         s_last, s_cand, s_boxes, lane);
+                                                         s_last, s_cand, s_boxes, s_pref, lane);
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         const uint64_t e = (uint64_t)hdr.e_first + lane + 32 * c;
@@ -1451,7 +1531,8 @@ static size_t smem_bytes_t(uint32_t consumer_warps) {
   constexpr int NBAR = NSTAGE * full_barriers_per_stage(IPT);
   constexpr size_t kOffFull = (size_t)NSTAGE * STAGE_BYTES;
   constexpr size_t kOffCnt = kOffFull + (NBAR + 1) * sizeof(uint64_t) + 8;
-  constexpr size_t kOffCand = (kOffCnt + 3 * 4 * ((NSTAGE + 3) & ~3) + 15) & ~(size_t)15;
+  constexpr size_t kOffCand =
+      (kOffCnt + 3 * 4 * ((NSTAGE + 3) & ~3) + 4 * (MAXJ + 1) + 15) & ~(size_t)15;
   constexpr size_t kOffBoxes =
       (kOffCand + (FILTER ? (size_t)NSTAGE * kRoundSlots * 4 : 0) + 127) & ~(size_t)127;
   constexpr size_t kOffQueues = kOffBoxes + (size_t)kBoxAreas * kBoxAreaFloats * 4;
@@ -1507,7 +1588,8 @@ static cudaError_t launch_classify_t(const ClassifyParams<MAXJ>& p, const Classi
   bool filtered = false;
   for (uint32_t j = 0; j < p.njobs && j < (uint32_t)MAXJ; ++j) filtered |= p.job[j].rcand != nullptr;
   if (filtered && p.total_tiles) {
-    round_filter_kernel<MAXJ><<<(unsigned)((p.total_tiles + 7) / 8), 256, 0, s>>>(p);
+    // a warp per 32 tiles
+    round_filter_kernel<MAXJ><<<(unsigned)((p.total_tiles + 255) / 256), 256, 0, s>>>(p);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

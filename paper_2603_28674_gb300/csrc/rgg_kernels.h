@@ -25,7 +25,7 @@ namespace rgg {
   X(4, 4, 51 * 1024, 17, 1)        \
   X(5, 3, 69 * 1024, 23, 1)        \
   X(6, 4, 51 * 1024, 16, 2)        \
-  X(7, 7, 27 * 1024, 23, 1)        \
+  X(7, 7, 27 * 1024, 23, 2)        \
   X(8, 6, 32 * 1024, 27, 1)        \
   X(9, 5, 38 * 1024, 31, 1)
 constexpr int kNumVariants = 10;
@@ -84,6 +84,9 @@ struct BoxUpdateParams {
 struct BoxPrepJob {
   const float* stage;     // staging rows of the pending entries
   float* out;             // [C][24]
+  // the roadmap's count of spatially filtered tiles, zeroed here before the
+  // pass's filter kernel appends to its list (null: no list)
+  uint32_t* tcount = nullptr;
   uint32_t C;
   uint32_t ids[kBoxesPerPass];
   uint16_t rows[kBoxesPerPass];  // staging row of pass position p

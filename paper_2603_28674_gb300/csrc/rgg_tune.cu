@@ -11,11 +11,14 @@ extern "C" {
 // Autotuner: time the classify launch of these roadmaps at every supported
 // launch shape, on their own records and boxes, and keep the fastest.
 // ---------------------------------------------------------------------------
-// One classify launch over the roadmaps' tiles with C[i] boxes each, OR-ing
-// into the scratch accumulators acc[i] (labels and box sets are untouched).
+// One pass over the roadmaps' tiles with C[i] boxes each, OR-ing into the
+// scratch accumulators acc[i] (labels and box sets are untouched): the box
+// prep (which also starts the spatial filter's tile lists afresh), then the
+// classify launch.
 static int tune_launch(rgg_roadmap_t* rs, uint32_t n, const std::vector<uint32_t*>& acc,
-                const std::vector<uint32_t>& C, ClassifyParams<kMaxJobs>* cpp,
-                cudaStream_t s) {
+                const std::vector<uint32_t>& C, const BoxPrepParams& bp,
+                ClassifyParams<kMaxJobs>* cpp, cudaStream_t s) {
+  RGG_CK(launch_box_prep(bp, s));
   ClassifyParams<1> cp1;
   uint32_t nj = 0;
   uint64_t tiles = 0;
@@ -88,6 +91,7 @@ int rgg_autotune(rgg_roadmap_t* rs, uint32_t n, uint32_t reps, rgg_tune_result* 
     pj.stage = r->d_table;
     pj.out = r->d_changed;
     pj.C = 0;
+    pj.tcount = nullptr;
     for (uint32_t b = 0; b < r->M && pj.C < (uint32_t)kBoxesPerPass; ++b)
       if (r->present[b]) {
         pj.ids[pj.C] = b;
@@ -98,7 +102,6 @@ int rgg_autotune(rgg_roadmap_t* rs, uint32_t n, uint32_t reps, rgg_tune_result* 
     any = any || (pj.C > 0 && r->es.N > 0);
   }
   if (!any) return RGG_OK;  // nothing to time: the shape stays
-  RGG_CK(launch_box_prep(*bpp, s));
   std::vector<uint32_t*> acc(n, nullptr);
   auto free_acc = [&]() {
     for (uint32_t* p : acc) cudaFree(p);
@@ -123,9 +126,14 @@ int rgg_autotune(rgg_roadmap_t* rs, uint32_t n, uint32_t reps, rgg_tune_result* 
       if (!shape_ok((uint32_t)v, cw)) continue;
       for (uint32_t i = 0; i < n && rc == RGG_OK; ++i) rc = apply_shape(rs[i], v, cw);
       if (rc != RGG_OK) break;
-      rc = tune_launch(rs, n, acc, C, cpp.get(), s);  // warm-up
+      // the filter's list count of each shape's launches (filter_active
+      // depends on the shape)
+      for (uint32_t i = 0; i < n; ++i)
+        bpp->job[i].tcount = filter_active(rs[i]) ? rs[i]->es.d_tlist + rs[i]->es.T : nullptr;
+      rc = tune_launch(rs, n, acc, C, *bpp, cpp.get(), s);  // warm-up
       if (rc == RGG_OK && cudaEventRecord(ev.a, s) != cudaSuccess) rc = RGG_ERR_CUDA;
-      for (uint32_t k = 0; k < reps && rc == RGG_OK; ++k) rc = tune_launch(rs, n, acc, C, cpp.get(), s);
+      for (uint32_t k = 0; k < reps && rc == RGG_OK; ++k)
+        rc = tune_launch(rs, n, acc, C, *bpp, cpp.get(), s);
       if (rc == RGG_OK && cudaEventRecord(ev.b, s) != cudaSuccess) rc = RGG_ERR_CUDA;
       float ms = 0.f;
       if (rc == RGG_OK && (cudaEventSynchronize(ev.b) != cudaSuccess ||
