@@ -63,6 +63,10 @@ def parse():
                          "finer resampling (0: off)")
     ap.add_argument("--serve-seconds", type=float, default=10.0,
                     help="serving: seconds of Poisson arrivals at 2000 requests/s")
+    ap.add_argument("--serve-stress-rate", type=float, default=16000.0,
+                    help="serving: a second, shorter stream at this rate (requests/s), above "
+                         "what one request per launch sustains; 0: off")
+    ap.add_argument("--serve-stress-seconds", type=float, default=2.0)
     ap.add_argument("--no-extras", action="store_true",
                     help="default workload: skip the mixed-label scene and the batched and "
                          "serving measurements that follow the headline")
@@ -116,14 +120,19 @@ def workload_config(name: str, sc, world: int = 1) -> dict:
 def kernel_sha() -> str:
     """Hash of the code classify_kernel is compiled from: the two kernel
     headers and the classify section of rgg_kernels.cu (from its a2..a5
-    banner to the a6 banner), so that edits to the other kernels do not
-    invalidate the traffic profile."""
+    banner to the a6 banner) without the spatial filter's own kernels inside
+    it, so that edits to the other kernels do not invalidate the traffic
+    profile."""
     h = hashlib.sha256()
     for p in KERNEL_HEADERS:
         h.update(open(p, "rb").read())
     t = open(KERNEL_FILE, "rb").read()
     a = t.index(b"// a2..a5: persistent streaming classification")
-    h.update(t[a:t.index(b"// a6: merge", a)])
+    sec = t[a:t.index(b"// a6: merge", a)]
+    f0 = sec.index(b"// Spatial filter (Sec. 4.3)")
+    f1 = sec.index(b"// Bound of the producer's final wait", f0)
+    h.update(sec[:f0])
+    h.update(sec[f1:])
     return h.hexdigest()[:16]
 
 
@@ -568,6 +577,11 @@ def run_gpu(args):
         with ClockSampler(local) as clk_s:
             line["serving"] = measure_serving(args, args.serve_seconds)
         line["serving"]["clocks"] = clk_s.summary()
+        if args.serve_stress_rate > 0:
+            with ClockSampler(local) as clk_t:
+                line["serving_stress"] = measure_serving(args, args.serve_stress_seconds,
+                                                         args.serve_stress_rate)
+            line["serving_stress"]["clocks"] = clk_t.summary()
     if rank == 0:
         print(json.dumps(line))
     if dist is not None:
@@ -974,14 +988,16 @@ def run_batched(args):
     return 0 if res["labels_identical_across_modes"] else 1
 
 
-def measure_serving(args, seconds: float):
+def measure_serving(args, seconds: float, rate_hz: float = 2000.0):
     """Workload 5: a Poisson stream of obstacle-update requests against eight
     resident roadmaps, served with continuous batching and, for comparison,
     one request per classify launch.  Each mode starts from the same box
-    state; the final labels of every roadmap must agree between the modes."""
+    state; the final labels of every roadmap must agree between the modes.
+    The workload's rate is 2,000 requests/s; a higher rate shows the two
+    modes once one request per launch can no longer keep up."""
     import torch
     from paper_2603_28674_gb300 import serve as SV
-    scenes, reqs = W.workload_serving(duration_s=seconds)
+    scenes, reqs = W.workload_serving(rate_hz=rate_hz, duration_s=seconds)
     srv = SV.Server(device=torch.cuda.current_device())
     for sc in scenes:
         rm = sc.roadmap
@@ -1014,7 +1030,7 @@ def measure_serving(args, seconds: float):
     b, p = out["batched"], out["one_at_a_time"]
     return {"roadmaps": len(scenes), "edges": [i["num_edges"] for i in infos],
             "record_gb": sum(i["record_bytes"] for i in infos) / 1e9,
-            "requests": len(requests), "arrival_window_s": seconds,
+            "requests": len(requests), "arrival_window_s": seconds, "rate_hz": rate_hz,
             "offered_req_s": b["offered_req_s"], "moved_per_request": "1-8",
             "batched": b, "one_at_a_time": p,
             "p50_speedup": p["latency_ms_p50"] / b["latency_ms_p50"],

@@ -456,8 +456,10 @@ __global__ void __launch_bounds__(256) round_bounds_kernel(const __grid_constant
 // a box that touches one of them (distance <= r + margin) passes this test;
 // the slack covers FP32 rounding in both tests.  One warp per 32 consecutive
 // tiles, taken one after the other, one lane per round.  The warp stages its
-// roadmap's box records in shared memory (again when the roadmap changes),
-// and a box whose bounding sphere is out of reach skips the exact distance.
+// roadmap's box records in shared memory (again when the roadmap changes).
+// A sphere about the tile's round spheres is tested against all boxes first;
+// only the boxes it may reach are tested per round, and there a box whose
+// bounding sphere is out of reach skips the exact distance.
 // The tiles with a round to test are appended to their roadmap's tile list,
 // one atomic per roadmap and warp; the list's order is arbitrary.
 template <int MAXJ>
@@ -484,13 +486,35 @@ __global__ void __launch_bounds__(256) round_filter_kernel(const __grid_constant
       staged = jb;
     }
     const uint64_t slot = (t - J.tile_base) * kRoundSlots + lane;
+    const float4 sph = lane < kRoundSlots - 1 ? J.rsph[slot] : make_float4(0.0f, 0.0f, 0.0f, -1.0f);
+    const bool on = sph.w >= 0.0f;
+    const uint32_t live = __ballot_sync(0xffffffffu, on);
     uint32_t m = 0;
-    if (lane < kRoundSlots - 1) {
-      const float4 sph = J.rsph[slot];
-      if (sph.w >= 0.0f) {
+    if (live) {
+      // first the tile: a sphere about its rounds' spheres (centred on the
+      // midpoint of the first and the last live round's centres), against
+      // every box at once (lane b: box b); only the boxes it may reach are
+      // tested against the rounds
+      const int lo = __ffs(live) - 1, hi = 31 - __clz(live);
+      const float cx = 0.5f * (__shfl_sync(0xffffffffu, sph.x, lo) + __shfl_sync(0xffffffffu, sph.x, hi));
+      const float cy = 0.5f * (__shfl_sync(0xffffffffu, sph.y, lo) + __shfl_sync(0xffffffffu, sph.y, hi));
+      const float cz = 0.5f * (__shfl_sync(0xffffffffu, sph.z, lo) + __shfl_sync(0xffffffffu, sph.z, hi));
+      const float dx = sph.x - cx, dy = sph.y - cy, dz = sph.z - cz;
+      const float reach = on ? sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) + sph.w : 0.0f;
+      const float rt = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(reach)));
+      bool cb = false;
+      if (lane < C) {
+        const float4 b0 = bx[6 * lane];
+        const float ex = b0.x - cx, ey = b0.y - cy, ez = b0.z - cz;
+        const float thr = (rt + b0.w + J.margin) * (1.0f + 1e-5f) + 1e-5f;
+        cb = fmaf(ex, ex, fmaf(ey, ey, ez * ez)) <= thr * thr;
+      }
+      const uint32_t tile_cand = __ballot_sync(0xffffffffu, cb);
+      if (on) {
         const float thr = (sph.w + J.margin) * (1.0f + 1e-6f) + 1e-5f;
         const float thr2 = thr * thr;
-        for (int b = 0; b < C; ++b) {
+        for (uint32_t mm = tile_cand; mm; mm &= mm - 1) {
+          const int b = __ffs(mm) - 1;
           const float4 b0 = bx[6 * b];
           const float ex = sph.x - b0.x, ey = sph.y - b0.y, ez = sph.z - b0.z;
           const float reach = thr + b0.w;  // the box lies in the sphere of radius |h|

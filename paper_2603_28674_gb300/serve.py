@@ -40,6 +40,7 @@ first arrival), so a latency is arrival -> labels in host memory.
 from __future__ import annotations
 
 import collections
+import heapq
 import dataclasses
 import time
 from typing import Dict, List, Optional, Sequence
@@ -61,13 +62,18 @@ class RequestQueue:
 
     ``arrive`` refuses a request when ``max_len`` requests already wait;
     ``sweep`` drops the waiting requests whose cancellation time has come.
-    Refused and cancelled requests are recorded."""
+    Refused and cancelled requests are recorded.  A sweep looks up the
+    cancellation time of each arrival once and keeps the due times in a
+    heap, so its cost does not grow with the queue."""
 
     def __init__(self, max_len: Optional[int] = None):
         self.items: collections.deque = collections.deque()
         self.max_len = max_len
         self.refused: list = []
         self.cancelled: list = []
+        self._new: list = []   # arrivals the next sweep has not seen
+        self._due: list = []   # heap of (cancellation time, arrival number, item)
+        self._seq = 0
 
     def __len__(self) -> int:
         return len(self.items)
@@ -77,19 +83,23 @@ class RequestQueue:
             self.refused.append(item)
             return False
         self.items.append(item)
+        self._new.append(item)
         return True
 
     def sweep(self, now: float, cancel_at) -> None:
-        if not self.items:
-            return
-        keep = collections.deque()
-        for item in self.items:
+        for item in self._new:
             t = cancel_at(item)
-            if t is not None and t <= now:
-                self.cancelled.append(item)
-            else:
-                keep.append(item)
-        self.items = keep
+            if t is not None:
+                heapq.heappush(self._due, (t, self._seq, item))
+                self._seq += 1
+        self._new.clear()
+        while self._due and self._due[0][0] <= now:
+            item = heapq.heappop(self._due)[2]
+            try:
+                self.items.remove(item)    # still waiting (not admitted meanwhile)?
+            except ValueError:
+                continue
+            self.cancelled.append(item)
 
 
 class Planner:
@@ -105,20 +115,23 @@ class Planner:
         self.free_slots = host_slots
 
     def admit(self, queue: collections.deque, roadmap_of, limit: Optional[int] = None) -> list:
-        taken, keep, blocked = [], [], set()
-        for item in queue:
+        # walk the queue only while a request can still be taken: a slot is
+        # free, the limit is not reached and some roadmap has a free handle
+        # (a roadmap without one blocks its later requests)
+        taken, keep = [], []
+        n_open = sum(1 for h in self.free_handles if h > 0)
+        while queue and self.free_slots > 0 and n_open > 0 and (limit is None or len(taken) < limit):
+            item = queue.popleft()
             k = roadmap_of(item)
-            ok = (k not in blocked and self.free_handles[k] > 0 and self.free_slots > 0
-                  and (limit is None or len(taken) < limit))
-            if ok:
+            if self.free_handles[k] > 0:
                 self.free_handles[k] -= 1
                 self.free_slots -= 1
+                if self.free_handles[k] == 0:
+                    n_open -= 1
                 taken.append(item)
             else:
-                blocked.add(k)
                 keep.append(item)
-        queue.clear()
-        queue.extend(keep)
+        queue.extendleft(reversed(keep))
         return taken
 
     def release(self, roadmap: int) -> None:
