@@ -136,22 +136,50 @@ def kernel_sha() -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(workload: str):
-    """DRAM bytes per classify launch from the committed ncu summary, or None
-    when it is missing, for another workload, or the kernel changed since."""
+def profiled_counters(workload: str) -> dict:
+    """ncu counters of one classify launch from the committed summary
+    (bytes_per_launch, and when recorded inst_per_launch and issue_active),
+    or an empty dict when it is missing, for another workload, or the kernel
+    changed since."""
     if not os.path.exists(PROFILE_TRAFFIC):
-        return None
+        return {}
     kv = {}
     for line in open(PROFILE_TRAFFIC):
         if "=" in line and not line.startswith("#"):
             k, v = line.strip().split("=", 1)
             kv[k.strip()] = v.strip()
     if kv.get("kernel_sha") != kernel_sha() or kv.get("workload") != workload:
+        return {}
+    out = {}
+    for k in ("bytes_per_launch", "inst_per_launch", "issue_active"):
+        try:
+            out[k] = float(kv[k])
+        except (KeyError, ValueError):
+            pass
+    return out
+
+
+def profiled_traffic(workload: str):
+    """DRAM bytes per classify launch from the committed ncu summary (None
+    when it does not apply)."""
+    return profiled_counters(workload).get("bytes_per_launch")
+
+
+def issue_roofline(counters: dict, k_ms: float, sm_mhz, num_sms: int):
+    """The classify kernel against the schedulers' issue rate: ncu's warp
+    instructions per launch over the live launch time, against one warp
+    instruction per cycle on each of an SM's 4 schedulers at the sampled SM
+    clock.  None without counters or a clock sample."""
+    inst = counters.get("inst_per_launch")
+    if not inst or not sm_mhz or k_ms <= 0:
         return None
-    try:
-        return float(kv["bytes_per_launch"])
-    except (KeyError, ValueError):
-        return None
+    peak = num_sms * 4 * sm_mhz * 1e6
+    achieved = inst / (k_ms / 1000.0)
+    return {"warp_instructions_per_launch": inst, "achieved_warp_inst_per_s": achieved,
+            "peak_warp_inst_per_s": peak, "frac": achieved / peak,
+            "issue_active_ncu": counters.get("issue_active"),
+            "note": "instructions from the committed ncu summary (classify kernel only); time "
+                    "is the live classify interval, which includes the round filter"}
 
 
 def hbm_peak():
@@ -409,6 +437,7 @@ def run_gpu(args):
     streamed = r.streamed_bytes()
     ms = max_over_ranks(dist, ms, f"cuda:{local}")
     clk = clocks.summary()
+    num_sms = torch.cuda.get_device_properties(local).multi_processor_count
 
     # ---- end to end through the C ABI with host buffers
     for i in range(min(args.warmup, 3)):
@@ -477,7 +506,8 @@ def run_gpu(args):
     rec_per_launch = streamed / max(1, k_launches)
     b_alg = algorithmic_bytes(info, rec_per_launch)
     achieved = b_alg / (k_avg_ms / 1000.0) / 1e9
-    traffic = profiled_traffic(args.workload)
+    counters = profiled_counters(args.workload)
+    traffic = counters.get("bytes_per_launch")
     filt = None
     if filtered is not None:
         on = bool(filtered["info"]["round_filter"])
@@ -542,7 +572,10 @@ def run_gpu(args):
                      "peak_source": f"{peak_kind} HBM copy bandwidth",
                      "kernel": "classify_kernel", "bytes_per_launch": b_alg,
                      "kernel_ms": k_avg_ms,
-                     "merge_kernel_ms": m_ms / max(1, k_launches)},
+                     "merge_kernel_ms": m_ms / max(1, k_launches),
+                     # the bound the dense scene actually meets: instruction issue
+                     "issue": issue_roofline(counters, k_avg_ms, clk.get("sm_mhz"),
+                                             num_sms)},
         "round_filter_used": bool(info["round_filter"]),
         "other_filter_state": filt,
         # label mix after the end-to-end steps (the paper's roadmaps: 0.3-10% gray)

@@ -81,3 +81,12 @@ def test_sjf_groups_order_and_counts():
     assert [len(x) for x in g] == [3, 2, 3]                      # (nearly) equal counts
     assert bench.sjf_groups(sizes, 100) == [[k] for k in flat]   # at most one per roadmap
     assert bench.sjf_groups([7], 8) == [[0]]
+
+
+def test_issue_roofline_uses_four_schedulers_per_sm_at_the_sampled_clock():
+    r = bench.issue_roofline({"inst_per_launch": 4e9, "issue_active": 0.8}, 2.0, 2000.0, 100)
+    assert r["peak_warp_inst_per_s"] == 100 * 4 * 2000e6
+    assert abs(r["achieved_warp_inst_per_s"] - 2e12) < 1.0
+    assert abs(r["frac"] - 2.5) < 1e-12
+    assert bench.issue_roofline({}, 2.0, 2000.0, 100) is None
+    assert bench.issue_roofline({"inst_per_launch": 4e9}, 2.0, None, 100) is None
