@@ -371,19 +371,17 @@ __device__ __forceinline__ int find_job(const ClassifyParams<MAXJ>& P, uint64_t 
 // ---------------------------------------------------------------------------
 // Spatial filter (Sec. 4.3): per-round bounding spheres, and the per-pass test
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double warp_max_d(double v) {
-#pragma unroll
-  for (int m = 16; m; m >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, m));
-  return v;
-}
-
 // Radius of the sphere about (cx, cy, cz) that holds every active lane's
-// sphere, in FP64 from the FP32 records, rounded up to FP32.
+// sphere, from the FP32 records in FP32.  Each step is one correctly rounded
+// operation (the differences, then sums of non-negative terms and a square
+// root), so the computed radius is within 8 * 2^-24 of the exact one,
+// relatively; enlarged by 2e-6 relative and rounded up it is an upper bound.
 __device__ __forceinline__ float cover_radius(float x, float y, float z, float r, bool on,
                                               float cx, float cy, float cz) {
-  const double dx = (double)x - cx, dy = (double)y - cy, dz = (double)z - cz;
-  const double v = on ? sqrt(dx * dx + dy * dy + dz * dz) + (double)r : 0.0;
-  return __double2float_ru(warp_max_d(v));
+  const float dx = x - cx, dy = y - cy, dz = z - cz;
+  const float v = on ? sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) + r : 0.0f;
+  const float m = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(v)));
+  return __fmul_ru(m, 1.000002f);
 }
 
 // One warp per tile.  Round r's outer spheres are those of the intervals the
