@@ -459,29 +459,35 @@ __device__ __forceinline__ float seg_point_dist_f(float4 p0, float4 p1, float4 x
   return sqrtf(cx * cx + cy * cy + cz * cz);
 }
 
-// Persistent blocks take (box, cell, chunk) items; threads take the chunk's
-// OBBs.
-// A (OBB, box) pair is tested only in the cell holding the low corner of the
-// two AABBs' overlap, so a pair listed in several cells counts once.  A
-// touching pair (separation <= margin) sets the edge's touch bit for the
-// pass position; then the body's splines are tested against the box's inner
-// sphere (its centre, radius = smallest half-extent): a segment within
-// radius - margin sets the hit bit.  (A spline lies inside its body's box,
-// so only touching pairs can hit.)
+// Persistent blocks take (box, cell, chunk) items.  A (OBB, box) pair is
+// tested only in the cell holding the low corner of the two AABBs' overlap,
+// so a pair listed in several cells counts once.  A touching pair
+// (separation <= margin) sets the edge's touch bit for the pass position;
+// then the body's splines are tested against the box's inner sphere (its
+// centre, radius = smallest half-extent): a segment within radius - margin
+// sets the hit bit.  (A spline lies inside its body's box, so only touching
+// pairs can hit.)  Each stage compacts its survivors into a block queue, so
+// that whole warps run the next test: the chunk's AABBs (one per thread),
+// then the separating-axis tests of the pairs whose AABBs meet (one pair per
+// thread), then the splines of the touching pairs (one spline per thread).
 __global__ void __launch_bounds__(256) obb_query_kernel(const __grid_constant__ ObbQueryParams p) {
   __shared__ uint2 s_pair;
   __shared__ unsigned long long s_work[2];
+  __shared__ uint32_t s_n[2];                  // pairs queued for SAT, touching pairs queued
+  __shared__ uint32_t s_sat[kObbChunkMax];     // OBBs whose AABB meets the box's in this cell
+  __shared__ uint32_t s_spl[kObbChunkMax];     // touching OBBs whose splines are tested
   const uint32_t total = min(p.counters[0], p.pair_cap);
-  const uint32_t chunk = p.counters[2];  // chosen by obb_pairs_kernel for this pass
+  const uint32_t chunk = min(p.counters[2], kObbChunkMax);  // chosen by obb_pairs_kernel
+  const int lane = threadIdx.x & 31;
   for (;;) {
     if (threadIdx.x == 0) {
       const uint32_t k = atomicAdd(&p.counters[1], 1u);
       s_pair = k < total ? p.pairs[k] : make_uint2(0xffffffffu, 0u);
       s_work[0] = s_work[1] = 0;
+      s_n[0] = s_n[1] = 0;
     }
     __syncthreads();
     const uint2 pr = s_pair;
-    __syncthreads();
     if (pr.x == 0xffffffffu) break;
     const uint32_t bpos = pr.x & 31u, cell = pr.y;
     const uint32_t k0 = p.cell_off[cell] + (pr.x >> 5) * chunk;
@@ -492,39 +498,57 @@ __global__ void __launch_bounds__(256) obb_query_kernel(const __grid_constant__ 
     const float4 bc = B[0];
     const float rin = fminf(B[4].x, fminf(B[4].y, B[4].z)) - p.margin;
     const uint32_t bit = 1u << bpos;
-    unsigned long long n_sat = 0, n_seg = 0;
-    for (uint32_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
-      const float4 ia = p.cell_items[2 * (size_t)k], ib = p.cell_items[2 * (size_t)k + 1];
-      const float lo[3] = {ia.x, ia.y, ia.z}, hi[3] = {ib.x, ib.y, ib.z};
-      if (lo[0] > bhi[0] || lo[1] > bhi[1] || lo[2] > bhi[2] || blo[0] > hi[0] ||
-          blo[1] > hi[1] || blo[2] > hi[2])
-        continue;
-      const uint32_t o = __float_as_uint(ia.w);
-      const float4* ob = p.obb + 4 * (size_t)o;
-      const uint32_t rx = cell_coord(fmaxf(lo[0], blo[0]), p.g.ox, p.g.cell, p.g.gx);
-      const uint32_t ry = cell_coord(fmaxf(lo[1], blo[1]), p.g.oy, p.g.cell, p.g.gy);
-      const uint32_t rz = cell_coord(fmaxf(lo[2], blo[2]), p.g.oz, p.g.cell, p.g.gz);
-      if ((rz * p.g.gy + ry) * p.g.gx + rx != cell) continue;
-      ++n_sat;
-      if (!obb_box_touch(ob, B, p.margin)) continue;
-      const uint64_t e = o / p.L;
-      atomicOr(&p.edge_acc[2 * e + 1], bit);
-      if (rin <= 0.0f) continue;
-      bool hit = false;
-      for (uint32_t s = 0; s < p.K && !hit; ++s) {
-        const uint64_t sp = (uint64_t)o * p.K + s;
-        for (uint64_t v = p.spl_off[sp]; v + 1 < p.spl_off[sp + 1]; ++v) {
-          ++n_seg;
-          if (seg_point_dist_f(p.spl_v[v], p.spl_v[v + 1], bc) <= rin) {
-            hit = true;
-            break;
-          }
+    // 1. AABBs, and the cell that owns the pair
+    for (uint32_t kb = k0; kb < k1; kb += blockDim.x) {
+      const uint32_t k = kb + threadIdx.x;
+      bool keep = false;
+      uint32_t o = 0;
+      if (k < k1) {
+        const float4 ia = p.cell_items[2 * (size_t)k], ib = p.cell_items[2 * (size_t)k + 1];
+        const float lo[3] = {ia.x, ia.y, ia.z}, hi[3] = {ib.x, ib.y, ib.z};
+        if (!(lo[0] > bhi[0] || lo[1] > bhi[1] || lo[2] > bhi[2] || blo[0] > hi[0] ||
+              blo[1] > hi[1] || blo[2] > hi[2])) {
+          const uint32_t rx = cell_coord(fmaxf(lo[0], blo[0]), p.g.ox, p.g.cell, p.g.gx);
+          const uint32_t ry = cell_coord(fmaxf(lo[1], blo[1]), p.g.oy, p.g.cell, p.g.gy);
+          const uint32_t rz = cell_coord(fmaxf(lo[2], blo[2]), p.g.oz, p.g.cell, p.g.gz);
+          keep = (rz * p.g.gy + ry) * p.g.gx + rx == cell;
+          o = __float_as_uint(ia.w);
         }
       }
-      if (hit) atomicOr(&p.edge_acc[2 * e], bit);
+      const uint32_t m = __ballot_sync(0xffffffffu, keep);
+      uint32_t at = 0;
+      if (lane == 0 && m) at = atomicAdd(&s_n[0], (uint32_t)__popc(m));
+      at = __shfl_sync(0xffffffffu, at, 0);
+      if (keep) s_sat[at + __popc(m & ((1u << lane) - 1u))] = o;
+    }
+    __syncthreads();
+    const uint32_t n_sat = s_n[0];
+    // 2. separating-axis tests
+    for (uint32_t i = threadIdx.x; i < n_sat; i += blockDim.x) {
+      const uint32_t o = s_sat[i];
+      if (!obb_box_touch(p.obb + 4 * (size_t)o, B, p.margin)) continue;
+      atomicOr(&p.edge_acc[2 * (uint64_t)(o / p.L) + 1], bit);
+      if (rin > 0.0f) s_spl[atomicAdd(&s_n[1], 1u)] = o;
+    }
+    __syncthreads();
+    const uint32_t n_spl = s_n[1];
+    // 3. the touching bodies' splines against the box's inner sphere
+    unsigned long long n_seg = 0;
+    for (uint32_t i = threadIdx.x; i < n_spl * p.K; i += blockDim.x) {
+      const uint32_t o = s_spl[i / p.K];
+      const uint64_t sp = (uint64_t)o * p.K + (i % p.K);
+      bool hit = false;
+      for (uint64_t v = p.spl_off[sp]; v + 1 < p.spl_off[sp + 1]; ++v) {
+        ++n_seg;
+        if (seg_point_dist_f(p.spl_v[v], p.spl_v[v + 1], bc) <= rin) {
+          hit = true;
+          break;
+        }
+      }
+      if (hit) atomicOr(&p.edge_acc[2 * (uint64_t)(o / p.L)], bit);
     }
     if (p.work) {
-      atomicAdd(&s_work[0], n_sat);
+      if (threadIdx.x == 0) s_work[0] = n_sat;
       atomicAdd(&s_work[1], n_seg);
       __syncthreads();
       if (threadIdx.x == 0) {
