@@ -578,30 +578,30 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
 constexpr int kMaxWorkers = kMaxClassifyThreads / 32;
 __host__ __device__ constexpr int full_barriers_per_stage(int ipt) { return ipt >= kMaxWorkers - 1 ? 1 : (kMaxWorkers - 2) / ipt + 1; }
 
-// Fill ring slot `slot` of this CTA (stage slot % NSTAGE) with its tile,
-// blockIdx.x + slot * gridDim.x, or with an end marker once past the last
-// tile.  The slot's tile is fixed by its number, so every worker sees the
-// tiles in slot order and every end marker after the last tile.  Called by
-// one whole warp: lanes derive the copies, lane 0 writes the header and arms
-// the stage's barrier, and the lanes issue the bulk copies together.
-template <int MAXJ, int NSTAGE, int STAGE_BYTES, int NBAR, bool FILTER>
-__device__ __forceinline__ void fill_slot(const ClassifyParams<MAXJ>& P, uint32_t slot,
-                                          unsigned char* stages, uint64_t* full_bars, int* s_sjob,
-                                          uint32_t* s_last, uint32_t* s_cand, float4* s_boxes,
-                                          const uint32_t* s_pref, int lane) {
-  const int stage = (int)(slot % NSTAGE);
-  uint64_t* bar = &full_bars[slot % NBAR];
-  unsigned char* sb = stages + (size_t)stage * STAGE_BYTES;
+// What a slot's fill needs to know of its tile: the job, the local tile, its
+// descriptor and halo count, and with the spatial filter the tile's round
+// mask and (per lane) the outer range of round `lane`.  Loading it takes a
+// chain of dependent global loads (the list entry, then the tile's own
+// rows), so each fill also loads the metadata of the stage's next slot and
+// leaves it in shared memory for the warp that will fill that slot.
+struct SlotMeta {
+  int jb;
+  uint32_t lt;
+  TileDesc d;
+  uint32_t halo, need, ro;
+  int end;
+};
+constexpr int kMetaWords = 48;  // per stage: 16 header words, then ro of the 32 lanes
+
+template <int MAXJ, bool FILTER>
+__device__ __forceinline__ SlotMeta slot_meta(const ClassifyParams<MAXJ>& P, uint32_t slot,
+                                              const uint32_t* s_pref, int lane) {
+  SlotMeta m{};
   const uint64_t t = blockIdx.x + (uint64_t)slot * gridDim.x;
   const uint32_t nj = MAXJ == 1 ? 1u : min(P.njobs, (uint32_t)MAXJ);
   if (t >= s_pref[nj]) {
-    if (lane == 0) {
-      reinterpret_cast<StageHdr*>(sb)->end = 1;
-      s_last[stage] = slot;
-      mbar_arrive(bar);
-    }
-    __syncwarp();
-    return;
+    m.end = 1;
+    return m;
   }
   // the job whose range of the launch's tiles holds t (the last with
   // s_pref[jb] <= t; jobs without tiles have empty ranges)
@@ -618,15 +618,106 @@ __device__ __forceinline__ void fill_slot(const ClassifyParams<MAXJ>& P, uint32_
   // a listed job's slots take its listed tiles (entries are below num_tiles;
   // the bound only keeps a stale entry inside the tile table)
   const uint64_t lt = (FILTER && J.tlist) ? min((uint64_t)J.tlist[u], J.num_tiles - 1) : u;
-  const TileDesc d = J.tiles[lt];
-  const uint32_t halo = J.joints ? J.tile_halo[lt] : 0u;
-  uint32_t need = ~0u, ro = 0;
+  m.jb = jb;
+  m.lt = (uint32_t)lt;
+  m.d = J.tiles[lt];
+  m.halo = J.joints ? J.tile_halo[lt] : 0u;
+  m.need = ~0u;
   if constexpr (FILTER) {
     if (J.rcand) {
-      need = J.rcand[lt * kRoundSlots + kRoundSlots - 1];
-      ro = J.rout[lt * kRoundSlots + lane];
+      m.need = J.rcand[lt * kRoundSlots + kRoundSlots - 1];
+      m.ro = J.rout[lt * kRoundSlots + lane];
     }
   }
+  return m;
+}
+
+template <int NSTAGE>
+__device__ __forceinline__ void store_meta(uint32_t* s_meta, uint32_t* s_meta_slot, int stage,
+                                           uint32_t slot, const SlotMeta& m, int lane) {
+  uint32_t* w = s_meta + stage * kMetaWords;
+  if (lane == 0) {
+    w[0] = (uint32_t)m.jb;
+    w[1] = m.lt;
+    w[2] = (uint32_t)m.d.packed;
+    w[3] = (uint32_t)(m.d.packed >> 32);
+    w[4] = m.d.etab;
+    w[5] = m.d.e_first;
+    w[6] = m.halo;
+    w[7] = m.need;
+    w[8] = (uint32_t)m.end;
+  }
+  w[16 + lane] = m.ro;
+  __syncwarp();
+  if (lane == 0) {
+    __threadfence_block();
+    *reinterpret_cast<volatile uint32_t*>(&s_meta_slot[stage]) = slot;
+  }
+}
+
+// The metadata the stage's previous fill left for `slot` (false if it did
+// not arrive within the wait limit).
+__device__ __forceinline__ bool take_meta(const uint32_t* s_meta, const uint32_t* s_meta_slot,
+                                          int stage, uint32_t slot, uint64_t limit_ns,
+                                          SlotMeta& m, int lane) {
+  int ok = 1;
+  if (lane == 0) {
+    const volatile uint32_t* f = &s_meta_slot[stage];
+    if (*f != slot) {
+      const uint64_t t0 = global_ns();
+      while (*f != slot)
+        if (global_ns() - t0 > limit_ns) {
+          ok = 0;
+          break;
+        }
+    }
+    __threadfence_block();
+  }
+  ok = __shfl_sync(0xffffffffu, ok, 0);
+  if (!ok) return false;
+  const volatile uint32_t* w = s_meta + stage * kMetaWords;
+  m.jb = (int)w[0];
+  m.lt = w[1];
+  m.d.packed = (uint64_t)w[2] | ((uint64_t)w[3] << 32);
+  m.d.etab = w[4];
+  m.d.e_first = w[5];
+  m.halo = w[6];
+  m.need = w[7];
+  m.end = (int)w[8];
+  m.ro = w[16 + lane];
+  return true;
+}
+
+// Fill ring slot `slot` of this CTA (stage slot % NSTAGE) with its tile,
+// blockIdx.x + slot * gridDim.x of the launch's tiles (metadata `m`), or with
+// an end marker once past the last tile.  The slot's tile is fixed by its
+// number, so every worker sees the tiles in slot order and every end marker
+// after the last tile.  Called by one whole warp: lanes derive the copies,
+// lane 0 writes the header and arms the stage's barrier, and the lanes issue
+// the bulk copies together.
+template <int MAXJ, int NSTAGE, int STAGE_BYTES, int NBAR, bool FILTER>
+__device__ __forceinline__ void fill_slot(const ClassifyParams<MAXJ>& P, uint32_t slot,
+                                          const SlotMeta& m, unsigned char* stages,
+                                          uint64_t* full_bars, int* s_sjob, uint32_t* s_last,
+                                          uint32_t* s_cand, float4* s_boxes, int lane) {
+  const int stage = (int)(slot % NSTAGE);
+  uint64_t* bar = &full_bars[slot % NBAR];
+  unsigned char* sb = stages + (size_t)stage * STAGE_BYTES;
+  if (m.end) {
+    if (lane == 0) {
+      reinterpret_cast<StageHdr*>(sb)->end = 1;
+      s_last[stage] = slot;
+      mbar_arrive(bar);
+    }
+    __syncwarp();
+    return;
+  }
+  const int jb = m.jb;
+  const ClassifyJob& J = P.job[jb];
+  const uint64_t lt = m.lt;
+  const TileDesc d = m.d;
+  const uint32_t halo = m.halo;
+  const uint32_t need = m.need, ro = m.ro;
   const uint64_t K = J.K;
   const uint64_t g0 = lt * J.S;
   const uint64_t g1 = min(g0 + J.S, J.G);
@@ -789,7 +880,9 @@ __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const 
   constexpr size_t kOffSjob = kOffCnt + 4 * ((NSTAGE + 3) & ~3);
   constexpr size_t kOffLast = kOffSjob + 4 * ((NSTAGE + 3) & ~3);
   constexpr size_t kOffPref = kOffLast + 4 * ((NSTAGE + 3) & ~3);
-  constexpr size_t kOffCand = (kOffPref + 4 * (MAXJ + 1) + 15) & ~(size_t)15;
+  constexpr size_t kOffMetaSlot = kOffPref + 4 * (MAXJ + 1);
+  constexpr size_t kOffMeta = (kOffMetaSlot + 4 * NSTAGE + 15) & ~(size_t)15;
+  constexpr size_t kOffCand = (kOffMeta + 4 * (size_t)NSTAGE * kMetaWords + 15) & ~(size_t)15;
   constexpr size_t kOffBoxes =
       (kOffCand + (FILTER ? (size_t)NSTAGE * kRoundSlots * 4 : 0) + 127) & ~(size_t)127;
   constexpr size_t kOffQueues = kOffBoxes + (size_t)kBoxAreas * kBoxAreaFloats * 4;
@@ -804,6 +897,10 @@ __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const 
   // s_pref[j]: the launch's tiles before job j (the filter's listed tiles
   // for a job with a list); s_pref[njobs] = tiles of the launch
   uint32_t* s_pref = reinterpret_cast<uint32_t*>(smem + kOffPref);
+  // per stage: the slot whose metadata the stage's last fill left, and that
+  // metadata (see SlotMeta)
+  uint32_t* s_meta_slot = reinterpret_cast<uint32_t*>(smem + kOffMetaSlot);
+  uint32_t* s_meta = reinterpret_cast<uint32_t*>(smem + kOffMeta);
   // per stage (spatial filter): the moved boxes that may reach each round of
   // its tile, 0 for a round that was not copied
   uint32_t* s_cand = reinterpret_cast<uint32_t*>(smem + kOffCand);
@@ -835,6 +932,7 @@ __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const 
     s_cnt[i] = 0;
     s_sjob[i] = -1;
     s_last[i] = 0xffffffffu;
+    s_meta_slot[i] = 0xffffffffu;
   }
   fence_proxy_async_smem();
   if (threadIdx.x == 0) {
@@ -876,9 +974,15 @@ __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const 
   }
   __syncthreads();
   // the first NSTAGE slots, one warp each
-  for (int s = warp; s < NSTAGE; s += nw)
-    fill_slot<MAXJ, NSTAGE, STAGE_BYTES, NBAR, FILTER>(P, (uint32_t)s, stages, full, s_sjob,
-                                                       s_last, s_cand, s_boxes, s_pref, lane);
+  for (int s = warp; s < NSTAGE; s += nw) {
+    const SlotMeta m = slot_meta<MAXJ, FILTER>(P, (uint32_t)s, s_pref, lane);
+    fill_slot<MAXJ, NSTAGE, STAGE_BYTES, NBAR, FILTER>(P, (uint32_t)s, m, stages, full, s_sjob,
+                                                       s_last, s_cand, s_boxes, lane);
+    // the stage's next slot (a stage that ends here is never refilled)
+    if (!m.end)
+      store_meta<NSTAGE>(s_meta, s_meta_slot, s, (uint32_t)s + NSTAGE,
+                         slot_meta<MAXJ, FILTER>(P, (uint32_t)s + NSTAGE, s_pref, lane), lane);
+  }
 
   // ------------------------------------------------------------- workers
   uint32_t* queue = queues + (size_t)warp * kPairQueue;
@@ -1166,15 +1270,27 @@ __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const 
       }
       if (lane == 0) s_cnt[stage] = 0;
       __syncwarp();
-      // the stage is free: this warp loads it with the slot NSTAGE ahead
-      fill_slot<MAXJ, NSTAGE, STAGE_BYTES, NBAR, FILTER>(P, slot + NSTAGE, stages, full, s_sjob,
-                                                         s_last, s_cand, s_boxes, s_pref, lane);
+      // the stage is free: this warp loads it with the slot NSTAGE ahead,
+      // from the metadata the stage's last fill left (a bounded wait: that
+      // fill's loads may still be in flight)
+      SlotMeta m;
+      if (!take_meta(s_meta, s_meta_slot, stage, slot + NSTAGE, P.wait_ns, m, lane)) {
+        if (lane == 0) atomicCAS(P.status, 0, (int)kStatusTimeoutFull);
+        m = SlotMeta{};
+        m.end = 1;
+      }
+      fill_slot<MAXJ, NSTAGE, STAGE_BYTES, NBAR, FILTER>(P, slot + NSTAGE, m, stages, full, s_sjob,
+                                                         s_last, s_cand, s_boxes, lane);
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         const uint64_t e = (uint64_t)hdr.e_first + lane + 32 * c;
         if (hv[c]) atomicOr(&J.edge_acc[2 * e], hv[c]);
         if (tv[c]) atomicOr(&J.edge_acc[2 * e + 1], tv[c]);
       }
+      // and the metadata of the stage's slot after that
+      if (!m.end)
+        store_meta<NSTAGE>(s_meta, s_meta_slot, stage, slot + 2 * NSTAGE,
+                           slot_meta<MAXJ, FILTER>(P, slot + 2 * NSTAGE, s_pref, lane), lane);
     }
   }
   if (COUNT && lane == 0 && P.work) {
@@ -1374,6 +1490,9 @@ __global__ void __launch_bounds__(256) resolve_gray_kernel(const __grid_constant
   // One block per gray edge at a time: its 256 threads take the edge's
   // configurations in steps of 256 (a long edge no longer runs on one warp).
   __shared__ float s_box[32][16];
+  // per joint: the start angle and the step per configuration, each as an
+  // FP32 pair (high part, remainder) of its FP64 value
+  __shared__ float4 s_q[kMaxBuildLinks];
   __shared__ uint32_t s_best;                 // block's running minimum (float_key)
   __shared__ float s_red_best[8];
   __shared__ unsigned long long s_evals[8];
@@ -1392,11 +1511,14 @@ __global__ void __launch_bounds__(256) resolve_gray_kernel(const __grid_constant
     }
     const uint64_t n = p.soff[e + 1] - p.soff[e];
     const uint64_t m = (n - 1) * (uint64_t)p.F;
-    const double inv_m = 1.0 / (double)m;
-    const double* qa = p.qa + e * L;
-    const double* qb = p.qb + e * L;
     const uint32_t* tw = p.touch + e * Wm;
     if (tid == 0) s_best = float_key(INFINITY);
+    if (tid < L) {
+      const double a = p.qa[e * L + tid];
+      const double d = (p.qb[e * L + tid] - a) / (double)m;
+      const float ah = (float)a, dh = (float)d;
+      s_q[tid] = make_float4(ah, (float)(a - (double)ah), dh, (float)(d - (double)dh));
+    }
     float best = INFINITY;
     unsigned long long evals = 0;
     bool red = false;
@@ -1426,11 +1548,21 @@ __global__ void __launch_bounds__(256) resolve_gray_kernel(const __grid_constant
         // prune against the block's best so far, not only this thread's
         best = fminf(best, key_float(*reinterpret_cast<volatile uint32_t*>(&s_best)));
         if (c <= m) {
-          const double tt = (double)c * inv_m;
+          const float cf = (float)c;  // exact: c < 2^24
           float R[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
           float o[3] = {0, 0, 0};
           for (uint32_t i = 0; i < L; ++i) {
-            const float q = (float)(qa[i] + tt * (qb[i] - qa[i]));
+            // q = a + c d, rounded once to FP32 (as the FP64 value would be,
+            // without FP64 arithmetic): c * d_high exactly as p + pe (an FMA
+            // gives the product's rounding error), a_high + p exactly as
+            // s + se (Knuth's two-sum), then the small terms added to s
+            const float4 z = s_q[i];
+            const float pp = __fmul_rn(cf, z.z);
+            const float pe = fmaf(cf, z.z, -pp);
+            const float s = __fadd_rn(z.x, pp);
+            const float sb = __fsub_rn(s, z.x);
+            const float se = __fadd_rn(__fsub_rn(z.x, __fsub_rn(s, sb)), __fsub_rn(pp, sb));
+            const float q = __fadd_rn(s, __fadd_rn(se, __fadd_rn(pe, fmaf(cf, z.w, z.y))));
             float st, ct;
             sincosf(q, &st, &ct);
             const float v0 = p.a[i] * ct, v1 = p.a[i] * st, v2 = p.d[i];
@@ -1553,8 +1685,8 @@ static size_t smem_bytes_t(uint32_t consumer_warps) {
   constexpr int NBAR = NSTAGE * full_barriers_per_stage(IPT);
   constexpr size_t kOffFull = (size_t)NSTAGE * STAGE_BYTES;
   constexpr size_t kOffCnt = kOffFull + (NBAR + 1) * sizeof(uint64_t) + 8;
-  constexpr size_t kOffCand =
-      (kOffCnt + 3 * 4 * ((NSTAGE + 3) & ~3) + 4 * (MAXJ + 1) + 15) & ~(size_t)15;
+  constexpr size_t kOffMeta = (kOffCnt + 3 * 4 * ((NSTAGE + 3) & ~3) + 4 * (MAXJ + 1) + 4 * NSTAGE + 15) & ~(size_t)15;
+  constexpr size_t kOffCand = (kOffMeta + 4 * (size_t)NSTAGE * kMetaWords + 15) & ~(size_t)15;
   constexpr size_t kOffBoxes =
       (kOffCand + (FILTER ? (size_t)NSTAGE * kRoundSlots * 4 : 0) + 127) & ~(size_t)127;
   constexpr size_t kOffQueues = kOffBoxes + (size_t)kBoxAreas * kBoxAreaFloats * 4;
