@@ -1093,6 +1093,10 @@ __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const 
           }
           cand = __ballot_sync(0xffffffffu, cb) & rc;
         }
+        // a box already known to hit the edge of every lane in this pass is
+        // done there: a hit implies a touch, so its tests could add no bit
+        cand &= ~__reduce_and_sync(
+            0xffffffffu, valid ? *reinterpret_cast<volatile uint32_t*>(&acc_hit[j]) : ~0u);
         any_cand = cand;
         const float rt = r + margin;
         const float rt2 = rt * rt;
