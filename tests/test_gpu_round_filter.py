@@ -1,4 +1,4 @@
-"""The sphere geometry's opt-in spatial filter (Sec. 4.3, spatially filtered
+"""The sphere geometry's spatial filter (Sec. 4.3, spatially filtered
 many-to-many checking, applied to the streamed records): every round of 31
 configurations of a tile has a bounding sphere of its outer spheres; before
 each pass the rounds are tested against the moved boxes and the classify
@@ -12,6 +12,9 @@ Rules checked:
   * the filtered launches copy fewer record bytes than record_bytes per
     pass, and none for a pass whose boxes are far from every edge
     (unfiltered launches copy every record and are not counted);
+  * a batched launch whose filtered roadmaps list no tile (their moved
+    boxes far from every edge), in the middle, at the ends or all of them,
+    leaves the same state as unfiltered launches;
   * the filtered labels agree with the FP64 oracle (pinned edges equal,
     other differences GPU gray).
 """
@@ -227,3 +230,48 @@ def test_far_boxes_copy_nothing_and_clear_their_bits(rgg):
             with pytest.raises(rgg.RGGError) as e:
                 o.set_round_filter(False)
             assert e.value.status == rgg.RGG_ERR_STATE
+
+
+def test_batched_launch_with_empty_tile_lists(rgg):
+    # A batched launch numbers the filtered roadmaps' listed tiles one roadmap
+    # after another; roadmaps whose moved boxes reach no tile (empty lists) in
+    # the middle, at both ends, and a launch where every list is empty must
+    # leave the same state as unfiltered launches of each roadmap alone.
+    scenes = W.workload_batched(n_roadmaps=5, edge_lo=300, edge_hi=3000, n_updates=1)
+    filt, plain = [], []
+    for sc in scenes:
+        for lst, flt in ((filt, True), (plain, False)):
+            r = built(rgg, sc.roadmap, sc.boxes.count, flt)
+            r.update_obstacles(np.arange(sc.boxes.count), f32(sc.boxes.poses()))
+            lst.append(r)
+    rgg.classify_many(filt)
+    for r in plain:
+        r.classify()
+
+    def far_move(sc, k):
+        ids = np.arange(min(2, sc.boxes.count), dtype=np.uint32)
+        poses = f32(sc.boxes.poses()[ids])
+        poses[:, :3] = [[80.0 + k, 80.0, 0.0], [80.0 + k, 82.0, 0.0]][:len(ids)]
+        return ids, poses
+
+    for step in range(2):
+        for i, (sc, a, b) in enumerate(zip(scenes, filt, plain)):
+            if step == 1 or i % 2 == 0:
+                ids, poses = far_move(sc, i)
+            else:
+                ids, poses = sc.updates[0].ids, f32(sc.updates[0].poses)
+            a.update_obstacles(ids, poses)
+            b.update_obstacles(ids, poses)
+        for r in filt:
+            r.streamed_bytes()             # restart the copied-byte counters
+        rgg.classify_many(filt)
+        for b in plain:
+            b.classify()
+        for i, (a, b) in enumerate(zip(filt, plain)):
+            same_state(a, b, f"roadmap {i} step {step}")
+        if step == 1:
+            # every moved box is far away: no tile listed, no record copied
+            assert sum(r.streamed_bytes() for r in filt) == 0
+    for r in filt + plain:
+        r.check_status()
+        r.close()
