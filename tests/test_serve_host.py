@@ -52,6 +52,37 @@ def test_one_at_a_time_limit():
     assert order == list(range(6))
 
 
+def test_queue_and_admission_work_does_not_grow_with_the_backlog():
+    # a long backlog (one request per launch falling behind) must not make
+    # every loop iteration walk it: a sweep looks up each arrival's
+    # cancellation time once, and admission stops once nothing more fits
+    q = RequestQueue()
+    for i in range(10000):
+        q.arrive(i)
+    calls = []
+
+    def cancel_at(i):
+        calls.append(i)
+        return None
+
+    for _ in range(50):
+        q.sweep(1.0, cancel_at)
+    assert len(calls) == 10000
+    pl = Planner(n_roadmaps=1, handles_per_roadmap=64, host_slots=64)
+    seen = []
+
+    def roadmap_of(i):
+        seen.append(i)
+        return 0
+
+    assert pl.admit(q.items, roadmap_of, limit=1) == [0]
+    assert seen == [0] and q.items[0] == 1 and len(q.items) == 9999
+    # without a limit the walk ends when the roadmap's 64 handles are taken
+    seen.clear()
+    got = pl.admit(q.items, roadmap_of)
+    assert got == list(range(1, 64)) and len(seen) == 63 and q.items[0] == 64
+
+
 @pytest.fixture(scope="module")
 def built():
     from paper_2603_28674_gb300 import build
