@@ -21,6 +21,7 @@ from __future__ import annotations
 import argparse
 import ctypes
 import hashlib
+import re
 import json
 import os
 import subprocess
@@ -117,22 +118,29 @@ def workload_config(name: str, sc, world: int = 1) -> dict:
     return cfg
 
 
+def _code_only(src: bytes) -> bytes:
+    """C++ source without // comments and with runs of blank space
+    collapsed: edits to comments do not change what is compiled."""
+    out = re.sub(rb"//[^\n]*", b"", src)
+    return re.sub(rb"\s+", b" ", out).strip()
+
+
 def kernel_sha() -> str:
     """Hash of the code classify_kernel is compiled from: the two kernel
     headers and the classify section of rgg_kernels.cu (from its a2..a5
     banner to the a6 banner) without the spatial filter's own kernels inside
-    it, so that edits to the other kernels do not invalidate the traffic
-    profile."""
+    it, comments left out, so that edits to the other kernels or to comments
+    do not invalidate the traffic profile."""
     h = hashlib.sha256()
     for p in KERNEL_HEADERS:
-        h.update(open(p, "rb").read())
+        h.update(_code_only(open(p, "rb").read()))
     t = open(KERNEL_FILE, "rb").read()
     a = t.index(b"// a2..a5: persistent streaming classification")
     sec = t[a:t.index(b"// a6: merge", a)]
     f0 = sec.index(b"// Spatial filter (Sec. 4.3)")
-    f1 = sec.index(b"// Bound of the producer's final wait", f0)
-    h.update(sec[:f0])
-    h.update(sec[f1:])
+    f1 = sec.index(b"// Bound of the final wait for the CTA's own bulk copies", f0)
+    h.update(_code_only(sec[:f0]))
+    h.update(_code_only(sec[f1:]))
     return h.hexdigest()[:16]
 
 

@@ -542,8 +542,8 @@ __global__ void __launch_bounds__(256) round_filter_kernel(const __grid_constant
   }
 }
 
-// Bound of the producer's final wait for its own bulk copies before the CTA
-// exits (copies always land; the bound only keeps the wait finite).
+// Bound of the final wait for the CTA's own bulk copies before it exits
+// (copies always land; the bound only keeps the wait finite).
 constexpr uint64_t kDrainLimit = 500000000ull;
 
 __device__ __forceinline__ void write_stage_hdr(unsigned char* sb, int job, uint64_t g0, uint64_t g1,
