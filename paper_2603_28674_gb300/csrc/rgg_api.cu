@@ -188,10 +188,11 @@ int set_tiles(rgg_roadmap* r, EdgeState* es, cudaStream_t s) {
 }
 
 // Bytes of the spatial filter's data for T tiles: per round slot a bounding
-// sphere, an outer range and a candidate mask; per tile a list entry; the
-// list's count.
+// sphere, an outer range and a candidate mask; per tile a sphere about its
+// rounds and a list entry; the list's count.
 uint64_t round_data_bytes(uint64_t T) {
-  return T * kRoundSlots * (sizeof(float4) + 2 * sizeof(uint32_t)) + (T + 1) * sizeof(uint32_t);
+  return T * kRoundSlots * (sizeof(float4) + 2 * sizeof(uint32_t)) + T * sizeof(float4) +
+         (T + 1) * sizeof(uint32_t);
 }
 
 void release_rounds(EdgeState* es) {
@@ -226,7 +227,7 @@ int compute_rounds(rgg_roadmap* r, EdgeState* es, cudaStream_t s) {
   release_rounds(es);
   if (!filter_wanted(r, es) || r->geometry != RGG_GEOMETRY_SPHERES || es->T == 0) return RGG_OK;
   const uint64_t n = es->T * kRoundSlots;
-  cudaError_t e = dalloc(&es->d_rsph, n);
+  cudaError_t e = dalloc(&es->d_rsph, n + es->T);  // the round spheres, then the tile spheres
   if (e == cudaSuccess) e = dalloc(&es->d_rout, n);
   if (e == cudaSuccess) e = dalloc(&es->d_rcand, n);
   // the per-pass tile list and its count, zeroed so that no entry is ever
@@ -255,6 +256,7 @@ int compute_rounds(rgg_roadmap* r, EdgeState* es, cudaStream_t s) {
   p.S = es->tiling.S;
   p.rsph = es->d_rsph;
   p.rout = es->d_rout;
+  p.tsph = es->d_rsph + n;
   RGG_CK(launch_round_bounds(p, r->num_sms, s));
   return RGG_OK;
 }
@@ -479,6 +481,7 @@ ClassifyJob make_job(rgg_roadmap* r, uint32_t C, uint64_t tile_base) {
   j.inv_km1 = r->K > 1 ? 1.0f / (float)(r->K - 1) : 0.0f;
   if (filter_active(r)) {
     j.rsph = es.d_rsph;
+    j.tsph = es.d_rsph + es.T * kRoundSlots;
     j.rout = es.d_rout;
     j.rcand = es.d_rcand;
     j.tlist = es.d_tlist;

@@ -32,12 +32,14 @@
 //
 // Rounds: round r of a tile is its samples [31r, 31r+31) and the intervals
 // that follow its local samples 31r-1 .. 31r+30 (those a consumer warp tests
-// in one step).  Opt-in spatial filter (Sec. 4.3, "spatially filtered
-// many-to-many checking"): while it is on, every round has a bounding
-// sphere of those intervals' outer spheres and their range of outer records
-// (recomputed whenever the tiles change); before each pass a small kernel
-// tests the spheres against the pass's moved boxes, and the producer copies
-// only the rounds some box can reach and skips a tile none can.
+// in one step).  Spatial filter (Sec. 4.3, "spatially filtered many-to-many
+// checking"; on by default for link-end records): while it is on, every
+// round has a bounding sphere of those intervals' outer spheres and their
+// range of outer records, and every tile a sphere holding its rounds'
+// spheres (recomputed whenever the tiles change); before each pass a small
+// kernel tests the spheres against the pass's moved boxes and lists the
+// tiles some box can reach, and the classify kernel copies only those tiles'
+// rounds that some box can reach.
 #pragma once
 
 #include <cstdint>
@@ -102,8 +104,9 @@ struct ClassifyJob {
   uint32_t joints;
   const uint32_t* tile_halo;        // [T] link-end entries copied before a tile's first sample
   float inv_k, inv_km1;             // 1/K and 1/(K-1) (0 when K = 1)
-  // spatial filter (all three null: every round of every tile is copied)
+  // spatial filter (null: every round of every tile is copied)
   const float4* rsph;               // [T][kRoundSlots] bounding sphere (radius < 0: empty)
+  const float4* tsph = nullptr;     // [T] a sphere holding the tile's round spheres (radius < 0: none)
   const uint32_t* rout;             // [T][kRoundSlots] outer records lo | hi << 16, tile-local
   uint32_t* rcand;                  // [T][kRoundSlots] moved boxes that may reach the round
   // the pass's tiles that some moved box may reach: local tile indices in no
@@ -126,7 +129,7 @@ struct ClassifyParams {
   uint64_t wait_ns = 4000000000ull; // limit of every bounded wait, ns of wall time
 };
 
-// Per-stage header written by the producer warp.
+// Per-stage header, written by the warp that fills the stage.
 struct StageHdr {
   int32_t job;
   int32_t n_samp;      // configurations in the tile

@@ -400,6 +400,7 @@ __global__ void __launch_bounds__(256) round_bounds_kernel(const __grid_constant
     const int* etab = reinterpret_cast<const int*>(p.etab + d.etab);
     const uint64_t g0 = t * p.S;
     const int n_samp = (int)(min(g0 + p.S, p.G) - g0);
+    float4 mine = make_float4(0.0f, 0.0f, 0.0f, -1.0f);  // lane r: round r's sphere
     for (int rnd = 0; rnd < kRoundSlots; ++rnd) {
       const int base = 31 * rnd;
       float4 sph = make_float4(0.0f, 0.0f, 0.0f, -1.0f);
@@ -444,7 +445,22 @@ __global__ void __launch_bounds__(256) round_bounds_kernel(const __grid_constant
         p.rsph[t * kRoundSlots + rnd] = sph;
         p.rout[t * kRoundSlots + rnd] = range;
       }
+      if (lane == rnd) mine = sph;
     }
+    // the tile's sphere: about the midpoint of its first and last live round
+    // centres, holding every round sphere (the radius bound as in
+    // cover_radius; the round radii are upper bounds already)
+    const bool on = mine.w >= 0.0f;
+    const uint32_t live = __ballot_sync(0xffffffffu, on);
+    float4 ts = make_float4(0.0f, 0.0f, 0.0f, -1.0f);
+    if (live) {
+      const int lo = __ffs(live) - 1, hi = 31 - __clz(live);
+      const float cx = 0.5f * (__shfl_sync(0xffffffffu, mine.x, lo) + __shfl_sync(0xffffffffu, mine.x, hi));
+      const float cy = 0.5f * (__shfl_sync(0xffffffffu, mine.y, lo) + __shfl_sync(0xffffffffu, mine.y, hi));
+      const float cz = 0.5f * (__shfl_sync(0xffffffffu, mine.z, lo) + __shfl_sync(0xffffffffu, mine.z, hi));
+      ts = make_float4(cx, cy, cz, cover_radius(mine.x, mine.y, mine.z, mine.w, on, cx, cy, cz));
+    }
+    if (lane == 0) p.tsph[t] = ts;
   }
 }
 
@@ -470,6 +486,12 @@ __global__ void __launch_bounds__(256) round_filter_kernel(const __grid_constant
   const int nt = (int)min((uint64_t)32, P.total_tiles - t0);
   int staged = -1;
   bool listed = false;  // lane i: tile t0 + i goes on its roadmap's list
+  // lane i: the sphere about tile t0 + i's rounds (radius < 0: none)
+  float4 tile_s = make_float4(0.0f, 0.0f, 0.0f, -1.0f);
+  if (lane < nt) {
+    const ClassifyJob& Jl = P.job[MAXJ == 1 ? 0 : find_job(P, t0 + (uint64_t)lane)];
+    if (Jl.rcand) tile_s = Jl.tsph[t0 + (uint64_t)lane - Jl.tile_base];
+  }
   for (int i = 0; i < nt; ++i) {
     const uint64_t t = t0 + (uint64_t)i;
     const int jb = MAXJ == 1 ? 0 : find_job(P, t);
@@ -483,42 +505,39 @@ __global__ void __launch_bounds__(256) round_filter_kernel(const __grid_constant
       __syncwarp();
       staged = jb;
     }
+    // first the tile: its sphere against every box at once (lane b: box
+    // b).  A tile no box may reach is done: its rounds are not loaded and
+    // its candidate row is not written (the classify kernel reads the rows
+    // of listed tiles only)
+    const float ts_x = __shfl_sync(0xffffffffu, tile_s.x, i);
+    const float ts_y = __shfl_sync(0xffffffffu, tile_s.y, i);
+    const float ts_z = __shfl_sync(0xffffffffu, tile_s.z, i);
+    const float ts_r = __shfl_sync(0xffffffffu, tile_s.w, i);
+    if (ts_r < 0.0f) continue;
+    bool cb = false;
+    if (lane < C) {
+      const float4 b0 = bx[6 * lane];
+      const float ex = b0.x - ts_x, ey = b0.y - ts_y, ez = b0.z - ts_z;
+      const float thr = (ts_r + b0.w + J.margin) * (1.0f + 1e-5f) + 1e-5f;
+      cb = fmaf(ex, ex, fmaf(ey, ey, ez * ez)) <= thr * thr;
+    }
+    const uint32_t tile_cand = __ballot_sync(0xffffffffu, cb);
+    if (tile_cand == 0u) continue;
+    // then the rounds, against the boxes the tile's sphere may reach
     const uint64_t slot = (t - J.tile_base) * kRoundSlots + lane;
     const float4 sph = lane < kRoundSlots - 1 ? J.rsph[slot] : make_float4(0.0f, 0.0f, 0.0f, -1.0f);
     const bool on = sph.w >= 0.0f;
-    const uint32_t live = __ballot_sync(0xffffffffu, on);
     uint32_t m = 0;
-    if (live) {
-      // first the tile: a sphere about its rounds' spheres (centred on the
-      // midpoint of the first and the last live round's centres), against
-      // every box at once (lane b: box b); only the boxes it may reach are
-      // tested against the rounds
-      const int lo = __ffs(live) - 1, hi = 31 - __clz(live);
-      const float cx = 0.5f * (__shfl_sync(0xffffffffu, sph.x, lo) + __shfl_sync(0xffffffffu, sph.x, hi));
-      const float cy = 0.5f * (__shfl_sync(0xffffffffu, sph.y, lo) + __shfl_sync(0xffffffffu, sph.y, hi));
-      const float cz = 0.5f * (__shfl_sync(0xffffffffu, sph.z, lo) + __shfl_sync(0xffffffffu, sph.z, hi));
-      const float dx = sph.x - cx, dy = sph.y - cy, dz = sph.z - cz;
-      const float reach = on ? sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) + sph.w : 0.0f;
-      const float rt = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(reach)));
-      bool cb = false;
-      if (lane < C) {
-        const float4 b0 = bx[6 * lane];
-        const float ex = b0.x - cx, ey = b0.y - cy, ez = b0.z - cz;
-        const float thr = (rt + b0.w + J.margin) * (1.0f + 1e-5f) + 1e-5f;
-        cb = fmaf(ex, ex, fmaf(ey, ey, ez * ez)) <= thr * thr;
-      }
-      const uint32_t tile_cand = __ballot_sync(0xffffffffu, cb);
-      if (on) {
-        const float thr = (sph.w + J.margin) * (1.0f + 1e-6f) + 1e-5f;
-        const float thr2 = thr * thr;
-        for (uint32_t mm = tile_cand; mm; mm &= mm - 1) {
-          const int b = __ffs(mm) - 1;
-          const float4 b0 = bx[6 * b];
-          const float ex = sph.x - b0.x, ey = sph.y - b0.y, ez = sph.z - b0.z;
-          const float reach = thr + b0.w;  // the box lies in the sphere of radius |h|
-          if (fmaf(ex, ex, fmaf(ey, ey, ez * ez)) > reach * reach * (1.0f + 1e-6f)) continue;
-          if (box_dist2(sph.x, sph.y, sph.z, bx + 6 * b) <= thr2) m |= 1u << b;
-        }
+    if (on) {
+      const float thr = (sph.w + J.margin) * (1.0f + 1e-6f) + 1e-5f;
+      const float thr2 = thr * thr;
+      for (uint32_t mm = tile_cand; mm; mm &= mm - 1) {
+        const int b = __ffs(mm) - 1;
+        const float4 b0 = bx[6 * b];
+        const float ex = sph.x - b0.x, ey = sph.y - b0.y, ez = sph.z - b0.z;
+        const float reach = thr + b0.w;  // the box lies in the sphere of radius |h|
+        if (fmaf(ex, ex, fmaf(ey, ey, ez * ez)) > reach * reach * (1.0f + 1e-6f)) continue;
+        if (box_dist2(sph.x, sph.y, sph.z, bx + 6 * b) <= thr2) m |= 1u << b;
       }
     }
     // the last slot (never a round: tiles have at most 31 rounds) holds the

@@ -193,6 +193,7 @@ struct RoundBoundsParams {
   uint32_t S;
   float4* rsph;               // [T][kRoundSlots]
   uint32_t* rout;             // [T][kRoundSlots]
+  float4* tsph;               // [T] a sphere about each tile's round spheres
 };
 
 size_t classify_smem_bytes(int variant, uint32_t consumer_warps);
