@@ -500,16 +500,17 @@ int rgg_load(rgg_roadmap_t r, const char* path, void* stream);
  * records; rgg_set_round_filter(r, 0 or 1) overrides the default.
  * While it is on, every round of 31 configurations of a tile
  * (rgg_info.tile_samples configurations per tile) has a bounding sphere of
- * its outer spheres (24 B per round slot, 32 slots per tile, computed when it
- * is switched on and whenever the tiles change).  Before each pass a small
- * kernel tests those spheres against the pass's moved boxes (exact box
- * distance, radius plus margin, FP32 slack 1e-5 m); the classify kernel skips
- * a tile no box may reach, copies only the runs of rounds some box may
- * reach, and tests only the boxes that may reach each round.  Labels and box
- * sets are the same with and without it (a round no box reaches holds no
- * touch).  It applies with the default launch shape only (rgg_info.
- * round_filter reports whether it is active).  Its round data take 24 B per
- * round slot (32 per tile).
+ * its outer spheres and every tile a sphere holding its rounds' spheres
+ * (computed when it is switched on and whenever the tiles change).  Before
+ * each pass a small kernel tests those spheres against the pass's moved
+ * boxes (exact box distance, radius plus margin, FP32 slack 1e-5 m) and lists
+ * the tiles some box may reach; the classify kernel takes only the listed
+ * tiles, copies only their runs of rounds some box may reach, and tests only
+ * the boxes that may reach each round.  Labels and box sets are the same with
+ * and without it (a round no box reaches holds no touch).  It applies with
+ * the default launch shape only (rgg_info.round_filter reports whether it is
+ * active).  Its data take 24 B per round slot (32 per tile) plus 20 B per
+ * tile.
  * rgg_set_round_filter synchronises the device.  RGG_ERR_STATE on an
  * OBB-geometry roadmap.
  * rgg_streamed_bytes returns the record bytes (inner and outer planes, with
