@@ -275,7 +275,7 @@ class ClockSampler:
 
 
 ROUND_SLOT_BYTES = 16 + 4 + 4 + 4   # per (tile, round) slot: sphere, candidates written + read, range
-TILE_LIST_BYTES = 4 + 4             # per tile: its entry in the pass's tile list, written and read
+TILE_LIST_BYTES = 4 + 4 + 16        # per tile: its list entry written and read, its sphere read
 
 
 def algorithmic_bytes(info: dict, record_bytes_per_launch=None) -> int:
@@ -284,7 +284,8 @@ def algorithmic_bytes(info: dict, record_bytes_per_launch=None) -> int:
     sphere, 16 B per outer sphere; with the spatial filter: the rounds some
     moved box may reach, as counted on the device), each edge's pass result (hit and touch words, 8 B) and,
     with the filter, its per-round data (bounding sphere read, candidate
-    mask written and read, record range read) and its tile list.  Tile
+    mask written and read, record range read), its tile spheres and its tile
+    list.  Tile
     descriptors, edge tables and the moved boxes' records are overhead and
     not counted."""
     if record_bytes_per_launch is None or not info.get("round_filter"):

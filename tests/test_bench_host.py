@@ -44,7 +44,7 @@ def test_algorithmic_bytes():
     assert bench.algorithmic_bytes(info, 400) == 1000 + 80      # unfiltered: counter ignored
     f = dict(info, round_filter=1)
     # filtered: the copied record bytes, the pass bits and 28 B per round slot (32 per tile)
-    assert bench.algorithmic_bytes(f, 400) == 400 + 80 + (28 * 32 + 8) * 3
+    assert bench.algorithmic_bytes(f, 400) == 400 + 80 + (28 * 32 + 24) * 3
 
 
 def test_clock_sampler_summary(tmp_path):
