@@ -793,7 +793,7 @@ int rgg_roadmap_create(const rgg_roadmap_desc* desc, rgg_roadmap_t* out) {
   if (e == cudaSuccess) e = dalloc(&r->d_changed, (size_t)kBoxAreaFloats);
   if (e == cudaSuccess) e = cudaMemset(r->d_changed, 0, (size_t)kBoxAreaFloats * sizeof(float));
   if (e == cudaSuccess) e = dalloc(&r->d_status, 4);
-  if (e == cudaSuccess) e = dalloc(&r->d_work, 4);
+  if (e == cudaSuccess) e = dalloc(&r->d_work, 6);
   if (e == cudaSuccess) e = dalloc(&r->d_count, 3);
   if (e == cudaSuccess) e = cudaMemset(r->d_count, 0, 3 * sizeof(unsigned long long));
   if (e == cudaSuccess) e = dalloc(&r->d_obbwork, 2);

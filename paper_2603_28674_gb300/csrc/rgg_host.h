@@ -126,6 +126,7 @@ struct EdgeState {
   double* d_qb = nullptr;
   uint8_t* d_resolved = nullptr;  // [N] labels of the last gray resolution
   float* d_clear = nullptr;       // [N] its clearances
+  uint32_t* d_gray = nullptr;     // [N] the gray edges a resolution lists
   // OBB / spline geometry (Sec. 4.2): boxes per (edge, body), spline CSR,
   // the uniform grid over the boxes, and the per-pass work list
   float4* d_obb = nullptr;        // [N * L][4]
@@ -170,6 +171,7 @@ struct EdgeState {
     cudaFree(d_qb);
     cudaFree(d_resolved);
     cudaFree(d_clear);
+    cudaFree(d_gray);
     cudaFree(d_obb);
     cudaFree(d_spl_off);
     cudaFree(d_spl_v);
@@ -209,7 +211,7 @@ struct rgg_roadmap {
   // the robot of edges built by rgg_build_edges (for the gray resolution)
   bool has_robot = false;
   double dh_a[RGG_MAX_LINKS], dh_alpha[RGG_MAX_LINKS], dh_d[RGG_MAX_LINKS], dh_radius[RGG_MAX_LINKS];
-  unsigned long long* d_work = nullptr;  // [4] resolution counters
+  unsigned long long* d_work = nullptr;  // [6] resolution counters and the gray list's cursors
   unsigned long long* d_count = nullptr; // [3] classify work counters (rgg_work_counts)
   bool counting = false;
   EdgeState es;

@@ -1491,15 +1491,15 @@ __device__ __forceinline__ float seg_box_dist2(const float p[3], const float dlt
   return best;
 }
 
-// One warp per edge.  Edges that are not gray keep their label.  For a gray
-// edge the warp gathers up to 32 boxes of its touch set at a time (only
-// boxes an outer sphere touched can meet the capsules) and lane k takes the
-// configurations k, k+32, ... of t_c = c / ((n_e - 1) F): FP32 kinematics,
-// then, per link and box, the capsule-axis-to-box distance minus the link
-// radius.  A (link, box) pair whose bounding spheres cannot beat the lane's
-// best is skipped, so the minimum is exact.  The warp stops at the first
-// clearance below -thr (RED); otherwise the edge is GREEN when the minimum
-// is at least thr, and stays GRAY in between.
+// Edges that are not gray keep their label.  A gray edge's block gathers up
+// to 32 boxes of its touch set at a time (only boxes an outer sphere touched
+// can meet the capsules) and thread k takes the configurations k, k+256, ...
+// of t_c = c / ((n_e - 1) F): FP32 kinematics, then, per link and box, the
+// capsule-axis-to-box distance minus the link radius.  A (link, box) pair
+// whose bounding spheres cannot beat the best so far is skipped, so the
+// minimum is exact.  The block stops after the first step with a clearance
+// below -thr (RED); otherwise the edge is GREEN when the minimum is at least
+// thr, and stays GRAY in between.
 // Order-preserving map of a float onto an unsigned int (for atomicMin).
 __device__ __forceinline__ uint32_t float_key(float f) {
   const uint32_t b = __float_as_uint(f);
@@ -1509,10 +1509,35 @@ __device__ __forceinline__ float key_float(uint32_t k) {
   return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
 }
 
+// Lists the gray edges (one warp-aggregated atomic per warp, in no
+// particular order) for resolve_gray_kernel, and passes every other edge's
+// label through.
+__global__ void __launch_bounds__(256) gray_list_kernel(const __grid_constant__ ResolveParams p) {
+  const uint32_t lane = threadIdx.x & 31;
+  for (uint64_t e0 = (uint64_t)blockIdx.x * blockDim.x; e0 < p.n_edges;
+       e0 += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t e = e0 + threadIdx.x;
+    const uint8_t lab = e < p.n_edges ? p.labels[e] : 0;
+    const bool gray = e < p.n_edges && lab == 1;
+    if (e < p.n_edges && !gray) {
+      p.out[e] = lab;
+      p.clearance[e] = __int_as_float(0x7fc00000);
+    }
+    const uint32_t m = __ballot_sync(0xffffffffu, gray);
+    unsigned long long at = 0;
+    if (lane == 0 && m) at = atomicAdd(&p.work[4], (unsigned long long)__popc(m));
+    at = __shfl_sync(0xffffffffu, at, 0);
+    if (gray) p.gray[at + __popc(m & ((1u << lane) - 1u))] = (uint32_t)e;
+  }
+}
+
 __global__ void __launch_bounds__(256) resolve_gray_kernel(const __grid_constant__ ResolveParams p) {
   // One block per gray edge at a time: its 256 threads take the edge's
   // configurations in steps of 256 (a long edge no longer runs on one warp).
+  // Blocks take the listed gray edges one at a time from a shared cursor, so
+  // that the long edges do not pile up on a few blocks.
   __shared__ float s_box[32][16];
+  __shared__ uint64_t s_e;
   // per joint: the start angle and the step per configuration, each as an
   // FP32 pair (high part, remainder) of its FP64 value
   __shared__ float4 s_q[kMaxBuildLinks];
@@ -1523,15 +1548,15 @@ __global__ void __launch_bounds__(256) resolve_gray_kernel(const __grid_constant
   const uint32_t lane = tid & 31;
   const uint32_t wib = tid >> 5;
   const uint32_t L = p.L, Wm = p.Wm;
-  for (uint64_t e = blockIdx.x; e < p.n_edges; e += gridDim.x) {
-    const uint8_t lab = p.labels[e];
-    if (lab != 1) {
-      if (tid == 0) {
-        p.out[e] = lab;
-        p.clearance[e] = __int_as_float(0x7fc00000);
-      }
-      continue;
+  const uint64_t n_gray = min((uint64_t)p.work[4], p.n_edges);
+  for (;;) {
+    if (tid == 0) {
+      const unsigned long long i = atomicAdd(&p.work[5], 1ull);
+      s_e = i < n_gray ? (uint64_t)p.gray[i] : ~0ull;
     }
+    __syncthreads();
+    const uint64_t e = s_e;
+    if (e == ~0ull) break;
     const uint64_t n = p.soff[e + 1] - p.soff[e];
     const uint64_t m = (n - 1) * (uint64_t)p.F;
     const uint32_t* tw = p.touch + e * Wm;
@@ -1813,8 +1838,13 @@ cudaError_t launch_round_bounds(const RoundBoundsParams& p, int num_sms, cudaStr
 
 cudaError_t launch_resolve_gray(const ResolveParams& p, int num_sms, cudaStream_t s) {
   if (p.n_edges == 0) return cudaSuccess;
-  // a block per edge at a time; as many blocks as are resident at once, so
-  // that every block starts with the launch
+  // the gray edges first (work[4] and work[5] start at zero)
+  const uint64_t lb = (p.n_edges + 255) / 256, lcap = (uint64_t)num_sms * 8;
+  gray_list_kernel<<<(unsigned)(lb < lcap ? lb : lcap), 256, 0, s>>>(p);
+  const cudaError_t le = cudaGetLastError();
+  if (le != cudaSuccess) return le;
+  // a block per gray edge at a time; as many blocks as are resident at once,
+  // so that every block starts with the launch
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, resolve_gray_kernel, 256, 0) !=
           cudaSuccess || per_sm < 1)

@@ -119,7 +119,9 @@ struct ResolveParams {
   const float* table;               // [M][16] box poses
   uint8_t* out;                     // [N] resolved labels
   float* clearance;                 // [N] minimum clearance found (NaN: not gray)
-  unsigned long long* work;         // [4]: gray edges, red, green, segment-box evaluations
+  unsigned long long* work;         // [6]: gray edges, red, green, segment-box evaluations,
+                                    // gray edges listed, gray edges taken
+  uint32_t* gray;                   // [N] the gray edges, in no particular order
   uint64_t n_edges;
 };
 

@@ -23,14 +23,19 @@ int rgg_resolve_gray(rgg_roadmap_t r, uint32_t factor, uint8_t* labels_out, floa
   if (N && !es.d_resolved) {
     cudaError_t e = dalloc(&es.d_resolved, N);
     if (e == cudaSuccess) e = dalloc(&es.d_clear, N);
+    if (e == cudaSuccess) e = dalloc(&es.d_gray, N);
     if (e != cudaSuccess) {
       cudaFree(es.d_resolved);
+      cudaFree(es.d_clear);
+      cudaFree(es.d_gray);
       es.d_resolved = nullptr;
+      es.d_clear = nullptr;
+      es.d_gray = nullptr;
       return cuda_status(e);
     }
-    es.device_bytes += 5 * N;
+    es.device_bytes += 9 * N;
   }
-  RGG_CK(cudaMemsetAsync(r->d_work, 0, 4 * sizeof(unsigned long long), s));
+  RGG_CK(cudaMemsetAsync(r->d_work, 0, 6 * sizeof(unsigned long long), s));
   ResolveParams p{};
   p.L = r->L;
   p.Wm = r->Wm;
@@ -53,6 +58,7 @@ int rgg_resolve_gray(rgg_roadmap_t r, uint32_t factor, uint8_t* labels_out, floa
   p.out = es.d_resolved;
   p.clearance = es.d_clear;
   p.work = r->d_work;
+  p.gray = es.d_gray;
   p.n_edges = N;
   RGG_CK(launch_resolve_gray(p, r->num_sms, s));
   const cudaMemcpyKind kind = dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
