@@ -464,12 +464,19 @@ __global__ void __launch_bounds__(256) round_bounds_kernel(const __grid_constant
   }
 }
 
+// Tiles per warp of the filter kernel (at most 32: lane i holds tile i's
+// sphere and list flag).  Fewer tiles per warp give more, shorter blocks, so
+// the launch's last wave of blocks is a smaller part of it.
+constexpr int kFilterTilesPerWarp = 16;
+static_assert(kFilterTilesPerWarp >= 1 && kFilterTilesPerWarp <= 32, "filter tiles per warp");
+
 // Before a pass: per (tile, round), the moved boxes whose exact distance
 // from the round's bounding sphere centre is within its radius plus the
 // margin.  Any outer sphere of the round lies inside the bounding sphere, so
 // a box that touches one of them (distance <= r + margin) passes this test;
-// the slack covers FP32 rounding in both tests.  One warp per 32 consecutive
-// tiles, taken one after the other, one lane per round.  The warp stages its
+// the slack covers FP32 rounding in both tests.  One warp per
+// kFilterTilesPerWarp consecutive tiles, taken one after the other, one lane
+// per round.  The warp stages its
 // roadmap's box records in shared memory (again when the roadmap changes).
 // A sphere about the tile's round spheres is tested against all boxes first;
 // only the boxes it may reach are tested per round, and there a box whose
@@ -480,10 +487,11 @@ template <int MAXJ>
 __global__ void __launch_bounds__(256) round_filter_kernel(const __grid_constant__ ClassifyParams<MAXJ> P) {
   __shared__ float4 s_bx[8][kBoxesPerPass * 6];
   const int lane = threadIdx.x & 31;
-  const uint64_t t0 = (((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32;
+  const uint64_t t0 =
+      (((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * (uint64_t)kFilterTilesPerWarp;
   if (t0 >= P.total_tiles) return;  // whole warps: t0 is the same on every lane
   float4* bx = s_bx[threadIdx.x >> 5];
-  const int nt = (int)min((uint64_t)32, P.total_tiles - t0);
+  const int nt = (int)min((uint64_t)kFilterTilesPerWarp, P.total_tiles - t0);
   int staged = -1;
   bool listed = false;  // lane i: tile t0 + i goes on its roadmap's list
   // lane i: the sphere about tile t0 + i's rounds (radius < 0: none)
@@ -1119,15 +1127,20 @@ __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const 
         any_cand = cand;
         const float rt = r + margin;
         const float rt2 = rt * rt;
-        // two candidate boxes per iteration for instruction-level parallelism
+        // two candidate boxes per iteration for instruction-level parallelism,
+        // and a last single box on its own (cand is the same on every lane)
         while (cand) {
           const int b0 = __ffs(cand) - 1;
           cand &= cand - 1;
-          const int b1 = cand ? __ffs(cand) - 1 : b0;
-          cand &= cand - 1;
-          const float d0 = box_dist2(x, y, z, bx + 6 * b0);
-          const float d1 = box_dist2(x, y, z, bx + 6 * b1);
-          bits |= (d0 <= rt2 ? 1u << b0 : 0u) | (d1 <= rt2 ? 1u << b1 : 0u);
+          if (cand) {
+            const int b1 = __ffs(cand) - 1;
+            cand &= cand - 1;
+            const float d0 = box_dist2(x, y, z, bx + 6 * b0);
+            const float d1 = box_dist2(x, y, z, bx + 6 * b1);
+            bits |= (d0 <= rt2 ? 1u << b0 : 0u) | (d1 <= rt2 ? 1u << b1 : 0u);
+          } else {
+            bits |= box_dist2(x, y, z, bx + 6 * b0) <= rt2 ? 1u << b0 : 0u;
+          }
         }
         if (!has_next) bits = 0;
         if (bits) atomicOr(&acc_touch[j], bits);
@@ -1790,8 +1803,10 @@ static cudaError_t launch_classify_t(const ClassifyParams<MAXJ>& p, const Classi
   bool filtered = false;
   for (uint32_t j = 0; j < p.njobs && j < (uint32_t)MAXJ; ++j) filtered |= p.job[j].rcand != nullptr;
   if (filtered && p.total_tiles) {
-    // a warp per 32 tiles
-    round_filter_kernel<MAXJ><<<(unsigned)((p.total_tiles + 255) / 256), 256, 0, s>>>(p);
+    // a warp per kFilterTilesPerWarp tiles, 8 warps per block
+    constexpr uint64_t per_block = 8 * (uint64_t)kFilterTilesPerWarp;
+    round_filter_kernel<MAXJ>
+        <<<(unsigned)((p.total_tiles + per_block - 1) / per_block), 256, 0, s>>>(p);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
