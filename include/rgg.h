@@ -358,8 +358,9 @@ int rgg_roadmap_info(rgg_roadmap_t r, rgg_info* out);
 int rgg_check_status(rgg_roadmap_t r, void* stream);
 
 /* Limit, in nanoseconds of wall time, of every bounded wait in the classify
- * kernel (a consumer warp waiting for its tile's records, the producer
- * waiting for a free stage).  A wait that runs out ends the launch with
+ * kernel (a worker warp waiting for its tile's records or for the box
+ * records, a refilling warp waiting for the stage's prefetched tile
+ * metadata).  A wait that runs out ends the launch with
  * RGG_ERR_TIMEOUT latched (see the top).  The default, 4 s, is far above any
  * wait of a healthy launch (microseconds); very small limits exist to test
  * the failure path.  RGG_ERR_INVALID for 0. */
@@ -371,6 +372,20 @@ int rgg_set_wait_limit(rgg_roadmap_t r, uint64_t limit_ns);
  * RGG_ERR_OOM with the roadmap unchanged.  0 turns it off; it also turns off
  * by itself once it has fired.  The paper has no counterpart. */
 int rgg_inject_alloc_failure(uint64_t nth);
+
+/* Guard bytes, a check for writes past the end of a buffer where no memory
+ * checker can run: every device buffer the library allocates is followed by
+ * 64 bytes of a fixed pattern (0xA5) at its requested size rounded up to
+ * 16 B.  rgg_check_guards synchronises each device that holds library buffers
+ * (so it waits for all work on them), reads every live buffer's guard and
+ * stores, when the pointers are not NULL, the number of buffers checked and
+ * the number whose guard changed.  Returns RGG_OK when every guard is intact,
+ * RGG_ERR_STATE when one changed (a kernel or copy wrote past a buffer's end)
+ * and RGG_ERR_CUDA when a synchronisation or read failed.  Buffers are
+ * listed from allocation to release, so a call made while another thread
+ * creates or destroys roadmaps sees each buffer either whole or not at all.
+ * A debugging aid; the paper has no counterpart. */
+int rgg_check_guards(uint64_t* n_checked, uint64_t* n_bad);
 
 /* Device bytes a sphere-geometry roadmap created with `desc` holds once
  * rgg_build_edges(num_edges, q_from, q_to, step) has run: record planes,

@@ -4,6 +4,8 @@
 // geometry, persistence, the autotuner and step graphs, and the gray
 // resolution have their own host files.
 #include <atomic>
+#include <mutex>
+#include <unordered_map>
 
 #include "rgg_host.h"
 
@@ -17,6 +19,19 @@ namespace rgg_host {
 // of memory.
 static std::atomic<uint64_t> g_fail_countdown{0};
 
+// Guard bytes: every allocation holds kGuardBytes of the byte kGuardByte
+// after its requested size (rounded up to 16 B), and the live allocations are
+// listed here with the offset of their guard and their device, so that
+// rgg_check_guards can tell whether anything wrote past the end of a buffer.
+constexpr size_t kGuardBytes = 64;
+constexpr unsigned char kGuardByte = 0xA5;
+struct Guarded {
+  size_t offset;
+  int device;
+};
+static std::mutex g_guard_mu;
+static std::unordered_map<void*, Guarded> g_guards;
+
 cudaError_t device_alloc(void** p, size_t bytes) {
   uint64_t c = g_fail_countdown.load();
   while (c != 0) {
@@ -28,7 +43,32 @@ cudaError_t device_alloc(void** p, size_t bytes) {
       break;
     }
   }
-  return cudaMalloc(p, bytes);
+  const size_t off = (bytes + 15) & ~(size_t)15;
+  cudaError_t e = cudaMalloc(p, off + kGuardBytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return e;
+  }
+  int dev = 0;
+  e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaMemset(static_cast<unsigned char*>(*p) + off, kGuardByte, kGuardBytes);
+  if (e != cudaSuccess) {
+    cudaFree(*p);
+    *p = nullptr;
+    return e;
+  }
+  std::lock_guard<std::mutex> lk(g_guard_mu);
+  g_guards[*p] = Guarded{off, dev};
+  return cudaSuccess;
+}
+
+void device_free(void* p) {
+  if (p == nullptr) return;
+  {
+    std::lock_guard<std::mutex> lk(g_guard_mu);
+    g_guards.erase(p);
+  }
+  cudaFree(p);
 }
 
 // Device bytes every roadmap holds whatever its edges: the box table, the
@@ -165,17 +205,17 @@ int set_tiles(rgg_roadmap* r, EdgeState* es, cudaStream_t s) {
   // the host vectors must outlive the copies
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
-    cudaFree(d_tiles);
-    cudaFree(d_etab);
-    cudaFree(d_halo);
+    device_free(d_tiles);
+    device_free(d_etab);
+    device_free(d_halo);
     return cuda_status(e);
   }
   release_rounds(es);  // they describe the old tiles
   es->device_bytes -= es->T * sizeof(TileDesc) + es->n_etab * sizeof(int4) +
                       (es->d_tile_halo ? es->T * sizeof(uint32_t) : 0);
-  cudaFree(es->d_tiles);
-  cudaFree(es->d_etab);
-  cudaFree(es->d_tile_halo);
+  device_free(es->d_tiles);
+  device_free(es->d_etab);
+  device_free(es->d_tile_halo);
   es->d_tiles = d_tiles;
   es->d_etab = d_etab;
   es->d_tile_halo = d_halo;
@@ -197,10 +237,10 @@ uint64_t round_data_bytes(uint64_t T) {
 
 void release_rounds(EdgeState* es) {
   if (es->d_rsph) es->device_bytes -= round_data_bytes(es->T);
-  cudaFree(es->d_rsph);
-  cudaFree(es->d_rout);
-  cudaFree(es->d_rcand);
-  cudaFree(es->d_tlist);
+  device_free(es->d_rsph);
+  device_free(es->d_rout);
+  device_free(es->d_rcand);
+  device_free(es->d_tlist);
   es->d_rsph = nullptr;
   es->d_rout = nullptr;
   es->d_rcand = nullptr;
@@ -235,10 +275,10 @@ int compute_rounds(rgg_roadmap* r, EdgeState* es, cudaStream_t s) {
   if (e == cudaSuccess) e = dalloc(&es->d_tlist, es->T + 1);
   if (e == cudaSuccess) e = cudaMemsetAsync(es->d_tlist, 0, (es->T + 1) * sizeof(uint32_t), s);
   if (e != cudaSuccess) {
-    cudaFree(es->d_rsph);
-    cudaFree(es->d_rout);
-    cudaFree(es->d_rcand);
-    cudaFree(es->d_tlist);
+    device_free(es->d_rsph);
+    device_free(es->d_rout);
+    device_free(es->d_rcand);
+    device_free(es->d_tlist);
     es->d_rsph = nullptr;
     es->d_rout = nullptr;
     es->d_rcand = nullptr;
@@ -803,14 +843,14 @@ int rgg_roadmap_create(const rgg_roadmap_desc* desc, rgg_roadmap_t* out) {
   if (e == cudaSuccess) e = cudaMemset(r->d_table, 0, (size_t)r->M * 16 * sizeof(float));
   if (e == cudaSuccess) e = cudaMemset(r->d_status, 0, 4 * sizeof(int));
   if (e != cudaSuccess) {
-    cudaFree(r->d_table);
-    cudaFree(r->d_stage);
-    cudaFree(r->d_changed);
-    cudaFree(r->d_status);
-    cudaFree(r->d_work);
-    cudaFree(r->d_count);
-    cudaFree(r->d_obbwork);
-    cudaFree(r->d_streamed);
+    device_free(r->d_table);
+    device_free(r->d_stage);
+    device_free(r->d_changed);
+    device_free(r->d_status);
+    device_free(r->d_work);
+    device_free(r->d_count);
+    device_free(r->d_obbwork);
+    device_free(r->d_streamed);
     delete r;
     return cuda_status(e);
   }
@@ -823,14 +863,14 @@ int rgg_roadmap_destroy(rgg_roadmap_t r) {
   DeviceGuard g(r->device);
   cudaDeviceSynchronize();
   r->es.release();
-  cudaFree(r->d_table);
-  cudaFree(r->d_stage);
-  cudaFree(r->d_changed);
-  cudaFree(r->d_status);
-  cudaFree(r->d_work);
-  cudaFree(r->d_count);
-  cudaFree(r->d_obbwork);
-  cudaFree(r->d_streamed);
+  device_free(r->d_table);
+  device_free(r->d_stage);
+  device_free(r->d_changed);
+  device_free(r->d_status);
+  device_free(r->d_work);
+  device_free(r->d_count);
+  device_free(r->d_obbwork);
+  device_free(r->d_streamed);
   for (auto& ev : r->events)
     for (cudaEvent_t x : ev) cudaEventDestroy(x);
   delete r;
@@ -918,10 +958,10 @@ int rgg_build_edges(rgg_roadmap_t r, const rgg_robot_desc* robot, uint64_t num_e
   if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   auto cleanup = [&]() {
-    cudaFree(d_qa);
-    cudaFree(d_qb);
-    cudaFree(d_counts);
-    cudaFree(d_bad);
+    device_free(d_qa);
+    device_free(d_qb);
+    device_free(d_counts);
+    device_free(d_bad);
   };
   if (e != cudaSuccess) {
     cleanup();
@@ -971,11 +1011,11 @@ int rgg_build_edges(rgg_roadmap_t r, const rgg_robot_desc* robot, uint64_t num_e
     e = launch_build_records(bp, r->num_sms, s);
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  cudaFree(d_counts);
-  cudaFree(d_bad);
+  device_free(d_counts);
+  device_free(d_bad);
   if (e != cudaSuccess) {
-    cudaFree(d_qa);
-    cudaFree(d_qb);
+    device_free(d_qa);
+    device_free(d_qb);
     es.release();
     return cuda_status(e);
   }
@@ -1332,6 +1372,57 @@ int rgg_set_wait_limit(rgg_roadmap_t r, uint64_t limit_ns) {
 int rgg_inject_alloc_failure(uint64_t nth) {
   g_fail_countdown.store(nth);
   return RGG_OK;
+}
+
+int rgg_check_guards(uint64_t* n_checked, uint64_t* n_bad) {
+  std::lock_guard<std::mutex> lk(g_guard_mu);
+  uint64_t checked = 0, bad = 0;
+  int prev = -1;
+  if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+  int status = RGG_OK;
+  std::vector<int> synced;
+  unsigned char got[kGuardBytes];
+  for (const auto& kv : g_guards) {
+    const int dev = kv.second.device;
+    if (cudaSetDevice(dev) != cudaSuccess) {
+      status = RGG_ERR_CUDA;
+      break;
+    }
+    if (std::find(synced.begin(), synced.end(), dev) == synced.end()) {
+      if (cudaDeviceSynchronize() != cudaSuccess) {
+        status = RGG_ERR_CUDA;
+        break;
+      }
+      synced.push_back(dev);
+    }
+    // read only what the runtime still knows as device memory: a buffer
+    // released without device_free would be an address nothing backs (it is
+    // counted as changed, since its guard cannot be read)
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, kv.first) != cudaSuccess || at.type != cudaMemoryTypeDevice) {
+      cudaGetLastError();
+      ++checked;
+      ++bad;
+      continue;
+    }
+    if (cudaMemcpy(got, static_cast<const unsigned char*>(kv.first) + kv.second.offset, kGuardBytes,
+                   cudaMemcpyDeviceToHost) != cudaSuccess) {
+      status = RGG_ERR_CUDA;
+      break;
+    }
+    ++checked;
+    for (size_t i = 0; i < kGuardBytes; ++i)
+      if (got[i] != kGuardByte) {
+        ++bad;
+        break;
+      }
+  }
+  if (prev >= 0) cudaSetDevice(prev);
+  if (status != RGG_OK) cudaGetLastError();
+  if (n_checked) *n_checked = checked;
+  if (n_bad) *n_bad = bad;
+  if (status == RGG_OK && bad) status = RGG_ERR_STATE;
+  return status;
 }
 
 int rgg_estimate_bytes(const rgg_roadmap_desc* desc, uint64_t num_edges, const double* q_from,

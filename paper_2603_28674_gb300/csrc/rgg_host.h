@@ -44,8 +44,11 @@ inline int cuda_status(cudaError_t e) {
   } while (0)
 
 // Every device allocation of the library goes through here, so that a test
-// can make the n-th one fail (rgg_inject_alloc_failure).
+// can make the n-th one fail (rgg_inject_alloc_failure) and so that each
+// buffer carries guard bytes after its end (rgg_check_guards).  Buffers from
+// device_alloc are released with device_free.
 cudaError_t device_alloc(void** p, size_t bytes);
+void device_free(void* p);
 
 template <class T>
 cudaError_t dalloc(T** p, size_t count) {
@@ -156,34 +159,34 @@ struct EdgeState {
   uint32_t max_n = 0;
 
   void release() {
-    cudaFree(d_soff);
-    cudaFree(d_inner);
-    cudaFree(d_outer);
-    cudaFree(d_tiles);
-    cudaFree(d_etab);
-    cudaFree(d_red);
-    cudaFree(d_touch);
-    cudaFree(d_counts);
-    cudaFree(d_labels);
-    cudaFree(d_edge_acc);
-    cudaFree(d_hist);
-    cudaFree(d_qa);
-    cudaFree(d_qb);
-    cudaFree(d_resolved);
-    cudaFree(d_clear);
-    cudaFree(d_gray);
-    cudaFree(d_obb);
-    cudaFree(d_spl_off);
-    cudaFree(d_spl_v);
-    cudaFree(d_cell_off);
-    cudaFree(d_cell_items);
-    cudaFree(d_pairs);
-    cudaFree(d_qcnt);
-    cudaFree(d_rsph);
-    cudaFree(d_rout);
-    cudaFree(d_rcand);
-    cudaFree(d_tlist);
-    cudaFree(d_tile_halo);
+    device_free(d_soff);
+    device_free(d_inner);
+    device_free(d_outer);
+    device_free(d_tiles);
+    device_free(d_etab);
+    device_free(d_red);
+    device_free(d_touch);
+    device_free(d_counts);
+    device_free(d_labels);
+    device_free(d_edge_acc);
+    device_free(d_hist);
+    device_free(d_qa);
+    device_free(d_qb);
+    device_free(d_resolved);
+    device_free(d_clear);
+    device_free(d_gray);
+    device_free(d_obb);
+    device_free(d_spl_off);
+    device_free(d_spl_v);
+    device_free(d_cell_off);
+    device_free(d_cell_items);
+    device_free(d_pairs);
+    device_free(d_qcnt);
+    device_free(d_rsph);
+    device_free(d_rout);
+    device_free(d_rcand);
+    device_free(d_tlist);
+    device_free(d_tile_halo);
     *this = EdgeState();
   }
 };

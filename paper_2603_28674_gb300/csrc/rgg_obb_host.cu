@@ -29,8 +29,8 @@ int build_obb(rgg_roadmap* r, EdgeState* es, const rgg_robot_desc* robot, const 
   uint32_t* d_count = nullptr;
   cudaError_t e = cudaSuccess;
   auto done = [&](int rc) {
-    cudaFree(scratch);
-    cudaFree(d_count);
+    device_free(scratch);
+    device_free(d_count);
     return rc;
   };
 #define RGG_OB(ptr, cnt)                        \
@@ -79,7 +79,7 @@ int build_obb(rgg_roadmap* r, EdgeState* es, const rgg_robot_desc* robot, const 
   if (e == cudaSuccess) e = launch_obb_build(bp, (uint32_t)warps, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return done(cuda_status(e));
-  cudaFree(scratch);
+  device_free(scratch);
   scratch = nullptr;
   // ---- the grid
   GridSpec g{};
@@ -94,7 +94,7 @@ int build_obb(rgg_roadmap* r, EdgeState* es, const rgg_robot_desc* robot, const 
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(part.data(), d_part, part.size() * sizeof(float), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    cudaFree(d_part);
+    device_free(d_part);
     if (e != cudaSuccess) return done(cuda_status(e));
     float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
     double side = 0.0;
@@ -136,7 +136,7 @@ int build_obb(rgg_roadmap* r, EdgeState* es, const rgg_robot_desc* robot, const 
     e = cudaMemcpyAsync(cc.data(), d_cc, cc.size() * sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
-    cudaFree(d_cc);
+    device_free(d_cc);
     return done(cuda_status(e));
   }
   std::vector<uint32_t> coff(es->n_cells + 1, 0);
@@ -144,7 +144,7 @@ int build_obb(rgg_roadmap* r, EdgeState* es, const rgg_robot_desc* robot, const 
   for (uint32_t c = 0; c < es->n_cells; ++c) {
     items += cc[c];
     if (items > 0xffffffffull) {
-      cudaFree(d_cc);
+      device_free(d_cc);
       return done(RGG_ERR_CAPACITY);
     }
     coff[c + 1] = (uint32_t)items;
@@ -161,7 +161,7 @@ int build_obb(rgg_roadmap* r, EdgeState* es, const rgg_robot_desc* robot, const 
   gp.pass = 1;
   if (e == cudaSuccess) e = launch_obb_grid(gp, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  cudaFree(d_cc);
+  device_free(d_cc);
   // every moved box may list every chunk of every cell, at the smallest chunk
   es->pair_cap = (uint32_t)std::min<uint64_t>(
       0xffffffffull, (uint64_t)kBoxesPerPass * (es->n_cells + items / kObbChunkMin + 1));

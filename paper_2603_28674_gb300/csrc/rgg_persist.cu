@@ -212,7 +212,7 @@ int rgg_load(rgg_roadmap_t r, const char* path, void* stream) {
   if (rc == RGG_OK && stored != io.hash.digest()) rc = RGG_ERR_INVALID;
   if (rc != RGG_OK) {
     es.release();
-    cudaFree(d_table);
+    device_free(d_table);
     return rc;
   }
   // the file checks out: swap in the edges, the state and the boxes
@@ -223,7 +223,7 @@ int rgg_load(rgg_roadmap_t r, const char* path, void* stream) {
     e = cudaMemcpyAsync(r->d_changed + kBoxesPerPass * kBoxRecFloats, link_r, sizeof(link_r),
                         cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  cudaFree(d_table);
+  device_free(d_table);
   if (e != cudaSuccess) {
     es.release();
     return cuda_status(e);

@@ -25,9 +25,9 @@ int rgg_resolve_gray(rgg_roadmap_t r, uint32_t factor, uint8_t* labels_out, floa
     if (e == cudaSuccess) e = dalloc(&es.d_clear, N);
     if (e == cudaSuccess) e = dalloc(&es.d_gray, N);
     if (e != cudaSuccess) {
-      cudaFree(es.d_resolved);
-      cudaFree(es.d_clear);
-      cudaFree(es.d_gray);
+      device_free(es.d_resolved);
+      device_free(es.d_clear);
+      device_free(es.d_gray);
       es.d_resolved = nullptr;
       es.d_clear = nullptr;
       es.d_gray = nullptr;

@@ -104,7 +104,7 @@ int rgg_autotune(rgg_roadmap_t* rs, uint32_t n, uint32_t reps, rgg_tune_result* 
   if (!any) return RGG_OK;  // nothing to time: the shape stays
   std::vector<uint32_t*> acc(n, nullptr);
   auto free_acc = [&]() {
-    for (uint32_t* p : acc) cudaFree(p);
+    for (uint32_t* p : acc) device_free(p);
   };
   for (uint32_t i = 0; i < n; ++i) {
     cudaError_t e = dalloc(&acc[i], 2 * rs[i]->es.N);

@@ -45,7 +45,7 @@ EXPORTS = (
     "rgg_step_graph_destroy", "rgg_save", "rgg_load", "rgg_resolve_gray", "rgg_fetch_boxes",
     "rgg_set_obb_filter", "rgg_obb_work", "rgg_fetch_obb_records", "rgg_set_round_filter",
     "rgg_streamed_bytes", "rgg_set_wait_limit", "rgg_inject_alloc_failure", "rgg_estimate_bytes",
-    "rgg_set_work_counting", "rgg_work_counts",
+    "rgg_set_work_counting", "rgg_work_counts", "rgg_check_guards",
 )
 
 
@@ -165,6 +165,7 @@ def _lib():
         "rgg_set_work_counting": [vp, i32],
         "rgg_work_counts": [vp, ctypes.POINTER(u64), ctypes.POINTER(u64), ctypes.POINTER(u64)],
         "rgg_inject_alloc_failure": [u64],
+        "rgg_check_guards": [ctypes.POINTER(u64), ctypes.POINTER(u64)],
         "rgg_estimate_bytes": [ctypes.POINTER(_Desc), u64, vp, vp, dbl, ctypes.POINTER(u64)],
     }
     for name, args in sig.items():
@@ -506,6 +507,18 @@ def inject_alloc_failure(nth: int) -> None:
     """Make the nth device allocation of the library from now fail (0: off);
     a test hook (rgg_inject_alloc_failure)."""
     _check("rgg_inject_alloc_failure", _lib().rgg_inject_alloc_failure(int(nth)))
+
+
+def check_guards() -> tuple:
+    """(buffers checked, buffers whose guard bytes changed) over every live
+    device buffer of the library (rgg_check_guards; synchronises the devices
+    that hold them).  A changed guard means something wrote past the end of
+    a buffer; it is reported in the count, not raised."""
+    checked, bad = ctypes.c_uint64(0), ctypes.c_uint64(0)
+    st = _lib().rgg_check_guards(ctypes.byref(checked), ctypes.byref(bad))
+    if st not in (RGG_OK, RGG_ERR_STATE):
+        _check("rgg_check_guards", st)
+    return int(checked.value), int(bad.value)
 
 
 def estimate_bytes(num_links: int, inner_per_link: int, max_obstacles: int, q_from, q_to,

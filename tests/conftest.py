@@ -33,3 +33,18 @@ def oracle():
     import oracle as _oracle
     _oracle._load()
     return _oracle
+
+
+@pytest.fixture(autouse=True)
+def _guard_bytes(request):
+    """After every GPU test: no library buffer had its guard bytes changed
+    (rgg_check_guards), i.e. nothing wrote past the end of a buffer."""
+    yield
+    if "gpu" not in request.keywords:
+        return
+    import torch
+    if not torch.cuda.is_available():
+        return
+    from paper_2603_28674_gb300 import rgg
+    checked, bad = rgg.check_guards()
+    assert bad == 0, f"{bad} of {checked} library buffers had their guard bytes changed"

@@ -2,7 +2,7 @@
 
 Device side: the classify kernel's bounded waits are given a limit of one
 nanosecond (rgg_set_wait_limit), so that a wait for a tile's records or for
-a free stage runs out in the first launch.  The launch then ends on its own
+the box records runs out in the first launch.  The launch then ends on its own
 (its copies drained), the error is latched, later passes are skipped, and
 the host reads RGG_ERR_TIMEOUT.  After that the roadmap must recover: the
 next classify with the normal limit re-tests every present box, and the
@@ -11,6 +11,11 @@ labels and box sets equal those of a fresh roadmap at the same poses.
 Host side: rgg_inject_alloc_failure makes the nth device allocation fail as
 if the device were full; every call that hits it returns RGG_ERR_OOM and
 leaves the roadmap usable and unchanged.
+
+Guard bytes: every library buffer is followed by 64 bytes of a fixed pattern
+(rgg_check_guards).  A byte of the label array's guard, which lies inside
+the allocation, is changed from the host side and must be reported; every
+GPU test also ends with a check that no guard changed (tests/conftest.py).
 """
 import numpy as np
 import pytest
@@ -188,3 +193,36 @@ def test_allocation_failures_leave_the_roadmap_usable(rgg):
     finally:
         rgg.inject_alloc_failure(0)
     assert {"create", "build", "rebuild", "request"} <= seen, seen
+
+
+def test_guard_bytes_report_a_write_past_a_buffer(rgg):
+    import torch
+    rm, boxes, ups = scene(n_nodes=200)
+    with rgg.Roadmap(rm.robot.num_links, rm.robot.inner_per_link, boxes.count) as r:
+        r.build_edges(rm.robot, rm.q_from, rm.q_to, rm.step)
+        r.update_obstacles(np.arange(boxes.count), boxes.poses().astype(np.float32))
+        r.classify()
+        for up in ups:
+            r.update_obstacles(up.ids, up.poses.astype(np.float32))
+            r.classify()
+        checked, bad = rgg.check_guards()
+        assert checked >= 10 and bad == 0
+        # the label array (N bytes) has its guard at N rounded up to 16 B:
+        # inside the allocation, so this host-side write stays in bounds
+        n = r.info()["num_edges"]
+        at = r.labels_device_ptr() + ((n + 15) & ~15)
+
+        class View:
+            __cuda_array_interface__ = {"shape": (1,), "typestr": "|u1", "data": (at, False),
+                                        "version": 3}
+
+        g = torch.as_tensor(View(), device="cuda")
+        assert int(g.item()) == 0xA5
+        g.fill_(0x5A)
+        torch.cuda.synchronize()
+        assert rgg.check_guards() == (checked, 1)
+        g.fill_(0xA5)
+        torch.cuda.synchronize()
+        assert rgg.check_guards() == (checked, 0)
+    # the roadmap's buffers are no longer listed once it is destroyed
+    assert rgg.check_guards()[0] <= checked - 10
