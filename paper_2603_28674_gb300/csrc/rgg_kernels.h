@@ -39,7 +39,7 @@ constexpr int kDefaultVariantLinkEnds = 7;
 constexpr uint32_t kDefaultConsumerWarpsLinkEnds = 27;
 // The spatial filter's kernel instance exists for the two default variants.
 constexpr bool filter_variant(int v) { return v == kDefaultVariant || v == kDefaultVariantLinkEnds; }
-constexpr int kMaxClassifyThreads = 896;  // producer warp + up to 27 consumer warps
+constexpr int kMaxClassifyThreads = 896;  // up to 28 worker warps
 struct VariantShape {
   int stages, stage_bytes, rounds, rounds_per_item;
 };
