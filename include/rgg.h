@@ -118,7 +118,7 @@ enum {
   RGG_MAX_INNER = 16,          /* inner_per_link                               */
   RGG_MAX_OBSTACLES = 4096,    /* max_obstacles                                */
   RGG_BOXES_PER_PASS = 32,     /* moved boxes tested per streaming pass        */
-  RGG_NUM_VARIANTS = 10,       /* compiled pipeline shapes (rgg_set_launch_shape) */
+  RGG_NUM_VARIANTS = 12,       /* compiled pipeline shapes (rgg_set_launch_shape) */
   RGG_MAX_REQUESTS = 64,       /* open requests per roadmap (rgg_update_request) */
   RGG_PENDING_EXTRA = 4096,    /* pending entries beyond max_obstacles          */
   RGG_MAX_RESOLVE_FACTOR = 100, /* rgg_resolve_gray: resampling factor           */
@@ -430,8 +430,10 @@ int rgg_work_counts(rgg_roadmap_t r, uint64_t* rounds, uint64_t* outer_tests,
 /* Launch shape of the streaming classify kernel: `variant` picks one of the
  * compiled pipeline shapes (shared-memory ring depth x stage size x rounds of
  * 31 configurations per tile; RGG_NUM_VARIANTS in all, 0 = smallest tiles,
- * 5 the default) and `consumer_warps` the warps per CTA that test records
- * (0 = default 24; 1..27).  With edges present the tiles are rebuilt for the new shape (the
+ * 5 the default for sphere records, 10 for link-end records; the spatial
+ * filter runs with variants 5, 7, 10 and 11 only) and `consumer_warps` the
+ * warps per CTA that test records (0 = the format's default, 24 for sphere
+ * records and 27 for link ends; 1..27).  With edges present the tiles are rebuilt for the new shape (the
  * call synchronises the device).  Roadmaps classified together by
  * rgg_classify_many must share the variant.  RGG_ERR_INVALID for an
  * unsupported shape (nothing changes). */

@@ -1466,7 +1466,8 @@ int rgg_estimate_bytes(const rgg_roadmap_desc* desc, uint64_t num_edges, const d
   uint32_t max_n = 0;
   for (uint64_t e = 0; e < N; ++e) max_n = std::max<uint64_t>(max_n, soff[e + 1] - soff[e]);
   if (N) {
-    const Tiling t = choose_tiling(L, K, G, 2 * (uint32_t)sms, kDefaultVariant, joints, max_n);
+    const Tiling t = choose_tiling(L, K, G, 2 * (uint32_t)sms,
+                                   joints ? kDefaultVariantLinkEnds : kDefaultVariant, joints, max_n);
     if (t.S == 0) return RGG_ERR_INVALID;
     std::vector<TileDesc> tiles;
     std::vector<int4> etab;

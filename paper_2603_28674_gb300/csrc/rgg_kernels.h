@@ -16,7 +16,10 @@ namespace rgg {
 // the tile's job's box records.
 // Variants 7..9 keep big tiles but hold more of them in flight: link-end
 // records need 12 B per sample instead of 16*K, so a 23..31-round tile fits
-// a 27..38 KB stage.
+// a 27..38 KB stage.  Variants 10 and 11 trade tile size for ring depth
+// (8 x 20-round and 10 x 16-round tiles): a sparse pass, whose tiles carry
+// few live rounds, is bound by how many tiles each CTA has in flight.  Every
+// shape also fits the batched launch, whose stages each keep a box area.
 #define RGG_VARIANTS(X)             \
   X(0, 14, 10 * 1024, 3, 1)        \
   X(1, 7, 28 * 1024, 9, 1)         \
@@ -27,18 +30,23 @@ namespace rgg {
   X(6, 4, 51 * 1024, 16, 2)        \
   X(7, 7, 27 * 1024, 23, 2)        \
   X(8, 6, 32 * 1024, 27, 1)        \
-  X(9, 5, 38 * 1024, 31, 1)
-constexpr int kNumVariants = 10;
+  X(9, 5, 38 * 1024, 31, 1)        \
+  X(10, 8, 23 * 1024, 20, 2)       \
+  X(11, 10, 18 * 1024, 16, 2)
+constexpr int kNumVariants = 12;
 // Default shapes: sphere records take variant 5 with 24 consumer warps;
-// link-end records (a third of the bytes per tile) variant 7, whose deeper
-// ring keeps more tiles in flight, with 27 (measured by the autotuner on the
-// large, mixed-label and 7-DOF roadmaps).
+// link-end records (a third of the bytes per tile) variant 10, whose deeper
+// ring keeps more tiles in flight, with 27: of the shapes timed on the large
+// dense, large mixed-label and 7-DOF roadmaps it was the one faster than
+// variant 7 on all three (variant 11 is faster still on the sparse two and
+// slower on the dense one).
 constexpr int kDefaultVariant = 5;
 constexpr uint32_t kDefaultConsumerWarps = 24;
-constexpr int kDefaultVariantLinkEnds = 7;
+constexpr int kDefaultVariantLinkEnds = 10;
 constexpr uint32_t kDefaultConsumerWarpsLinkEnds = 27;
-// The spatial filter's kernel instance exists for the two default variants.
-constexpr bool filter_variant(int v) { return v == kDefaultVariant || v == kDefaultVariantLinkEnds; }
+// The spatial filter's kernel instance exists for the default variants and
+// the other deep-ring link-end shapes.
+constexpr bool filter_variant(int v) { return v == kDefaultVariant || v == 7 || v == 10 || v == 11; }
 constexpr int kMaxClassifyThreads = 896;  // up to 28 worker warps
 struct VariantShape {
   int stages, stage_bytes, rounds, rounds_per_item;

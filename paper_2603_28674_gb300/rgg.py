@@ -26,7 +26,7 @@ RGG_ERR_IO = -7
 NOALLOC_MAX_EDGES = 131072
 NOALLOC_MAX_TILES = 16384
 BOXES_PER_PASS = 32
-NUM_VARIANTS = 10
+NUM_VARIANTS = 12
 MAX_REQUESTS = 64
 PENDING_EXTRA = 4096
 

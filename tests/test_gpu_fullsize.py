@@ -53,7 +53,7 @@ def test_full_size_roadmap_sampled_against_oracle(rgg, which):
     with rgg.Roadmap(robot.num_links, robot.inner_per_link, boxes.count) as r:
         r.build_edges(robot, rm.q_from, rm.q_to, rm.step)
         info = r.info()
-        assert info["tile_samples"] == 713          # the benchmark's default pipeline shape
+        assert info["tile_samples"] == 620          # the default link-end shape: 20 rounds of 31
         r.update_obstacles(np.arange(boxes.count), f32(boxes.poses()))
         r.classify()
         for up in sc.updates:
@@ -77,7 +77,7 @@ def test_full_size_mixed_label_scene_sampled_against_oracle(rgg):
     sample = np.sort(rng.choice(rm.num_edges, size=1500, replace=False))
     with rgg.Roadmap(robot.num_links, robot.inner_per_link, boxes.count) as r:
         r.build_edges(robot, rm.q_from, rm.q_to, rm.step)
-        assert r.info()["tile_samples"] == 713
+        assert r.info()["tile_samples"] == 620
         r.update_obstacles(np.arange(boxes.count), f32(boxes.poses()))
         r.classify()
         for k, up in enumerate(sc.updates):

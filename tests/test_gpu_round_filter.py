@@ -126,7 +126,7 @@ def test_every_launch_shape(rgg, fmt):
                 assert f.info()["round_filter"] == 1
             else:
                 f.set_launch_shape(variant, 16)
-                assert f.info()["round_filter"] == (1 if variant in (5, 7) else 0)
+                assert f.info()["round_filter"] == (1 if variant in (5, 7, 10, 11) else 0)
             f.update_obstacles(np.arange(m), f32(boxes.poses()))
             f.classify()
             for up in ups:
