@@ -118,7 +118,7 @@ enum {
   RGG_MAX_INNER = 16,          /* inner_per_link                               */
   RGG_MAX_OBSTACLES = 4096,    /* max_obstacles                                */
   RGG_BOXES_PER_PASS = 32,     /* moved boxes tested per streaming pass        */
-  RGG_NUM_VARIANTS = 12,       /* compiled pipeline shapes (rgg_set_launch_shape) */
+  RGG_NUM_VARIANTS = 13,       /* compiled pipeline shapes (rgg_set_launch_shape) */
   RGG_MAX_REQUESTS = 64,       /* open requests per roadmap (rgg_update_request) */
   RGG_PENDING_EXTRA = 4096,    /* pending entries beyond max_obstacles          */
   RGG_MAX_RESOLVE_FACTOR = 100, /* rgg_resolve_gray: resampling factor           */
@@ -172,6 +172,8 @@ typedef struct {
   uint64_t spline_vertices; /* OBB geometry: kept spline vertices                 */
   uint32_t round_filter;    /* 1: the spatial filter is on and active (see below)  */
   uint32_t record_format;   /* enum rgg_record_format of the resident records     */
+  uint32_t variant;         /* the roadmap's launch variant (rgg_set_launch_shape) */
+  uint32_t last_variant;    /* the variant its last classify launch ran            */
 } rgg_info;
 
 /* ------------------------------------------------------------------------ */
@@ -431,7 +433,10 @@ int rgg_work_counts(rgg_roadmap_t r, uint64_t* rounds, uint64_t* outer_tests,
  * compiled pipeline shapes (shared-memory ring depth x stage size x rounds of
  * 31 configurations per tile; RGG_NUM_VARIANTS in all, 0 = smallest tiles,
  * 5 the default for sphere records, 10 for link-end records; the spatial
- * filter runs with variants 5, 7, 10 and 11 only) and `consumer_warps` the
+ * filter runs with variants 5, 7, 10, 11 and 12 only; 12 is 10's tiles with
+ * 3 rounds per work item, which a roadmap of at least 262,144 tiles left on
+ * its default shape runs for a pass whose previous pass listed at least 95%
+ * of its tiles) and `consumer_warps` the
  * warps per CTA that test records (0 = the format's default, 24 for sphere
  * records and 27 for link ends; 1..27).  With edges present the tiles are rebuilt for the new shape (the
  * call synchronises the device).  Roadmaps classified together by

@@ -712,6 +712,16 @@ int classify_group(rgg_roadmap_t* rs, uint32_t n, cudaStream_t s) {
     ClassifyLaunch lc;
     lc.consumer_warps = r0->consumer_warps;
     lc.variant = r0->variant;
+    // a roadmap on its default link-end shape whose last pass listed nearly
+    // every tile runs variant 12 (the same tiles, 3 rounds per work item);
+    // the count may be a pass old, which only affects speed
+    const bool track = n == 1 && !r0->shape_set && r0->variant == kDefaultVariantLinkEnds &&
+                       r0->d_listed && filter_active(r0) && r0->es.T >= kDensePassMinTiles;
+    if (track &&
+        (uint64_t)*reinterpret_cast<volatile uint32_t*>(r0->h_listed) * 1000 >=
+            (uint64_t)kDensePassPermille * r0->es.T)
+      lc.variant = kDenseVariantLinkEnds;
+    for (uint32_t i = 0; i < n; ++i) rs[i]->last_variant = lc.variant;
     lc.grid = (uint32_t)std::min<uint64_t>((tiles + 1) / 2, launch_ctas(r0));
     lc.grid = std::max<uint32_t>(lc.grid, 1);
     cudaEvent_t* ev = timed ? next_events(timed) : nullptr;
@@ -722,6 +732,7 @@ int classify_group(rgg_roadmap_t* rs, uint32_t n, cudaStream_t s) {
       cp1.status = r0->d_status;
       cp1.wait_ns = r0->wait_ns;
       cp1.work = r0->counting ? r0->d_count : nullptr;
+      cp1.listed_out = track ? r0->d_listed : nullptr;
       RGG_CK(launch_classify_single(cp1, lc, s));
     } else {
       cpp->njobs = nj;
@@ -854,6 +865,17 @@ int rgg_roadmap_create(const rgg_roadmap_desc* desc, rgg_roadmap_t* out) {
     delete r;
     return cuda_status(e);
   }
+  // one mapped page-locked word for the listed-tile count (optional: without
+  // it every pass runs the roadmap's own variant)
+  if (cudaHostAlloc(reinterpret_cast<void**>(&r->h_listed), sizeof(uint32_t), cudaHostAllocMapped) !=
+          cudaSuccess ||
+      cudaHostGetDevicePointer(reinterpret_cast<void**>(&r->d_listed), r->h_listed, 0) != cudaSuccess) {
+    cudaGetLastError();
+    if (r->h_listed) cudaFreeHost(r->h_listed);
+    r->h_listed = r->d_listed = nullptr;
+  } else {
+    *r->h_listed = 0;
+  }
   *out = r;
   return RGG_OK;
 }
@@ -871,6 +893,7 @@ int rgg_roadmap_destroy(rgg_roadmap_t r) {
   device_free(r->d_count);
   device_free(r->d_obbwork);
   device_free(r->d_streamed);
+  if (r->h_listed) cudaFreeHost(r->h_listed);
   for (auto& ev : r->events)
     for (cudaEvent_t x : ev) cudaEventDestroy(x);
   delete r;
@@ -1284,6 +1307,8 @@ int rgg_roadmap_info(rgg_roadmap_t r, rgg_info* out) {
   out->grid_items = es.n_items;
   out->spline_vertices = es.n_spl_v;
   out->round_filter = filter_active(r) ? 1u : 0u;
+  out->variant = (uint32_t)r->variant;
+  out->last_variant = (uint32_t)(r->last_variant >= 0 ? r->last_variant : r->variant);
   if (r->geometry == RGG_GEOMETRY_OBB) {
     // boxes, spline vertices and spline offsets
     out->num_inner = es.n_spl_v;

@@ -127,6 +127,9 @@ struct ClassifyParams {
   int* status;                      // device status word of the launch (0 = ok)
   unsigned long long* work = nullptr;  // [3] work counters (counting launches only)
   uint64_t wait_ns = 4000000000ull; // limit of every bounded wait, ns of wall time
+  // a mapped page-locked host word that receives the launch's listed tiles
+  // (filtered single-roadmap launches; the host picks the next pass's shape)
+  uint32_t* listed_out = nullptr;
 };
 
 // Per-stage header, written by the warp that fills the stage.

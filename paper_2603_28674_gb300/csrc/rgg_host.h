@@ -202,6 +202,12 @@ struct rgg_roadmap {
   uint32_t ctas_per_sm = 1, consumer_warps = rgg::kDefaultConsumerWarps;
   int variant = rgg::kDefaultVariant;
   bool shape_set = false;      // the caller or the autotuner chose the launch shape
+  int last_variant = -1;       // the variant the last classify launch ran
+  // the spatial filter's listed-tile count of the last single-roadmap pass,
+  // copied to page-locked memory after the pass (read back one pass later,
+  // so it may be a pass old; it only picks between variants 10 and 12)
+  uint32_t* h_listed = nullptr;
+  uint32_t* d_listed = nullptr;  // its device address
   bool has_edges = false;
   uint64_t gen = 0;            // bumped whenever tiles or edges are replaced
   uint32_t geometry = RGG_GEOMETRY_SPHERES;

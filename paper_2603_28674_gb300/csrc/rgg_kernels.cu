@@ -1000,6 +1000,10 @@ __global__ void __launch_bounds__(kMaxClassifyThreads, 1) classify_kernel(const 
     }
   }
   __syncthreads();
+  // the launch's listed tiles, for the host's choice of the next pass's shape
+  if (FILTER && P.listed_out && blockIdx.x == 0 && threadIdx.x == 0)
+    *reinterpret_cast<volatile uint32_t*>(P.listed_out) =
+        s_pref[MAXJ == 1 ? 1u : min(P.njobs, (uint32_t)MAXJ)];
   // the first NSTAGE slots, one warp each
   for (int s = warp; s < NSTAGE; s += nw) {
     const SlotMeta m = slot_meta<MAXJ, FILTER>(P, (uint32_t)s, s_pref, lane);

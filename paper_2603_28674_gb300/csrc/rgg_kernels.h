@@ -32,8 +32,9 @@ namespace rgg {
   X(8, 6, 32 * 1024, 27, 1)        \
   X(9, 5, 38 * 1024, 31, 1)        \
   X(10, 8, 23 * 1024, 20, 2)       \
-  X(11, 10, 18 * 1024, 16, 2)
-constexpr int kNumVariants = 12;
+  X(11, 10, 18 * 1024, 16, 2)      \
+  X(12, 8, 23 * 1024, 20, 3)
+constexpr int kNumVariants = 13;
 // Default shapes: sphere records take variant 5 with 24 consumer warps;
 // link-end records (a third of the bytes per tile) variant 10, whose deeper
 // ring keeps more tiles in flight, with 27: of the shapes timed on the large
@@ -44,9 +45,22 @@ constexpr int kDefaultVariant = 5;
 constexpr uint32_t kDefaultConsumerWarps = 24;
 constexpr int kDefaultVariantLinkEnds = 10;
 constexpr uint32_t kDefaultConsumerWarpsLinkEnds = 27;
+// Variant 12 is variant 10 (the same stages and tiles) with 3 rounds per work
+// item: faster when nearly every tile has rounds to test (each item's later
+// rounds see its earlier rounds' hits, and a tile has fewer items), slower
+// when tiles carry few live rounds (fewer warps share a tile).  A roadmap on
+// the default shape with at least kDensePassMinTiles tiles runs it for a pass
+// when its previous pass listed at least kDensePassPermille / 1000 of its
+// tiles.  The count reaches the host through one store of the classify
+// kernel into mapped host memory, which measured about 2 us longer per launch
+// on a 46k-tile roadmap and nothing measurable on longer launches: smaller
+// roadmaps keep variant 10 and skip the store.
+constexpr int kDenseVariantLinkEnds = 12;
+constexpr uint32_t kDensePassPermille = 950;
+constexpr uint64_t kDensePassMinTiles = 262144;
 // The spatial filter's kernel instance exists for the default variants and
 // the other deep-ring link-end shapes.
-constexpr bool filter_variant(int v) { return v == kDefaultVariant || v == 7 || v == 10 || v == 11; }
+constexpr bool filter_variant(int v) { return v == kDefaultVariant || v == 7 || v >= 10; }
 constexpr int kMaxClassifyThreads = 896;  // up to 28 worker warps
 struct VariantShape {
   int stages, stage_bytes, rounds, rounds_per_item;

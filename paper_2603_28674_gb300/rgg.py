@@ -26,7 +26,7 @@ RGG_ERR_IO = -7
 NOALLOC_MAX_EDGES = 131072
 NOALLOC_MAX_TILES = 16384
 BOXES_PER_PASS = 32
-NUM_VARIANTS = 12
+NUM_VARIANTS = 13
 MAX_REQUESTS = 64
 PENDING_EXTRA = 4096
 
@@ -104,7 +104,8 @@ class Info(ctypes.Structure):
                 ("open_requests", ctypes.c_uint32), ("pending_capacity", ctypes.c_uint32),
                 ("geometry", ctypes.c_uint32), ("grid_cells", ctypes.c_uint32),
                 ("grid_items", ctypes.c_uint64), ("spline_vertices", ctypes.c_uint64),
-                ("round_filter", ctypes.c_uint32), ("record_format", ctypes.c_uint32)]
+                ("round_filter", ctypes.c_uint32), ("record_format", ctypes.c_uint32),
+                ("variant", ctypes.c_uint32), ("last_variant", ctypes.c_uint32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

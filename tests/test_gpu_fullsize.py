@@ -88,36 +88,44 @@ def test_full_size_mixed_label_scene_sampled_against_oracle(rgg):
             mix = np.bincount(r.fetch_labels(), minlength=3) / rm.num_edges
             assert np.all(mix > 0.05), f"mixed scene lost a label: {mix}"
             assert np.all(np.bincount(r.fetch_labels()[sample], minlength=3) > 50)
+            # few tiles are listed on these passes: the default 2 rounds per item
+            assert r.info()["last_variant"] == 10
         r.check_status()
 
 
 def test_full_size_filter_changes_no_bit(rgg):
-    """The large roadmap with and without the spatial filter (2 x 26.8 GB):
-    identical labels and box sets after every update, fewer record bytes
-    copied than the roadmap holds."""
+    """The large roadmap with and without the spatial filter, and with the
+    filter at a launch shape fixed to variant 10 (3 x 7.8 GB): identical
+    labels and box sets after every update, fewer record bytes copied than
+    the roadmap holds.  The roadmap on its default shape runs variant 12 (3
+    rounds per work item) on these dense passes, the fixed one variant 10."""
     sc = W.workload_large(n_updates=3)
     rm, robot = sc.roadmap, sc.roadmap.robot
     m = sc.boxes.count
     rs = []
-    for flt in (True, False):
+    for flt, fixed in ((True, False), (False, False), (True, True)):
         r = rgg.Roadmap(robot.num_links, robot.inner_per_link, m)
         r.build_edges(robot, rm.q_from, rm.q_to, rm.step)
         r.set_round_filter(flt)
+        if fixed:
+            r.set_launch_shape(10, 27)
         r.update_obstacles(np.arange(m), f32(sc.boxes.poses()))
         r.classify()
         r.streamed_bytes()
         rs.append(r)
-    f, u = rs
+    f, u, v10 = rs
     for k, up in enumerate(sc.updates):
         for x in rs:
             x.update_obstacles(up.ids, f32(up.poses))
             x.classify()
-        np.testing.assert_array_equal(f.fetch_labels(), u.fetch_labels(), err_msg=f"update {k}")
-        hf, tf = f.fetch_box_sets()
         hu, tu = u.fetch_box_sets()
-        np.testing.assert_array_equal(hf, hu, err_msg=f"update {k}")
-        np.testing.assert_array_equal(tf, tu, err_msg=f"update {k}")
+        for x in (f, v10):
+            np.testing.assert_array_equal(x.fetch_labels(), u.fetch_labels(), err_msg=f"update {k}")
+            hx, tx = x.fetch_box_sets()
+            np.testing.assert_array_equal(hx, hu, err_msg=f"update {k}")
+            np.testing.assert_array_equal(tx, tu, err_msg=f"update {k}")
         assert f.streamed_bytes() < f.info()["record_bytes"]
+        assert f.info()["last_variant"] == 12 and v10.info()["last_variant"] == 10
     for r in rs:
         r.check_status()
         r.close()

@@ -16,7 +16,11 @@ Rules checked:
     boxes far from every edge), in the middle, at the ends or all of them,
     leaves the same state as unfiltered launches;
   * the filtered labels agree with the FP64 oracle (pinned edges equal,
-    other differences GPU gray).
+    other differences GPU gray);
+  * a roadmap below 262,144 tiles stays on variant 10 on a dense scene, with
+    the labels and box sets of a roadmap fixed to it (the switch to variant
+    12 on dense passes of larger roadmaps is checked on the full-size
+    roadmap, tests/test_gpu_fullsize.py).
 """
 import numpy as np
 import pytest
@@ -126,7 +130,7 @@ def test_every_launch_shape(rgg, fmt):
                 assert f.info()["round_filter"] == 1
             else:
                 f.set_launch_shape(variant, 16)
-                assert f.info()["round_filter"] == (1 if variant in (5, 7, 10, 11) else 0)
+                assert f.info()["round_filter"] == (1 if variant in (5, 7, 10, 11, 12) else 0)
             f.update_obstacles(np.arange(m), f32(boxes.poses()))
             f.classify()
             for up in ups:
@@ -275,3 +279,37 @@ def test_batched_launch_with_empty_tile_lists(rgg):
     for r in filt + plain:
         r.check_status()
         r.close()
+
+
+def test_small_roadmaps_keep_the_default_shape_on_dense_passes(rgg):
+    dense = True
+    rng = np.random.default_rng(67)
+    rm = W.prm_roadmap(rng, W.seven_dof_arm(), 400, 10, 0.02)
+    # dense: 32 large boxes about the arm, so that nearly every tile is listed;
+    # sparse: small boxes spread over a large cube, so that few are
+    boxes = (W.random_boxes(rng, 32, extent=0.8, half_lo=0.35, half_hi=0.5) if dense
+             else W.random_boxes(rng, 32, extent=3.0, half_lo=0.02, half_hi=0.04))
+    ups = W.update_stream(rng, boxes, 3, 32)
+    m = boxes.count
+    with rgg.Roadmap(rm.robot.num_links, rm.robot.inner_per_link, m) as a, \
+            rgg.Roadmap(rm.robot.num_links, rm.robot.inner_per_link, m) as b:
+        a.build_edges(rm.robot, rm.q_from, rm.q_to, rm.step)
+        b.build_edges(rm.robot, rm.q_from, rm.q_to, rm.step)
+        b.set_launch_shape(10, 27)
+        assert a.info()["variant"] == 10 and a.info()["round_filter"] == 1
+        for r in (a, b):
+            r.update_obstacles(np.arange(m), f32(boxes.poses()))
+            r.classify()
+            r.fetch_labels()  # the pass has run: the next one reads its count
+        seen = set()
+        for up in ups:
+            for r in (a, b):
+                r.update_obstacles(up.ids, f32(up.poses))
+                r.classify()
+            seen.add(a.info()["last_variant"])
+            assert b.info()["last_variant"] == 10
+            assert np.array_equal(a.fetch_labels(), b.fetch_labels())
+            ha, ta = a.fetch_box_sets()
+            hb, tb = b.fetch_box_sets()
+            assert np.array_equal(ha, hb) and np.array_equal(ta, tb)
+        assert seen == {10}
