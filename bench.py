@@ -693,11 +693,17 @@ def measure_mixed(r, args, stream, peak: float) -> dict:
         out["other_filter_state"] = other
     r.set_round_filter(default_on)
     # the library's autotuner on this scene: it times every compiled launch
-    # shape on the roadmap's own records (a pass of its first 32 boxes, into
-    # its own accumulators) and keeps the fastest; the same steps then run at
-    # that shape, and the labels must not change
+    # shape on the roadmap's own records (a pass of its first 32 present
+    # boxes at their current poses, into its own accumulators) and keeps the
+    # fastest.  The boxes go back to the scene's initial poses first: after
+    # hundreds of random-walk updates the first 32 may have drifted out of
+    # the robot's reach, and a pass of them would stand for nothing.  The
+    # same steps then run at the chosen shape (absolute poses: the same final
+    # state), and the labels must not change
     from paper_2603_28674_gb300 import rgg
-    tuned = rgg.autotune([r], reps=1, stream=stream)
+    r.update_obstacles(np.arange(boxes.count), boxes.poses().astype(np.float32), stream)
+    r.classify(stream)
+    tuned = rgg.autotune([r], reps=3, stream=stream)
     if tuned:
         at, lab_a = timed(min(3, args.steps))
         at["chosen"] = tuned[0]

@@ -566,8 +566,8 @@ int rgg_obb_work(rgg_roadmap_t r, uint64_t* sat_tests, uint64_t* segment_tests);
  * roadmaps at every supported shape -- each compiled pipeline variant (ring
  * depth x tile size, i.e. records per block) with 16, 20, 24 and 27 consumer
  * warps -- on their own resident records and their first 32 present boxes
- * (warm-up launch, then `reps` timed launches, CUDA events on `stream`), and
- * sets the fastest shape on every roadmap.  Labels, box sets and pending
+ * (warm-up launch, then `reps` launches each timed by its own CUDA events on
+ * `stream`; the median counts), and sets the fastest shape on every roadmap.  Labels, box sets and pending
  * moves are not changed: the timed launches accumulate into scratch memory
  * the call allocates and frees.  Synchronous; it synchronises the device
  * whenever the tiles are rebuilt.
@@ -580,7 +580,7 @@ int rgg_obb_work(rgg_roadmap_t r, uint64_t* sat_tests, uint64_t* segment_tests);
 typedef struct {
   uint32_t variant;         /* pipeline variant (rgg_set_launch_shape)          */
   uint32_t consumer_warps;  /* consumer warps per CTA                          */
-  float classify_ms;        /* mean duration of one timed launch, ms           */
+  float classify_ms;        /* median duration of the timed launches, ms       */
   float reserved;
 } rgg_tune_result;
 

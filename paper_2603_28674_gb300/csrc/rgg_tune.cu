@@ -131,19 +131,25 @@ int rgg_autotune(rgg_roadmap_t* rs, uint32_t n, uint32_t reps, rgg_tune_result* 
       for (uint32_t i = 0; i < n; ++i)
         bpp->job[i].tcount = filter_active(rs[i]) ? rs[i]->es.d_tlist + rs[i]->es.T : nullptr;
       rc = tune_launch(rs, n, acc, C, *bpp, cpp.get(), s);  // warm-up
-      if (rc == RGG_OK && cudaEventRecord(ev.a, s) != cudaSuccess) rc = RGG_ERR_CUDA;
-      for (uint32_t k = 0; k < reps && rc == RGG_OK; ++k)
-        rc = tune_launch(rs, n, acc, C, *bpp, cpp.get(), s);
-      if (rc == RGG_OK && cudaEventRecord(ev.b, s) != cudaSuccess) rc = RGG_ERR_CUDA;
-      float ms = 0.f;
-      if (rc == RGG_OK && (cudaEventSynchronize(ev.b) != cudaSuccess ||
-                           cudaEventElapsedTime(&ms, ev.a, ev.b) != cudaSuccess))
-        rc = RGG_ERR_CUDA;
+      // each repetition between its own events; the median is kept, so that
+      // one odd reading cannot pick the shape
+      std::vector<float> times;
+      for (uint32_t k = 0; k < reps && rc == RGG_OK; ++k) {
+        if (cudaEventRecord(ev.a, s) != cudaSuccess) rc = RGG_ERR_CUDA;
+        if (rc == RGG_OK) rc = tune_launch(rs, n, acc, C, *bpp, cpp.get(), s);
+        float ms = 0.f;
+        if (rc == RGG_OK && (cudaEventRecord(ev.b, s) != cudaSuccess ||
+                             cudaEventSynchronize(ev.b) != cudaSuccess ||
+                             cudaEventElapsedTime(&ms, ev.a, ev.b) != cudaSuccess))
+          rc = RGG_ERR_CUDA;
+        times.push_back(ms);
+      }
       if (rc != RGG_OK) break;
+      std::sort(times.begin(), times.end());
       rgg_tune_result t{};
       t.variant = (uint32_t)v;
       t.consumer_warps = cw;
-      t.classify_ms = ms / (float)reps;
+      t.classify_ms = times[times.size() / 2];
       res.push_back(t);
     }
   cudaStreamSynchronize(s);
