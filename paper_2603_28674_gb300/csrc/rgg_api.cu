@@ -903,6 +903,7 @@ int rgg_roadmap_destroy(rgg_roadmap_t r) {
 int rgg_upload_edges(rgg_roadmap_t r, uint64_t num_edges, const uint64_t* sample_off,
                      const float* inner_xyzr, const float* outer_xyzr, int src_is_device,
                      void* stream) {
+  TraceRange trace_("rgg_upload_edges");
   if (!r || !sample_off) return RGG_ERR_INVALID;
   if (r->geometry != RGG_GEOMETRY_SPHERES) return RGG_ERR_STATE;  // boxes and splines are built here
   if (!valid_soff(sample_off, num_edges, r->L)) return RGG_ERR_INVALID;
@@ -949,6 +950,7 @@ int rgg_upload_edges(rgg_roadmap_t r, uint64_t num_edges, const uint64_t* sample
 
 int rgg_build_edges(rgg_roadmap_t r, const rgg_robot_desc* robot, uint64_t num_edges,
                     const double* q_from, const double* q_to, double step, void* stream) {
+  TraceRange trace_("rgg_build_edges");
   if (!r || !robot || robot->num_links != r->L || !robot->a || !robot->alpha || !robot->d ||
       !robot->radius)
     return RGG_ERR_INVALID;
@@ -1071,6 +1073,7 @@ int rgg_build_edges(rgg_roadmap_t r, const rgg_robot_desc* robot, uint64_t num_e
 
 int rgg_update_obstacles(rgg_roadmap_t r, uint32_t n_changed, const uint32_t* ids,
                          const float* pose, int src_is_device, void* stream) {
+  TraceRange trace_("rgg_update_obstacles");
   if (!r) return RGG_ERR_INVALID;
   if (n_changed == 0) return RGG_OK;
   if (!ids || !pose) return RGG_ERR_INVALID;
@@ -1085,6 +1088,7 @@ int rgg_update_obstacles(rgg_roadmap_t r, uint32_t n_changed, const uint32_t* id
 
 int rgg_update_request(rgg_roadmap_t r, uint32_t n_changed, const uint32_t* ids,
                        const float* pose, int src_is_device, uint32_t* handle, void* stream) {
+  TraceRange trace_("rgg_update_request");
   if (!r || !handle || n_changed == 0 || !ids || !pose) return RGG_ERR_INVALID;
   if (!r->has_edges) return RGG_ERR_STATE;
   uint32_t fresh = 0;
@@ -1114,6 +1118,7 @@ int rgg_update_request(rgg_roadmap_t r, uint32_t n_changed, const uint32_t* ids,
 }
 
 int rgg_classify(rgg_roadmap_t r, void* stream) {
+  TraceRange trace_("rgg_classify");
   if (!r) return RGG_ERR_INVALID;
   if (!r->has_edges) return RGG_ERR_STATE;
   if (r->pending.empty()) return RGG_OK;
@@ -1124,6 +1129,7 @@ int rgg_classify(rgg_roadmap_t r, void* stream) {
 }
 
 int rgg_classify_many(rgg_roadmap_t* rs, uint32_t n, void* stream) {
+  TraceRange trace_("rgg_classify_many");
   if (!rs && n) return RGG_ERR_INVALID;
   for (uint32_t i = 0; i < n; ++i) {
     if (!rs[i]) return RGG_ERR_INVALID;
@@ -1149,6 +1155,7 @@ int rgg_classify_many(rgg_roadmap_t* rs, uint32_t n, void* stream) {
 
 int rgg_fetch_labels(rgg_roadmap_t r, uint8_t* out, uint64_t first, uint64_t count,
                      int dst_is_device, void* stream) {
+  TraceRange trace_("rgg_fetch_labels");
   if (!r || (!out && count) || dst_is_device < 0 || dst_is_device > 2) return RGG_ERR_INVALID;
   if (!r->has_edges && count) return RGG_ERR_STATE;
   if (first > r->es.N || count > r->es.N - first) return RGG_ERR_INVALID;
@@ -1164,6 +1171,7 @@ int rgg_fetch_labels(rgg_roadmap_t r, uint8_t* out, uint64_t first, uint64_t cou
 
 int rgg_fetch_request_labels(rgg_roadmap_t r, uint32_t handle, uint8_t* out, uint64_t first,
                              uint64_t count, int dst_is_device, void* stream) {
+  TraceRange trace_("rgg_fetch_request_labels");
   if (!r || handle >= RGG_MAX_REQUESTS || (!out && count) || dst_is_device < 0 ||
       dst_is_device > 2)
     return RGG_ERR_INVALID;

@@ -12,12 +12,23 @@
 #include <utility>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "rgg.h"
 #include "rgg_kernels.h"
 
 namespace rgg_host {
 
 using namespace rgg;
+
+// A named NVTX range around a C-ABI call, for timeline tools (Nsight Systems,
+// ncu --nvtx): without a tool attached the calls do nothing.
+struct TraceRange {
+  explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+  ~TraceRange() { nvtxRangePop(); }
+  TraceRange(const TraceRange&) = delete;
+  TraceRange& operator=(const TraceRange&) = delete;
+};
 
 struct DeviceGuard {
   int prev = -1;

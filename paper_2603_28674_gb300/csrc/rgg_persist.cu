@@ -107,6 +107,7 @@ static int load_device(FileIO& io, void* dst, size_t bytes, cudaStream_t s) {
 }
 
 int rgg_save(rgg_roadmap_t r, const char* path, void* stream) {
+  TraceRange trace_("rgg_save");
   if (!r || !path) return RGG_ERR_INVALID;
   if (!r->has_edges || !r->pending.empty() || r->geometry != RGG_GEOMETRY_SPHERES)
     return RGG_ERR_STATE;
@@ -158,6 +159,7 @@ int rgg_save(rgg_roadmap_t r, const char* path, void* stream) {
 }
 
 int rgg_load(rgg_roadmap_t r, const char* path, void* stream) {
+  TraceRange trace_("rgg_load");
   if (!r || !path) return RGG_ERR_INVALID;
   if (r->geometry != RGG_GEOMETRY_SPHERES) return RGG_ERR_STATE;
   DeviceGuard g(r->device);

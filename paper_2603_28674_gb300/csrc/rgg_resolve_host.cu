@@ -11,6 +11,7 @@ extern "C" {
 // ---------------------------------------------------------------------------
 int rgg_resolve_gray(rgg_roadmap_t r, uint32_t factor, uint8_t* labels_out, float* clearance_out,
                      int dst_is_device, rgg_resolve_stats* stats, void* stream) {
+  TraceRange trace_("rgg_resolve_gray");
   if (!r || factor < 1 || factor > RGG_MAX_RESOLVE_FACTOR || dst_is_device < 0 ||
       dst_is_device > 1)
     return RGG_ERR_INVALID;

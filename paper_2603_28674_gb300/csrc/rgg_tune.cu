@@ -64,6 +64,7 @@ struct EventPair {
 
 int rgg_autotune(rgg_roadmap_t* rs, uint32_t n, uint32_t reps, rgg_tune_result* results,
                  uint32_t max_results, uint32_t* n_results, void* stream) {
+  TraceRange trace_("rgg_autotune");
   if (!rs || n == 0 || n > (uint32_t)kMaxJobs || (max_results && !results)) return RGG_ERR_INVALID;
   for (uint32_t i = 0; i < n; ++i) {
     if (!rs[i]) return RGG_ERR_INVALID;
@@ -253,6 +254,7 @@ int rgg_step_graph_create(rgg_roadmap_t* rs, uint32_t n, const uint32_t* n_ids,
 }
 
 int rgg_step_graph_launch(rgg_step_graph_t g, void* stream) {
+  TraceRange trace_("rgg_step_graph_launch");
   if (!g) return RGG_ERR_INVALID;
   for (size_t i = 0; i < g->rs.size(); ++i)
     if (g->rs[i]->gen != g->gens[i] || !g->rs[i]->pending.empty()) return RGG_ERR_STATE;
